@@ -1,0 +1,204 @@
+"""Pins of the oracle to what the paper prints: the five test-suite tables, the hand-computed
+intermediates, the closed-form lengths, the ambiguity examples and the stated identities."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2006_00686_gb300.inputs import Geometry
+
+pi = math.pi
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+r2, r3 = math.sqrt(2.0), math.sqrt(3.0)
+tan12, sin12, cos12 = math.tan(pi / 12), math.sin(pi / 12), math.cos(pi / 12)
+
+
+def _table(name):
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and not ln.startswith("#")]
+    return np.array([int(r[0]) for r in rows]), np.array([float(r[1]) for r in rows])
+
+
+# The paper prints float output to six significant digits (Section 5, first paragraph).
+PRINT_TOL = 5e-6
+
+TS1 = Geometry("par2d", 3, 3, angles=[pi / 4], n_cols=1, u0=1.0)
+TS2 = Geometry("fan2d_arc", 4, 4, angles=[pi / 2], n_cols=1, u0=-pi / 6, sod=4.0, sdd=4.0)
+TS3 = Geometry("par3d", 3, 3, 3, angles=[[pi / 4, pi / 4]])
+TS4 = Geometry("cone_arc", 4, 4, 4, angles=[pi / 4], u0=pi / 12, v0=pi / 12, sod=4.0, sdd=4.0)
+TS5 = Geometry("helix_arc", 4, 4, 4, angles=[pi / 4], src_z=[0.5], u0=pi / 12, v0=pi / 12, sod=4.0, sdd=4.0)
+
+
+@pytest.mark.parametrize("geom,table", [
+    (TS1, "ts1_par2d.txt"),
+    (TS2, "ts2_fan_equiangular.txt"),
+    (TS3, "ts3_par3d.txt"),
+    (TS4, "ts4_cone_equiangular.txt"),
+    (TS5, "ts5_helix_equiangular.txt"),
+])
+def test_paper_tables(geom, table):
+    want_i, want_l = _table(table)
+    idx, ln = O.ray_units(geom, 0)
+    np.testing.assert_array_equal(idx, want_i)
+    np.testing.assert_allclose(ln, want_l, rtol=0, atol=PRINT_TOL)
+
+
+def test_ts1_geometric_lengths():
+    # Section 5.1: lengths 2 - sqrt2, 2sqrt2 - 2, 2sqrt2 - 2 for pixels (0,0), (0,1), (1,0)
+    idx, ln = O.ray_units(TS1, 0)
+    np.testing.assert_allclose(ln, [2 - r2, 2 * r2 - 2, 2 * r2 - 2], rtol=1e-14)
+
+
+def test_ts2_params_and_lengths():
+    # Section 5.2: (s, phi) = (-2, -pi/6), i.e. the ray (2, 5pi/6); lengths 2sqrt3/3, 4 - 2sqrt3
+    s, phi = O.ray_params(TS2, 0)
+    assert s == pytest.approx(2.0, abs=1e-14) and phi == pytest.approx(5 * pi / 6, abs=1e-14)
+    idx, ln = O.ray_units(TS2, 0)
+    np.testing.assert_allclose(ln, [2 * r3 / 3, 4 - 2 * r3], rtol=1e-14)
+
+
+def test_ts3_geometric_lengths():
+    idx, ln = O.ray_units(TS3, 0)
+    np.testing.assert_allclose(ln, [1.5 * r2 - 1, 1 - r2 / 2, r2, 1 - r2 / 2, 1.5 * r2 - 1], rtol=1e-14)
+
+
+def test_ts4_params_and_closed_forms():
+    # Section 5.4: phi1 = pi/3, phi2 = pi/12, s1 = 4 sin(pi/12), s2 = 4 sin(pi/12) cos(pi/12)
+    s1, s2, p1, p2 = O.ray_params(TS4, 0)
+    np.testing.assert_allclose([s1, s2, p1, p2], [4 * sin12, 4 * sin12 * cos12, pi / 3, pi / 12], rtol=1e-14)
+    q = (4 - r2) * tan12 * math.sin(5 * pi / 12) / math.sin(pi / 3)
+    closed = {
+        28: 2 * (1 - q) / cos12,  # voxel (1,3,0)
+        24: 2 * r3 / (3 * cos12),  # voxel (1,2,0)
+        20: 2 * (q - r3 / 3) / cos12,  # voxel (1,1,0)
+        1: 2 * r3 / (3 * cos12),  # voxel (0,0,1)
+        21: (1 - (4 * r2 - 2) * tan12) / sin12,  # voxel (1,1,1)
+        5: (((4 - r2) * (r2 - 2 * tan12 * math.sin(5 * pi / 12) / math.sin(pi / 3)) + 4 * r3 / 3) * tan12 - 1)
+        / sin12,  # voxel (0,1,1)
+    }
+    idx, ln = O.ray_units(TS4, 0)
+    got = dict(zip(idx.tolist(), ln.tolist()))
+    assert set(got) == set(closed)
+    for k, v in closed.items():
+        assert got[k] == pytest.approx(v, rel=1e-12), k
+
+
+def test_ts5_params_and_closed_forms():
+    # Section 5.5: s2 = 4 cos(pi/12) sin(pi/12) + cos(pi/12)/2.  The printed closed forms for
+    # voxels (0,3,0) and (1,3,0) are attached to the opposite voxels in the table; the table
+    # (and the brute force) puts A at voxel (1,3,0) = index 28 and B at (0,3,0) = index 12.
+    s1, s2, p1, p2 = O.ray_params(TS5, 0)
+    np.testing.assert_allclose([s1, s2], [4 * sin12, 4 * cos12 * sin12 + cos12 / 2], rtol=1e-14)
+    q = (4 - r2) * tan12 * math.sin(5 * pi / 12) / math.sin(pi / 3)
+    A = (0.5 - (4 * r2 - 4) * tan12) / sin12
+    B = 2 * (1 - q) / cos12 - A
+    closed = {
+        8: 2 * r3 / (3 * cos12),  # (0,2,0)
+        4: 2 * (q - r3 / 3) / cos12,  # (0,1,0)
+        1: 2 * r3 / (3 * cos12),  # (0,0,1)
+        5: (2 - (8 - 2 * r2) * tan12 * math.sin(5 * pi / 12)) / (math.cos(pi / 6) * cos12),  # (0,1,1)
+        28: A,
+        12: B,
+    }
+    idx, ln = O.ray_units(TS5, 0)
+    got = dict(zip(idx.tolist(), ln.tolist()))
+    assert set(got) == set(closed)
+    for k, v in closed.items():
+        assert got[k] == pytest.approx(v, rel=1e-12), k
+
+
+def test_helix_h0_equals_circular_cone():
+    # Section 5.5: with H = 0 the helical output equals the circular cone output
+    g = Geometry("helix_arc", 4, 4, 4, angles=[pi / 4], src_z=[0.0], u0=pi / 12, v0=pi / 12, sod=4.0, sdd=4.0)
+    a, b = O.ray_units(g, 0), O.ray_units(TS4, 0)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def _steps(trace, kind):
+    return [r for r in trace if r[0] == kind]
+
+
+def test_ts1_hand_intermediates():
+    # Section 5.1 (i)-(iii)
+    _, _, tr = O.ray_units(TS1, 0, trace=True)
+    drive = _steps(tr, 0)
+    cand = _steps(tr, 1)
+    assert drive[0][2] == pytest.approx(1 - 3 * r2 / 2) and drive[0][3] == pytest.approx(3 - r2)
+    # (ii) prints C_1 = 5/2 - 3sqrt2/2 for i = 1; eq. restriction_j with the printed
+    # C_x = 1 - sqrt2/2 gives 2 - sqrt2 (C_1 falls by tan(phi) = 1 per step of i).  Both leave
+    # the single valid j = 0 that the paper states; the consistent value is pinned.
+    assert drive[1][2] == pytest.approx(1 - r2 / 2) and drive[1][3] == pytest.approx(2 - r2)
+    assert drive[0][3] - drive[1][3] == pytest.approx(1.0)
+    valid = {(int(r[1]), int(r[2])): r for r in cand}
+    assert sorted(valid) == [(0, 0), (0, 1), (1, 0)]  # (i, j); i = 2 has no valid j
+    assert valid[(0, 0)][3] == pytest.approx(1.5 * r2 - 1)
+    assert valid[(0, 1)][3] == pytest.approx(r2 / 2 - 1)
+    assert valid[(1, 0)][3] == pytest.approx(1.5 * r2 - 1)
+
+
+def test_ts2_hand_intermediates():
+    # Section 5.2 (i)-(iii): phi = 5pi/6 lies outside Case 1; the open j-range is the one
+    # the paper computes by hand.
+    _, _, tr = O.ray_units(TS2, 0, trace=True)
+    drive = _steps(tr, 0)
+    assert drive[0][2] == pytest.approx(2 * r3 / 3)
+    assert (drive[0][4], drive[0][5]) == pytest.approx((1 + 2 * r3 / 3, 2 + r3))
+    assert drive[1][2] == pytest.approx(0.0, abs=1e-12)
+    assert (drive[1][4], drive[1][5]) == pytest.approx((1 + r3, 2 + 4 * r3 / 3))
+    cand = _steps(tr, 1)
+    assert [(int(r[1]), int(r[2])) for r in cand] == [(0, 3), (1, 3)]
+    assert cand[0][3] == pytest.approx(2 * r3 - 2) and cand[1][3] == pytest.approx(2 * r3 - 2)
+
+
+def test_ts3_hand_intermediates():
+    # Section 5.3 (i)-(iii): C_x, the j-range, C_y and the k-range for each i
+    _, _, tr = O.ray_units(TS3, 0, trace=True)
+    drive = _steps(tr, 0)
+    assert [d[2] for d in drive] == pytest.approx([-3.0, -1.0, 1.0])
+    assert [(d[4], d[5]) for d in drive] == [pytest.approx((1, 3)), pytest.approx((0, 2)), pytest.approx((-1, 1))]
+    cand = _steps(tr, 1)
+    assert [(int(r[1]), int(r[2])) for r in cand] == [(0, 2), (1, 1), (2, 0)]
+    assert [r[3] for r in cand] == pytest.approx([-1.0, 1.0, 3.0])
+    want_k = [((1 + r2) / 2, (3 + 3 * r2) / 2), ((1 - r2) / 2, (3 + r2) / 2), ((1 - 3 * r2) / 2, (3 - r2) / 2)]
+    for r, (lo, hi) in zip(cand, want_k):
+        assert (r[4], r[5]) == pytest.approx((lo, hi))
+
+
+def test_ambiguity_2d_grid_line():
+    # Section 4.1, first example: 5x5, ray (1.5, 0) lies on a grid line -> pixel (1, i)
+    g = Geometry("par2d", 5, 5, angles=[0.0], n_cols=1, u0=1.5)
+    idx, ln = O.ray_units(g, 0)
+    np.testing.assert_array_equal(idx, 5 + np.arange(5))
+    np.testing.assert_allclose(ln, 1.0)
+
+
+def test_ambiguity_3d_grid_edge():
+    # Section 4.1, second example: 4x4x4, ray (1, 1, 0, 0) on a grid edge -> voxels (1, 1, i)
+    g = Geometry("par3d", 4, 4, 4, angles=[[0.0, 0.0]], u0=1.0, v0=1.0)
+    idx, ln = O.ray_units(g, 0)
+    np.testing.assert_array_equal(idx, (1 * 4 + 1) * 4 + np.arange(4))
+    np.testing.assert_allclose(ln, 1.0)
+
+
+def test_ambiguity_3d_grid_plane():
+    # Section 4.1, third example: 3x3x3, ray (-0.5, sqrt2, 0, pi/4) in a grid plane: only
+    # i = 0 with k = 0 and length sqrt2, voxels (0,1,0) and (0,2,0) -> (0,2,0), index 6
+    g = Geometry("par3d", 3, 3, 3, angles=[[0.0, pi / 4]], u0=-0.5, v0=r2)
+    idx, ln = O.ray_units(g, 0)
+    np.testing.assert_array_equal(idx, [6])
+    np.testing.assert_allclose(ln, [r2], rtol=1e-12)
+
+
+def test_edge_rays_keep_edge_units():
+    # A ray on the outer boundary of the image still crosses the edge row / column
+    for s, want_j in ((2.5, 0), (-2.5, 4)):
+        g = Geometry("par2d", 5, 5, angles=[0.0], n_cols=1, u0=s)
+        idx, ln = O.ray_units(g, 0)
+        np.testing.assert_array_equal(idx, want_j * 5 + np.arange(5))
+    g = Geometry("par2d", 5, 5, angles=[pi / 2], n_cols=1, u0=2.5)  # x = -2.5: left edge
+    idx, _ = O.ray_units(g, 0)
+    np.testing.assert_array_equal(idx, np.arange(5) * 5 + 0)
+    g = Geometry("par2d", 5, 5, angles=[0.0], n_cols=1, u0=2.5000001)  # just outside
+    assert O.ray_units(g, 0)[0].size == 0
