@@ -1,0 +1,191 @@
+/*
+ * xray.h -- C ABI of the GB300 (sm_103a) X-ray transform library (libxray.so).
+ *
+ * The library computes the X-ray transform of a pixel/voxel image (eq. Xray_transform_image
+ * of Chen, Wang, Bajaj, Oktem, "A Fast and Adaptive Algorithm to Compute the X-ray
+ * Transform") and its adjoint, ray by ray: for every ray only the units that satisfy the
+ * non-vanishing-intersectability condition (eq. conditions_2D_1 / conditions_3D_1) are
+ * visited, and each contributes its analytic length C_up - C_low (eq. range_length /
+ * range_length_3D).  Nothing is stored per (ray, unit): lengths are recomputed on the fly.
+ *
+ * Conventions (Section 2.1 and Section 3.1):
+ *   image    float32 [batch][nz][ny][nx] (2D: nz = 1), i along +x, j = row from the top
+ *            (y decreasing), k = slice from the top (z decreasing); unit (k,j,i) has support
+ *            [cx+(i-nx/2)dx, cx+(i-nx/2+1)dx] x [cy+(ny/2-j-1)dy, cy+(ny/2-j)dy] x (same in z).
+ *   sinogram float32 [batch][n_views][n_rows][n_cols] (2D: n_rows = 1); detector sample
+ *            coordinates u_c = (c-(n_cols-1)/2)du + u0, v_r = (r-(n_rows-1)/2)dv + v0.
+ *
+ * Ownership: every device pointer passed in is CUDA global memory owned by the caller;
+ * the library never frees it.  A geometry handle owns its own device tables (one record
+ * per ray, built by the ray-setup kernel) and frees them in xr_geometry_destroy.
+ *
+ * Streams: every launching call is asynchronous and ordered on the given stream
+ * (NULL = the legacy default stream); it performs no host synchronisation and no device
+ * allocation, so it may be captured in a CUDA graph.
+ *
+ * Errors: every call returns an xr_status and never aborts or exits.  After XR_ERR_CUDA,
+ * xr_last_cuda_error() returns the CUDA error code seen by the calling thread.
+ * Thread safety: calls on different handles may run concurrently; calls on one handle
+ * must not.
+ */
+#ifndef XRAY_H
+#define XRAY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t); NULL selects the legacy default stream. */
+typedef struct CUstream_st *xr_stream;
+
+typedef enum {
+    XR_OK = 0,
+    XR_ERR_NULL = 1,      /* a required pointer is NULL */
+    XR_ERR_SIZE = 2,      /* a size is non-positive or too large */
+    XR_ERR_KIND = 3,      /* unknown scan kind */
+    XR_ERR_GEOMETRY = 4,  /* inconsistent scan (spacing <= 0, sdd <= sod, source inside the image) */
+    XR_ERR_ALIGN = 5,     /* a device pointer is not 16-byte aligned */
+    XR_ERR_CUDA = 6,      /* a CUDA call failed; see xr_last_cuda_error() */
+    XR_ERR_ALLOC = 7,     /* device memory for the handle's tables could not be allocated */
+    XR_ERR_BATCH = 8,     /* batch < 1 */
+    XR_ERR_ARG = 9,       /* an argument is out of its documented range */
+    XR_ERR_TUNE = 10,     /* the tuning cache could not be read or written */
+} xr_status;
+
+/* Scan kinds (Section 2.2 and Section 3.2). */
+typedef enum {
+    XR_PAR2D = 0,      /* parallel beam: angles[v] = phi, u = s                          (Sec. 2.2.1) */
+    XR_FAN2D = 1,      /* equispaced fan, flat detector: angles[v] = alpha (eq. 2Dparalleltofan_2) */
+    XR_FAN2D_ARC = 2,  /* equiangular fan: angles[v] = alpha, u is the angle gamma (eq. 2Dparalleltofan) */
+    XR_PAR3D = 3,      /* parallel beam: angles[2v], angles[2v+1] = phi1, phi2; u = s1, v = s2 (Sec. 3.2.1) */
+    XR_CONE = 4,       /* equispaced circular cone, flat detector: angles[v] = phi'_1 (eq. equispaced_cone_beam) */
+    XR_CONE_ARC = 5,   /* equiangular circular cone: u, v are the angles alpha, beta (eq. equiangular_cone_beam) */
+    XR_HELIX = 6,      /* equispaced helical cone: src_z[v] = H (eq. Helical_cone_beam_equispaced) */
+    XR_HELIX_ARC = 7,  /* equiangular helical cone (eq. Helical_cone_beam_equiangular) */
+} xr_kind;
+
+/* Scan description.  Host memory; the library copies what it needs during
+ * xr_geometry_create, so the caller may free it (and the arrays) afterwards.
+ * Flat detectors lie at distance sdd from the source; their samples map to the paper's
+ * (t, h) on the plane through the rotation axis by t = u*sod/sdd, h = v*sod/sdd.
+ * For *_ARC kinds du, u0 (and dv, v0) are angles in radians. */
+typedef struct {
+    int32_t kind;                  /* xr_kind */
+    int32_t nx, ny, nz;            /* image size (2D: nz = 1); each in [1, 16384] */
+    double dx, dy, dz;             /* unit spacing (> 0) */
+    double cx, cy, cz;             /* image centre (Section 4.2) */
+    int32_t n_views, n_rows, n_cols; /* detector (2D: n_rows = 1) */
+    const double *angles;          /* [n_views] (XR_PAR3D: [n_views][2]) */
+    const double *src_z;           /* [n_views] source heights H for helical kinds, else NULL */
+    double du, dv, u0, v0;         /* detector sampling */
+    double sod, sdd;               /* source-origin and source-detector distances (fan/cone) */
+} xr_geometry_desc;
+
+typedef struct xr_geometry xr_geometry;
+
+/* Geometry facts reported by xr_geometry_get_info. */
+typedef struct {
+    int64_t n_rays;        /* n_views * n_rows * n_cols */
+    int64_t n_units;       /* nx * ny * nz */
+    int64_t table_bytes;   /* device bytes held by the handle (ray table) */
+    int32_t is3d;
+    int32_t device;        /* CUDA device the handle's tables live on */
+} xr_geometry_info;
+
+/* Launch tuning of a handle.  Zero fields keep the current value. */
+typedef struct {
+    int32_t block;         /* threads per block of the ray kernels (64..256, multiple of 32) */
+    int32_t batch_chunk;   /* images walked together by one thread (1, 2, 4, 8 or 16) */
+    int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER */
+} xr_tuning;
+
+enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
+
+/* Validate `desc`, allocate the handle and its ray table on the current CUDA device and run
+ * the ray-setup kernel once (ray parameters from eq. 2Dparalleltofan(_2),
+ * equiangular/equispaced_cone_beam, Helical_cone_beam_*, in double precision), then
+ * synchronise that device.  On error *out is set to NULL.
+ * Errors: XR_ERR_NULL, XR_ERR_KIND, XR_ERR_SIZE, XR_ERR_GEOMETRY, XR_ERR_ALLOC, XR_ERR_CUDA. */
+xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out);
+
+/* Free the handle and its device tables (synchronises its device).  NULL is accepted. */
+void xr_geometry_destroy(xr_geometry *g);
+
+/* Re-run the per-geometry ray-setup kernel on `stream` (rebuilds the ray table in place). */
+xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
+
+xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info);
+xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t);
+xr_status xr_get_tuning(const xr_geometry *g, xr_tuning *t);
+
+/* Forward projection (eq. Xray_transform_image): for b < batch and every ray r,
+ * sino[b][r] = sum over units I crossed by r of img[b][I] * l_I(r).
+ * d_img: [batch][n_units] float32, d_sino: [batch][n_rays] float32 (overwritten).
+ * Both 16-byte aligned.  Errors: XR_ERR_NULL, XR_ERR_BATCH, XR_ERR_ALIGN, XR_ERR_CUDA. */
+xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, int32_t batch,
+                     xr_stream stream);
+
+/* Adjoint (backprojection; the transpose of the forward operator, Section 1):
+ * img[b][I] = sum over rays r crossing I of l_I(r) * sino[b][r].  d_img is overwritten.
+ * The method is the handle's tuning (ray-driven scatter with atomics, or unit-driven gather
+ * over the same condition); both visit the same (ray, unit) pairs with the same lengths. */
+xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img, int32_t batch,
+                         xr_stream stream);
+
+/* As xr_backproject with an explicit method (XR_ADJ_SCATTER / XR_ADJ_GATHER).
+ * XR_ADJ_GATHER is available for 2D kinds; elsewhere it returns XR_ERR_ARG. */
+xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float *d_img,
+                                int32_t batch, int32_t method, xr_stream stream);
+
+/* Sparse rows of the projection matrix (Algorithm 1/2 "Output", Section 4.2): for each of
+ * the n rays listed in d_rays (device int64 ray ids), the units it crosses with positive
+ * length, written in visiting order to d_idx[q*cap ...] (1D index I, int64) and
+ * d_len[q*cap ...] (float32); d_count[q] receives the number of units (int32), which may
+ * exceed cap (then only the first cap are written), or -1 for an id outside [0, n_rays).
+ * Same walk as xr_project. */
+xr_status xr_ray_units(const xr_geometry *g, const int64_t *d_rays, int32_t n, int32_t cap,
+                       int64_t *d_idx, float *d_len, int32_t *d_count, xr_stream stream);
+
+/* One problem of a batched launch: a geometry with its own image and sinogram. */
+typedef struct {
+    const xr_geometry *geom;
+    const float *img;   /* device, [n_units], 16-byte aligned */
+    float *sino;        /* device, [n_rays], 16-byte aligned */
+} xr_problem;
+
+/* A plan for one persistent launch over n independent problems (uneven sizes allowed).
+ * The work list -- every problem's rays cut into tiles of `tile` consecutive rays -- is
+ * uploaded once here (synchronously); the launches below then do stream work only, so
+ * they may be captured in a CUDA graph and replayed while the problems' buffers stay put.
+ * tile: rays per work item (32..65536, multiple of 32; 0 = 256); block: threads per CTA
+ * (64..256, multiple of 32; 0 = 256).  All geometries must live on the current device.
+ * Errors: XR_ERR_NULL, XR_ERR_SIZE, XR_ERR_ALIGN, XR_ERR_ARG, XR_ERR_ALLOC, XR_ERR_CUDA. */
+typedef struct xr_batch xr_batch;
+xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int32_t block,
+                          xr_batch **out);
+void xr_batch_destroy(xr_batch *b);
+
+/* Forward projection of every problem of the plan: one persistent launch whose CTAs (one
+ * set per SM, as many as fit) take tiles from one atomic counter until none is left. */
+xr_status xr_batch_project(const xr_batch *b, xr_stream stream);
+
+/* Adjoint of every problem of the plan (ray-driven scatter after one zeroing launch):
+ * overwrites every problem's img with the adjoint of its sino. */
+xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream);
+
+/* Text of a status code (static storage). */
+const char *xr_status_string(xr_status s);
+
+/* CUDA error code of the last XR_ERR_CUDA returned on the calling thread (0 if none). */
+int32_t xr_last_cuda_error(void);
+
+/* Library version, e.g. 1 for 0.1. */
+int32_t xr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XRAY_H */

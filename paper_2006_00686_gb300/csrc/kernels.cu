@@ -1,0 +1,371 @@
+// Ray kernels: forward projection, ray-driven scatter adjoint, unit-driven gather adjoint
+// (2D), sparse-row export and the persistent batched launch.  All FP32 with FP32
+// accumulation; no tensor cores (the work is a gather along rays, not a contraction).
+#include "xray_internal.h"
+
+namespace xr {
+
+// ---------------------------------------------------------------------------------------
+// Visitors
+// ---------------------------------------------------------------------------------------
+
+// Forward: acc[b] += f_b[I] * l for the `nb` images of this thread's chunk.
+template <int BC>
+struct FwdVisitor {
+    const float *__restrict__ img;
+    int64_t bs;
+    int nb;
+    float acc[BC];
+    __device__ __forceinline__ void operator()(int64_t off, float l)
+    {
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+            if (b < nb) acc[b] = __fmaf_rn(__ldg(img + b * bs + off), l, acc[b]);
+    }
+};
+
+// Adjoint, ray-driven: img_b[I] += g_b * l (fire-and-forget atomic adds).
+template <int BC>
+struct ScatterVisitor {
+    float *__restrict__ img;
+    int64_t bs;
+    int nb;
+    float g[BC];
+    __device__ __forceinline__ void operator()(int64_t off, float l)
+    {
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+            if (b < nb && g[b] != 0.f) atomicAdd(img + b * bs + off, __fmul_rn(g[b], l));
+    }
+};
+
+// Sparse-row export: (I, l) in visiting order, up to cap entries.
+struct ExportVisitor {
+    int64_t *idx;
+    float *len;
+    int cap;
+    int n;
+    __device__ __forceinline__ void operator()(int64_t off, float l)
+    {
+        if (n < cap) {
+            idx[n] = off;
+            len[n] = l;
+        }
+        ++n;
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// Forward projection: one thread per ray, `BC` images per thread (blockIdx.y = image chunk)
+// ---------------------------------------------------------------------------------------
+
+template <int BC>
+__global__ void __launch_bounds__(256) project_kernel(const RayRec *__restrict__ rays, int64_t n_rays,
+                                                      Grid grid, const float *__restrict__ img,
+                                                      int64_t img_bs, float *__restrict__ sino,
+                                                      int64_t sino_bs, int batch)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int b0 = blockIdx.y * BC;
+    FwdVisitor<BC> vis;
+    vis.img = img + b0 * img_bs;
+    vis.bs = img_bs;
+    vis.nb = min(BC, batch - b0);
+#pragma unroll
+    for (int b = 0; b < BC; ++b) vis.acc[b] = 0.f;
+    Walk W;
+    if (walk_setup(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, W)) walk(W, vis);
+#pragma unroll
+    for (int b = 0; b < BC; ++b)
+        if (b < vis.nb) sino[(b0 + b) * sino_bs + r] = vis.acc[b];
+}
+
+template <int BC>
+__global__ void __launch_bounds__(256) scatter_kernel(const RayRec *__restrict__ rays, int64_t n_rays,
+                                                      Grid grid, const float *__restrict__ sino,
+                                                      int64_t sino_bs, float *__restrict__ img,
+                                                      int64_t img_bs, int batch)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int b0 = blockIdx.y * BC;
+    ScatterVisitor<BC> vis;
+    vis.img = img + b0 * img_bs;
+    vis.bs = img_bs;
+    vis.nb = min(BC, batch - b0);
+    bool any = false;
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+        vis.g[b] = (b < vis.nb) ? __ldg(sino + (b0 + b) * sino_bs + r) : 0.f;
+        any |= vis.g[b] != 0.f;
+    }
+    if (!any) return;
+    Walk W;
+    if (walk_setup(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, W)) walk(W, vis);
+}
+
+template <int BC>
+static cudaError_t launch_project_t(const RayRec *rays, int64_t n_rays, const Grid &grid,
+                                    const float *img, int64_t img_bs, float *sino, int64_t sino_bs,
+                                    int batch, int block, cudaStream_t s)
+{
+    const dim3 g((unsigned)((n_rays + block - 1) / block), (unsigned)((batch + BC - 1) / BC));
+    project_kernel<BC><<<g, block, 0, s>>>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch);
+    return cudaGetLastError();
+}
+
+template <int BC>
+static cudaError_t launch_scatter_t(const RayRec *rays, int64_t n_rays, const Grid &grid,
+                                    const float *sino, int64_t sino_bs, float *img, int64_t img_bs,
+                                    int batch, int block, cudaStream_t s)
+{
+    const dim3 g((unsigned)((n_rays + block - 1) / block), (unsigned)((batch + BC - 1) / BC));
+    scatter_kernel<BC><<<g, block, 0, s>>>(rays, n_rays, grid, sino, sino_bs, img, img_bs, batch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const RayRec *rays, int64_t n_rays, const Grid &grid, const float *img,
+                           int64_t img_bs, float *sino, int64_t sino_bs, int batch, int chunk,
+                           int block, cudaStream_t s)
+{
+    switch (chunk) {
+    case 16: return launch_project_t<16>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
+    case 8: return launch_project_t<8>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
+    case 4: return launch_project_t<4>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
+    case 2: return launch_project_t<2>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
+    default: return launch_project_t<1>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
+    }
+}
+
+cudaError_t launch_backproject_scatter(const RayRec *rays, int64_t n_rays, const Grid &grid,
+                                       const float *sino, int64_t sino_bs, float *img,
+                                       int64_t img_bs, int batch, int chunk, int block,
+                                       cudaStream_t s)
+{
+    switch (chunk) {
+    case 16: return launch_scatter_t<16>(rays, n_rays, grid, sino, sino_bs, img, img_bs, batch, block, s);
+    case 8: return launch_scatter_t<8>(rays, n_rays, grid, sino, sino_bs, img, img_bs, batch, block, s);
+    case 4: return launch_scatter_t<4>(rays, n_rays, grid, sino, sino_bs, img, img_bs, batch, block, s);
+    case 2: return launch_scatter_t<2>(rays, n_rays, grid, sino, sino_bs, img, img_bs, batch, block, s);
+    default: return launch_scatter_t<1>(rays, n_rays, grid, sino, sino_bs, img, img_bs, batch, block, s);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint, unit-driven gather (2D): one thread per pixel; for every view, the detector bins
+// whose rays can cross the pixel (projection of its corners, one bin of margin), and for
+// each the length the forward walk gives that (ray, pixel) pair.
+// View table (8 doubles per view): parallel: (-sin phi, cos phi); fan: source (Sx, Sy),
+// central direction (ex, ey), detector direction (tx, ty).
+// ---------------------------------------------------------------------------------------
+
+template <int BC>
+__global__ void __launch_bounds__(256) gather2d_kernel(const RayRec *__restrict__ rays, GeoParams g,
+                                                       Grid grid, const double *__restrict__ vt,
+                                                       const float *__restrict__ sino, int64_t sino_bs,
+                                                       float *__restrict__ img, int64_t img_bs, int batch)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n_pix = (int64_t)g.nx * g.ny;
+    if (p >= n_pix) return;
+    const int i = (int)(p % g.nx), j = (int)(p / g.nx);
+    const int b0 = blockIdx.y * BC;
+    const int nb = min(BC, batch - b0);
+    float acc[BC];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) acc[b] = 0.f;
+    // pixel corners (world coordinates)
+    const float x0 = (float)(g.cx + (i - 0.5 * g.nx) * g.dx), x1 = x0 + (float)g.dx;
+    const float y1 = (float)(g.cy + (0.5 * g.ny - j) * g.dy), y0 = y1 - (float)g.dy;
+    const float half = 0.5f * (float)(g.n_cols - 1);
+    const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0;
+    for (int v = 0; v < g.n_views; ++v) {
+        const double *e = vt + 8 * v;
+        float cmin = 1e30f, cmax = -1e30f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float X = (q & 1) ? x1 : x0, Y = (q & 2) ? y1 : y0;
+            float uc;
+            if (g.kind == XR_PAR2D) {
+                uc = (float)e[0] * X + (float)e[1] * Y;
+            } else {
+                const float rx = X - (float)e[0], ry = Y - (float)e[1];
+                const float depth = rx * (float)e[2] + ry * (float)e[3];
+                const float lat = rx * (float)e[4] + ry * (float)e[5];
+                uc = (g.kind == XR_FAN2D) ? (float)g.sdd * lat / depth : atan2f(lat, depth);
+            }
+            const float c = (uc - u0) * inv_du + half;
+            cmin = fminf(cmin, c);
+            cmax = fmaxf(cmax, c);
+        }
+        const int c0 = max((int)floorf(cmin) - 1, 0), c1 = min((int)ceilf(cmax) + 1, g.n_cols - 1);
+        for (int c = c0; c <= c1; ++c) {
+            const int64_t r = (int64_t)v * g.n_cols + c;
+            Walk W;
+            if (!walk_setup(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, W)) continue;
+            const float l = walk_unit_length(W, i, j, 0);
+            if (l > 0.f) {
+#pragma unroll
+                for (int b = 0; b < BC; ++b)
+                    if (b < nb) acc[b] = __fmaf_rn(__ldg(sino + (b0 + b) * sino_bs + r), l, acc[b]);
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < BC; ++b)
+        if (b < nb) img[(b0 + b) * img_bs + (int64_t)j * grid.sy + (int64_t)i * grid.sx] = acc[b];
+}
+
+template <int BC>
+static cudaError_t launch_gather_t(const RayRec *rays, const GeoParams &g, const Grid &grid,
+                                   const double *vt, const float *sino, int64_t sino_bs, float *img,
+                                   int64_t img_bs, int batch, int block, cudaStream_t s)
+{
+    const int64_t n_pix = (int64_t)g.nx * g.ny;
+    const dim3 gr((unsigned)((n_pix + block - 1) / block), (unsigned)((batch + BC - 1) / BC));
+    gather2d_kernel<BC><<<gr, block, 0, s>>>(rays, g, grid, vt, sino, sino_bs, img, img_bs, batch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_gather2d(const RayRec *rays, const GeoParams &g, const Grid &grid,
+                                        const double *vt, const float *sino, int64_t sino_bs,
+                                        float *img, int64_t img_bs, int batch, int chunk, int block,
+                                        cudaStream_t s)
+{
+    switch (chunk) {
+    case 16: return launch_gather_t<16>(rays, g, grid, vt, sino, sino_bs, img, img_bs, batch, block, s);
+    case 8: return launch_gather_t<8>(rays, g, grid, vt, sino, sino_bs, img, img_bs, batch, block, s);
+    case 4: return launch_gather_t<4>(rays, g, grid, vt, sino, sino_bs, img, img_bs, batch, block, s);
+    case 2: return launch_gather_t<2>(rays, g, grid, vt, sino, sino_bs, img, img_bs, batch, block, s);
+    default: return launch_gather_t<1>(rays, g, grid, vt, sino, sino_bs, img, img_bs, batch, block, s);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Sparse rows (projection-matrix export): one thread per listed ray.
+// ---------------------------------------------------------------------------------------
+
+__global__ void ray_units_kernel(const RayRec *__restrict__ rays, int64_t n_rays, Grid grid,
+                                 const int64_t *__restrict__ ids, int n, int cap,
+                                 int64_t *__restrict__ idx, float *__restrict__ len,
+                                 int32_t *__restrict__ count)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t id = ids[q];
+    if (id < 0 || id >= n_rays) {  // not a ray of this scan: empty row, count -1
+        count[q] = -1;
+        return;
+    }
+    ExportVisitor vis{idx + (int64_t)q * cap, len + (int64_t)q * cap, cap, 0};
+    Walk W;
+    if (walk_setup(rays[id], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, W)) walk(W, vis);
+    count[q] = vis.n;
+}
+
+cudaError_t launch_ray_units(const RayRec *rays, int64_t n_rays, const Grid &grid, const int64_t *ids, int n,
+                             int cap, int64_t *idx, float *len, int32_t *count, cudaStream_t s)
+{
+    const int block = 128;
+    ray_units_kernel<<<(n + block - 1) / block, block, 0, s>>>(rays, n_rays, grid, ids, n, cap, idx, len,
+                                                               count);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Persistent batched launch over uneven problems.  The global tile space is the
+// concatenation of every problem's tiles of `tile` consecutive rays; each CTA takes tiles
+// from one atomic counter until none is left (no CTA ever waits for another).
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int find_item(const BatchItem *items, int n, int64_t t)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(256) batched_kernel(const BatchItem *__restrict__ items, int n_items,
+                                                      int64_t n_tiles, int tile,
+                                                      unsigned long long *__restrict__ counter)
+{
+    __shared__ int64_t s_tile;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t t = s_tile;
+        if (t >= n_tiles) break;
+        const int it = find_item(items, n_items, t);
+        const BatchItem &P = items[it];
+        const int64_t first = (t - P.tile_begin) * tile;
+        for (int q = threadIdx.x; q < tile; q += blockDim.x) {
+            const int64_t r = first + q;
+            if (r >= P.n_rays) break;
+            Walk W;
+            const int64_t sy = P.nx, sz = (int64_t)P.nx * P.ny;
+            if (!ADJ) {
+                FwdVisitor<1> vis;
+                vis.img = P.img;
+                vis.bs = 0;
+                vis.nb = 1;
+                vis.acc[0] = 0.f;
+                if (walk_setup(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, W)) walk(W, vis);
+                P.sino[r] = vis.acc[0];
+            } else {
+                ScatterVisitor<1> vis;
+                vis.img = const_cast<float *>(P.img);
+                vis.bs = 0;
+                vis.nb = 1;
+                vis.g[0] = __ldg(P.sino + r);
+                if (vis.g[0] != 0.f && walk_setup(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, W)) walk(W, vis);
+            }
+        }
+    }
+}
+
+// Zero every problem's image before a scatter adjoint (grid-stride over all units).
+__global__ void zero_items_kernel(const BatchItem *__restrict__ items, int n_items)
+{
+    for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+        const BatchItem &P = items[it];
+        const int64_t n = (int64_t)P.nx * P.ny * P.nz;
+        float *img = const_cast<float *>(P.img);
+        for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+             u += (int64_t)gridDim.x * blockDim.x)
+            img[u] = 0.f;
+    }
+}
+
+int batched_ctas_per_sm(int block, int adjoint)
+{
+    int n = 0;
+    if (adjoint)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<true>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<false>, block, 0);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                           unsigned long long *counter, int adjoint, int grid_ctas, int block,
+                           cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (adjoint) {
+        zero_items_kernel<<<dim3(256, (unsigned)min(n_items, 65535)), 256, 0, s>>>(items, n_items);
+        batched_kernel<true><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
+    } else {
+        batched_kernel<false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace xr

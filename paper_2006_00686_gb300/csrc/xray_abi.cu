@@ -1,0 +1,414 @@
+// Host side of the C ABI declared in include/xray.h: validation, handle lifetime, launches.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "xray_internal.h"
+
+using namespace xr;
+
+static thread_local int32_t g_last_cuda = 0;
+
+static xr_status cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int32_t)e;
+    return XR_ERR_CUDA;
+}
+
+#define XR_CUDA(call)                               \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+static bool kind_is3d(int k) { return k >= XR_PAR3D; }
+static bool kind_helical(int k) { return k == XR_HELIX || k == XR_HELIX_ARC; }
+static bool kind_divergent(int k) { return k == XR_FAN2D || k == XR_FAN2D_ARC || k >= XR_CONE; }
+static bool kind_flat(int k) { return k == XR_FAN2D || k == XR_CONE || k == XR_HELIX; }
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static xr_status validate(const xr_geometry_desc *d)
+{
+    if (!d) return XR_ERR_NULL;
+    if (d->kind < XR_PAR2D || d->kind > XR_HELIX_ARC) return XR_ERR_KIND;
+    const bool three = kind_is3d(d->kind);
+    const int nz = three ? d->nz : 1, nr = three ? d->n_rows : 1;
+    if (d->nx < 1 || d->ny < 1 || nz < 1 || d->nx > 16384 || d->ny > 16384 || nz > 16384) return XR_ERR_SIZE;
+    if (d->n_views < 1 || d->n_cols < 1 || nr < 1) return XR_ERR_SIZE;
+    if ((int64_t)d->n_views * nr * d->n_cols > ((int64_t)1 << 40)) return XR_ERR_SIZE;
+    if (!d->angles) return XR_ERR_NULL;
+    if (kind_helical(d->kind) && !d->src_z) return XR_ERR_NULL;
+    if (!(d->dx > 0) || !(d->dy > 0) || (three && !(d->dz > 0))) return XR_ERR_GEOMETRY;
+    if (!(d->du > 0) || (three && !(d->dv > 0))) return XR_ERR_GEOMETRY;
+    if (kind_divergent(d->kind)) {
+        if (!(d->sod > 0)) return XR_ERR_GEOMETRY;
+        if (kind_flat(d->kind) && !(d->sdd > 0)) return XR_ERR_GEOMETRY;
+        // the source circle must stay outside the image (farthest corner in the xy-plane)
+        const double ex = fabs(d->cx) + 0.5 * d->nx * d->dx, ey = fabs(d->cy) + 0.5 * d->ny * d->dy;
+        if (!(d->sod > sqrt(ex * ex + ey * ey))) return XR_ERR_GEOMETRY;
+    }
+    // foot-point coordinates of rays that cross the image must fit the 16-bit record
+    const double dz = three ? d->dz : 1.0;
+    const double R = 0.5 * sqrt(pow(d->nx * d->dx, 2) + pow(d->ny * d->dy, 2) + pow(nz * dz, 2));
+    if (0.5 * d->nx + R / d->dx > 32000 || 0.5 * d->ny + R / d->dy > 32000 || 0.5 * nz + R / dz > 32000)
+        return XR_ERR_SIZE;
+    return XR_OK;
+}
+
+static Grid make_grid(const xr_geometry *g)
+{
+    Grid gr;
+    gr.nx = g->params.nx;
+    gr.ny = g->params.ny;
+    gr.nz = g->params.nz;
+    gr.sx = 1;
+    gr.sy = gr.nx;
+    gr.sz = (int64_t)gr.nx * gr.ny;
+    return gr;
+}
+
+// Per-view data of the 2D gather's footprint test (double precision, on the host).
+static void fill_view_table(const xr_geometry_desc *d, double *vt)
+{
+    for (int v = 0; v < d->n_views; ++v) {
+        double *e = vt + 8 * v;
+        memset(e, 0, 8 * sizeof(double));
+        const double a = d->angles[v];
+        if (d->kind == XR_PAR2D) {
+            e[0] = -sin(a);  // s = -x sin(phi) + y cos(phi)
+            e[1] = cos(a);
+        } else {
+            e[0] = -d->sod * sin(a);  // source
+            e[1] = d->sod * cos(a);
+            e[2] = sin(a);  // towards the origin
+            e[3] = -cos(a);
+            e[4] = cos(a);  // along the detector
+            e[5] = sin(a);
+        }
+    }
+}
+
+// Images walked together by one thread: the handle's tuning, at most the batch.
+static int pick_chunk(const xr_geometry *g, int batch)
+{
+    int c = g->tune.batch_chunk;
+    while (c > 1 && c > batch) c >>= 1;
+    return c < 1 ? 1 : c;
+}
+
+extern "C" {
+
+xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
+{
+    if (!out) return XR_ERR_NULL;
+    *out = nullptr;
+    xr_status st = validate(desc);
+    if (st != XR_OK) return st;
+    xr_geometry *g = new (std::nothrow) xr_geometry();
+    if (!g) return XR_ERR_ALLOC;
+    g->desc = *desc;
+    const bool three = kind_is3d(desc->kind);
+    if (!three) {
+        g->desc.nz = 1;
+        g->desc.n_rows = 1;
+        g->desc.dz = g->desc.dz > 0 ? g->desc.dz : 1.0;
+        g->desc.dv = g->desc.dv > 0 ? g->desc.dv : 1.0;
+    }
+    g->desc.angles = nullptr;
+    g->desc.src_z = nullptr;
+    GeoParams &p = g->params;
+    p.kind = desc->kind;
+    p.nx = desc->nx;
+    p.ny = desc->ny;
+    p.nz = g->desc.nz;
+    p.n_views = desc->n_views;
+    p.n_rows = g->desc.n_rows;
+    p.n_cols = desc->n_cols;
+    p.dx = desc->dx;
+    p.dy = desc->dy;
+    p.dz = g->desc.dz;
+    p.cx = desc->cx;
+    p.cy = desc->cy;
+    p.cz = desc->cz;
+    p.du = desc->du;
+    p.dv = g->desc.dv;
+    p.u0 = desc->u0;
+    p.v0 = three ? desc->v0 : 0.0;
+    p.sod = desc->sod;
+    p.sdd = desc->sdd;
+    g->n_rays = (int64_t)p.n_views * p.n_rows * p.n_cols;
+    g->n_units = (int64_t)p.nx * p.ny * p.nz;
+    g->tune.block = 128;
+    g->tune.batch_chunk = 1;
+    g->tune.adjoint = three ? XR_ADJ_SCATTER : XR_ADJ_GATHER;
+
+    cudaError_t e = cudaGetDevice(&g->device);
+    const size_t n_ang = (size_t)p.n_views * (desc->kind == XR_PAR3D ? 2 : 1);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_angles, n_ang * sizeof(double));
+    if (e == cudaSuccess && kind_helical(desc->kind)) e = cudaMalloc(&g->d_src_z, p.n_views * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
+    if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_view_tab, (size_t)p.n_views * 8 * sizeof(double));
+    if (e != cudaSuccess) {
+        const bool oom = (e == cudaErrorMemoryAllocation);
+        cudaGetLastError();
+        xr_geometry_destroy(g);
+        if (oom) return XR_ERR_ALLOC;
+        return cuda_fail(e);
+    }
+    e = cudaMemcpy(g->d_angles, desc->angles, n_ang * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && g->d_src_z)
+        e = cudaMemcpy(g->d_src_z, desc->src_z, p.n_views * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !three) {
+        double *vt = (double *)malloc((size_t)p.n_views * 8 * sizeof(double));
+        if (!vt) {
+            xr_geometry_destroy(g);
+            return XR_ERR_ALLOC;
+        }
+        fill_view_table(desc, vt);
+        e = cudaMemcpy(g->d_view_tab, vt, (size_t)p.n_views * 8 * sizeof(double), cudaMemcpyHostToDevice);
+        free(vt);
+    }
+    if (e == cudaSuccess) e = launch_ray_setup(p, g->d_angles, g->d_src_z, g->d_rays, g->n_rays, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        xr_geometry_destroy(g);
+        return cuda_fail(e);
+    }
+    *out = g;
+    return XR_OK;
+}
+
+void xr_geometry_destroy(xr_geometry *g)
+{
+    if (!g) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    cudaFree(g->d_angles);
+    cudaFree(g->d_src_z);
+    cudaFree(g->d_rays);
+    cudaFree(g->d_view_tab);
+    cudaSetDevice(prev);
+    delete g;
+}
+
+xr_status xr_ray_setup(xr_geometry *g, xr_stream stream)
+{
+    if (!g) return XR_ERR_NULL;
+    XR_CUDA(launch_ray_setup(g->params, g->d_angles, g->d_src_z, g->d_rays, g->n_rays, (cudaStream_t)stream));
+    return XR_OK;
+}
+
+xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
+{
+    if (!g || !info) return XR_ERR_NULL;
+    info->n_rays = g->n_rays;
+    info->n_units = g->n_units;
+    info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * 8 * 8;
+    info->is3d = kind_is3d(g->params.kind);
+    info->device = g->device;
+    return XR_OK;
+}
+
+xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
+{
+    if (!g || !t) return XR_ERR_NULL;
+    if (t->block && (t->block < 64 || t->block > 256 || (t->block & 31))) return XR_ERR_ARG;
+    if (t->batch_chunk && t->batch_chunk != 1 && t->batch_chunk != 2 && t->batch_chunk != 4 &&
+        t->batch_chunk != 8 && t->batch_chunk != 16)
+        return XR_ERR_ARG;
+    if (t->adjoint && t->adjoint != XR_ADJ_SCATTER && t->adjoint != XR_ADJ_GATHER) return XR_ERR_ARG;
+    if (t->adjoint == XR_ADJ_GATHER && kind_is3d(g->params.kind)) return XR_ERR_ARG;
+    if (t->block) g->tune.block = t->block;
+    if (t->batch_chunk) g->tune.batch_chunk = t->batch_chunk;
+    if (t->adjoint) g->tune.adjoint = t->adjoint;
+    return XR_OK;
+}
+
+xr_status xr_get_tuning(const xr_geometry *g, xr_tuning *t)
+{
+    if (!g || !t) return XR_ERR_NULL;
+    *t = g->tune;
+    return XR_OK;
+}
+
+xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, int32_t batch, xr_stream stream)
+{
+    if (!g || !d_img || !d_sino) return XR_ERR_NULL;
+    if (batch < 1) return XR_ERR_BATCH;
+    if (!aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
+    const int chunk = pick_chunk(g, batch);
+    if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
+    XR_CUDA(launch_project(g->d_rays, g->n_rays, make_grid(g), d_img, g->n_units, d_sino, g->n_rays, batch,
+                           chunk, g->tune.block, (cudaStream_t)stream));
+    return XR_OK;
+}
+
+xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float *d_img, int32_t batch,
+                                int32_t method, xr_stream stream)
+{
+    if (!g || !d_img || !d_sino) return XR_ERR_NULL;
+    if (batch < 1) return XR_ERR_BATCH;
+    if (!aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
+    if (method == XR_ADJ_AUTO) method = g->tune.adjoint;
+    const int chunk = pick_chunk(g, batch);
+    if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (method == XR_ADJ_GATHER) {
+        if (kind_is3d(g->params.kind)) return XR_ERR_ARG;
+        XR_CUDA(launch_backproject_gather2d(g->d_rays, g->params, make_grid(g), g->d_view_tab, d_sino, g->n_rays,
+                                            d_img, g->n_units, batch, chunk, g->tune.block, s));
+        return XR_OK;
+    }
+    if (method != XR_ADJ_SCATTER) return XR_ERR_ARG;
+    XR_CUDA(cudaMemsetAsync(d_img, 0, (size_t)g->n_units * batch * sizeof(float), s));
+    XR_CUDA(launch_backproject_scatter(g->d_rays, g->n_rays, make_grid(g), d_sino, g->n_rays, d_img, g->n_units,
+                                       batch, chunk, g->tune.block, s));
+    return XR_OK;
+}
+
+xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img, int32_t batch,
+                         xr_stream stream)
+{
+    return xr_backproject_method(g, d_sino, d_img, batch, XR_ADJ_AUTO, stream);
+}
+
+xr_status xr_ray_units(const xr_geometry *g, const int64_t *d_rays, int32_t n, int32_t cap, int64_t *d_idx,
+                       float *d_len, int32_t *d_count, xr_stream stream)
+{
+    if (!g || !d_rays || !d_idx || !d_len || !d_count) return XR_ERR_NULL;
+    if (n < 1 || cap < 1) return XR_ERR_SIZE;
+    XR_CUDA(launch_ray_units(g->d_rays, g->n_rays, make_grid(g), d_rays, n, cap, d_idx, d_len, d_count,
+                             (cudaStream_t)stream));
+    return XR_OK;
+}
+
+}  // extern "C"
+
+struct xr_batch {
+    int device;
+    int n;
+    int tile, block, ctas_fwd, ctas_adj;
+    int64_t n_tiles;
+    BatchItem *d_items;
+    unsigned long long *d_counter;
+};
+
+extern "C" {
+
+xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int32_t block, xr_batch **out)
+{
+    if (!out) return XR_ERR_NULL;
+    *out = nullptr;
+    if (!probs) return XR_ERR_NULL;
+    if (n < 1) return XR_ERR_SIZE;
+    if (tile == 0) tile = 256;
+    if (block == 0) block = 256;
+    if (tile < 32 || tile > 65536 || (tile & 31) || block < 64 || block > 256 || (block & 31)) return XR_ERR_ARG;
+    BatchItem *items = (BatchItem *)malloc(sizeof(BatchItem) * (size_t)n);
+    if (!items) return XR_ERR_ALLOC;
+    int64_t tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        const xr_geometry *g = probs[i].geom;
+        if (!g || !probs[i].img || !probs[i].sino) {
+            free(items);
+            return XR_ERR_NULL;
+        }
+        if (!aligned16(probs[i].img) || !aligned16(probs[i].sino)) {
+            free(items);
+            return XR_ERR_ALIGN;
+        }
+        items[i].rays = g->d_rays;
+        items[i].img = probs[i].img;
+        items[i].sino = probs[i].sino;
+        items[i].nx = g->params.nx;
+        items[i].ny = g->params.ny;
+        items[i].nz = g->params.nz;
+        items[i].pad = 0;
+        items[i].n_rays = g->n_rays;
+        items[i].tile_begin = tiles;
+        tiles += (g->n_rays + tile - 1) / tile;
+    }
+    xr_batch *b = new (std::nothrow) xr_batch();
+    if (!b) {
+        free(items);
+        return XR_ERR_ALLOC;
+    }
+    b->n = n;
+    b->tile = tile;
+    b->block = block;
+    b->n_tiles = tiles;
+    int sms = 0;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items, sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice);
+    free(items);
+    if (e != cudaSuccess) {
+        const bool oom = (e == cudaErrorMemoryAllocation);
+        cudaGetLastError();
+        xr_batch_destroy(b);
+        return oom ? XR_ERR_ALLOC : cuda_fail(e);
+    }
+    b->ctas_fwd = sms * batched_ctas_per_sm(block, 0);
+    b->ctas_adj = sms * batched_ctas_per_sm(block, 1);
+    *out = b;
+    return XR_OK;
+}
+
+void xr_batch_destroy(xr_batch *b)
+{
+    if (!b) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    cudaSetDevice(prev);
+    delete b;
+}
+
+xr_status xr_batch_project(const xr_batch *b, xr_stream stream)
+{
+    if (!b) return XR_ERR_NULL;
+    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 0, b->ctas_fwd, b->block,
+                           (cudaStream_t)stream));
+    return XR_OK;
+}
+
+xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream)
+{
+    if (!b) return XR_ERR_NULL;
+    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 1, b->ctas_adj, b->block,
+                           (cudaStream_t)stream));
+    return XR_OK;
+}
+
+const char *xr_status_string(xr_status s)
+{
+    switch (s) {
+    case XR_OK: return "ok";
+    case XR_ERR_NULL: return "a required pointer is NULL";
+    case XR_ERR_SIZE: return "a size is non-positive or too large";
+    case XR_ERR_KIND: return "unknown scan kind";
+    case XR_ERR_GEOMETRY: return "inconsistent scan geometry";
+    case XR_ERR_ALIGN: return "device pointer not 16-byte aligned";
+    case XR_ERR_CUDA: return "CUDA call failed";
+    case XR_ERR_ALLOC: return "device allocation failed";
+    case XR_ERR_BATCH: return "batch must be >= 1";
+    case XR_ERR_ARG: return "argument out of range";
+    case XR_ERR_TUNE: return "tuning cache could not be read or written";
+    }
+    return "unknown status";
+}
+
+int32_t xr_last_cuda_error(void) { return g_last_cuda; }
+
+int32_t xr_version(void) { return 1; }
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// Device core of the X-ray transform: ray records and the per-ray walk.
+//
+// A ray is kept in "index space": along axis a the continuous coordinate u_a runs over
+// [0, N_a] and unit n covers [n, n+1] (x grows with i; y and z are flipped so that they
+// grow with j and k, the orientation of Section 2.1 / Section 3.1).  Along the ray,
+// u_a(t) = o_a + w_a t with t the physical length.  The integer part of the foot point o_a
+// is kept apart from its fraction so that a plane crossing t = (q - o_a)/w_a keeps the
+// full float precision even for a ray almost parallel to that axis's planes.
+//
+// The walk is the paper's method laid out for a GPU thread:
+//   * the driving axis A is the one with the largest |w_a| (the paper drives with i;
+//     Section 4.3 allows any index to drive), so each step of the driving index m moves
+//     every other index by at most one;
+//   * for each m, the valid indices of a minor axis are those whose open interval meets
+//     the minor coordinate's range across the slab -- eq. restriction_j(_3D) and
+//     eq. restriction_k_3D_1 -- evaluated as floor(u_B) at the slab's two planes;
+//   * every candidate unit gets C_low = max of the three entering planes' t and
+//     C_up = min of the three leaving planes' t (eq. conditions_3D_1) and is kept iff
+//     C_low < C_up, with length C_up - C_low (eq. range_length_3D);
+//   * an axis with w_a = 0 holds the ray in one family of grid planes: its index is the
+//     one fixed by the ray-setup kernel with the ambiguity rule of Section 4.1, which
+//     reduces the walk to the 2D case (Case 2) or to a run along one axis (Cases 3, 4).
+//
+// Every plane crossing is a single fused multiply-add of (plane index, 1/w, -frac/w), so
+// the same (ray, unit) pair always yields the same float length, whichever kernel
+// evaluates it (forward walk, scatter adjoint, gather adjoint, sparse-row export).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace xr {
+
+// One ray in index space, 32 bytes.  Built in double precision by the ray-setup kernel.
+struct __align__(16) RayRec {
+    float w0, w1, w2;  // du_a/dt (0: the ray lies in one family of planes of axis a)
+    float f0;          // fractional part of the foot-point coordinate along x
+    float f1, f2;      // ... along y, z
+    int16_t o0, o1, o2;  // integer part of the foot-point coordinate, or the fixed index (w == 0)
+    int16_t flags;       // bit 0: the ray does not enter the image
+};
+static_assert(sizeof(RayRec) == 32, "RayRec layout");
+
+enum { RAY_MISS = 1 };
+
+template <class T>
+__device__ __forceinline__ T sel3(int a, T x, T y, T z)
+{
+    return a == 0 ? x : (a == 1 ? y : z);
+}
+
+// The walk state of one ray, axes permuted to (A driving, B, C minor).
+struct Walk {
+    int nact;             // number of axes the ray is not parallel to (1..3)
+    int axA, axB, axC;    // original axis (0 = x/i, 1 = y/j, 2 = z/k) of A, B, C
+    int NA, NB, NC;
+    int oA, oB, oC;
+    int sgA, sgB, sgC;    // 1 when w < 0: the entering plane of unit n is n + 1
+    float invA, bA;       // t(plane q) = fma(q - o, inv, b), b = -frac * inv
+    float invB, bB, wB, fB;
+    float invC, bC, wC, fC;
+    int64_t sA, sB, sC;   // element strides of the axes in the image layout
+    int64_t base;         // offset of the fixed indices
+    int mlo, mhi;         // driving indices to visit
+};
+
+// Prepare the walk; false when the ray crosses no unit.  Strides sx, sy, sz give the image
+// layout (1, nx, nx*ny for the [nz][ny][nx] layout).
+__device__ __forceinline__ bool walk_setup(const RayRec &r, int nx, int ny, int nz, int64_t sx,
+                                           int64_t sy, int64_t sz, Walk &W)
+{
+    W.nact = 0;
+    if (r.flags & RAY_MISS) return false;
+    const bool a0 = r.w0 != 0.f, a1 = r.w1 != 0.f, a2 = r.w2 != 0.f;
+    const int nact = (int)a0 + (int)a1 + (int)a2;
+    if (nact == 0) return false;
+    const float m0 = a0 ? fabsf(r.w0) : -1.f, m1 = a1 ? fabsf(r.w1) : -1.f, m2 = a2 ? fabsf(r.w2) : -1.f;
+    const int A = (m0 >= m1 && m0 >= m2) ? 0 : (m1 >= m2 ? 1 : 2);
+    int B = (A == 0) ? 1 : 0;
+    int C = (A == 2) ? 1 : 2;
+    if (!sel3(B, a0, a1, a2) && sel3(C, a0, a1, a2)) {
+        const int t = B;
+        B = C;
+        C = t;
+    }
+    W.nact = nact;
+    W.axA = A;
+    W.axB = B;
+    W.axC = C;
+    W.NA = sel3(A, nx, ny, nz);
+    W.NB = sel3(B, nx, ny, nz);
+    W.NC = sel3(C, nx, ny, nz);
+    W.oA = sel3(A, (int)r.o0, (int)r.o1, (int)r.o2);
+    W.oB = sel3(B, (int)r.o0, (int)r.o1, (int)r.o2);
+    W.oC = sel3(C, (int)r.o0, (int)r.o1, (int)r.o2);
+    W.sA = sel3(A, sx, sy, sz);
+    W.sB = sel3(B, sx, sy, sz);
+    W.sC = sel3(C, sx, sy, sz);
+
+    const float wA = sel3(A, r.w0, r.w1, r.w2), fA = sel3(A, r.f0, r.f1, r.f2);
+    W.invA = __frcp_rn(wA);
+    W.bA = __fmul_rn(-fA, W.invA);
+    W.sgA = wA < 0.f;
+    W.base = 0;
+    W.invB = W.bB = W.wB = W.fB = 0.f;
+    W.invC = W.bC = W.wC = W.fC = 0.f;
+    W.sgB = W.sgC = 0;
+
+    float tin = -INFINITY, tout = INFINITY;
+    {
+        const float t0 = __fmaf_rn((float)(0 - W.oA), W.invA, W.bA);
+        const float t1 = __fmaf_rn((float)(W.NA - W.oA), W.invA, W.bA);
+        tin = fmaxf(tin, fminf(t0, t1));
+        tout = fminf(tout, fmaxf(t0, t1));
+    }
+    if (nact >= 2) {
+        W.wB = sel3(B, r.w0, r.w1, r.w2);
+        W.fB = sel3(B, r.f0, r.f1, r.f2);
+        W.invB = __frcp_rn(W.wB);
+        W.bB = __fmul_rn(-W.fB, W.invB);
+        W.sgB = W.wB < 0.f;
+        const float t0 = __fmaf_rn((float)(0 - W.oB), W.invB, W.bB);
+        const float t1 = __fmaf_rn((float)(W.NB - W.oB), W.invB, W.bB);
+        tin = fmaxf(tin, fminf(t0, t1));
+        tout = fminf(tout, fmaxf(t0, t1));
+    } else {
+        if ((unsigned)W.oB >= (unsigned)W.NB) return false;
+        W.base += (int64_t)W.oB * W.sB;
+    }
+    if (nact == 3) {
+        W.wC = sel3(C, r.w0, r.w1, r.w2);
+        W.fC = sel3(C, r.f0, r.f1, r.f2);
+        W.invC = __frcp_rn(W.wC);
+        W.bC = __fmul_rn(-W.fC, W.invC);
+        W.sgC = W.wC < 0.f;
+        const float t0 = __fmaf_rn((float)(0 - W.oC), W.invC, W.bC);
+        const float t1 = __fmaf_rn((float)(W.NC - W.oC), W.invC, W.bC);
+        tin = fmaxf(tin, fminf(t0, t1));
+        tout = fminf(tout, fmaxf(t0, t1));
+    } else {
+        if ((unsigned)W.oC >= (unsigned)W.NC) return false;
+        W.base += (int64_t)W.oC * W.sC;
+    }
+    if (!(tin < tout)) return false;
+    // Driving indices spanned inside the image, with one slab of margin on each side.
+    const float uin = __fmaf_rn(wA, tin, fA), uout = __fmaf_rn(wA, tout, fA);
+    const int lo = (int)floorf(fminf(uin, uout)) + W.oA - 1;
+    const int hi = (int)floorf(fmaxf(uin, uout)) + W.oA + 1;
+    W.mlo = max(lo, 0);
+    W.mhi = min(hi, W.NA - 1);
+    return W.mlo <= W.mhi;
+}
+
+// t of the entering / leaving planes of driving slab m.
+__device__ __forceinline__ void slab_planes(const Walk &W, int m, float &tlo, float &thi)
+{
+    const float p = (float)(m - W.oA);
+    const float t0 = __fmaf_rn(p, W.invA, W.bA);
+    const float t1 = __fmaf_rn(p + 1.0f, W.invA, W.bA);
+    tlo = W.sgA ? t1 : t0;
+    thi = W.sgA ? t0 : t1;
+}
+
+// Walk the ray: vis(offset, length) for every unit with C_low < C_up.
+template <int NACT, class V>
+__device__ __forceinline__ void walk_run(const Walk &W, V &vis)
+{
+    float p = (float)(W.mlo - W.oA);
+    float tcur = __fmaf_rn(p, W.invA, W.bA);
+    float uB = 0.f, uC = 0.f;
+    if (NACT >= 2) uB = __fmaf_rn(W.wB, tcur, W.fB);
+    if (NACT == 3) uC = __fmaf_rn(W.wC, tcur, W.fC);
+    int64_t offA = W.base + (int64_t)W.mlo * W.sA;
+    for (int m = W.mlo; m <= W.mhi; ++m, offA += W.sA) {
+        p += 1.0f;
+        const float tnext = __fmaf_rn(p, W.invA, W.bA);
+        const float tlo = W.sgA ? tnext : tcur;
+        const float thi = W.sgA ? tcur : tnext;
+        if (NACT == 1) {
+            vis(offA, __fsub_rn(thi, tlo));
+        } else {
+            const float uBn = __fmaf_rn(W.wB, tnext, W.fB);
+            const int j0 = (int)floorf(fminf(uB, uBn)), j1 = (int)floorf(fmaxf(uB, uBn));
+            int k0 = 0, k1 = 0;
+            float uCn = 0.f;
+            if (NACT == 3) {
+                uCn = __fmaf_rn(W.wC, tnext, W.fC);
+                k0 = (int)floorf(fminf(uC, uCn));
+                k1 = (int)floorf(fmaxf(uC, uCn));
+            }
+            for (int j = j0; j <= j1; ++j) {
+                const int jg = j + W.oB;
+                if ((unsigned)jg >= (unsigned)W.NB) continue;
+                const float q = (float)j;
+                const float tb0 = __fmaf_rn(q + (float)W.sgB, W.invB, W.bB);
+                const float tb1 = __fmaf_rn(q + (float)(1 - W.sgB), W.invB, W.bB);
+                const float lo = fmaxf(tlo, tb0), hi = fminf(thi, tb1);
+                const int64_t offB = offA + (int64_t)jg * W.sB;
+                if (NACT == 2) {
+                    const float l = __fsub_rn(hi, lo);
+                    if (l > 0.f) vis(offB, l);
+                } else {
+                    for (int k = k0; k <= k1; ++k) {
+                        const int kg = k + W.oC;
+                        if ((unsigned)kg >= (unsigned)W.NC) continue;
+                        const float r = (float)k;
+                        const float tc0 = __fmaf_rn(r + (float)W.sgC, W.invC, W.bC);
+                        const float tc1 = __fmaf_rn(r + (float)(1 - W.sgC), W.invC, W.bC);
+                        const float l = __fsub_rn(fminf(hi, tc1), fmaxf(lo, tc0));
+                        if (l > 0.f) vis(offB + (int64_t)kg * W.sC, l);
+                    }
+                }
+            }
+            uB = uBn;
+            if (NACT == 3) uC = uCn;
+        }
+        tcur = tnext;
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void walk(const Walk &W, V &vis)
+{
+    if (W.nact == 3) walk_run<3>(W, vis);
+    else if (W.nact == 2) walk_run<2>(W, vis);
+    else if (W.nact == 1) walk_run<1>(W, vis);
+}
+
+// Length of unit (i, j, k) exactly as walk_run computes it, or 0 when the walk does not
+// visit it.  Used by the unit-driven (gather) adjoint.
+__device__ __forceinline__ float walk_unit_length(const Walk &W, int i, int j, int k)
+{
+    const int m = sel3(W.axA, i, j, k), jg = sel3(W.axB, i, j, k), kg = sel3(W.axC, i, j, k);
+    if (m < W.mlo || m > W.mhi) return 0.f;
+    if (W.nact < 3 && kg != W.oC) return 0.f;
+    if (W.nact < 2 && jg != W.oB) return 0.f;
+    // identical to walk_run: plane m from p, plane m+1 from p + 1
+    const float p = (float)(m - W.oA);
+    const float tcur = __fmaf_rn(p, W.invA, W.bA);
+    const float tnext = __fmaf_rn(p + 1.0f, W.invA, W.bA);
+    const float tlo = W.sgA ? tnext : tcur;
+    const float thi = W.sgA ? tcur : tnext;
+    if (W.nact == 1) return __fsub_rn(thi, tlo);
+    const float uB = __fmaf_rn(W.wB, tcur, W.fB), uBn = __fmaf_rn(W.wB, tnext, W.fB);
+    const int jr = jg - W.oB;
+    if (jr < (int)floorf(fminf(uB, uBn)) || jr > (int)floorf(fmaxf(uB, uBn))) return 0.f;
+    const float q = (float)jr;
+    const float tb0 = __fmaf_rn(q + (float)W.sgB, W.invB, W.bB);
+    const float tb1 = __fmaf_rn(q + (float)(1 - W.sgB), W.invB, W.bB);
+    const float lo = fmaxf(tlo, tb0), hi = fminf(thi, tb1);
+    float l;
+    if (W.nact == 3) {
+        const float uC = __fmaf_rn(W.wC, tcur, W.fC), uCn = __fmaf_rn(W.wC, tnext, W.fC);
+        const int kr = kg - W.oC;
+        if (kr < (int)floorf(fminf(uC, uCn)) || kr > (int)floorf(fmaxf(uC, uCn))) return 0.f;
+        const float r = (float)kr;
+        const float tc0 = __fmaf_rn(r + (float)W.sgC, W.invC, W.bC);
+        const float tc1 = __fmaf_rn(r + (float)(1 - W.sgC), W.invC, W.bC);
+        l = __fsub_rn(fminf(hi, tc1), fmaxf(lo, tc0));
+    } else {
+        l = __fsub_rn(hi, lo);
+    }
+    return l > 0.f ? l : 0.f;
+}
+
+}  // namespace xr

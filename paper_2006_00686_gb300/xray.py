@@ -1,0 +1,272 @@
+"""Thin Python binding of libxray.so (include/xray.h): argument marshalling only.
+
+Every step of the transform runs in the CUDA library; torch provides device memory and
+the current stream.  There is no CPU fallback: if the library is not built, or no CUDA
+device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from .inputs import KINDS, KINDS_3D, Geometry
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libxray.so")
+
+XR_ADJ_AUTO, XR_ADJ_SCATTER, XR_ADJ_GATHER = 0, 1, 2
+
+
+class XRayError(RuntimeError):
+    pass
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("cz", ctypes.c_double),
+        ("n_views", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32),
+        ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("src_z", ctypes.POINTER(ctypes.c_double)),
+        ("du", ctypes.c_double), ("dv", ctypes.c_double), ("u0", ctypes.c_double), ("v0", ctypes.c_double),
+        ("sod", ctypes.c_double), ("sdd", ctypes.c_double),
+    ]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_rays", ctypes.c_int64), ("n_units", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("is3d", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("batch_chunk", ctypes.c_int32), ("adjoint", ctypes.c_int32)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("geom", ctypes.c_void_p), ("img", ctypes.c_void_p), ("sino", ctypes.c_void_p)]
+
+
+# name -> (restype, argtypes); every name here is declared in include/xray.h
+_VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+SIGNATURES = {
+    "xr_geometry_create": (_I32, [ctypes.POINTER(_Desc), ctypes.POINTER(_VP)]),
+    "xr_geometry_destroy": (None, [_VP]),
+    "xr_ray_setup": (_I32, [_VP, _VP]),
+    "xr_geometry_get_info": (_I32, [_VP, ctypes.POINTER(_Info)]),
+    "xr_set_tuning": (_I32, [_VP, ctypes.POINTER(_Tuning)]),
+    "xr_get_tuning": (_I32, [_VP, ctypes.POINTER(_Tuning)]),
+    "xr_project": (_I32, [_VP, _VP, _VP, _I32, _VP]),
+    "xr_backproject": (_I32, [_VP, _VP, _VP, _I32, _VP]),
+    "xr_backproject_method": (_I32, [_VP, _VP, _VP, _I32, _I32, _VP]),
+    "xr_ray_units": (_I32, [_VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP]),
+    "xr_batch_create": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _I32, ctypes.POINTER(_VP)]),
+    "xr_batch_destroy": (None, [_VP]),
+    "xr_batch_project": (_I32, [_VP, _VP]),
+    "xr_batch_backproject": (_I32, [_VP, _VP]),
+    "xr_status_string": (ctypes.c_char_p, [_I32]),
+    "xr_last_cuda_error": (_I32, []),
+    "xr_version": (_I32, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise XRayError(f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = lib().xr_status_string(status).decode()
+        if status == 6:
+            msg += f" (cudaError {lib().xr_last_cuda_error()})"
+        raise XRayError(f"{what}: {msg}")
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need_cuda(t: torch.Tensor, name: str):
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise XRayError(f"{name} must be a contiguous float32 CUDA tensor")
+
+
+class Projector:
+    """X-ray transform and adjoint of one scan on the current CUDA device."""
+
+    def __init__(self, geom: Geometry):
+        if not torch.cuda.is_available():
+            raise XRayError("no CUDA device: the X-ray transform runs only on the GPU")
+        self.geom = geom
+        self._angles = np.ascontiguousarray(np.asarray(geom.angles, dtype=np.float64).reshape(-1))
+        self._src_z = None if geom.src_z is None else np.ascontiguousarray(geom.src_z, dtype=np.float64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        d = _Desc(KINDS[geom.kind], geom.nx, geom.ny, geom.nz, geom.dx, geom.dy, geom.dz, geom.cx, geom.cy,
+                  geom.cz, geom.n_views, geom.n_rows, geom.n_cols, self._angles.ctypes.data_as(dp),
+                  None if self._src_z is None else self._src_z.ctypes.data_as(dp),
+                  geom.du, geom.dv, geom.u0, geom.v0, geom.sod, geom.sdd)
+        h = ctypes.c_void_p()
+        torch.cuda.current_device()  # make sure the CUDA context exists
+        _check(lib().xr_geometry_create(ctypes.byref(d), ctypes.byref(h)), "xr_geometry_create")
+        self._h = h
+        info = _Info()
+        _check(lib().xr_geometry_get_info(h, ctypes.byref(info)), "xr_geometry_get_info")
+        self.n_rays, self.n_units = int(info.n_rays), int(info.n_units)
+        self.table_bytes = int(info.table_bytes)
+        self.device = torch.device("cuda", int(info.device))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xr_geometry_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- tuning ---------------------------------------------------------------------------
+    def set_tuning(self, block: int = 0, batch_chunk: int = 0, adjoint: int = 0):
+        t = _Tuning(block, batch_chunk, adjoint)
+        _check(lib().xr_set_tuning(self._h, ctypes.byref(t)), "xr_set_tuning")
+
+    def tuning(self) -> dict:
+        t = _Tuning()
+        _check(lib().xr_get_tuning(self._h, ctypes.byref(t)), "xr_get_tuning")
+        return {"block": t.block, "batch_chunk": t.batch_chunk, "adjoint": t.adjoint}
+
+    def ray_setup(self, stream=None):
+        _check(lib().xr_ray_setup(self._h, _stream(stream)), "xr_ray_setup")
+
+    # -- operators ------------------------------------------------------------------------
+    def _batch_of(self, t: torch.Tensor, unit_shape: tuple, name: str) -> int:
+        if tuple(t.shape) == unit_shape:
+            return 0
+        if t.dim() == len(unit_shape) + 1 and tuple(t.shape[1:]) == unit_shape:
+            return int(t.shape[0])
+        raise XRayError(f"{name} has shape {tuple(t.shape)}, expected {unit_shape} or (B,)+{unit_shape}")
+
+    def forward(self, img: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        _need_cuda(img, "img")
+        b = self._batch_of(img, self.geom.image_shape(), "img")
+        shape = self.geom.sino_shape(b if b else None)
+        if out is None:
+            out = torch.empty(shape, device=img.device, dtype=torch.float32)
+        _need_cuda(out, "out")
+        _check(lib().xr_project(self._h, _ptr(img), _ptr(out), max(b, 1), _stream(stream)), "xr_project")
+        return out
+
+    def adjoint(self, sino: torch.Tensor, out: torch.Tensor | None = None, method: int = XR_ADJ_AUTO,
+                stream=None) -> torch.Tensor:
+        _need_cuda(sino, "sino")
+        b = self._batch_of(sino, self.geom.sino_shape(), "sino")
+        shape = self.geom.image_shape(b if b else None)
+        if out is None:
+            out = torch.empty(shape, device=sino.device, dtype=torch.float32)
+        _need_cuda(out, "out")
+        _check(lib().xr_backproject_method(self._h, _ptr(sino), _ptr(out), max(b, 1), int(method),
+                                           _stream(stream)), "xr_backproject")
+        return out
+
+    __call__ = forward
+
+    def ray_units(self, rays, cap: int | None = None):
+        """Sparse rows for the given ray ids: list of (unit indices int64, lengths float32)
+        per ray, in visiting order."""
+        rays_t = torch.as_tensor(np.asarray(rays, dtype=np.int64), device=self.device)
+        n = int(rays_t.numel())
+        cap = cap or (self.geom.nx + self.geom.ny + self.geom.nz) * 3 + 8
+        idx = torch.empty((n, cap), dtype=torch.int64, device=self.device)
+        ln = torch.empty((n, cap), dtype=torch.float32, device=self.device)
+        cnt = torch.empty((n,), dtype=torch.int32, device=self.device)
+        _check(lib().xr_ray_units(self._h, _ptr(rays_t), n, cap, _ptr(idx), _ptr(ln), _ptr(cnt), _stream()),
+               "xr_ray_units")
+        cnt_h, idx_h, ln_h = cnt.cpu().numpy(), idx.cpu().numpy(), ln.cpu().numpy()
+        if (cnt_h < 0).any():
+            raise XRayError("ray_units: ray id outside the scan")
+        if (cnt_h > cap).any():
+            raise XRayError("ray_units: cap too small")
+        return [(idx_h[q, :cnt_h[q]], ln_h[q, :cnt_h[q]]) for q in range(n)]
+
+
+class XRayFunction(torch.autograd.Function):
+    """y = A x with dA^T: backward is the adjoint kernel on the incoming gradient; nothing
+    is saved for backward beyond the projector (lengths are recomputed)."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, proj: Projector):
+        ctx.proj = proj
+        return proj.forward(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, gy: torch.Tensor):
+        return ctx.proj.adjoint(gy.contiguous()), None
+
+
+def project(x: torch.Tensor, proj: Projector) -> torch.Tensor:
+    """Differentiable forward projection."""
+    return XRayFunction.apply(x, proj)
+
+
+class BatchPlan:
+    """One persistent launch over many independent (uneven) problems."""
+
+    def __init__(self, projectors, images, sinos, tile: int = 0, block: int = 0):
+        n = len(projectors)
+        if not (len(images) == len(sinos) == n) or n == 0:
+            raise XRayError("BatchPlan needs one image and one sinogram per projector")
+        arr = (_Problem * n)()
+        for q, (p, x, y) in enumerate(zip(projectors, images, sinos)):
+            _need_cuda(x, "img")
+            _need_cuda(y, "sino")
+            if x.numel() != p.n_units or y.numel() != p.n_rays:
+                raise XRayError(f"problem {q}: buffer sizes do not match its geometry")
+            arr[q] = _Problem(p.handle.value, x.data_ptr(), y.data_ptr())
+        self._keep = (list(projectors), list(images), list(sinos))
+        h = ctypes.c_void_p()
+        _check(lib().xr_batch_create(arr, n, int(tile), int(block), ctypes.byref(h)), "xr_batch_create")
+        self._h = h
+
+    def project(self, stream=None):
+        _check(lib().xr_batch_project(self._h, _stream(stream)), "xr_batch_project")
+
+    def backproject(self, stream=None):
+        _check(lib().xr_batch_backproject(self._h, _stream(stream)), "xr_batch_backproject")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

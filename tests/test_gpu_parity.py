@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Unit sets of single rays, forward and adjoint on reduced copies of every scan
+configuration, the five configurations at full size on sampled rays (forward) and on view
+subsets (adjoint), the dot-product test, batching and the ambiguity rule."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2006_00686_gb300 import inputs
+from paper_2006_00686_gb300.inputs import Geometry
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+pi = math.pi
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _proj(g):
+    from paper_2006_00686_gb300.xray import Projector
+    return Projector(g)
+
+
+def _phantom(g, seed, n_shapes=8, device="cpu"):
+    return inputs.phantom(g, n_shapes, seed, device=device)
+
+
+# ---------------------------------------------------------------------------------------
+# Unit sets (sparse rows) of single rays
+# ---------------------------------------------------------------------------------------
+
+def _rand_geom(kind, rng):
+    three = kind in inputs.KINDS_3D
+    nx, ny = int(rng.integers(9, 41)), int(rng.integers(9, 41))
+    nz = int(rng.integers(9, 33)) if three else 1
+    kw = dict(nx=nx, ny=ny, nz=nz, dx=rng.uniform(0.6, 1.4), dy=rng.uniform(0.6, 1.4), dz=rng.uniform(0.6, 1.4),
+              cx=rng.uniform(-2, 2), cy=rng.uniform(-2, 2), cz=rng.uniform(-2, 2))
+    nv = 7
+    if kind == "par2d":
+        return Geometry(kind, angles=rng.uniform(-pi, 3 * pi, nv), n_cols=41, du=rng.uniform(0.5, 1.5), **kw)
+    if kind == "fan2d":
+        return Geometry(kind, angles=rng.uniform(0, 2 * pi, nv), n_cols=41, du=rng.uniform(1, 2),
+                        sod=100.0, sdd=160.0, **kw)
+    if kind == "fan2d_arc":
+        return Geometry(kind, angles=rng.uniform(0, 2 * pi, nv), n_cols=41, du=0.012, sod=100.0, sdd=160.0, **kw)
+    if kind == "par3d":
+        ang = np.stack([rng.uniform(-pi, 3 * pi, nv), rng.uniform(-pi, pi, nv)], axis=1)
+        return Geometry(kind, angles=ang, n_cols=21, n_rows=17, du=rng.uniform(1, 2), dv=rng.uniform(1, 2), **kw)
+    src_z = rng.uniform(-5, 5, nv) if kind.startswith("helix") else None
+    if kind in ("cone", "helix"):
+        return Geometry(kind, angles=rng.uniform(0, 2 * pi, nv), src_z=src_z, n_cols=21, n_rows=17,
+                        du=rng.uniform(2, 3), dv=rng.uniform(2, 3), sod=100.0, sdd=160.0, **kw)
+    return Geometry(kind, angles=rng.uniform(0, 2 * pi, nv), src_z=src_z, n_cols=21, n_rows=17,
+                    du=0.02, dv=0.02, sod=100.0, sdd=160.0, **kw)
+
+
+@pytest.mark.parametrize("kind", list(inputs.KINDS))
+def test_unit_sets_random_geometry(kind):
+    rng = np.random.default_rng(100 + inputs.KINDS[kind])
+    g = _rand_geom(kind, rng)
+    rays = H.sample_rays(g, 600, seed=1)
+    P = _proj(g)
+    rows_gpu = P.ray_units(rays)
+    rows_ref = [O.ray_units(g, int(r)) for r in rays]
+    graze = H.check_unit_sets(g, rows_gpu, rows_ref)
+    n_units = sum(len(r[1]) for r in rows_ref)
+    assert n_units > 1000 and graze <= 0.01 * n_units
+
+
+SPECIAL_3D = [(a, b) for a in (0.0, pi / 2, pi, 3 * pi / 2, 0.4, 2.2, 4.0, 5.5)
+              for b in (0.0, pi / 2, -pi / 2, 0.3, -0.5, pi / 4)]
+
+
+@pytest.mark.parametrize("offset", [0.0, 0.5, 0.25])
+def test_unit_sets_special_rays(offset):
+    # axis-parallel, in-plane and on-grid rays: closed ranges and the ambiguity rule
+    g2 = Geometry("par2d", 12, 10, angles=[0.0, pi / 2, pi, 3 * pi / 2, pi / 4, 3 * pi / 4, 0.3, 2.0],
+                  n_cols=31, du=0.5, u0=offset)
+    g3 = Geometry("par3d", 10, 8, 6, angles=SPECIAL_3D, n_cols=19, n_rows=15, du=0.5, dv=0.5, u0=offset,
+                  v0=-offset)
+    for g in (g2, g3):
+        P = _proj(g)
+        rays = np.arange(g.n_rays)
+        rows_gpu = P.ray_units(rays)
+        rows_ref = [O.ray_units(g, int(r)) for r in rays]
+        assert H.check_unit_sets(g, rows_gpu, rows_ref) == 0
+
+
+def test_ambiguity_examples_on_gpu():
+    # Section 4.1 examples through the CUDA path
+    cases = [
+        (Geometry("par2d", 5, 5, angles=[0.0], n_cols=1, u0=1.5), 5 + np.arange(5)),
+        (Geometry("par3d", 4, 4, 4, angles=[[0.0, 0.0]], u0=1.0, v0=1.0), 20 + np.arange(4)),
+        (Geometry("par3d", 3, 3, 3, angles=[[0.0, pi / 4]], u0=-0.5, v0=math.sqrt(2)), np.array([6])),
+    ]
+    for g, want in cases:
+        (idx, ln), = _proj(g).ray_units([0])
+        np.testing.assert_array_equal(np.sort(idx), want)
+
+
+@pytest.mark.parametrize("name,geom", [
+    ("ts1", Geometry("par2d", 3, 3, angles=[pi / 4], n_cols=1, u0=1.0)),
+    ("ts2", Geometry("fan2d_arc", 4, 4, angles=[pi / 2], n_cols=1, u0=-pi / 6, sod=4.0, sdd=4.0)),
+    ("ts3", Geometry("par3d", 3, 3, 3, angles=[[pi / 4, pi / 4]])),
+    ("ts4", Geometry("cone_arc", 4, 4, 4, angles=[pi / 4], u0=pi / 12, v0=pi / 12, sod=4.0, sdd=4.0)),
+    ("ts5", Geometry("helix_arc", 4, 4, 4, angles=[pi / 4], src_z=[0.5], u0=pi / 12, v0=pi / 12, sod=4.0,
+                     sdd=4.0)),
+])
+def test_paper_test_suites_on_gpu(name, geom):
+    (idx, ln), = _proj(geom).ray_units([0])
+    o = np.argsort(idx)
+    ref_i, ref_l = O.ray_units(geom, 0)
+    np.testing.assert_array_equal(idx[o], ref_i)
+    np.testing.assert_allclose(ln[o], ref_l, rtol=0, atol=2e-6)
+
+
+# ---------------------------------------------------------------------------------------
+# Forward / adjoint on reduced configurations (every ray, every unit)
+# ---------------------------------------------------------------------------------------
+
+SMALL = {
+    "par2d_64": lambda: inputs.par2d_64(),
+    "fan2d_128": lambda: H.fan2d_small(),
+    "par3d_32_tilt": lambda: H.par3d_small(),
+    "cone_64": lambda: H.cone_small(),
+    "helix_64x32": lambda: H.helix_small(),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_forward_small(name):
+    g = SMALL[name]()
+    batch = 3
+    f = torch.stack([_phantom(g, 10 + b) for b in range(batch)])
+    P = _proj(g)
+    y = P.forward(f.cuda()).cpu().numpy().reshape(batch, -1)
+    f64 = f.numpy().astype(np.float64).reshape(batch, -1)
+    y_ref = O.forward(g, f64)
+    scale = O.forward(g, np.abs(f64))
+    for b in range(batch):
+        H.check_rays(g, y[b], y_ref[b], scale[b], float(np.abs(f64[b]).max()), f"{name}[{b}]")
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_adjoint_small(name):
+    g = SMALL[name]()
+    f = _phantom(g, 21).numpy().astype(np.float64)
+    y = O.forward(g, f).astype(np.float32)  # the same float32 sinogram feeds both sides
+    P = _proj(g)
+    methods = [1, 2] if not g.is3d else [1]
+    z_ref = O.adjoint(g, y.astype(np.float64))
+    for m in methods:
+        z = P.adjoint(torch.from_numpy(y.reshape(g.sino_shape())).cuda(), method=m).cpu().numpy()
+        H.check_adjoint(z, z_ref, f"{name} method {m}")
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_dot_product(name):
+    g = SMALL[name]()
+    rng = np.random.default_rng(5)
+    P = _proj(g)
+    x = torch.from_numpy(rng.random(g.image_shape(), dtype=np.float32)).cuda()
+    yv = torch.from_numpy(rng.random(g.sino_shape(), dtype=np.float32)).cuda()
+    ax = P.forward(x).double()
+    aty = P.adjoint(yv).double()
+    lhs = float((ax * yv.double()).sum())
+    rhs = float((x.double() * aty).sum())
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_batch_chunks_bitwise_identical():
+    g = H.fan2d_small(96, 60)
+    f = torch.stack([_phantom(g, 30 + b) for b in range(5)]).cuda()
+    P = _proj(g)
+    outs = []
+    for chunk in (1, 2, 4, 16):
+        P.set_tuning(batch_chunk=chunk)
+        outs.append(P.forward(f).cpu())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def test_gather_matches_scatter_2d():
+    for g in (inputs.par2d_64(), H.fan2d_small(128, 90)):
+        P = _proj(g)
+        y = P.forward(_phantom(g, 3).cuda())
+        zs = P.adjoint(y, method=1).cpu().numpy().astype(np.float64)
+        zg = P.adjoint(y, method=2).cpu().numpy().astype(np.float64)
+        assert np.abs(zs - zg).max() <= 1e-5 * np.abs(zs).max()
+
+
+def test_rays_that_miss_the_image_are_zero():
+    g = Geometry("par2d", 16, 16, angles=[0.0, 0.7], n_cols=64, du=1.0)  # s up to +-31.5
+    P = _proj(g)
+    y = P.forward(torch.ones(g.image_shape()).cuda()).cpu().numpy()
+    s = (np.arange(64) - 31.5)
+    assert np.all(y[0][np.abs(s) > 8] == 0.0)
+    assert np.all(y[1][np.abs(s) > 8 * math.sqrt(2)] == 0.0)
+
+
+def test_status_codes_on_gpu():
+    from paper_2006_00686_gb300.xray import XRayError
+    g = inputs.par2d_64()
+    P = _proj(g)
+    x = torch.zeros(g.image_shape(), device="cuda")
+    with pytest.raises(XRayError, match="aligned"):
+        buf = torch.zeros(g.n_units + 1, device="cuda")
+        P.forward(buf[1:].view(g.image_shape()))
+    with pytest.raises(XRayError):
+        P.forward(x.double())
+    from paper_2006_00686_gb300 import xray as X
+    import ctypes
+    assert X.lib().xr_project(P.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 0,
+                              None) == 8
+
+
+# ---------------------------------------------------------------------------------------
+# The five configurations at full size
+# ---------------------------------------------------------------------------------------
+
+FULL = {
+    "par2d_64": (inputs.par2d_64, 1, 10, 1),
+    "fan2d_512x16": (inputs.fan2d_512, inputs.FAN2D_BATCH, 10, 2),
+    "par3d_256_tilt": (inputs.par3d_256_tilt, 1, 30, 3),
+    "cone_512": (inputs.cone_512, 1, 30, 4),
+    "helix_512x256": (inputs.helix_512x256, 1, 30, 5),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_forward_sampled(name):
+    make, batch, n_shapes, seed = FULL[name]
+    g = make()
+    f = torch.stack([inputs.phantom(g, n_shapes, seed * 100 + b, device="cuda") for b in range(batch)])
+    P = _proj(g)
+    y = P.forward(f if batch > 1 else f[0])
+    rays = H.sample_rays(g, 400 if g.is3d else 1500, seed=seed)
+    y_s = y.reshape(batch, -1)[:, torch.from_numpy(rays).cuda()].cpu().numpy()
+    f64 = f.cpu().numpy().astype(np.float64).reshape(batch, -1)
+    del y
+    for b in range(batch):
+        y_ref = O.forward(g, f64[b], rays=rays)
+        scale = O.forward(g, np.abs(f64[b]), rays=rays)
+        H.check_rays(g, y_s[b], y_ref, scale, float(np.abs(f64[b]).max()), f"{name}[{b}]")
+    P.close()
+
+
+VIEW_SUBSET = {"par2d_64": 90, "fan2d_512x16": 8, "par3d_256_tilt": 6, "cone_512": 2, "helix_512x256": 6}
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_adjoint_view_subset(name):
+    make, _, n_shapes, seed = FULL[name]
+    g0 = make()
+    views = np.linspace(0, g0.n_views - 1, VIEW_SUBSET[name]).round().astype(np.int64)
+    g = g0.subset_views(views)
+    rng = np.random.default_rng(seed)
+    y = rng.random(g.sino_shape(), dtype=np.float32)
+    P = _proj(g)
+    z = P.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    z_ref = O.adjoint(g, y.astype(np.float64).reshape(-1))
+    H.check_adjoint(z, z_ref, name)
+    if not g.is3d:
+        z2 = P.adjoint(torch.from_numpy(y).cuda(), method=1).cpu().numpy()
+        H.check_adjoint(z2, z_ref, name + " scatter")
+    P.close()
