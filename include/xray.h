@@ -52,6 +52,7 @@ typedef enum {
     XR_ERR_BATCH = 8,     /* batch < 1 */
     XR_ERR_ARG = 9,       /* an argument is out of its documented range */
     XR_ERR_TUNE = 10,     /* the tuning cache could not be read or written */
+    XR_ERR_CAPACITY = 11, /* more problems than XR_NOALLOC_MAX_PROBLEMS */
 } xr_status;
 
 /* Scan kinds (Section 2.2 and Section 3.2). */
@@ -174,6 +175,25 @@ xr_status xr_batch_project(const xr_batch *b, xr_stream stream);
 /* Adjoint of every problem of the plan (ray-driven scatter after one zeroing launch):
  * overwrites every problem's img with the adjoint of its sino. */
 xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream);
+
+/* Batched forward projection that allocates nothing (the paper has no counterpart; this
+ * serves callers that cannot call cudaMalloc where they project: code running during a
+ * global-mode stream capture, hosts whose allocator owns the whole device pool, loops that
+ * cannot afford the synchronisation of an allocation).  Same result as xr_batch_project on
+ * the same problems, but the work list and tile counter live in one fixed array in device
+ * memory that the library reserves on every device that loads it, until the process exits
+ * (XR_NOALLOC_MAX_PROBLEMS work-list entries, about 14 KiB).  The caller still passes and
+ * owns every image and sinogram.
+ * The first call on a device looks up the array's device address (once, with that device
+ * current); make that first call before any stream capture.  Each call rewrites the work
+ * list and zeroes the counter, stream-ordered; calls that overlap on the GPU race on the
+ * shared array, so order them (one stream, or events).
+ * tile: rays per work item (32..65536, multiple of 32; 0 = 256).
+ * Errors: XR_ERR_NULL, XR_ERR_SIZE (n < 1), XR_ERR_CAPACITY (n > XR_NOALLOC_MAX_PROBLEMS),
+ * XR_ERR_ARG, XR_ERR_ALIGN, XR_ERR_CUDA. */
+#define XR_NOALLOC_MAX_PROBLEMS 256
+xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t n, int32_t tile,
+                                     xr_stream stream);
 
 /* Text of a status code (static storage). */
 const char *xr_status_string(xr_status s);

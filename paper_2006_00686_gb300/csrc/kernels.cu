@@ -368,4 +368,11 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
     return cudaGetLastError();
 }
 
+cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s)
+{
+    batched_kernel<false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
+    return cudaGetLastError();
+}
+
 }  // namespace xr

@@ -11,11 +11,13 @@ using namespace xr;
 
 static thread_local int32_t g_last_cuda = 0;
 
-static xr_status cuda_fail(cudaError_t e)
+xr_status xr_fail_cuda(cudaError_t e)
 {
     g_last_cuda = (int32_t)e;
     return XR_ERR_CUDA;
 }
+
+static xr_status cuda_fail(cudaError_t e) { return xr_fail_cuda(e); }
 
 #define XR_CUDA(call)                               \
     do {                                            \
@@ -403,6 +405,7 @@ const char *xr_status_string(xr_status s)
     case XR_ERR_BATCH: return "batch must be >= 1";
     case XR_ERR_ARG: return "argument out of range";
     case XR_ERR_TUNE: return "tuning cache could not be read or written";
+    case XR_ERR_CAPACITY: return "more problems than the fixed no-allocation scratch holds";
     }
     return "unknown status";
 }

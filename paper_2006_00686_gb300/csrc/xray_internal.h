@@ -60,9 +60,17 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
                            unsigned long long *counter, int adjoint, int grid_ctas, int block,
                            cudaStream_t s);
 
+// Forward persistent launch over a work list already in device memory; the tile counter
+// must be zero (no memset here).
+cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s);
+
 int batched_ctas_per_sm(int block, int adjoint);
 
 }  // namespace xr
+
+// Record a CUDA error for xr_last_cuda_error() and return XR_ERR_CUDA.
+xr_status xr_fail_cuda(cudaError_t e);
 
 // The handle behind the opaque xr_geometry.
 struct xr_geometry {

@@ -68,6 +68,7 @@ SIGNATURES = {
     "xr_batch_destroy": (None, [_VP]),
     "xr_batch_project": (_I32, [_VP, _VP]),
     "xr_batch_backproject": (_I32, [_VP, _VP]),
+    "xr_project_batched_noalloc": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _VP]),
     "xr_status_string": (ctypes.c_char_p, [_I32]),
     "xr_last_cuda_error": (_I32, []),
     "xr_version": (_I32, []),

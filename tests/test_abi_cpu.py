@@ -44,7 +44,7 @@ def test_binding_covers_header(X):
 
 
 def test_status_strings(X):
-    for code in range(0, 11):
+    for code in range(0, 12):
         s = X.lib().xr_status_string(code).decode()
         assert s and s != "unknown status"
     assert X.lib().xr_status_string(99).decode() == "unknown status"
