@@ -98,7 +98,8 @@ typedef struct {
 /* Launch tuning of a handle.  Zero fields keep the current value. */
 typedef struct {
     int32_t block;         /* threads per block of the ray kernels (64..256, multiple of 32) */
-    int32_t batch_chunk;   /* images walked together by one thread (1, 2, 4, 8 or 16) */
+    int32_t batch_chunk;   /* images walked together by one thread (1, 2, 4, 8 or 16);
+                              1 also disables the batched fast path */
     int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER */
 } xr_tuning;
 
@@ -114,8 +115,21 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out);
 /* Free the handle and its device tables (synchronises its device).  NULL is accepted. */
 void xr_geometry_destroy(xr_geometry *g);
 
-/* Re-run the per-geometry ray-setup kernel on `stream` (rebuilds the ray table in place). */
+/* Re-run the per-geometry ray setup on `stream`: the detector-sample kernel (the
+ * transcendental part of the transformation formulas) and the per-ray kernel (rebuilds the
+ * ray table in place). */
 xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
+
+/* Reserve the handle's workspace for batches of up to max_batch images (allocates on the
+ * handle's device and synchronises it; do this outside stream capture).  With a workspace,
+ * xr_project and the gather adjoint take the batched fast path for batches of 4 or more:
+ * the images (or sinograms) of each chunk of 16 are first interleaved so that one unit's
+ * values sit in one 64-byte line, in two spatial orders (x fastest and y fastest), and each
+ * ray is walked by 4 lanes that own 4 images each.  Without a workspace, or for larger
+ * batches, the calls use the one-thread-per-ray kernels (same results).
+ * Workspace bytes: 4 * padded_batch * (2 * (nx+4)(ny+4)nz + n_rays).
+ * Errors: XR_ERR_NULL, XR_ERR_BATCH, XR_ERR_ALLOC, XR_ERR_CUDA. */
+xr_status xr_reserve(xr_geometry *g, int32_t max_batch);
 
 xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info);
 xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t);

@@ -1,0 +1,443 @@
+// Batched fast path for rays with at most two active axes (every 2D scan, and 3D rays
+// that stay in one coordinate plane), for batches of 4 or more images.
+//
+// Layout.  The images of one batch chunk (Bp = 4 * LPR images) are interleaved so that the
+// Bp values of one unit are contiguous (64 bytes for Bp = 16), in two spatial orders:
+//   IL0 = [nz][ny+2P][nx+2P][Bp]  (x fastest)  used by warps whose rays are driven along y,
+//   IL1 = [nz][nx+2P][ny+2P][Bp]  (y fastest)  used by warps whose rays are driven along x,
+// so that the rays of a warp -- neighbouring detector bins, which sit on neighbouring
+// units of the minor axis at every driving step -- read neighbouring 64-byte chunks.
+// A border of P = 2 zero units surrounds the image in x and y: the walk visits driving
+// slabs one beyond the image's extent, where the minor index can leave the image by at
+// most two, so every row the kernel can touch is valid memory and holds zero outside the
+// image -- no per-unit range test is needed.
+//
+// Mapping.  LPR lanes cooperate on one ray; each lane owns 4 images and loads them as one
+// float4.  A warp holds 32/LPR rays that step through the driving index in lockstep.
+//
+// Slab step (2D form of the walk in xray_core.cuh).  Between driving planes m and m+1 the
+// ray moves from row jc = floor(u_B(m)) to row jn = floor(u_B(m+1)); if they differ it
+// crosses the plane max(jc, jn) at tc, and the slab splits into |tc - t_m| in row jc and
+// |t_{m+1} - tc| in row jn.  These are C_up - C_low of the two units with the same plane
+// values the walk uses; the rare step that crosses two rows falls back to the general
+// per-candidate formula.
+#include "xray_internal.h"
+
+// Zero border (units) around the interleaved images.
+#define XR_IL_PAD 2
+
+// Resident blocks per SM the forward kernel is compiled for (a register budget).
+#ifndef XR_FWD_MIN_BLOCKS
+#define XR_FWD_MIN_BLOCKS 4
+#endif
+
+namespace xr {
+
+// ---------------------------------------------------------------------------------------
+// Interleave: user images [B][nz][ny][nx] -> IL0 / IL1 of chunk c ([chunk][...][Bp])
+// ---------------------------------------------------------------------------------------
+
+__global__ void interleave_images_kernel(const float *__restrict__ img, int batch, int nx, int ny, int nz,
+                                         int Bp, float *__restrict__ il0, float *__restrict__ il1)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int chunk = blockIdx.y;
+    const int i = (int)(u % nx);
+    const int64_t rest = u / nx;
+    const int j = (int)(rest % ny);
+    const int k = (int)(rest / ny);
+    const int px = nx + 2 * XR_IL_PAD, py = ny + 2 * XR_IL_PAD;
+    const int64_t np = (int64_t)px * py * nz;  // padded units per image
+    const int64_t o0 = ((int64_t)chunk * np + ((int64_t)k * py + j + XR_IL_PAD) * px + i + XR_IL_PAD) * Bp;
+    const int64_t o1 = ((int64_t)chunk * np + ((int64_t)k * px + i + XR_IL_PAD) * py + j + XR_IL_PAD) * Bp;
+    for (int b4 = 0; b4 < Bp; b4 += 4) {
+        float4 v;
+        const int b = chunk * Bp + b4;
+        v.x = (b + 0 < batch) ? __ldg(img + (int64_t)(b + 0) * n + u) : 0.f;
+        v.y = (b + 1 < batch) ? __ldg(img + (int64_t)(b + 1) * n + u) : 0.f;
+        v.z = (b + 2 < batch) ? __ldg(img + (int64_t)(b + 2) * n + u) : 0.f;
+        v.w = (b + 3 < batch) ? __ldg(img + (int64_t)(b + 3) * n + u) : 0.f;
+        *reinterpret_cast<float4 *>(il0 + o0 + b4) = v;
+        *reinterpret_cast<float4 *>(il1 + o1 + b4) = v;
+    }
+}
+
+// user sinograms [B][n_rays] -> [chunk][Bp/4][n_rays][4]: the 4 images of one quad of one ray
+// are one float4, and neighbouring rays' float4 of the same quad are neighbours in memory.
+__global__ void interleave_sino_kernel(const float *__restrict__ sino, int batch, int64_t n_rays, int Bp,
+                                       float *__restrict__ out)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int chunk = blockIdx.y;
+    for (int b4 = 0; b4 < Bp; b4 += 4) {
+        float4 v;
+        const int b = chunk * Bp + b4;
+        v.x = (b + 0 < batch) ? __ldg(sino + (int64_t)(b + 0) * n_rays + r) : 0.f;
+        v.y = (b + 1 < batch) ? __ldg(sino + (int64_t)(b + 1) * n_rays + r) : 0.f;
+        v.z = (b + 2 < batch) ? __ldg(sino + (int64_t)(b + 2) * n_rays + r) : 0.f;
+        v.w = (b + 3 < batch) ? __ldg(sino + (int64_t)(b + 3) * n_rays + r) : 0.f;
+        reinterpret_cast<float4 *>(out)[((int64_t)chunk * (Bp / 4) + b4 / 4) * n_rays + r] = v;
+    }
+}
+
+__device__ __forceinline__ void fma4(float4 &acc, const float4 v, float l)
+{
+    acc.x = __fmaf_rn(v.x, l, acc.x);
+    acc.y = __fmaf_rn(v.y, l, acc.y);
+    acc.z = __fmaf_rn(v.z, l, acc.z);
+    acc.w = __fmaf_rn(v.w, l, acc.w);
+}
+
+// Rows jlo..jhi of the current slab with the per-candidate formula (a step that crosses
+// two rows: rare, only for rays within rounding of a diagonal).  Returns the contribution.
+__device__ __noinline__ float4 slab_rows_general(int oB, int NB, int sgB, float invB, float bB, float tlo,
+                                                 float thi, int jlo, int jhi, const float *__restrict__ base,
+                                                 int64_t sB)
+{
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = jlo; j <= jhi; ++j) {
+        const int jg = j + oB;
+        if ((unsigned)jg >= (unsigned)NB) continue;
+        const float q = (float)j;
+        const float tb0 = __fmaf_rn(q + (float)sgB, invB, bB);
+        const float tb1 = __fmaf_rn(q + (float)(1 - sgB), invB, bB);
+        const float l = __fsub_rn(fminf(thi, tb1), fmaxf(tlo, tb0));
+        if (l > 0.f) fma4(acc, __ldg(reinterpret_cast<const float4 *>(base + (int64_t)jg * sB)), l);
+    }
+    return acc;
+}
+
+// Visitor for rays with three active axes (general walk on the interleaved layout).
+struct Il4Visitor {
+    const float *il;
+    float4 acc;
+    __device__ __forceinline__ void operator()(int64_t off, float l)
+    {
+        fma4(acc, __ldg(reinterpret_cast<const float4 *>(il + off)), l);
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// Forward, LPR lanes per ray, 4 images per lane
+// ---------------------------------------------------------------------------------------
+
+// floor of |x| < 2^22 with one round-down add: the float floor and the integer floor
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+
+template <int LPR>
+__global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const RayRec *__restrict__ rays, int64_t n_rays,
+                                                           int nx, int ny, int nz, const float *__restrict__ il0,
+                                                           const float *__restrict__ il1, int Bp,
+                                                           float *__restrict__ sino, int batch)
+{
+    constexpr int RPW = 32 / LPR;  // rays per warp
+    const int lane = threadIdx.x & 31;
+    const int q = lane % LPR;  // image quad owned by this lane
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t r = warp * RPW + lane / LPR;
+    const int chunk = blockIdx.y;
+    const int px = nx + 2 * XR_IL_PAD, py = ny + 2 * XR_IL_PAD;
+    const int64_t np = (int64_t)px * py * nz;
+
+    Walk W;
+    bool ok = false;
+    // this kernel's slab step covers rays with at most two active axes whose minor axis has
+    // a border (x or y); the rest take the general walk, which tests every index
+    if (r < n_rays)
+        ok = walk_setup(rays[r], nx, ny, nz, 1, nx, (int64_t)nx * ny, W) && W.nact <= 2 &&
+             !(W.nact == 2 && W.axB == 2);
+    const bool general = (r < n_rays) && !ok;
+    // layout of the warp: the driving axis of its first ray
+    const int axA0 = __shfl_sync(0xffffffffu, ok ? W.axA : 1, 0);
+    const bool y_fast = (axA0 == 0);
+    // element strides (floats) of i, j, k in that layout; one padded chunk holds np*Bp < 2^31
+    const int si = y_fast ? py * Bp : Bp;
+    const int sj = y_fast ? Bp : px * Bp;
+    const int sk = px * py * Bp;
+    // unit (0, 0, 0) of the image inside the border
+    const float *il = (y_fast ? il1 : il0) + (int64_t)chunk * np * Bp + 4 * q + XR_IL_PAD * (si + sj);
+
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int wlo = __reduce_min_sync(0xffffffffu, ok ? W.mlo : INT_MAX);
+    const int whi = __reduce_max_sync(0xffffffffu, ok ? W.mhi : INT_MIN);
+    if (ok) {
+        const int sA = sel3(W.axA, si, sj, sk), sB = sel3(W.axB, si, sj, sk), sC = sel3(W.axC, si, sj, sk);
+        const bool bact = W.nact >= 2;
+        // offset of the fixed axes in this layout (walk_setup folded them with its own strides)
+        const int base = W.oC * sC + (bact ? 0 : W.oB * sB) + (bact ? W.oB * sB : 0);
+        const float *pA = il + base;
+        const float invA = W.invA, bA = W.bA, wB = W.wB, fB = W.fB, invB = W.invB, bB = W.bB;
+        const int mlo = W.mlo, mhi = W.mhi;
+        float p = (float)(wlo - W.oA);
+        float tcur = __fmaf_rn(p, invA, bA);
+        float sm = __fadd_rd(__fmaf_rn(wB, tcur, fB), kMagic);
+        float j0 = __fadd_rn(sm, -kMagic);
+        int moff = wlo * sA;
+        for (int m = wlo; m <= whi; m += 2, moff += 2 * sA) {
+            // slab m: planes m, m+1; slab m+1: planes m+1, m+2
+            const float t1 = __fmaf_rn(p + 1.0f, invA, bA);
+            const float t2 = __fmaf_rn(p + 2.0f, invA, bA);
+            const float s1 = __fadd_rd(__fmaf_rn(wB, t1, fB), kMagic);
+            const float s2 = __fadd_rd(__fmaf_rn(wB, t2, fB), kMagic);
+            const float j1 = __fadd_rn(s1, -kMagic), j2 = __fadd_rn(s2, -kMagic);
+            // rows relative to the ray's foot row; the border makes every reachable row valid
+            const int r0 = __float_as_int(sm) - kMagicBits;
+            const int r1 = __float_as_int(s1) - kMagicBits;
+            const int r2 = __float_as_int(s2) - kMagicBits;
+            const bool act0 = m >= mlo && m <= mhi, act1 = m + 1 >= mlo && m + 1 <= mhi;
+            if (fabsf(j1 - j0) < 1.5f && fabsf(j2 - j1) < 1.5f) {
+                const bool x01 = r1 != r0, x12 = r2 != r1;
+                // crossing planes of the two slabs (plane max(jc, jn) of the minor axis)
+                const float tc0 = __fmaf_rn(fmaxf(j0, j1), invB, bB);
+                const float tc1 = __fmaf_rn(fmaxf(j1, j2), invB, bB);
+                const float tcc0 = x01 ? fminf(fmaxf(tc0, fminf(tcur, t1)), fmaxf(tcur, t1)) : t1;
+                const float tcc1 = x12 ? fminf(fmaxf(tc1, fminf(t1, t2)), fmaxf(t1, t2)) : t2;
+                const float la = fabsf(__fsub_rn(tcc0, tcur)), lb = fabsf(__fsub_rn(t1, tcc0));
+                const float lc = fabsf(__fsub_rn(tcc1, t1)), ld = fabsf(__fsub_rn(t2, tcc1));
+                const float *p0 = pA + moff, *p1 = pA + moff + sA;
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 va = act0 ? __ldg(reinterpret_cast<const float4 *>(p0 + r0 * sB)) : z;
+                const float4 vb = (act0 && x01) ? __ldg(reinterpret_cast<const float4 *>(p0 + r1 * sB)) : z;
+                const float4 vc = act1 ? __ldg(reinterpret_cast<const float4 *>(p1 + r1 * sB)) : z;
+                const float4 vd = (act1 && x12) ? __ldg(reinterpret_cast<const float4 *>(p1 + r2 * sB)) : z;
+                fma4(acc, va, la);
+                fma4(acc, vb, lb);
+                fma4(acc, vc, lc);
+                fma4(acc, vd, ld);
+            } else {
+                // a step that crosses two rows (within rounding of a diagonal): per-candidate formula
+                if (act0) {
+                    const float tlo = W.sgA ? t1 : tcur, thi = W.sgA ? tcur : t1;
+                    const float4 a = slab_rows_general(W.oB, W.NB, W.sgB, invB, bB, tlo, thi, (int)fminf(j0, j1),
+                                                       (int)fmaxf(j0, j1), pA - W.oB * sB + moff, sB);
+                    acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+                }
+                if (act1) {
+                    const float tlo = W.sgA ? t2 : t1, thi = W.sgA ? t1 : t2;
+                    const float4 a = slab_rows_general(W.oB, W.NB, W.sgB, invB, bB, tlo, thi, (int)fminf(j1, j2),
+                                                       (int)fmaxf(j1, j2), pA - W.oB * sB + moff + sA, sB);
+                    acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+                }
+            }
+            p += 2.0f;
+            tcur = t2;
+            sm = s2;
+            j0 = j2;
+        }
+    } else if (general) {
+        Il4Visitor vis{il, make_float4(0.f, 0.f, 0.f, 0.f)};
+        Walk W2;
+        if (walk_setup(rays[r], nx, ny, nz, si, sj, sk, W2)) walk(W2, vis);
+        acc = vis.acc;
+    }
+    if (r < n_rays) {
+        const int b0 = chunk * Bp + 4 * q;
+        if (b0 + 0 < batch) sino[(int64_t)(b0 + 0) * n_rays + r] = acc.x;
+        if (b0 + 1 < batch) sino[(int64_t)(b0 + 1) * n_rays + r] = acc.y;
+        if (b0 + 2 < batch) sino[(int64_t)(b0 + 2) * n_rays + r] = acc.z;
+        if (b0 + 3 < batch) sino[(int64_t)(b0 + 3) * n_rays + r] = acc.w;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint gather for 2D scans: one pixel per group of 4 lanes; the lanes share the
+// pixel's footprint bins of each view and all Bp images, then reduce.
+// ---------------------------------------------------------------------------------------
+
+// Per-ray plane constants of both in-plane axes: t(plane q of axis a) = fma(q - o_a, inv_a, b_a).
+struct __align__(16) GatherRec {
+    float inv_x, b_x, inv_y, b_y;
+    float ox, oy;  // integer parts of the foot point (as floats, exact)
+    int flags;     // 1: the ray misses, 2: the ray is parallel to an axis (general path)
+    int pad;
+};
+static_assert(sizeof(GatherRec) == 32, "GatherRec layout");
+
+__global__ void gather_prep_kernel(const RayRec *__restrict__ rays, int64_t n_rays, GatherRec *__restrict__ out)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const RayRec R = rays[r];
+    GatherRec g;
+    g.flags = (R.flags & RAY_MISS) ? 1 : ((R.w0 == 0.f || R.w1 == 0.f) ? 2 : 0);
+    g.inv_x = R.w0 != 0.f ? __frcp_rn(R.w0) : 0.f;
+    g.b_x = __fmul_rn(-R.f0, g.inv_x);
+    g.inv_y = R.w1 != 0.f ? __frcp_rn(R.w1) : 0.f;
+    g.b_y = __fmul_rn(-R.f1, g.inv_y);
+    g.ox = (float)R.o0;
+    g.oy = (float)R.o1;
+    g.pad = 0;
+    out[r] = g;
+}
+
+template <int NB4, int KIND>  // Bp = 4 * NB4 images; KIND: XR_PAR2D, XR_FAN2D or XR_FAN2D_ARC
+__global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restrict__ rays,
+                                                           const GatherRec *__restrict__ grec, GeoParams g,
+                                                           const float *__restrict__ vt,
+                                                           const float *__restrict__ sil, int64_t n_rays,
+                                                           float *__restrict__ img, int batch)
+{
+    constexpr int Bp = 4 * NB4;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & 3;
+    const int64_t pix = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+    const int64_t n_pix = (int64_t)g.nx * g.ny;
+    const bool live = pix < n_pix;
+    const int i = live ? (int)(pix % g.nx) : 0, j = live ? (int)(pix / g.nx) : 0;
+    const int chunk = blockIdx.y;
+    const float4 *S4 = reinterpret_cast<const float4 *>(sil) + (int64_t)chunk * NB4 * n_rays;
+    float acc[Bp];
+#pragma unroll
+    for (int b = 0; b < Bp; ++b) acc[b] = 0.f;
+    // pixel centre and half extents
+    const float xc = (float)(g.cx + (i + 0.5 - 0.5 * g.nx) * g.dx);
+    const float yc = (float)(g.cy + (0.5 * g.ny - j - 0.5) * g.dy);
+    const float hx = (float)(0.5 * g.dx), hy = (float)(0.5 * g.dy);
+    const float half = 0.5f * (float)(g.n_cols - 1);
+    const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0, sdd = (float)g.sdd;
+    const float fi = (float)i, fj = (float)j;
+    for (int v = 0; v < g.n_views && live; ++v) {
+        // the same view record for every lane of the warp: one broadcast load
+        const float4 e0 = __ldg(reinterpret_cast<const float4 *>(vt) + 2 * v);
+        const float4 e1 = __ldg(reinterpret_cast<const float4 *>(vt) + 2 * v + 1);
+        float umin, umax;
+        if (KIND == XR_PAR2D) {
+            const float uc = e0.x * xc + e0.y * yc, hw = fabsf(e0.x) * hx + fabsf(e0.y) * hy;
+            umin = uc - hw;
+            umax = uc + hw;
+        } else {
+            const float rx = xc - e0.x, ry = yc - e0.y;
+            const float depth = rx * e0.z + ry * e0.w, lat = rx * e1.x + ry * e1.y;
+            const float dd = fabsf(e0.z) * hx + fabsf(e0.w) * hy, dl = fabsf(e1.x) * hx + fabsf(e1.y) * hy;
+            // footprint bounds only: an approximate reciprocal is enough (a 1e-3 bin margin follows)
+            const float r1 = __fdividef(1.0f, depth - dd), r2 = __fdividef(1.0f, depth + dd);
+            const float lo = lat - dl, hi = lat + dl;
+            const float a = fminf(lo * r1, lo * r2), b = fmaxf(hi * r1, hi * r2);
+            if (KIND == XR_FAN2D) {
+                umin = sdd * a;
+                umax = sdd * b;
+            } else {
+                umin = atanf(a);
+                umax = atanf(b);
+            }
+        }
+        // bin range; clamped before the round-up / round-down adds that turn floats into ints
+        const float c0f = fminf(fmaxf((umin - u0) * inv_du + half - 1e-3f, -1.0f), 4.0e6f);
+        const float c1f = fminf(fmaxf((umax - u0) * inv_du + half + 1e-3f, -1.0f), 4.0e6f);
+        const int c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
+        const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, g.n_cols - 1);
+        for (int c = c0 + sub; c <= c1; c += 4) {
+            const int64_t r = (int64_t)v * g.n_cols + c;
+            const float4 ga = __ldg(reinterpret_cast<const float4 *>(grec + r));
+            const float4 gb = __ldg(reinterpret_cast<const float4 *>(grec + r) + 1);
+            const int flags = __float_as_int(gb.z);
+            float l = 0.f;
+            if (flags == 0) {
+                // ga = (inv_x, b_x, inv_y, b_y), gb = (ox, oy, flags, -)
+                const float qx = fi - gb.x, qy = fj - gb.y;
+                const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
+                const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
+                l = __fsub_rn(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)));
+            } else if (flags == 2) {
+                Walk W;
+                if (walk_setup(rays[r], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
+                    l = walk_unit_length(W, i, j, 0);
+            }
+            if (l > 0.f) {
+#pragma unroll
+                for (int b4 = 0; b4 < NB4; ++b4) {
+                    const float4 s = __ldg(S4 + (int64_t)b4 * n_rays + r);
+                    acc[4 * b4 + 0] = __fmaf_rn(s.x, l, acc[4 * b4 + 0]);
+                    acc[4 * b4 + 1] = __fmaf_rn(s.y, l, acc[4 * b4 + 1]);
+                    acc[4 * b4 + 2] = __fmaf_rn(s.z, l, acc[4 * b4 + 2]);
+                    acc[4 * b4 + 3] = __fmaf_rn(s.w, l, acc[4 * b4 + 3]);
+                }
+            }
+        }
+    }
+    // reduce over the 4 lanes of the pixel
+#pragma unroll
+    for (int b = 0; b < Bp; ++b) {
+        acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 1);
+        acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 2);
+    }
+    if (live) {
+        // lane `sub` stores images sub, sub + 4, ... of this chunk
+#pragma unroll
+        for (int b = 0; b < Bp; ++b) {
+            const int bb = chunk * Bp + b;
+            if ((b & 3) == sub && bb < batch) img[(int64_t)bb * n_pix + pix] = acc[b];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------------------
+
+cudaError_t launch_interleave_images(const float *img, int batch, int nx, int ny, int nz, int Bp, float *il0,
+                                     float *il1, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int chunks = (batch + Bp - 1) / Bp;
+    interleave_images_kernel<<<dim3((unsigned)((n + 255) / 256), chunks), 256, 0, s>>>(img, batch, nx, ny, nz, Bp,
+                                                                                      il0, il1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,
+                                   cudaStream_t s)
+{
+    const int chunks = (batch + Bp - 1) / Bp;
+    interleave_sino_kernel<<<dim3((unsigned)((n_rays + 255) / 256), chunks), 256, 0, s>>>(sino, batch, n_rays,
+                                                                                         Bp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
+                                 const float *il1, int Bp, float *sino, int batch, int block, cudaStream_t s)
+{
+    const int lpr = Bp / 4;
+    const int64_t threads = n_rays * lpr;
+    const int64_t warps = (threads + 31) / 32;
+    const dim3 grid((unsigned)((warps * 32 + block - 1) / block), (unsigned)((batch + Bp - 1) / Bp));
+    if (lpr == 4) fwd_fast2_kernel<4><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
+    else if (lpr == 2) fwd_fast2_kernel<2><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
+    else fwd_fast2_kernel<1><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, cudaStream_t s)
+{
+    gather_prep_kernel<<<(unsigned)((n_rays + 255) / 256), 256, 0, s>>>(rays, n_rays,
+                                                                        reinterpret_cast<GatherRec *>(grec));
+    return cudaGetLastError();
+}
+
+size_t gather_rec_bytes() { return sizeof(GatherRec); }
+
+cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
+                                const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
+                                cudaStream_t s)
+{
+    const int64_t n_pix = (int64_t)g.nx * g.ny;
+    const dim3 grid((unsigned)((n_pix * 4 + block - 1) / block), (unsigned)((batch + Bp - 1) / Bp));
+    const GatherRec *G = reinterpret_cast<const GatherRec *>(grec);
+#define XR_GATHER_LAUNCH(K)                                                                                   \
+    do {                                                                                                      \
+        if (Bp == 16) gather_fast2_kernel<4, K><<<grid, block, 0, s>>>(rays, G, g, vt, sil, n_rays, img, batch); \
+        else if (Bp == 8) gather_fast2_kernel<2, K><<<grid, block, 0, s>>>(rays, G, g, vt, sil, n_rays, img, batch); \
+        else gather_fast2_kernel<1, K><<<grid, block, 0, s>>>(rays, G, g, vt, sil, n_rays, img, batch);     \
+    } while (0)
+    if (g.kind == XR_PAR2D) XR_GATHER_LAUNCH(XR_PAR2D);
+    else if (g.kind == XR_FAN2D) XR_GATHER_LAUNCH(XR_FAN2D);
+    else XR_GATHER_LAUNCH(XR_FAN2D_ARC);
+#undef XR_GATHER_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace xr

@@ -156,13 +156,13 @@ cudaError_t launch_backproject_scatter(const RayRec *rays, int64_t n_rays, const
 // Adjoint, unit-driven gather (2D): one thread per pixel; for every view, the detector bins
 // whose rays can cross the pixel (projection of its corners, one bin of margin), and for
 // each the length the forward walk gives that (ray, pixel) pair.
-// View table (8 doubles per view): parallel: (-sin phi, cos phi); fan: source (Sx, Sy),
+// View table (8 floats per view): parallel: (-sin phi, cos phi); fan: source (Sx, Sy),
 // central direction (ex, ey), detector direction (tx, ty).
 // ---------------------------------------------------------------------------------------
 
 template <int BC>
 __global__ void __launch_bounds__(256) gather2d_kernel(const RayRec *__restrict__ rays, GeoParams g,
-                                                       Grid grid, const double *__restrict__ vt,
+                                                       Grid grid, const float *__restrict__ vt,
                                                        const float *__restrict__ sino, int64_t sino_bs,
                                                        float *__restrict__ img, int64_t img_bs, int batch)
 {
@@ -181,18 +181,18 @@ __global__ void __launch_bounds__(256) gather2d_kernel(const RayRec *__restrict_
     const float half = 0.5f * (float)(g.n_cols - 1);
     const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0;
     for (int v = 0; v < g.n_views; ++v) {
-        const double *e = vt + 8 * v;
+        const float *e = vt + 8 * v;
         float cmin = 1e30f, cmax = -1e30f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const float X = (q & 1) ? x1 : x0, Y = (q & 2) ? y1 : y0;
             float uc;
             if (g.kind == XR_PAR2D) {
-                uc = (float)e[0] * X + (float)e[1] * Y;
+                uc = e[0] * X + e[1] * Y;
             } else {
-                const float rx = X - (float)e[0], ry = Y - (float)e[1];
-                const float depth = rx * (float)e[2] + ry * (float)e[3];
-                const float lat = rx * (float)e[4] + ry * (float)e[5];
+                const float rx = X - e[0], ry = Y - e[1];
+                const float depth = rx * e[2] + ry * e[3];
+                const float lat = rx * e[4] + ry * e[5];
                 uc = (g.kind == XR_FAN2D) ? (float)g.sdd * lat / depth : atan2f(lat, depth);
             }
             const float c = (uc - u0) * inv_du + half;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) gather2d_kernel(const RayRec *__restrict_
 
 template <int BC>
 static cudaError_t launch_gather_t(const RayRec *rays, const GeoParams &g, const Grid &grid,
-                                   const double *vt, const float *sino, int64_t sino_bs, float *img,
+                                   const float *vt, const float *sino, int64_t sino_bs, float *img,
                                    int64_t img_bs, int batch, int block, cudaStream_t s)
 {
     const int64_t n_pix = (int64_t)g.nx * g.ny;
@@ -229,7 +229,7 @@ static cudaError_t launch_gather_t(const RayRec *rays, const GeoParams &g, const
 }
 
 cudaError_t launch_backproject_gather2d(const RayRec *rays, const GeoParams &g, const Grid &grid,
-                                        const double *vt, const float *sino, int64_t sino_bs,
+                                        const float *vt, const float *sino, int64_t sino_bs,
                                         float *img, int64_t img_bs, int batch, int chunk, int block,
                                         cudaStream_t s)
 {

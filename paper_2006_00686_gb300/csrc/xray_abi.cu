@@ -71,12 +71,11 @@ static Grid make_grid(const xr_geometry *g)
     return gr;
 }
 
-// Per-view data of the 2D gather's footprint test (double precision, on the host).
-static void fill_view_table(const xr_geometry_desc *d, double *vt)
+// Per-view data of the 2D gather's footprint test (computed in double, stored as float).
+static void fill_view_table(const xr_geometry_desc *d, float *vt)
 {
     for (int v = 0; v < d->n_views; ++v) {
-        double *e = vt + 8 * v;
-        memset(e, 0, 8 * sizeof(double));
+        double e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         const double a = d->angles[v];
         if (d->kind == XR_PAR2D) {
             e[0] = -sin(a);  // s = -x sin(phi) + y cos(phi)
@@ -89,6 +88,7 @@ static void fill_view_table(const xr_geometry_desc *d, double *vt)
             e[4] = cos(a);  // along the detector
             e[5] = sin(a);
         }
+        for (int k = 0; k < 8; ++k) vt[8 * v + k] = (float)e[k];
     }
 }
 
@@ -98,6 +98,30 @@ static int pick_chunk(const xr_geometry *g, int batch)
     int c = g->tune.batch_chunk;
     while (c > 1 && c > batch) c >>= 1;
     return c < 1 ? 1 : c;
+}
+
+// Images per chunk of the batched fast path.
+static int fast_chunk(int batch) { return batch > 8 ? 16 : (batch > 4 ? 8 : 4); }
+
+// Units of one image in the fast path's padded interleaved layout (border of 2 in x and y).
+static size_t padded_units(const xr_geometry *g)
+{
+    return (size_t)(g->params.nx + 4) * (size_t)(g->params.ny + 4) * (size_t)g->params.nz;
+}
+
+static size_t fast_ws_bytes(const xr_geometry *g, int batch)
+{
+    const int Bp = fast_chunk(batch);
+    const size_t padded = (size_t)((batch + Bp - 1) / Bp) * Bp;
+    return padded * sizeof(float) * (2 * padded_units(g) + (size_t)g->n_rays);
+}
+
+// The batched fast path applies when the workspace holds the batch and the batch is >= 4.
+static bool use_fast(const xr_geometry *g, int batch)
+{
+    // the fast kernels index one chunk of interleaved images with 32-bit offsets
+    return batch >= 4 && batch <= g->ws_batch && g->tune.batch_chunk != 1 &&
+           (int64_t)padded_units(g) * fast_chunk(batch) < ((int64_t)1 << 31);
 }
 
 extern "C" {
@@ -140,18 +164,22 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     p.v0 = three ? desc->v0 : 0.0;
     p.sod = desc->sod;
     p.sdd = desc->sdd;
+    p.inv_dx = 1.0 / p.dx;
+    p.inv_dy = 1.0 / p.dy;
+    p.inv_dz = 1.0 / p.dz;
     g->n_rays = (int64_t)p.n_views * p.n_rows * p.n_cols;
     g->n_units = (int64_t)p.nx * p.ny * p.nz;
     g->tune.block = 128;
-    g->tune.batch_chunk = 1;
+    g->tune.batch_chunk = 16;
     g->tune.adjoint = three ? XR_ADJ_SCATTER : XR_ADJ_GATHER;
 
     cudaError_t e = cudaGetDevice(&g->device);
-    const size_t n_ang = (size_t)p.n_views * (desc->kind == XR_PAR3D ? 2 : 1);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_angles, n_ang * sizeof(double));
-    if (e == cudaSuccess && kind_helical(desc->kind)) e = cudaMalloc(&g->d_src_z, p.n_views * sizeof(double));
+    const size_t n_det = (size_t)p.n_rows * p.n_cols;
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_views, (size_t)p.n_views * sizeof(ViewRec));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_det, n_det * sizeof(DetRec));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
-    if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_view_tab, (size_t)p.n_views * 8 * sizeof(double));
+    if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_view_tab, (size_t)p.n_views * 8 * sizeof(float));
+    if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_grec, (size_t)g->n_rays * gather_rec_bytes());
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
         cudaGetLastError();
@@ -159,20 +187,39 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
         if (oom) return XR_ERR_ALLOC;
         return cuda_fail(e);
     }
-    e = cudaMemcpy(g->d_angles, desc->angles, n_ang * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && g->d_src_z)
-        e = cudaMemcpy(g->d_src_z, desc->src_z, p.n_views * sizeof(double), cudaMemcpyHostToDevice);
+    {
+        // per view: cos/sin of the view angle(s) and the source height, in double
+        ViewRec *vr = (ViewRec *)calloc((size_t)p.n_views, sizeof(ViewRec));
+        if (!vr) {
+            xr_geometry_destroy(g);
+            return XR_ERR_ALLOC;
+        }
+        for (int v = 0; v < p.n_views; ++v) {
+            const double a = desc->kind == XR_PAR3D ? desc->angles[2 * v] : desc->angles[v];
+            vr[v].c1 = cos(a);
+            vr[v].s1 = sin(a);
+            if (desc->kind == XR_PAR3D) {
+                vr[v].c2 = cos(desc->angles[2 * v + 1]);
+                vr[v].s2 = sin(desc->angles[2 * v + 1]);
+            }
+            vr[v].H = kind_helical(desc->kind) ? desc->src_z[v] : 0.0;
+        }
+        e = cudaMemcpy(g->d_views, vr, (size_t)p.n_views * sizeof(ViewRec), cudaMemcpyHostToDevice);
+        free(vr);
+    }
     if (e == cudaSuccess && !three) {
-        double *vt = (double *)malloc((size_t)p.n_views * 8 * sizeof(double));
+        float *vt = (float *)malloc((size_t)p.n_views * 8 * sizeof(float));
         if (!vt) {
             xr_geometry_destroy(g);
             return XR_ERR_ALLOC;
         }
         fill_view_table(desc, vt);
-        e = cudaMemcpy(g->d_view_tab, vt, (size_t)p.n_views * 8 * sizeof(double), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(g->d_view_tab, vt, (size_t)p.n_views * 8 * sizeof(float), cudaMemcpyHostToDevice);
         free(vt);
     }
-    if (e == cudaSuccess) e = launch_ray_setup(p, g->d_angles, g->d_src_z, g->d_rays, g->n_rays, nullptr);
+    if (e == cudaSuccess) e = launch_det_setup(p, g->d_det, nullptr);
+    if (e == cudaSuccess) e = launch_ray_setup(p, g->d_views, g->d_det, g->d_rays, g->n_rays, nullptr);
+    if (e == cudaSuccess && g->d_grec) e = launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
         xr_geometry_destroy(g);
@@ -189,10 +236,12 @@ void xr_geometry_destroy(xr_geometry *g)
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
     cudaDeviceSynchronize();
-    cudaFree(g->d_angles);
-    cudaFree(g->d_src_z);
+    cudaFree(g->d_views);
+    cudaFree(g->d_det);
     cudaFree(g->d_rays);
     cudaFree(g->d_view_tab);
+    cudaFree(g->d_grec);
+    cudaFree(g->d_ws);
     cudaSetDevice(prev);
     delete g;
 }
@@ -200,7 +249,37 @@ void xr_geometry_destroy(xr_geometry *g)
 xr_status xr_ray_setup(xr_geometry *g, xr_stream stream)
 {
     if (!g) return XR_ERR_NULL;
-    XR_CUDA(launch_ray_setup(g->params, g->d_angles, g->d_src_z, g->d_rays, g->n_rays, (cudaStream_t)stream));
+    XR_CUDA(launch_det_setup(g->params, g->d_det, (cudaStream_t)stream));
+    XR_CUDA(launch_ray_setup(g->params, g->d_views, g->d_det, g->d_rays, g->n_rays, (cudaStream_t)stream));
+    if (g->d_grec) XR_CUDA(launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, (cudaStream_t)stream));
+    return XR_OK;
+}
+
+xr_status xr_reserve(xr_geometry *g, int32_t max_batch)
+{
+    if (!g) return XR_ERR_NULL;
+    if (max_batch < 1) return XR_ERR_BATCH;
+    if (max_batch <= g->ws_batch) return XR_OK;
+    const size_t bytes = fast_ws_bytes(g, max_batch);
+    int prev = 0;
+    XR_CUDA(cudaGetDevice(&prev));
+    XR_CUDA(cudaSetDevice(g->device));
+    XR_CUDA(cudaDeviceSynchronize());  // the old workspace may still be in use
+    cudaFree(g->d_ws);
+    g->d_ws = nullptr;
+    g->ws_bytes = 0;
+    g->ws_batch = 0;
+    cudaError_t e = cudaMalloc(&g->d_ws, bytes);
+    // the borders of the interleaved copies stay zero: only interiors are ever written
+    if (e == cudaSuccess) e = cudaMemset(g->d_ws, 0, bytes);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g->d_ws = nullptr;
+        return e == cudaErrorMemoryAllocation ? XR_ERR_ALLOC : cuda_fail(e);
+    }
+    g->ws_bytes = bytes;
+    g->ws_batch = max_batch;
     return XR_OK;
 }
 
@@ -209,7 +288,9 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
     if (!g || !info) return XR_ERR_NULL;
     info->n_rays = g->n_rays;
     info->n_units = g->n_units;
-    info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * 8 * 8;
+    info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * (8 * 4 + sizeof(ViewRec)) +
+                        (int64_t)g->params.n_rows * g->params.n_cols * (int64_t)sizeof(DetRec) +
+                        (g->d_grec ? g->n_rays * (int64_t)gather_rec_bytes() : 0) + (int64_t)g->ws_bytes;
     info->is3d = kind_is3d(g->params.kind);
     info->device = g->device;
     return XR_OK;
@@ -242,6 +323,17 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
     if (!g || !d_img || !d_sino) return XR_ERR_NULL;
     if (batch < 1) return XR_ERR_BATCH;
     if (!aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
+    if (use_fast(g, batch)) {
+        const int Bp = fast_chunk(batch);
+        if ((batch + Bp - 1) / Bp > 65535) return XR_ERR_SIZE;
+        const size_t padded = (size_t)((batch + Bp - 1) / Bp) * Bp;
+        float *il0 = g->d_ws, *il1 = g->d_ws + padded * padded_units(g);
+        const cudaStream_t s = (cudaStream_t)stream;
+        XR_CUDA(launch_interleave_images(d_img, batch, g->params.nx, g->params.ny, g->params.nz, Bp, il0, il1, s));
+        XR_CUDA(launch_project_fast2(g->d_rays, g->n_rays, g->params.nx, g->params.ny, g->params.nz, il0, il1, Bp,
+                                     d_sino, batch, 256, s));
+        return XR_OK;
+    }
     const int chunk = pick_chunk(g, batch);
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
     XR_CUDA(launch_project(g->d_rays, g->n_rays, make_grid(g), d_img, g->n_units, d_sino, g->n_rays, batch,
@@ -261,6 +353,15 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     const cudaStream_t s = (cudaStream_t)stream;
     if (method == XR_ADJ_GATHER) {
         if (kind_is3d(g->params.kind)) return XR_ERR_ARG;
+        if (use_fast(g, batch)) {
+            const int Bp = fast_chunk(batch);
+            const size_t padded = (size_t)((batch + Bp - 1) / Bp) * Bp;
+            float *sil = g->d_ws + 2 * padded * padded_units(g);
+            XR_CUDA(launch_interleave_sino(d_sino, batch, g->n_rays, Bp, sil, s));
+            XR_CUDA(launch_gather_fast2(g->d_rays, g->d_grec, g->params, g->d_view_tab, sil, g->n_rays, d_img, batch,
+                                        Bp, 256, s));
+            return XR_OK;
+        }
         XR_CUDA(launch_backproject_gather2d(g->d_rays, g->params, make_grid(g), g->d_view_tab, d_sino, g->n_rays,
                                             d_img, g->n_units, batch, chunk, g->tune.block, s));
         return XR_OK;

@@ -64,8 +64,8 @@ struct Walk {
     int mlo, mhi;         // driving indices to visit
 };
 
-// Prepare the walk; false when the ray crosses no unit.  Strides sx, sy, sz give the image
-// layout (1, nx, nx*ny for the [nz][ny][nx] layout).
+// Prepare the walk; false when the ray crosses no unit (then W.nact == 0 and walk() does
+// nothing).  Strides sx, sy, sz give the image layout (1, nx, nx*ny for [nz][ny][nx]).
 __device__ __forceinline__ bool walk_setup(const RayRec &r, int nx, int ny, int nz, int64_t sx,
                                            int64_t sy, int64_t sz, Walk &W)
 {
@@ -83,7 +83,6 @@ __device__ __forceinline__ bool walk_setup(const RayRec &r, int nx, int ny, int 
         B = C;
         C = t;
     }
-    W.nact = nact;
     W.axA = A;
     W.axB = B;
     W.axC = C;
@@ -148,7 +147,10 @@ __device__ __forceinline__ bool walk_setup(const RayRec &r, int nx, int ny, int 
     const int hi = (int)floorf(fmaxf(uin, uout)) + W.oA + 1;
     W.mlo = max(lo, 0);
     W.mhi = min(hi, W.NA - 1);
-    return W.mlo <= W.mhi;
+    if (W.mlo > W.mhi) return false;
+    // only a complete setup makes the walk non-empty: on every early return nact stays 0
+    W.nact = nact;
+    return true;
 }
 
 // t of the entering / leaving planes of driving slab m.

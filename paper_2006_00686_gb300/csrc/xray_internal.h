@@ -17,6 +17,7 @@ namespace xr {
 struct GeoParams {
     int kind, nx, ny, nz, n_views, n_rows, n_cols;
     double dx, dy, dz, cx, cy, cz, du, dv, u0, v0, sod, sdd;
+    double inv_dx, inv_dy, inv_dz;  // 1/dx, 1/dy, 1/dz
 };
 
 // Image extents and layout strides passed to the ray kernels.
@@ -25,8 +26,20 @@ struct Grid {
     int64_t sx, sy, sz;  // element strides of i, j, k
 };
 
-cudaError_t launch_ray_setup(const GeoParams &g, const double *d_angles, const double *d_src_z,
-                             RayRec *d_rays, int64_t n_rays, cudaStream_t s);
+// Per detector sample: the parts of the ray parameters that depend on the detector only
+// (2D: s and cos/sin of gamma; 3D: s1, the detector part of s2, cos/sin of alpha and beta).
+struct DetRec {
+    double s1, s2, ca, sa, cb, sb;
+};
+
+// Per view: cos/sin of the view angle (PAR3D: of phi1 and phi2) and the source height.
+struct ViewRec {
+    double c1, s1, c2, s2, H, pad0, pad1, pad2;
+};
+
+cudaError_t launch_det_setup(const GeoParams &g, DetRec *d_det, cudaStream_t s);
+cudaError_t launch_ray_setup(const GeoParams &g, const ViewRec *d_views, const DetRec *d_det, RayRec *d_rays,
+                             int64_t n_rays, cudaStream_t s);
 
 cudaError_t launch_project(const RayRec *rays, int64_t n_rays, const Grid &grid, const float *img,
                            int64_t img_bs, float *sino, int64_t sino_bs, int batch, int chunk,
@@ -38,7 +51,7 @@ cudaError_t launch_backproject_scatter(const RayRec *rays, int64_t n_rays, const
                                        cudaStream_t s);
 
 cudaError_t launch_backproject_gather2d(const RayRec *rays, const GeoParams &g, const Grid &grid,
-                                        const double *d_view_tab, const float *sino,
+                                        const float *d_view_tab, const float *sino,
                                         int64_t sino_bs, float *img, int64_t img_bs, int batch,
                                         int chunk, int block, cudaStream_t s);
 
@@ -67,6 +80,19 @@ cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_
 
 int batched_ctas_per_sm(int block, int adjoint);
 
+// Batched fast path for rays with at most two active axes (fast2d.cu).
+cudaError_t launch_interleave_images(const float *img, int batch, int nx, int ny, int nz, int Bp, float *il0,
+                                     float *il1, cudaStream_t s);
+cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,
+                                   cudaStream_t s);
+cudaError_t launch_project_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
+                                 const float *il1, int Bp, float *sino, int batch, int block, cudaStream_t s);
+cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, cudaStream_t s);
+size_t gather_rec_bytes();
+cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
+                                const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
+                                cudaStream_t s);
+
 }  // namespace xr
 
 // Record a CUDA error for xr_last_cuda_error() and return XR_ERR_CUDA.
@@ -78,9 +104,13 @@ struct xr_geometry {
     xr::GeoParams params;
     int device;
     int64_t n_rays, n_units;
-    double *d_angles;
-    double *d_src_z;
+    xr::ViewRec *d_views;  // per view (host-computed cos/sin of the view angles)
+    xr::DetRec *d_det;     // per detector sample (det_setup_kernel)
     xr::RayRec *d_rays;
-    double *d_view_tab;  // per view: 2D gather footprint data
+    float *d_view_tab;   // per view: 2D gather footprint data (8 floats)
+    void *d_grec;        // per ray: plane constants of the 2D gather
+    float *d_ws;         // workspace of the batched fast path (interleaved copies)
+    size_t ws_bytes;
+    int ws_batch;        // largest batch the workspace holds (0: none reserved)
     xr_tuning tune;
 };

@@ -58,6 +58,7 @@ SIGNATURES = {
     "xr_geometry_destroy": (None, [_VP]),
     "xr_ray_setup": (_I32, [_VP, _VP]),
     "xr_geometry_get_info": (_I32, [_VP, ctypes.POINTER(_Info)]),
+    "xr_reserve": (_I32, [_VP, _I32]),
     "xr_set_tuning": (_I32, [_VP, ctypes.POINTER(_Tuning)]),
     "xr_get_tuning": (_I32, [_VP, ctypes.POINTER(_Tuning)]),
     "xr_project": (_I32, [_VP, _VP, _VP, _I32, _VP]),
@@ -137,6 +138,8 @@ class Projector:
         self.n_rays, self.n_units = int(info.n_rays), int(info.n_units)
         self.table_bytes = int(info.table_bytes)
         self.device = torch.device("cuda", int(info.device))
+        self.reserved = 0
+        self.auto_reserve = True
 
     @property
     def handle(self):
@@ -163,6 +166,11 @@ class Projector:
         _check(lib().xr_get_tuning(self._h, ctypes.byref(t)), "xr_get_tuning")
         return {"block": t.block, "batch_chunk": t.batch_chunk, "adjoint": t.adjoint}
 
+    def reserve(self, max_batch: int):
+        """Reserve the batched fast path's workspace (allocates; not during graph capture)."""
+        _check(lib().xr_reserve(self._h, int(max_batch)), "xr_reserve")
+        self.reserved = int(max_batch)
+
     def ray_setup(self, stream=None):
         _check(lib().xr_ray_setup(self._h, _stream(stream)), "xr_ray_setup")
 
@@ -174,9 +182,14 @@ class Projector:
             return int(t.shape[0])
         raise XRayError(f"{name} has shape {tuple(t.shape)}, expected {unit_shape} or (B,)+{unit_shape}")
 
+    def _maybe_reserve(self, b: int):
+        if b >= 4 and b > self.reserved and self.auto_reserve and not torch.cuda.is_current_stream_capturing():
+            self.reserve(b)
+
     def forward(self, img: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         _need_cuda(img, "img")
         b = self._batch_of(img, self.geom.image_shape(), "img")
+        self._maybe_reserve(b)
         shape = self.geom.sino_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=img.device, dtype=torch.float32)
@@ -188,6 +201,7 @@ class Projector:
                 stream=None) -> torch.Tensor:
         _need_cuda(sino, "sino")
         b = self._batch_of(sino, self.geom.sino_shape(), "sino")
+        self._maybe_reserve(b)
         shape = self.geom.image_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=sino.device, dtype=torch.float32)
