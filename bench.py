@@ -229,7 +229,10 @@ def run_ours(args, rank, world, local_rank):
            "e2e": {"value": round(rays_step * world / (e2e * 1e-3) / 1e9, 4), "unit": UNIT,
                    "h2d_bytes_per_step": int(x.numel() * 4),
                    "d2h_bytes_per_step": int(y.numel() * 4 + z.numel() * 4), "ms_per_step": round(e2e, 4)},
-           "gpu_launches": args.steps * (3 if args.adjoint == "gather" else 3),
+           # per step: detector setup, ray setup, image interleave, forward walk, then either
+           # the scatter walk + its de-interleave (two accumulator memsets are not kernels)
+           # or the sinogram interleave + gather
+           "gpu_launches": args.steps * 6,
            "kernel_ms": {"ray_setup": round(float(np.mean(setup_ms)), 4), "forward": round(fwd, 4),
                          "adjoint": round(adj, 4)},
            "clocks": clk.summary(), "roofline": roof, "wall_s": round(wall, 3)}
@@ -303,7 +306,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--adjoint", default="gather", choices=["gather", "scatter"])
+    ap.add_argument("--adjoint", default="scatter", choices=["gather", "scatter"])
     ap.add_argument("--chunk", type=int, default=16)
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

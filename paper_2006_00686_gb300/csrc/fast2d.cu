@@ -64,6 +64,33 @@ __global__ void interleave_images_kernel(const float *__restrict__ img, int batc
     }
 }
 
+// Adjoint accumulators -> user images: img[b][u] = IL0 + IL1 at unit u (interiors only).
+__global__ void deinterleave_sum_kernel(const float *__restrict__ il0, const float *__restrict__ il1, int batch,
+                                        int nx, int ny, int nz, int Bp, float *__restrict__ img)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int chunk = blockIdx.y;
+    const int i = (int)(u % nx);
+    const int64_t rest = u / nx;
+    const int j = (int)(rest % ny);
+    const int k = (int)(rest / ny);
+    const int px = nx + 2 * XR_IL_PAD, py = ny + 2 * XR_IL_PAD;
+    const int64_t np = (int64_t)px * py * nz;
+    const int64_t o0 = ((int64_t)chunk * np + ((int64_t)k * py + j + XR_IL_PAD) * px + i + XR_IL_PAD) * Bp;
+    const int64_t o1 = ((int64_t)chunk * np + ((int64_t)k * px + i + XR_IL_PAD) * py + j + XR_IL_PAD) * Bp;
+    for (int b4 = 0; b4 < Bp; b4 += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(il0 + o0 + b4);
+        const float4 c = *reinterpret_cast<const float4 *>(il1 + o1 + b4);
+        const int b = chunk * Bp + b4;
+        if (b + 0 < batch) img[(int64_t)(b + 0) * n + u] = a.x + c.x;
+        if (b + 1 < batch) img[(int64_t)(b + 1) * n + u] = a.y + c.y;
+        if (b + 2 < batch) img[(int64_t)(b + 2) * n + u] = a.z + c.z;
+        if (b + 3 < batch) img[(int64_t)(b + 3) * n + u] = a.w + c.w;
+    }
+}
+
 // user sinograms [B][n_rays] -> [chunk][Bp/4][n_rays][4]: the 4 images of one quad of one ray
 // are one float4, and neighbouring rays' float4 of the same quad are neighbours in memory.
 __global__ void interleave_sino_kernel(const float *__restrict__ sino, int batch, int64_t n_rays, int Bp,
@@ -110,6 +137,34 @@ __device__ __noinline__ float4 slab_rows_general(int oB, int NB, int sgB, float 
     return acc;
 }
 
+// Scatter counterpart of slab_rows_general: adds g * l into rows jlo..jhi of the slab.
+__device__ __noinline__ void scatter_rows_general(int oB, int NB, int sgB, float invB, float bB, float tlo,
+                                                  float thi, int jlo, int jhi, const float *__restrict__ base,
+                                                  int64_t sB, float4 g)
+{
+    for (int j = jlo; j <= jhi; ++j) {
+        const int jg = j + oB;
+        if ((unsigned)jg >= (unsigned)NB) continue;
+        const float q = (float)j;
+        const float tb0 = __fmaf_rn(q + (float)sgB, invB, bB);
+        const float tb1 = __fmaf_rn(q + (float)(1 - sgB), invB, bB);
+        const float l = __fsub_rn(fminf(thi, tb1), fmaxf(tlo, tb0));
+        if (l > 0.f)
+            atomicAdd(reinterpret_cast<float4 *>(const_cast<float *>(base + (int64_t)jg * sB)),
+                      make_float4(g.x * l, g.y * l, g.z * l, g.w * l));
+    }
+}
+
+// Scatter visitor for rays with three active axes on the interleaved layout.
+struct Il4ScatterVisitor {
+    float *il;
+    float4 g;
+    __device__ __forceinline__ void operator()(int64_t off, float l)
+    {
+        atomicAdd(reinterpret_cast<float4 *>(il + off), make_float4(g.x * l, g.y * l, g.z * l, g.w * l));
+    }
+};
+
 // Visitor for rays with three active axes (general walk on the interleaved layout).
 struct Il4Visitor {
     const float *il;
@@ -128,7 +183,24 @@ struct Il4Visitor {
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
-template <int LPR>
+// One unit of the walk: the forward gathers the unit's 4 images, the adjoint adds the ray's
+// 4 sinogram values times the length into them (one 128-bit vector atomic).
+template <bool ADJ>
+__device__ __forceinline__ void unit_op(const float *p, bool on, float l, float4 &acc)
+{
+    if (ADJ) {
+        if (on && l > 0.f)
+            atomicAdd(reinterpret_cast<float4 *>(const_cast<float *>(p)),
+                      make_float4(acc.x * l, acc.y * l, acc.z * l, acc.w * l));
+    } else {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        fma4(acc, on ? __ldg(reinterpret_cast<const float4 *>(p)) : z, l);
+    }
+}
+
+// ADJ = false: forward, il0/il1 are the interleaved images, sino the output.
+// ADJ = true: adjoint (scatter), sino is the input and il0/il1 the zeroed accumulators.
+template <int LPR, bool ADJ>
 __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const RayRec *__restrict__ rays, int64_t n_rays,
                                                            int nx, int ny, int nz, const float *__restrict__ il0,
                                                            const float *__restrict__ il1, int Bp,
@@ -162,6 +234,14 @@ __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const
     const float *il = (y_fast ? il1 : il0) + (int64_t)chunk * np * Bp + 4 * q + XR_IL_PAD * (si + sj);
 
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ADJ && r < n_rays) {
+        // the adjoint scatters g * l: acc holds this lane's 4 sinogram values
+        const int b0 = chunk * Bp + 4 * q;
+        acc.x = (b0 + 0 < batch) ? __ldg(sino + (int64_t)(b0 + 0) * n_rays + r) : 0.f;
+        acc.y = (b0 + 1 < batch) ? __ldg(sino + (int64_t)(b0 + 1) * n_rays + r) : 0.f;
+        acc.z = (b0 + 2 < batch) ? __ldg(sino + (int64_t)(b0 + 2) * n_rays + r) : 0.f;
+        acc.w = (b0 + 3 < batch) ? __ldg(sino + (int64_t)(b0 + 3) * n_rays + r) : 0.f;
+    }
     const int wlo = __reduce_min_sync(0xffffffffu, ok ? W.mlo : INT_MAX);
     const int whi = __reduce_max_sync(0xffffffffu, ok ? W.mhi : INT_MIN);
     if (ok) {
@@ -199,17 +279,33 @@ __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const
                 const float la = fabsf(__fsub_rn(tcc0, tcur)), lb = fabsf(__fsub_rn(t1, tcc0));
                 const float lc = fabsf(__fsub_rn(tcc1, t1)), ld = fabsf(__fsub_rn(t2, tcc1));
                 const float *p0 = pA + moff, *p1 = pA + moff + sA;
-                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 va = act0 ? __ldg(reinterpret_cast<const float4 *>(p0 + r0 * sB)) : z;
-                const float4 vb = (act0 && x01) ? __ldg(reinterpret_cast<const float4 *>(p0 + r1 * sB)) : z;
-                const float4 vc = act1 ? __ldg(reinterpret_cast<const float4 *>(p1 + r1 * sB)) : z;
-                const float4 vd = (act1 && x12) ? __ldg(reinterpret_cast<const float4 *>(p1 + r2 * sB)) : z;
-                fma4(acc, va, la);
-                fma4(acc, vb, lb);
-                fma4(acc, vc, lc);
-                fma4(acc, vd, ld);
+                if (ADJ) {
+                    unit_op<true>(p0 + r0 * sB, act0, la, acc);
+                    unit_op<true>(p0 + r1 * sB, act0 && x01, lb, acc);
+                    unit_op<true>(p1 + r1 * sB, act1, lc, acc);
+                    unit_op<true>(p1 + r2 * sB, act1 && x12, ld, acc);
+                } else {
+                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 va = act0 ? __ldg(reinterpret_cast<const float4 *>(p0 + r0 * sB)) : z;
+                    const float4 vb = (act0 && x01) ? __ldg(reinterpret_cast<const float4 *>(p0 + r1 * sB)) : z;
+                    const float4 vc = act1 ? __ldg(reinterpret_cast<const float4 *>(p1 + r1 * sB)) : z;
+                    const float4 vd = (act1 && x12) ? __ldg(reinterpret_cast<const float4 *>(p1 + r2 * sB)) : z;
+                    fma4(acc, va, la);
+                    fma4(acc, vb, lb);
+                    fma4(acc, vc, lc);
+                    fma4(acc, vd, ld);
+                }
             } else {
                 // a step that crosses two rows (within rounding of a diagonal): per-candidate formula
+                if (ADJ) {
+                    if (act0)
+                        scatter_rows_general(W.oB, W.NB, W.sgB, invB, bB, W.sgA ? t1 : tcur, W.sgA ? tcur : t1,
+                                             (int)fminf(j0, j1), (int)fmaxf(j0, j1), pA - W.oB * sB + moff, sB, acc);
+                    if (act1)
+                        scatter_rows_general(W.oB, W.NB, W.sgB, invB, bB, W.sgA ? t2 : t1, W.sgA ? t1 : t2,
+                                             (int)fminf(j1, j2), (int)fmaxf(j1, j2), pA - W.oB * sB + moff + sA, sB,
+                                             acc);
+                } else {
                 if (act0) {
                     const float tlo = W.sgA ? t1 : tcur, thi = W.sgA ? tcur : t1;
                     const float4 a = slab_rows_general(W.oB, W.NB, W.sgB, invB, bB, tlo, thi, (int)fminf(j0, j1),
@@ -222,6 +318,7 @@ __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const
                                                        (int)fmaxf(j1, j2), pA - W.oB * sB + moff + sA, sB);
                     acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
                 }
+                }
             }
             p += 2.0f;
             tcur = t2;
@@ -229,12 +326,17 @@ __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const
             j0 = j2;
         }
     } else if (general) {
-        Il4Visitor vis{il, make_float4(0.f, 0.f, 0.f, 0.f)};
         Walk W2;
-        if (walk_setup(rays[r], nx, ny, nz, si, sj, sk, W2)) walk(W2, vis);
-        acc = vis.acc;
+        if (ADJ) {
+            Il4ScatterVisitor vis{const_cast<float *>(il), acc};
+            if (walk_setup(rays[r], nx, ny, nz, si, sj, sk, W2)) walk(W2, vis);
+        } else {
+            Il4Visitor vis{il, make_float4(0.f, 0.f, 0.f, 0.f)};
+            if (walk_setup(rays[r], nx, ny, nz, si, sj, sk, W2)) walk(W2, vis);
+            acc = vis.acc;
+        }
     }
-    if (r < n_rays) {
+    if (!ADJ && r < n_rays) {
         const int b0 = chunk * Bp + 4 * q;
         if (b0 + 0 < batch) sino[(int64_t)(b0 + 0) * n_rays + r] = acc.x;
         if (b0 + 1 < batch) sino[(int64_t)(b0 + 1) * n_rays + r] = acc.y;
@@ -282,14 +384,18 @@ __global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restr
                                                            float *__restrict__ img, int batch)
 {
     constexpr int Bp = 4 * NB4;
+    // 32-bit indexing throughout (the host admits this path only when n_rays * Bp < 2^31)
     const int lane = threadIdx.x & 31;
     const int sub = lane & 3;
-    const int64_t pix = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
-    const int64_t n_pix = (int64_t)g.nx * g.ny;
+    const int pix = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2);
+    const int n_pix = g.nx * g.ny;
     const bool live = pix < n_pix;
-    const int i = live ? (int)(pix % g.nx) : 0, j = live ? (int)(pix / g.nx) : 0;
+    const int i = live ? pix % g.nx : 0, j = live ? pix / g.nx : 0;
     const int chunk = blockIdx.y;
-    const float4 *S4 = reinterpret_cast<const float4 *>(sil) + (int64_t)chunk * NB4 * n_rays;
+    const int nr = (int)n_rays;
+    const float4 *S4 = reinterpret_cast<const float4 *>(sil) + chunk * NB4 * nr;
+    const float4 *G4 = reinterpret_cast<const float4 *>(grec);
+    const float4 *V4 = reinterpret_cast<const float4 *>(vt);
     float acc[Bp];
 #pragma unroll
     for (int b = 0; b < Bp; ++b) acc[b] = 0.f;
@@ -300,10 +406,11 @@ __global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restr
     const float half = 0.5f * (float)(g.n_cols - 1);
     const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0, sdd = (float)g.sdd;
     const float fi = (float)i, fj = (float)j;
-    for (int v = 0; v < g.n_views && live; ++v) {
+    const int ncols = g.n_cols, nviews = live ? g.n_views : 0;
+    for (int v = 0, vbase = 0; v < nviews; ++v, vbase += ncols) {
         // the same view record for every lane of the warp: one broadcast load
-        const float4 e0 = __ldg(reinterpret_cast<const float4 *>(vt) + 2 * v);
-        const float4 e1 = __ldg(reinterpret_cast<const float4 *>(vt) + 2 * v + 1);
+        const float4 e0 = __ldg(V4 + 2 * v);
+        const float4 e1 = __ldg(V4 + 2 * v + 1);
         float umin, umax;
         if (KIND == XR_PAR2D) {
             const float uc = e0.x * xc + e0.y * yc, hw = fabsf(e0.x) * hx + fabsf(e0.y) * hy;
@@ -329,11 +436,11 @@ __global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restr
         const float c0f = fminf(fmaxf((umin - u0) * inv_du + half - 1e-3f, -1.0f), 4.0e6f);
         const float c1f = fminf(fmaxf((umax - u0) * inv_du + half + 1e-3f, -1.0f), 4.0e6f);
         const int c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
-        const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, g.n_cols - 1);
+        const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, ncols - 1);
         for (int c = c0 + sub; c <= c1; c += 4) {
-            const int64_t r = (int64_t)v * g.n_cols + c;
-            const float4 ga = __ldg(reinterpret_cast<const float4 *>(grec + r));
-            const float4 gb = __ldg(reinterpret_cast<const float4 *>(grec + r) + 1);
+            const int r = vbase + c;
+            const float4 ga = __ldg(G4 + 2 * r);
+            const float4 gb = __ldg(G4 + 2 * r + 1);
             const int flags = __float_as_int(gb.z);
             float l = 0.f;
             if (flags == 0) {
@@ -350,7 +457,7 @@ __global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restr
             if (l > 0.f) {
 #pragma unroll
                 for (int b4 = 0; b4 < NB4; ++b4) {
-                    const float4 s = __ldg(S4 + (int64_t)b4 * n_rays + r);
+                    const float4 s = __ldg(S4 + b4 * nr + r);
                     acc[4 * b4 + 0] = __fmaf_rn(s.x, l, acc[4 * b4 + 0]);
                     acc[4 * b4 + 1] = __fmaf_rn(s.y, l, acc[4 * b4 + 1]);
                     acc[4 * b4 + 2] = __fmaf_rn(s.z, l, acc[4 * b4 + 2]);
@@ -370,7 +477,7 @@ __global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restr
 #pragma unroll
         for (int b = 0; b < Bp; ++b) {
             const int bb = chunk * Bp + b;
-            if ((b & 3) == sub && bb < batch) img[(int64_t)bb * n_pix + pix] = acc[b];
+            if ((b & 3) == sub && bb < batch) img[(int64_t)bb * n_pix + pix] = acc[b];  // once per pixel
         }
     }
 }
@@ -405,9 +512,32 @@ cudaError_t launch_project_fast2(const RayRec *rays, int64_t n_rays, int nx, int
     const int64_t threads = n_rays * lpr;
     const int64_t warps = (threads + 31) / 32;
     const dim3 grid((unsigned)((warps * 32 + block - 1) / block), (unsigned)((batch + Bp - 1) / Bp));
-    if (lpr == 4) fwd_fast2_kernel<4><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
-    else if (lpr == 2) fwd_fast2_kernel<2><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
-    else fwd_fast2_kernel<1><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
+    if (lpr == 4) fwd_fast2_kernel<4, false><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
+    else if (lpr == 2) fwd_fast2_kernel<2, false><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
+    else fwd_fast2_kernel<1, false><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, float *acc0,
+                                 float *acc1, size_t acc_bytes, int Bp, const float *sino, float *img, int batch,
+                                 int block, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(acc0, 0, acc_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc1, 0, acc_bytes, s);
+    if (e != cudaSuccess) return e;
+    const int lpr = Bp / 4;
+    const int64_t threads = n_rays * lpr;
+    const int64_t warps = (threads + 31) / 32;
+    const dim3 grid((unsigned)((warps * 32 + block - 1) / block), (unsigned)((batch + Bp - 1) / Bp));
+    float *sv = const_cast<float *>(sino);
+    if (lpr == 4) fwd_fast2_kernel<4, true><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, acc0, acc1, Bp, sv, batch);
+    else if (lpr == 2) fwd_fast2_kernel<2, true><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, acc0, acc1, Bp, sv, batch);
+    else fwd_fast2_kernel<1, true><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, acc0, acc1, Bp, sv, batch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t n = (int64_t)nx * ny * nz;
+    deinterleave_sum_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)((batch + Bp - 1) / Bp)), 256, 0, s>>>(
+        acc0, acc1, batch, nx, ny, nz, Bp, img);
     return cudaGetLastError();
 }
 

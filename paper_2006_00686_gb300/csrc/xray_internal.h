@@ -87,6 +87,9 @@ cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays,
                                    cudaStream_t s);
 cudaError_t launch_project_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
                                  const float *il1, int Bp, float *sino, int batch, int block, cudaStream_t s);
+cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, float *acc0,
+                                 float *acc1, size_t acc_bytes, int Bp, const float *sino, float *img, int batch,
+                                 int block, cudaStream_t s);
 cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, cudaStream_t s);
 size_t gather_rec_bytes();
 cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,

@@ -216,10 +216,11 @@ def test_batched_fast_path(name, batch):
     for b in range(batch):
         H.check_rays(g, yh[b], y_ref[b], scale[b], float(np.abs(f64[b]).max()), f"{name}[{b}] fast")
     yin = torch.from_numpy(y_ref.astype(np.float32).reshape(g.sino_shape(batch))).cuda()
-    z = P.adjoint(yin, method=2).cpu().numpy().reshape(batch, -1)
     z_ref = O.adjoint(g, y_ref.astype(np.float32).astype(np.float64))
-    for b in range(batch):
-        H.check_adjoint(z[b], z_ref[b], f"{name}[{b}] fast gather")
+    for method, what in ((2, "gather"), (1, "scatter")):
+        z = P.adjoint(yin, method=method).cpu().numpy().reshape(batch, -1)
+        for b in range(batch):
+            H.check_adjoint(z[b], z_ref[b], f"{name}[{b}] fast {what}")
     # the one-thread-per-ray kernels agree with the fast path
     P.set_tuning(batch_chunk=1)
     y1 = P.forward(f.cuda())
