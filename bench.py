@@ -306,7 +306,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--adjoint", default="scatter", choices=["gather", "scatter"])
+    ap.add_argument("--adjoint", default="gather", choices=["gather", "scatter"])
     ap.add_argument("--chunk", type=int, default=16)
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

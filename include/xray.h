@@ -99,11 +99,19 @@ typedef struct {
 typedef struct {
     int32_t block;         /* threads per block of the ray kernels (64..256, multiple of 32) */
     int32_t batch_chunk;   /* images walked together by one thread (1, 2, 4, 8 or 16);
-                              1 also disables the batched fast path */
+                              1 also disables the batched paths */
     int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER */
+    int32_t path;          /* batched path for 2D scans and batches >= 4: XR_PATH_TILED,
+                              XR_PATH_INTERLEAVED or XR_PATH_RAY (one thread per ray) */
 } xr_tuning;
 
 enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
+
+/* Batched paths.  TILED: a CTA stages a 32x32 tile of up to 16 images in shared memory and
+ * walks every ray of a group of views through it (2D scans).  INTERLEAVED: images are
+ * interleaved per unit in device workspace (xr_reserve) and 4 lanes walk each ray.
+ * RAY: one thread per ray. */
+enum { XR_PATH_AUTO = 0, XR_PATH_TILED = 1, XR_PATH_INTERLEAVED = 2, XR_PATH_RAY = 3 };
 
 /* Validate `desc`, allocate the handle and its ray table on the current CUDA device and run
  * the ray-setup kernel once (ray parameters from eq. 2Dparalleltofan(_2),

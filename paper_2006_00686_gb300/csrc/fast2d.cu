@@ -40,25 +40,31 @@ namespace xr {
 __global__ void interleave_images_kernel(const float *__restrict__ img, int batch, int nx, int ny, int nz,
                                          int Bp, float *__restrict__ il0, float *__restrict__ il1)
 {
-    const int64_t n = (int64_t)nx * ny * nz;
-    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    const int chunk = blockIdx.y;
-    const int i = (int)(u % nx);
-    const int64_t rest = u / nx;
-    const int j = (int)(rest % ny);
-    const int k = (int)(rest / ny);
+    // the grid covers the padded units: the zero border is rewritten on every call
     const int px = nx + 2 * XR_IL_PAD, py = ny + 2 * XR_IL_PAD;
     const int64_t np = (int64_t)px * py * nz;  // padded units per image
-    const int64_t o0 = ((int64_t)chunk * np + ((int64_t)k * py + j + XR_IL_PAD) * px + i + XR_IL_PAD) * Bp;
-    const int64_t o1 = ((int64_t)chunk * np + ((int64_t)k * px + i + XR_IL_PAD) * py + j + XR_IL_PAD) * Bp;
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= np) return;
+    const int chunk = blockIdx.y;
+    const int ip = (int)(u % px);
+    const int64_t rest = u / px;
+    const int jp = (int)(rest % py);
+    const int k = (int)(rest / py);
+    const int i = ip - XR_IL_PAD, j = jp - XR_IL_PAD;
+    const bool inside = i >= 0 && i < nx && j >= 0 && j < ny;
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t uu = inside ? ((int64_t)k * ny + j) * nx + i : 0;
+    const int64_t o0 = ((int64_t)chunk * np + u) * Bp;
+    const int64_t o1 = ((int64_t)chunk * np + ((int64_t)k * px + ip) * py + jp) * Bp;
     for (int b4 = 0; b4 < Bp; b4 += 4) {
-        float4 v;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         const int b = chunk * Bp + b4;
-        v.x = (b + 0 < batch) ? __ldg(img + (int64_t)(b + 0) * n + u) : 0.f;
-        v.y = (b + 1 < batch) ? __ldg(img + (int64_t)(b + 1) * n + u) : 0.f;
-        v.z = (b + 2 < batch) ? __ldg(img + (int64_t)(b + 2) * n + u) : 0.f;
-        v.w = (b + 3 < batch) ? __ldg(img + (int64_t)(b + 3) * n + u) : 0.f;
+        if (inside) {
+            v.x = (b + 0 < batch) ? __ldg(img + (int64_t)(b + 0) * n + uu) : 0.f;
+            v.y = (b + 1 < batch) ? __ldg(img + (int64_t)(b + 1) * n + uu) : 0.f;
+            v.z = (b + 2 < batch) ? __ldg(img + (int64_t)(b + 2) * n + uu) : 0.f;
+            v.w = (b + 3 < batch) ? __ldg(img + (int64_t)(b + 3) * n + uu) : 0.f;
+        }
         *reinterpret_cast<float4 *>(il0 + o0 + b4) = v;
         *reinterpret_cast<float4 *>(il1 + o1 + b4) = v;
     }
@@ -280,10 +286,15 @@ __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const
                 const float lc = fabsf(__fsub_rn(tcc1, t1)), ld = fabsf(__fsub_rn(t2, tcc1));
                 const float *p0 = pA + moff, *p1 = pA + moff + sA;
                 if (ADJ) {
-                    unit_op<true>(p0 + r0 * sB, act0, la, acc);
-                    unit_op<true>(p0 + r1 * sB, act0 && x01, lb, acc);
-                    unit_op<true>(p1 + r1 * sB, act1, lc, acc);
-                    unit_op<true>(p1 + r2 * sB, act1 && x12, ld, acc);
+                    // only units inside the image receive anything (the border stays clean)
+                    const unsigned NBu = bact ? (unsigned)W.NB : 1u;
+                    const int rb = bact ? W.oB : 0;
+                    const bool in0 = (unsigned)(rb + r0) < NBu, in1 = (unsigned)(rb + r1) < NBu,
+                               in2 = (unsigned)(rb + r2) < NBu;
+                    unit_op<true>(p0 + r0 * sB, act0 && in0, la, acc);
+                    unit_op<true>(p0 + r1 * sB, act0 && x01 && in1, lb, acc);
+                    unit_op<true>(p1 + r1 * sB, act1 && in1, lc, acc);
+                    unit_op<true>(p1 + r2 * sB, act1 && x12 && in2, ld, acc);
                 } else {
                     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                     const float4 va = act0 ? __ldg(reinterpret_cast<const float4 *>(p0 + r0 * sB)) : z;
@@ -489,10 +500,10 @@ __global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restr
 cudaError_t launch_interleave_images(const float *img, int batch, int nx, int ny, int nz, int Bp, float *il0,
                                      float *il1, cudaStream_t s)
 {
-    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t np = (int64_t)(nx + 2 * XR_IL_PAD) * (ny + 2 * XR_IL_PAD) * nz;
     const int chunks = (batch + Bp - 1) / Bp;
-    interleave_images_kernel<<<dim3((unsigned)((n + 255) / 256), chunks), 256, 0, s>>>(img, batch, nx, ny, nz, Bp,
-                                                                                      il0, il1);
+    interleave_images_kernel<<<dim3((unsigned)((np + 255) / 256), chunks), 256, 0, s>>>(img, batch, nx, ny, nz, Bp,
+                                                                                       il0, il1);
     return cudaGetLastError();
 }
 
@@ -567,6 +578,307 @@ cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoP
     else if (g.kind == XR_FAN2D) XR_GATHER_LAUNCH(XR_FAN2D);
     else XR_GATHER_LAUNCH(XR_FAN2D_ARC);
 #undef XR_GATHER_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace xr
+
+// =======================================================================================
+// Quad-plane layout: one thread per ray (forward) or per pixel (gather) for all images.
+//
+// The images of the batch (padded to a multiple of 4) are stored as planes of 4 images:
+// plane q holds images 4q..4q+3 as one float4 per unit, in the same two bordered spatial
+// orders as above (IL0: x fastest, IL1: y fastest).  A thread walking a ray loads one float4
+// per plane for every unit; the neighbouring rays of a warp load neighbouring float4s of
+// the same plane, so every 128-bit load instruction is coalesced across the warp.  The walk
+// geometry is computed once per ray for all images.
+// =======================================================================================
+
+namespace xr {
+
+// user images [B][nz][ny][nx] -> planes [Q][padded units][4] in both orders.  The grid
+// covers the padded units, so the zero border is rewritten on every call (the workspace is
+// shared with the scatter adjoint's accumulators).
+__global__ void interleave_planes_kernel(const float *__restrict__ img, int batch, int nx, int ny, int nz,
+                                         float *__restrict__ il0, float *__restrict__ il1)
+{
+    const int px = nx + 2 * XR_IL_PAD, py = ny + 2 * XR_IL_PAD;
+    const int64_t np = (int64_t)px * py * nz;
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // padded unit in IL0 order
+    if (u >= np) return;
+    const int q = blockIdx.y;  // plane
+    const int ip = (int)(u % px);
+    const int64_t rest = u / px;
+    const int jp = (int)(rest % py);
+    const int k = (int)(rest / py);
+    const int i = ip - XR_IL_PAD, j = jp - XR_IL_PAD;
+    const int64_t n = (int64_t)nx * ny * nz;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i >= 0 && i < nx && j >= 0 && j < ny) {
+        const int64_t uu = ((int64_t)k * ny + j) * nx + i;
+        const int b = 4 * q;
+        v.x = (b + 0 < batch) ? __ldg(img + (int64_t)(b + 0) * n + uu) : 0.f;
+        v.y = (b + 1 < batch) ? __ldg(img + (int64_t)(b + 1) * n + uu) : 0.f;
+        v.z = (b + 2 < batch) ? __ldg(img + (int64_t)(b + 2) * n + uu) : 0.f;
+        v.w = (b + 3 < batch) ? __ldg(img + (int64_t)(b + 3) * n + uu) : 0.f;
+    }
+    const int64_t o0 = (int64_t)q * np + u;
+    const int64_t o1 = (int64_t)q * np + ((int64_t)k * px + ip) * py + jp;
+    reinterpret_cast<float4 *>(il0)[o0] = v;
+    reinterpret_cast<float4 *>(il1)[o1] = v;
+}
+
+// Forward: one thread per ray, NQ planes (4*NQ images) per thread; blockIdx.y = group of
+// NQ planes.  il0/il1: plane layout; sino: user layout.
+template <int NQ>
+__global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plane_kernel(const RayRec *__restrict__ rays,
+                                                                           int64_t n_rays, int nx, int ny, int nz,
+                                                                           const float4 *__restrict__ il0,
+                                                                           const float4 *__restrict__ il1,
+                                                                           int n_planes, float *__restrict__ sino,
+                                                                           int batch)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q0 = blockIdx.y * NQ;
+    const int px = nx + 2 * XR_IL_PAD, py = ny + 2 * XR_IL_PAD;
+    const int np = px * py * nz;  // padded units per plane (< 2^31 / 4, checked by the host)
+
+    Walk W;
+    bool ok = false;
+    if (r < n_rays)
+        ok = walk_setup(rays[r], nx, ny, nz, 1, nx, (int64_t)nx * ny, W) && W.nact <= 2 &&
+             !(W.nact == 2 && W.axB == 2);
+    const bool general = (r < n_rays) && !ok;
+    const int axA0 = __shfl_sync(0xffffffffu, ok ? W.axA : 1, 0);
+    const bool y_fast = (axA0 == 0);
+    const int si = y_fast ? py : 1, sj = y_fast ? 1 : px, sk = px * py;
+    const float4 *il = (y_fast ? il1 : il0) + (int64_t)q0 * np + XR_IL_PAD * (si + sj);
+
+    float4 acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int wlo = __reduce_min_sync(0xffffffffu, ok ? W.mlo : INT_MAX);
+    const int whi = __reduce_max_sync(0xffffffffu, ok ? W.mhi : INT_MIN);
+    if (ok) {
+        const int sA = sel3(W.axA, si, sj, sk), sB = sel3(W.axB, si, sj, sk), sC = sel3(W.axC, si, sj, sk);
+        const float4 *pA = il + (W.oC * sC + W.oB * sB);
+        const float invA = W.invA, bA = W.bA, wB = W.wB, fB = W.fB, invB = W.invB, bB = W.bB;
+        const int mlo = W.mlo, mhi = W.mhi;
+        float p = (float)(wlo - W.oA);
+        float tcur = __fmaf_rn(p, invA, bA);
+        float sc = __fadd_rd(__fmaf_rn(wB, tcur, fB), kMagic);
+        float jc = __fadd_rn(sc, -kMagic);
+        int moff = wlo * sA;
+        for (int m = wlo; m <= whi; ++m, moff += sA) {
+            p += 1.0f;
+            const float tn = __fmaf_rn(p, invA, bA);
+            const float sn = __fadd_rd(__fmaf_rn(wB, tn, fB), kMagic);
+            const float jn = __fadd_rn(sn, -kMagic);
+            const int rc = __float_as_int(sc) - kMagicBits, rn = __float_as_int(sn) - kMagicBits;
+            const bool act = m >= mlo && m <= mhi;
+            if (fabsf(jn - jc) < 1.5f) {
+                const bool cross = rn != rc;
+                const float tc = __fmaf_rn(fmaxf(jc, jn), invB, bB);
+                const float tcc = cross ? fminf(fmaxf(tc, fminf(tcur, tn)), fmaxf(tcur, tn)) : tn;
+                const float lc = fabsf(__fsub_rn(tcc, tcur)), ln = fabsf(__fsub_rn(tn, tcc));
+                const float4 *pc = pA + moff + rc * sB, *pn = pA + moff + rn * sB;
+                const bool oc = act, on = act && cross;
+                float4 vc[NQ], vn[NQ];
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    vc[q] = oc ? __ldg(pc + (int64_t)q * np) : z;
+                    vn[q] = on ? __ldg(pn + (int64_t)q * np) : z;
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    fma4(acc[q], vc[q], lc);
+                    fma4(acc[q], vn[q], ln);
+                }
+            } else if (act) {
+                // crossing two rows (within rounding of a diagonal): per-candidate formula
+                const float tlo = W.sgA ? tn : tcur, thi = W.sgA ? tcur : tn;
+                const int jlo = (int)fminf(jc, jn), jhi = (int)fmaxf(jc, jn);
+                for (int j = jlo; j <= jhi; ++j) {
+                    const int jg = j + W.oB;
+                    if ((unsigned)jg >= (unsigned)W.NB) continue;
+                    const float qq = (float)j;
+                    const float tb0 = __fmaf_rn(qq + (float)W.sgB, invB, bB);
+                    const float tb1 = __fmaf_rn(qq + (float)(1 - W.sgB), invB, bB);
+                    const float l = __fsub_rn(fminf(thi, tb1), fmaxf(tlo, tb0));
+                    if (l > 0.f) {
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) fma4(acc[q], __ldg(pA + moff + j * sB + (int64_t)q * np), l);
+                    }
+                }
+            }
+            tcur = tn;
+            sc = sn;
+            jc = jn;
+        }
+    } else if (general) {
+        Walk W2;
+        if (walk_setup(rays[r], nx, ny, nz, si, sj, sk, W2)) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                Il4Visitor vis{reinterpret_cast<const float *>(il + (int64_t)q * np), make_float4(0.f, 0.f, 0.f, 0.f)};
+                // the visitor indexes floats: scale the unit strides by 4
+                Walk W4 = W2;
+                W4.sA *= 4;
+                W4.sB *= 4;
+                W4.sC *= 4;
+                W4.base *= 4;
+                walk(W4, vis);
+                acc[q] = vis.acc;
+            }
+        }
+    }
+    if (r < n_rays) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int b = 4 * (q0 + q);
+            if (b + 0 < batch) sino[(int64_t)(b + 0) * n_rays + r] = acc[q].x;
+            if (b + 1 < batch) sino[(int64_t)(b + 1) * n_rays + r] = acc[q].y;
+            if (b + 2 < batch) sino[(int64_t)(b + 2) * n_rays + r] = acc[q].z;
+            if (b + 3 < batch) sino[(int64_t)(b + 3) * n_rays + r] = acc[q].w;
+        }
+    }
+}
+
+// Gather adjoint for 2D scans: one thread per pixel, NQ planes per thread; sil: sinogram
+// planes [Q][n_rays][4] (interleave_sino_kernel with Bp = 4 * Q, one chunk); blockIdx.y =
+// group of NQ planes.  The ray's plane constants are read first; its sinogram values only
+// when the pixel's length is positive.
+template <int NQ, int KIND>
+__global__ void __launch_bounds__(256) gather_plane_kernel(const RayRec *__restrict__ rays,
+                                                           const GatherRec *__restrict__ grec, GeoParams g,
+                                                           const float *__restrict__ vt,
+                                                           const float4 *__restrict__ sil, int64_t n_rays,
+                                                           float *__restrict__ img, int batch)
+{
+    const int pix = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int n_pix = g.nx * g.ny;
+    const bool live = pix < n_pix;
+    const int i = live ? pix % g.nx : 0, j = live ? pix / g.nx : 0;
+    const int q0 = blockIdx.y * NQ;
+    const int nr = (int)n_rays;
+    const float4 *S = sil + (int64_t)q0 * nr;
+    const float4 *G4 = reinterpret_cast<const float4 *>(grec);
+    const float4 *V4 = reinterpret_cast<const float4 *>(vt);
+    float4 acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float xc = (float)(g.cx + (i + 0.5 - 0.5 * g.nx) * g.dx);
+    const float yc = (float)(g.cy + (0.5 * g.ny - j - 0.5) * g.dy);
+    const float hx = (float)(0.5 * g.dx), hy = (float)(0.5 * g.dy);
+    const float half = 0.5f * (float)(g.n_cols - 1);
+    const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0, sdd = (float)g.sdd;
+    const float fi = (float)i, fj = (float)j;
+    const int ncols = g.n_cols, nviews = live ? g.n_views : 0;
+    for (int v = 0, vbase = 0; v < nviews; ++v, vbase += ncols) {
+        const float4 e0 = __ldg(V4 + 2 * v);
+        const float4 e1 = __ldg(V4 + 2 * v + 1);
+        float umin, umax;
+        if (KIND == XR_PAR2D) {
+            const float uc = e0.x * xc + e0.y * yc, hw = fabsf(e0.x) * hx + fabsf(e0.y) * hy;
+            umin = uc - hw;
+            umax = uc + hw;
+        } else {
+            const float rx = xc - e0.x, ry = yc - e0.y;
+            const float depth = rx * e0.z + ry * e0.w, lat = rx * e1.x + ry * e1.y;
+            const float dd = fabsf(e0.z) * hx + fabsf(e0.w) * hy, dl = fabsf(e1.x) * hx + fabsf(e1.y) * hy;
+            const float r1 = __fdividef(1.0f, depth - dd), r2 = __fdividef(1.0f, depth + dd);
+            const float lo = lat - dl, hi = lat + dl;
+            const float a = fminf(lo * r1, lo * r2), b = fmaxf(hi * r1, hi * r2);
+            if (KIND == XR_FAN2D) {
+                umin = sdd * a;
+                umax = sdd * b;
+            } else {
+                umin = atanf(a);
+                umax = atanf(b);
+            }
+        }
+        const float c0f = fminf(fmaxf((umin - u0) * inv_du + half - 1e-3f, -1.0f), 4.0e6f);
+        const float c1f = fminf(fmaxf((umax - u0) * inv_du + half + 1e-3f, -1.0f), 4.0e6f);
+        const int c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
+        const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, ncols - 1);
+        for (int c = c0; c <= c1; ++c) {
+            const int r = vbase + c;
+            const float4 ga = __ldg(G4 + 2 * r);
+            const float4 gb = __ldg(G4 + 2 * r + 1);
+            const int flags = __float_as_int(gb.z);
+            float l = 0.f;
+            if (flags == 0) {
+                const float qx = fi - gb.x, qy = fj - gb.y;
+                const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
+                const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
+                l = __fsub_rn(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)));
+            } else if (flags == 2) {
+                Walk W;
+                if (walk_setup(rays[r], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
+                    l = walk_unit_length(W, i, j, 0);
+            }
+            if (l > 0.f) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) fma4(acc[q], __ldg(S + q * nr + r), l);
+            }
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int b = 4 * (q0 + q);
+            if (b + 0 < batch) img[(int64_t)(b + 0) * n_pix + pix] = acc[q].x;
+            if (b + 1 < batch) img[(int64_t)(b + 1) * n_pix + pix] = acc[q].y;
+            if (b + 2 < batch) img[(int64_t)(b + 2) * n_pix + pix] = acc[q].z;
+            if (b + 3 < batch) img[(int64_t)(b + 3) * n_pix + pix] = acc[q].w;
+        }
+    }
+}
+
+cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny, int nz, float *il0, float *il1,
+                                     cudaStream_t s)
+{
+    const int64_t np = (int64_t)(nx + 2 * XR_IL_PAD) * (ny + 2 * XR_IL_PAD) * nz;
+    const int Q = (batch + 3) / 4;
+    interleave_planes_kernel<<<dim3((unsigned)((np + 255) / 256), Q), 256, 0, s>>>(img, batch, nx, ny, nz, il0, il1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
+                                 const float *il1, float *sino, int batch, int nq, cudaStream_t s)
+{
+    const int Q = (batch + 3) / 4;
+    const int groups = (Q + nq - 1) / nq;
+    const dim3 grid((unsigned)((n_rays + 255) / 256), (unsigned)groups);
+    const float4 *a = reinterpret_cast<const float4 *>(il0), *b = reinterpret_cast<const float4 *>(il1);
+    if (nq == 4) fwd_plane_kernel<4><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch);
+    else if (nq == 2) fwd_plane_kernel<2><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch);
+    else fwd_plane_kernel<1><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
+                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s)
+{
+    const int Q = (batch + 3) / 4;
+    const int groups = (Q + nq - 1) / nq;
+    const int64_t n_pix = (int64_t)g.nx * g.ny;
+    const dim3 grid((unsigned)((n_pix + 255) / 256), (unsigned)groups);
+    const GatherRec *G = reinterpret_cast<const GatherRec *>(grec);
+    const float4 *S = reinterpret_cast<const float4 *>(sil);
+#define XR_GP(NQV, K) gather_plane_kernel<NQV, K><<<grid, 256, 0, s>>>(rays, G, g, vt, S, n_rays, img, batch)
+#define XR_GP_K(K)                 \
+    do {                           \
+        if (nq == 4) XR_GP(4, K);  \
+        else if (nq == 2) XR_GP(2, K); \
+        else XR_GP(1, K);          \
+    } while (0)
+    if (g.kind == XR_PAR2D) XR_GP_K(XR_PAR2D);
+    else if (g.kind == XR_FAN2D) XR_GP_K(XR_FAN2D);
+    else XR_GP_K(XR_FAN2D_ARC);
+#undef XR_GP_K
+#undef XR_GP
     return cudaGetLastError();
 }
 

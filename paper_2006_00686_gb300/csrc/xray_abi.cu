@@ -117,10 +117,26 @@ static size_t fast_ws_bytes(const xr_geometry *g, int batch)
 }
 
 // The batched fast path applies when the workspace holds the batch and the batch is >= 4.
+// Planes (of 4 images) one thread walks: the handle's batch_chunk / 4, at most what the batch needs.
+static int plane_nq(const xr_geometry *g, int batch)
+{
+    int nq = g->tune.batch_chunk >= 16 ? 4 : (g->tune.batch_chunk >= 8 ? 2 : 1);
+    const int Q = (batch + 3) / 4;
+    while (nq > 1 && nq > Q) nq >>= 1;
+    return nq;
+}
+
+// Tiled path: 2D scans, batches of 4 or more (no workspace needed).
+static bool use_tiled(const xr_geometry *g, int batch)
+{
+    return !kind_is3d(g->params.kind) && batch >= 4 && g->tune.batch_chunk != 1 && g->tune.path == XR_PATH_TILED;
+}
+
 static bool use_fast(const xr_geometry *g, int batch)
 {
     // the fast kernels index one chunk of interleaved images with 32-bit offsets
-    return batch >= 4 && batch <= g->ws_batch && g->tune.batch_chunk != 1 &&
+    return batch >= 4 && batch <= g->ws_batch && g->tune.batch_chunk != 1 && g->tune.path != XR_PATH_RAY &&
+           !use_tiled(g, batch) &&
            (int64_t)padded_units(g) * fast_chunk(batch) < ((int64_t)1 << 31) &&
            g->n_rays * fast_chunk(batch) < ((int64_t)1 << 31) && g->n_units < ((int64_t)1 << 31);
 }
@@ -172,9 +188,10 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     g->n_units = (int64_t)p.nx * p.ny * p.nz;
     g->tune.block = 128;
     g->tune.batch_chunk = 16;
-    // measured on GB300 (fan beam 512^2 x 16): the vector-atomic scatter of the batched fast
-    // path beats the unit-driven gather (3.0 vs 5.5 ms); the tuner may revise this per scan
-    g->tune.adjoint = XR_ADJ_SCATTER;
+    // measured on GB300 (fan beam 512^2 x 16, quad planes): gather 2.87 ms, vector-atomic
+    // scatter 2.94 ms; 3D scans have only the scatter.  The tuner may revise this per scan.
+    g->tune.adjoint = three ? XR_ADJ_SCATTER : XR_ADJ_GATHER;
+    g->tune.path = XR_PATH_INTERLEAVED;
 
     cudaError_t e = cudaGetDevice(&g->device);
     const size_t n_det = (size_t)p.n_rows * p.n_cols;
@@ -308,6 +325,8 @@ xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
         return XR_ERR_ARG;
     if (t->adjoint && t->adjoint != XR_ADJ_SCATTER && t->adjoint != XR_ADJ_GATHER) return XR_ERR_ARG;
     if (t->adjoint == XR_ADJ_GATHER && kind_is3d(g->params.kind)) return XR_ERR_ARG;
+    if (t->path < 0 || t->path > XR_PATH_RAY) return XR_ERR_ARG;
+    if (t->path) g->tune.path = t->path;
     if (t->block) g->tune.block = t->block;
     if (t->batch_chunk) g->tune.batch_chunk = t->batch_chunk;
     if (t->adjoint) g->tune.adjoint = t->adjoint;
@@ -326,15 +345,21 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
     if (!g || !d_img || !d_sino) return XR_ERR_NULL;
     if (batch < 1) return XR_ERR_BATCH;
     if (!aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
+    if (use_tiled(g, batch)) {
+        if ((batch + 3) / 4 > 65535) return XR_ERR_SIZE;
+        XR_CUDA(launch_tile2d(g->d_rays, g->params, g->d_view_tab, d_img, d_sino, batch, 0, (cudaStream_t)stream));
+        return XR_OK;
+    }
     if (use_fast(g, batch)) {
-        const int Bp = fast_chunk(batch);
-        if ((batch + Bp - 1) / Bp > 65535) return XR_ERR_SIZE;
-        const size_t padded = (size_t)((batch + Bp - 1) / Bp) * Bp;
+        // quad planes, one thread per ray for plane_nq(g) * 4 images
+        const int Q = (batch + 3) / 4;
+        if (Q > 65535) return XR_ERR_SIZE;
+        const size_t padded = (size_t)((batch + fast_chunk(batch) - 1) / fast_chunk(batch)) * fast_chunk(batch);
         float *il0 = g->d_ws, *il1 = g->d_ws + padded * padded_units(g);
         const cudaStream_t s = (cudaStream_t)stream;
-        XR_CUDA(launch_interleave_images(d_img, batch, g->params.nx, g->params.ny, g->params.nz, Bp, il0, il1, s));
-        XR_CUDA(launch_project_fast2(g->d_rays, g->n_rays, g->params.nx, g->params.ny, g->params.nz, il0, il1, Bp,
-                                     d_sino, batch, 256, s));
+        XR_CUDA(launch_interleave_planes(d_img, batch, g->params.nx, g->params.ny, g->params.nz, il0, il1, s));
+        XR_CUDA(launch_project_plane(g->d_rays, g->n_rays, g->params.nx, g->params.ny, g->params.nz, il0, il1, d_sino,
+                                     batch, plane_nq(g, batch), s));
         return XR_OK;
     }
     const int chunk = pick_chunk(g, batch);
@@ -357,12 +382,12 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if (method == XR_ADJ_GATHER) {
         if (kind_is3d(g->params.kind)) return XR_ERR_ARG;
         if (use_fast(g, batch)) {
-            const int Bp = fast_chunk(batch);
-            const size_t padded = (size_t)((batch + Bp - 1) / Bp) * Bp;
+            const int Q = (batch + 3) / 4;
+            const size_t padded = (size_t)((batch + fast_chunk(batch) - 1) / fast_chunk(batch)) * fast_chunk(batch);
             float *sil = g->d_ws + 2 * padded * padded_units(g);
-            XR_CUDA(launch_interleave_sino(d_sino, batch, g->n_rays, Bp, sil, s));
-            XR_CUDA(launch_gather_fast2(g->d_rays, g->d_grec, g->params, g->d_view_tab, sil, g->n_rays, d_img, batch,
-                                        Bp, 256, s));
+            XR_CUDA(launch_interleave_sino(d_sino, batch, g->n_rays, 4 * Q, sil, s));
+            XR_CUDA(launch_gather_plane(g->d_rays, g->d_grec, g->params, g->d_view_tab, sil, g->n_rays, d_img, batch,
+                                        plane_nq(g, batch), s));
             return XR_OK;
         }
         XR_CUDA(launch_backproject_gather2d(g->d_rays, g->params, make_grid(g), g->d_view_tab, d_sino, g->n_rays,
@@ -370,6 +395,11 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         return XR_OK;
     }
     if (method != XR_ADJ_SCATTER) return XR_ERR_ARG;
+    if (use_tiled(g, batch)) {
+        if ((batch + 3) / 4 > 65535) return XR_ERR_SIZE;
+        XR_CUDA(launch_tile2d(g->d_rays, g->params, g->d_view_tab, d_sino, d_img, batch, 1, s));
+        return XR_OK;
+    }
     if (use_fast(g, batch)) {
         // ray-driven scatter into two zeroed interleaved accumulators, then summed back
         const int Bp = fast_chunk(batch);

@@ -91,6 +91,19 @@ cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int
                                  float *acc1, size_t acc_bytes, int Bp, const float *sino, float *img, int batch,
                                  int block, cudaStream_t s);
 cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, cudaStream_t s);
+
+// Quad-plane layout kernels (fast2d.cu): one thread per ray / pixel for 4*nq images.
+cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny, int nz, float *il0, float *il1,
+                                     cudaStream_t s);
+cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
+                                 const float *il1, float *sino, int batch, int nq, cudaStream_t s);
+cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
+                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s);
+
+// Tiled forward / adjoint for 2D scans and batches (tile2d.cu); in: user-layout input,
+// out: user-layout output (cleared inside).
+cudaError_t launch_tile2d(const RayRec *rays, const GeoParams &g, const float *vt, const float *in, float *out,
+                          int batch, int adjoint, cudaStream_t s);
 size_t gather_rec_bytes();
 cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
                                 const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,

@@ -219,7 +219,9 @@ def test_projector_graph_replay_batch16():
     z.zero_()
     graph.replay()
     torch.cuda.synchronize()
-    assert torch.equal(y, ry) and torch.equal(z, rz)
+    # paths that reduce with atomics are equal up to the order of the float additions
+    assert float((y - ry).abs().max()) <= 1e-6 * float(ry.abs().max())
+    assert float((z - rz).abs().max()) <= 1e-6 * float(rz.abs().max())
 
 
 def test_fans_uneven_64_full_size():

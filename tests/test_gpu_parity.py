@@ -200,13 +200,17 @@ def test_batch_chunks_bitwise_identical():
         assert torch.equal(o, outs[0])
 
 
+@pytest.mark.parametrize("path", ["tiled", "interleaved"])
 @pytest.mark.parametrize("name", ["par2d_64", "fan2d_128"])
 @pytest.mark.parametrize("batch", [4, 5, 16, 20])
-def test_batched_fast_path(name, batch):
-    # interleaved images, 4 lanes per ray / per pixel: forward and gather adjoint vs oracle
+def test_batched_fast_path(name, batch, path):
+    # batched paths: shared-memory tiles, or interleaved images with 4 lanes per ray;
+    # forward, scatter and gather adjoints vs the oracle
+    from paper_2006_00686_gb300.xray import XR_PATH_INTERLEAVED, XR_PATH_TILED
     g = SMALL[name]()
     f = torch.stack([_phantom(g, 70 + b) for b in range(batch)])
     P = _proj(g)
+    P.set_tuning(path=XR_PATH_TILED if path == "tiled" else XR_PATH_INTERLEAVED)
     P.reserve(batch)
     y = P.forward(f.cuda())
     f64 = f.numpy().astype(np.float64).reshape(batch, -1)
@@ -311,3 +315,18 @@ def test_full_size_adjoint_view_subset(name):
         z2 = P.adjoint(torch.from_numpy(y).cuda(), method=1).cpu().numpy()
         H.check_adjoint(z2, z_ref, name + " scatter")
     P.close()
+
+
+@pytest.mark.parametrize("path", ["tiled", "interleaved"])
+def test_calls_do_not_interfere(path):
+    # a forward after an adjoint (which shares the handle's workspace) gives the same result
+    from paper_2006_00686_gb300.xray import XR_PATH_INTERLEAVED, XR_PATH_TILED
+    g = H.fan2d_small(128, 90)
+    P = _proj(g)
+    P.set_tuning(path=XR_PATH_TILED if path == "tiled" else XR_PATH_INTERLEAVED)
+    x = torch.stack([_phantom(g, 90 + b) for b in range(16)]).cuda()
+    y1 = P.forward(x)
+    for method in (1, 2):
+        P.adjoint(y1, method=method)
+        y2 = P.forward(x)
+        assert float((y2 - y1).abs().max()) <= 1e-6 * float(y1.abs().max())
