@@ -749,12 +749,22 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
 // planes [Q][n_rays][4] (interleave_sino_kernel with Bp = 4 * Q, one chunk); blockIdx.y =
 // group of NQ planes.  The ray's plane constants are read first; its sinogram values only
 // when the pixel's length is positive.
+// Length of pixel (fi, fj) on ray record (ga, gb): the pixel's t-interval along x and y
+// intersected (C_up - C_low with the plane values the walk uses).
+__device__ __forceinline__ float gather_len(const float4 ga, const float4 gb, float fi, float fj)
+{
+    const float qx = fi - gb.x, qy = fj - gb.y;
+    const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
+    const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
+    return __fsub_rn(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)));
+}
+
 template <int NQ, int KIND>
-__global__ void __launch_bounds__(256) gather_plane_kernel(const RayRec *__restrict__ rays,
-                                                           const GatherRec *__restrict__ grec, GeoParams g,
-                                                           const float *__restrict__ vt,
-                                                           const float4 *__restrict__ sil, int64_t n_rays,
-                                                           float *__restrict__ img, int batch)
+__global__ void __launch_bounds__(256, NQ >= 4 ? 2 : 3) gather_plane_kernel(const RayRec *__restrict__ rays,
+                                                              const GatherRec *__restrict__ grec, GeoParams g,
+                                                              const float *__restrict__ vt,
+                                                              const float4 *__restrict__ sil, int64_t n_rays,
+                                                              float *__restrict__ img, int batch)
 {
     const int pix = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int n_pix = g.nx * g.ny;
@@ -775,6 +785,7 @@ __global__ void __launch_bounds__(256) gather_plane_kernel(const RayRec *__restr
     const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0, sdd = (float)g.sdd;
     const float fi = (float)i, fj = (float)j;
     const int ncols = g.n_cols, nviews = live ? g.n_views : 0;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int v = 0, vbase = 0; v < nviews; ++v, vbase += ncols) {
         const float4 e0 = __ldg(V4 + 2 * v);
         const float4 e1 = __ldg(V4 + 2 * v + 1);
@@ -784,12 +795,15 @@ __global__ void __launch_bounds__(256) gather_plane_kernel(const RayRec *__restr
             umin = uc - hw;
             umax = uc + hw;
         } else {
+            // the projections of the pixel's four corners from the source (exact footprint)
             const float rx = xc - e0.x, ry = yc - e0.y;
             const float depth = rx * e0.z + ry * e0.w, lat = rx * e1.x + ry * e1.y;
-            const float dd = fabsf(e0.z) * hx + fabsf(e0.w) * hy, dl = fabsf(e1.x) * hx + fabsf(e1.y) * hy;
-            const float r1 = __fdividef(1.0f, depth - dd), r2 = __fdividef(1.0f, depth + dd);
-            const float lo = lat - dl, hi = lat + dl;
-            const float a = fminf(lo * r1, lo * r2), b = fmaxf(hi * r1, hi * r2);
+            const float dpx = hx * e0.z, dpy = hy * e0.w, dlx = hx * e1.x, dly = hy * e1.y;
+            const float a0 = __fdividef(lat - dlx - dly, depth - dpx - dpy);
+            const float a1 = __fdividef(lat + dlx - dly, depth + dpx - dpy);
+            const float a2 = __fdividef(lat - dlx + dly, depth - dpx + dpy);
+            const float a3 = __fdividef(lat + dlx + dly, depth + dpx + dpy);
+            const float a = fminf(fminf(a0, a1), fminf(a2, a3)), b = fmaxf(fmaxf(a0, a1), fmaxf(a2, a3));
             if (KIND == XR_FAN2D) {
                 umin = sdd * a;
                 umax = sdd * b;
@@ -802,25 +816,36 @@ __global__ void __launch_bounds__(256) gather_plane_kernel(const RayRec *__restr
         const float c1f = fminf(fmaxf((umax - u0) * inv_du + half + 1e-3f, -1.0f), 4.0e6f);
         const int c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
         const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, ncols - 1);
-        for (int c = c0; c <= c1; ++c) {
-            const int r = vbase + c;
-            const float4 ga = __ldg(G4 + 2 * r);
-            const float4 gb = __ldg(G4 + 2 * r + 1);
-            const int flags = __float_as_int(gb.z);
-            float l = 0.f;
-            if (flags == 0) {
-                const float qx = fi - gb.x, qy = fj - gb.y;
-                const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
-                const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
-                l = __fsub_rn(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)));
-            } else if (flags == 2) {
-                Walk W;
-                if (walk_setup(rays[r], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
-                    l = walk_unit_length(W, i, j, 0);
-            }
-            if (l > 0.f) {
+        // two bins per step: their records and sinogram values are requested together
+        for (int c = c0; c <= c1; c += 2) {
+            const int r0 = vbase + c;
+            const bool two = c + 1 <= c1;
+            const int r1 = two ? r0 + 1 : r0;
+            const float4 ga0 = __ldg(G4 + 2 * r0), gb0 = __ldg(G4 + 2 * r0 + 1);
+            const float4 ga1 = __ldg(G4 + 2 * r1), gb1 = __ldg(G4 + 2 * r1 + 1);
+            float4 s0[NQ], s1[NQ];
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) fma4(acc[q], __ldg(S + q * nr + r), l);
+            for (int q = 0; q < NQ; ++q) {
+                s0[q] = __ldg(S + q * nr + r0);
+                s1[q] = two ? __ldg(S + q * nr + r1) : z4;
+            }
+            const int f0 = __float_as_int(gb0.z), f1 = __float_as_int(gb1.z);
+            float l0 = f0 == 0 ? gather_len(ga0, gb0, fi, fj) : 0.f;
+            float l1 = (two && f1 == 0) ? gather_len(ga1, gb1, fi, fj) : 0.f;
+            if (f0 == 2 || (two && f1 == 2)) {
+                // a ray parallel to an axis: the walk's own unit length (rare)
+                Walk W;
+                if (f0 == 2 && walk_setup(rays[r0], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
+                    l0 = walk_unit_length(W, i, j, 0);
+                if (two && f1 == 2 && walk_setup(rays[r1], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
+                    l1 = walk_unit_length(W, i, j, 0);
+            }
+            l0 = l0 > 0.f ? l0 : 0.f;
+            l1 = l1 > 0.f ? l1 : 0.f;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                fma4(acc[q], s0[q], l0);
+                fma4(acc[q], s1[q], l1);
             }
         }
     }
