@@ -125,7 +125,7 @@ def _peaks():
 def run_ours(args, rank, world, local_rank):
     import torch
 
-    from paper_2006_00686_gb300 import inputs
+    from paper_2006_00686_gb300 import inputs, parallel
     from paper_2006_00686_gb300.xray import Projector, XR_ADJ_GATHER, XR_ADJ_SCATTER
 
     torch.cuda.set_device(local_rank)
@@ -135,7 +135,7 @@ def run_ours(args, rank, world, local_rank):
     P = Projector(g)
     tune = {"batch_chunk": args.chunk, "adjoint": XR_ADJ_GATHER if args.adjoint == "gather" else XR_ADJ_SCATTER}
     P.set_tuning(block=args.block, **tune)
-    x = inputs.phantom_batch(g, B, 10, seed0=200 + 16 * rank, device=str(dev))
+    x = inputs.phantom_batch(g, B, 10, seed0=parallel.rank_seeds(rank, B, 200)[0], device=str(dev))
     y = torch.empty(g.sino_shape(B), device=dev)
     z = torch.empty(g.image_shape(B), device=dev)
     flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MiB > L2
@@ -177,10 +177,7 @@ def run_ours(args, rank, world, local_rank):
     adj_ms = [c.elapsed_time(d) for a, b, c, d in recs]
     step_ms = [a.elapsed_time(d) for a, b, c, d in recs]
     ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = parallel.max_over_ranks(ms, dev)
     rays_step = g.n_rays * B
     value = rays_step * world / (ms * 1e-3) / 1e9
 
@@ -203,10 +200,7 @@ def run_ours(args, rank, world, local_rank):
         if k >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
     e2e = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = parallel.max_over_ranks(e2e, dev)
 
     # roofline of the dominant kernel.  The path is bound by
     # neither HBM (the images and sinograms stay in L2; DRAM traffic is within ~15% of the
