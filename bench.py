@@ -104,12 +104,11 @@ class ClockSampler:
 # our CUDA path
 # ----------------------------------------------------------------------------------------
 
-def _intersections(g, P, x):
-    """Sum over rays of the units each ray crosses (counted on the GPU by projecting a
-    constant image of ones through a unit-length indicator is not possible; use the sparse
-    rows of a sample of rays and scale)."""
+def _intersections(g, P, sample=4096):
+    """Sum over rays of the units each ray crosses, estimated from the sparse rows (the
+    walk's own unit lists) of a seeded sample of rays."""
     rng = np.random.default_rng(0)
-    rays = rng.choice(g.n_rays, size=4096, replace=False)
+    rays = rng.choice(g.n_rays, size=min(sample, g.n_rays), replace=False)
     rows = P.ray_units(rays)
     return float(np.mean([len(r[0]) for r in rows])) * g.n_rays
 
@@ -122,41 +121,33 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def run_ours(args, rank, world, local_rank):
+WORKLOADS = {
+    # name: (geometry builder in inputs, images per rank, shapes per phantom, phantom seed base,
+    #        description)
+    "fan2d_512x16": ("fan2d_512", 16, 10, 200, None),
+    "par2d_64": ("par2d_64", 1, 10, 1, "2D parallel 64x64, 90 views, 95 bins"),
+    "par3d_256_tilt": ("par3d_256_tilt", 1, 30, 3,
+                       "3D parallel 256^3, one tilt axis, 181 tilts -60..60 deg, 256x256 detector"),
+    "cone_512": ("cone_512", 1, 30, 4, "circular cone 512^3 (0.8,0.8,1.0) centre (10,-5,3), 720 views, "
+                 "1024x768 flat detector, sod 1000, sdd 1500"),
+    "helix_512x256": ("helix_512x256", 1, 30, 5, "helical cone 512x512x256, 4 turns x 720 views, pitch 1, "
+                      "736x64 flat detector, sod 600, sdd 1100"),
+    "fans_uneven_64": (None, 64, 10, 500, "64 uneven 2D fans (sides 128..1024, seed 5), one persistent "
+                       "launch each for forward and adjoint"),
+}
+
+
+def _events(n):
     import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
-    from paper_2006_00686_gb300 import inputs, parallel
-    from paper_2006_00686_gb300.xray import Projector, XR_ADJ_GATHER, XR_ADJ_SCATTER
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    g = inputs.fan2d_512()
-    B = inputs.FAN2D_BATCH
-    P = Projector(g)
-    tune = {"batch_chunk": args.chunk, "adjoint": XR_ADJ_GATHER if args.adjoint == "gather" else XR_ADJ_SCATTER}
-    P.set_tuning(block=args.block, **tune)
-    x = inputs.phantom_batch(g, B, 10, seed0=parallel.rank_seeds(rank, B, 200)[0], device=str(dev))
-    y = torch.empty(g.sino_shape(B), device=dev)
-    z = torch.empty(g.image_shape(B), device=dev)
-    flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MiB > L2
-    stream = torch.cuda.current_stream()
-
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-
-    def step(times=None):
-        e = [ev() for _ in range(4)] if times is not None else None
-        if e: e[0].record(stream)
-        P.ray_setup(stream)
-        if e: e[1].record(stream)
-        P.forward(x, out=y, stream=stream)
-        if e: e[2].record(stream)
-        P.adjoint(y, out=z, stream=stream)
-        if e: e[3].record(stream)
-        if times is not None:
-            times.append(e)
-
+def _timed_loop(step, args, flush, world, local_rank):
+    """W untimed steps, then K timed steps (L2 flushed before each, outside its events);
+    returns per-step lists of event pairs per phase, the clock summary and the wall time."""
+    import torch
     for _ in range(args.warmup):
-        step()
+        step(None)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -165,19 +156,108 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            flush.fill_(1.0)  # evict L2 between timed steps (outside the step's events)
+            flush.fill_(1.0)
             step(recs)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    return recs, clk.summary(), wall
+
+
+def _e2e(step, host_in, dev_in, dev_out, host_out, args, flush):
+    """Mean ms of one step with the pinned H2D copies of its inputs and the D2H copies of
+    its results inside the timed region."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        a, b = _events(2)
+        a.record(stream)
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        step(None)
+        for h, d in zip(host_out, dev_out):
+            h.copy_(d, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k >= args.warmup:
+            out.append(a.elapsed_time(b))
+    return float(np.mean(out))
+
+
+def _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic):
+    # The path is bound by neither HBM (for the 2D workloads the images and sinograms stay
+    # in L2) nor tensor cores: every unit costs scalar FP32 work.  "alu": achieved =
+    # algorithmic FP32 FLOP per launch / launch time, with per (ray, unit) intersection one
+    # subtraction for the length C_up - C_low and one FMA (2 FLOP) per image; peak = 152 SMs
+    # x 128 FP32 lanes x 2 FLOP x maximum SM clock.
+    n_int = _intersections(g, P)
+    flop = n_int * (1.0 + 2.0 * B)
+    achieved = flop / (dom_ms * 1e-3) / 1e12
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    compulsory = 4.0 * (g.n_units + g.n_rays) * B
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({peak_kind} max clock)",
+            "algorithmic_flop": flop, "intersections_per_image": n_int, "ms": round(dom_ms, 4),
+            "hbm": {"compulsory_bytes": compulsory, "achieved_gbs": round(compulsory / (dom_ms * 1e-3) / 1e9, 1),
+                    "gather_bytes": 4.0 * n_int * B,
+                    "gather_gbs": round(4.0 * n_int * B / (dom_ms * 1e-3) / 1e9, 1),
+                    "peak_gbs": peaks["hbm_gbs"]}}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2006_00686_gb300 import inputs, parallel
+    from paper_2006_00686_gb300.xray import Projector, XR_ADJ_GATHER, XR_ADJ_SCATTER
+
+    if args.workload == "fans_uneven_64":
+        return run_uneven(args, rank, world, local_rank)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    builder, B, n_shapes, seed, desc = WORKLOADS[args.workload]
+    g = getattr(inputs, builder)()
+    P = Projector(g)
+    tune = {}
+    if args.adjoint:
+        tune["adjoint"] = XR_ADJ_GATHER if args.adjoint == "gather" else XR_ADJ_SCATTER
+    if args.chunk:
+        tune["batch_chunk"] = args.chunk
+    P.set_tuning(block=args.block, **tune)
+    seed0 = parallel.rank_seeds(rank, B, seed)[0]
+    if B > 1:
+        x = inputs.phantom_batch(g, B, n_shapes, seed0=seed0, device=str(dev))
+    else:
+        x = inputs.phantom(g, n_shapes, seed0, device=str(dev)).float().contiguous()
+    bshape = B if B > 1 else None
+    y = torch.empty(g.sino_shape(bshape), device=dev)
+    z = torch.empty(g.image_shape(bshape), device=dev)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(recs):
+        e = _events(4) if recs is not None else None
+        if e: e[0].record(stream)
+        P.ray_setup(stream)
+        if e: e[1].record(stream)
+        P.forward(x, out=y, stream=stream)
+        if e: e[2].record(stream)
+        P.adjoint(y, out=z, stream=stream)
+        if e: e[3].record(stream)
+        if recs is not None:
+            recs.append(e)
+
+    recs, clocks, wall = _timed_loop(step, args, flush, world, local_rank)
     setup_ms = [a.elapsed_time(b) for a, b, c, d in recs]
     fwd_ms = [b.elapsed_time(c) for a, b, c, d in recs]
     adj_ms = [c.elapsed_time(d) for a, b, c, d in recs]
     step_ms = [a.elapsed_time(d) for a, b, c, d in recs]
-    ms = float(np.mean(step_ms))
-    ms = parallel.max_over_ranks(ms, dev)
+    ms = parallel.max_over_ranks(float(np.mean(step_ms)), dev)
     rays_step = g.n_rays * B
     value = rays_step * world / (ms * 1e-3) / 1e9
 
@@ -186,65 +266,202 @@ def run_ours(args, rank, world, local_rank):
     x_h = x.cpu().pin_memory()
     y_h = torch.empty(y.shape, pin_memory=True)
     z_h = torch.empty(z.shape, pin_memory=True)
-    e2e_ms = []
-    for k in range(args.warmup + args.steps):
-        flush.fill_(1.0)
-        a, b = ev(), ev()
-        a.record(stream)
-        x.copy_(x_h, non_blocking=True)
-        step()
-        y_h.copy_(y, non_blocking=True)
-        z_h.copy_(z, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        if k >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
-    e2e = float(np.mean(e2e_ms))
-    e2e = parallel.max_over_ranks(e2e, dev)
+    e2e = parallel.max_over_ranks(_e2e(step, [x_h], [x], [y, z], [y_h, z_h], args, flush), dev)
 
-    # roofline of the dominant kernel.  The path is bound by
-    # neither HBM (the images and sinograms stay in L2; DRAM traffic is within ~15% of the
-    # compulsory bytes) nor tensor cores: every unit costs scalar FP32 work.  "alu":
-    # achieved = algorithmic FP32 FLOP per launch / launch time, with per (ray, unit)
-    # intersection one subtraction for the length C_up - C_low and one FMA (2 FLOP) per
-    # image; peak = 152 SMs x 128 FP32 lanes x 2 FLOP x maximum SM clock.
     peaks, peak_kind = _peaks()
-    n_int = _intersections(g, P, x)
     fwd, adj = float(np.mean(fwd_ms)), float(np.mean(adj_ms))
     dom, dom_ms = ("forward", fwd) if fwd >= adj else ("adjoint", adj)
-    flop = n_int * (1.0 + 2.0 * B)
-    achieved = flop / (dom_ms * 1e-3) / 1e12
-    peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    compulsory = 4.0 * (g.n_units + g.n_rays) * B
+    method = "gather" if P.tuning()["adjoint"] == XR_ADJ_GATHER else "scatter"
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
     # forward and gather kernels, from one ncu capture of this workload
-    traffic = {("adjoint", "gather"): 58.6e6, ("forward", "gather"): 61.9e6,
-               ("forward", "scatter"): 61.9e6}.get((dom, args.adjoint))
-    roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
-                           f"({peak_kind} max clock)",
-            "algorithmic_flop": flop, "intersections_per_image": n_int, "ms": round(dom_ms, 4),
-            "hbm": {"compulsory_bytes": compulsory, "achieved_gbs": round(compulsory / (dom_ms * 1e-3) / 1e9, 1),
-                    "peak_gbs": peaks["hbm_gbs"]}}
+    traffic = None
+    if args.workload == "fan2d_512x16":
+        traffic = {("adjoint", "gather"): 58.6e6, ("forward", "gather"): 61.9e6,
+                   ("forward", "scatter"): 61.9e6}.get((dom, method))
+    roof = _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic)
 
+    extra = {}
+    if args.workload == "fan2d_512x16":
+        config = _config({"adjoint": method, "batch_chunk": P.tuning()["batch_chunk"], "block": args.block})
+        # per step: detector setup, ray setup, image interleave, forward walk, then either
+        # the scatter walk + its de-interleave (two accumulator memsets are not kernels)
+        # or the sinogram interleave + gather
+        launches = 6
+    else:
+        config = {"workload": args.workload, "geometry": desc, "image": list(g.image_shape()),
+                  "views": g.n_views, "detector": [g.n_rows, g.n_cols], "batch_per_gpu": B, "adjoint": method,
+                  "l2": "flushed between timed steps (256 MiB write)"}
+        # detector setup, ray setup, forward walk, adjoint walk (the scatter's zero fill is
+        # a memset, not a kernel)
+        launches = 4
+        if args.workload == "par3d_256_tilt":
+            extra = _autograd_and_sirt(P, x, y, args)
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random-ellipse phantoms)",
-           "config": _config({"adjoint": args.adjoint, "batch_chunk": args.chunk, "block": args.block}),
+           "config": config,
            "e2e": {"value": round(rays_step * world / (e2e * 1e-3) / 1e9, 4), "unit": UNIT,
                    "h2d_bytes_per_step": int(x.numel() * 4),
                    "d2h_bytes_per_step": int(y.numel() * 4 + z.numel() * 4), "ms_per_step": round(e2e, 4)},
-           # per step: detector setup, ray setup, image interleave, forward walk, then either
-           # the scatter walk + its de-interleave (two accumulator memsets are not kernels)
-           # or the sinogram interleave + gather
-           "gpu_launches": args.steps * 6,
+           "gpu_launches": args.steps * launches,
            "kernel_ms": {"ray_setup": round(float(np.mean(setup_ms)), 4), "forward": round(fwd, 4),
                          "adjoint": round(adj, 4)},
-           "clocks": clk.summary(), "roofline": roof, "wall_s": round(wall, 3)}
+           "clocks": clocks, "roofline": roof, "wall_s": round(wall, 3)}
+    if extra:
+        out["extra"] = extra
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(g, x[:B].cpu().numpy(), budget_s=args.cpu_budget)
+        xs = x if B > 1 else x[None]
+        out["cpu_baseline"] = cpu_baseline(g, xs.cpu().numpy(), budget_s=args.cpu_budget)
     P.close()
+    return out
+
+
+def _autograd_and_sirt(P, x, y, args):
+    """Differentiable forms on the same scan: one autograd forward + backward of
+    0.5 ||A x - b||^2, and one SIRT iteration replayed from a CUDA graph."""
+    import torch
+
+    from paper_2006_00686_gb300 import recon
+    from paper_2006_00686_gb300.xray import project
+
+    b = y.clone()
+    xr = torch.zeros_like(x, requires_grad=True)
+
+    def ad():
+        xr.grad = None
+        loss = 0.5 * (project(xr, P) - b).square().sum()
+        loss.backward()
+
+    for _ in range(3):
+        ad()
+    torch.cuda.synchronize()
+    a, e = _events(2)
+    n = max(3, min(args.steps, 10))
+    a.record()
+    for _ in range(n):
+        ad()
+    e.record()
+    e.synchronize()
+    ad_ms = a.elapsed_time(e) / n
+    s = recon.SIRT(P, b)
+    s.capture()
+    for _ in range(3):
+        s._graph.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(n):
+        s._graph.replay()
+    e.record()
+    e.synchronize()
+    sirt_ms = a.elapsed_time(e) / n
+    rays = P.geom.n_rays
+    return {"autograd_fwd_bwd_ms": round(ad_ms, 3),
+            "autograd_grays_s": round(rays / (ad_ms * 1e-3) / 1e9, 4),
+            "sirt_iter_ms_graph": round(sirt_ms, 3),
+            "sirt_grays_s": round(rays / (sirt_ms * 1e-3) / 1e9, 4)}
+
+
+def run_uneven(args, rank, world, local_rank):
+    """64 uneven fans: one persistent launch for all forwards and one for all adjoints,
+    against the plain form (one launch per problem and operator)."""
+    import torch
+
+    from paper_2006_00686_gb300 import inputs, parallel
+    from paper_2006_00686_gb300.xray import BatchPlan, Projector
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    _, n, n_shapes, seed, desc = WORKLOADS[args.workload]
+    geoms = inputs.fans_uneven(n)
+    Ps = [Projector(gq) for gq in geoms]
+    seeds = parallel.rank_seeds(rank, n, seed)
+    xs = [inputs.phantom(gq, n_shapes, s, device=str(dev)).float().contiguous() for gq, s in zip(geoms, seeds)]
+    ys = [torch.empty(gq.sino_shape(), device=dev) for gq in geoms]
+    zs = [torch.empty(gq.image_shape(), device=dev) for gq in geoms]
+    fwd_plan = BatchPlan(Ps, xs, ys, tile=args.tile, block=args.plan_block)
+    adj_plan = BatchPlan(Ps, zs, ys, tile=args.tile, block=args.plan_block)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)
+    stream = torch.cuda.current_stream()
+    rays_step = sum(gq.n_rays for gq in geoms)
+
+    def batched(recs):
+        e = _events(4) if recs is not None else None
+        if e: e[0].record(stream)
+        for p in Ps:
+            p.ray_setup(stream)
+        if e: e[1].record(stream)
+        fwd_plan.project(stream)
+        if e: e[2].record(stream)
+        adj_plan.backproject(stream)
+        if e: e[3].record(stream)
+        if recs is not None:
+            recs.append(e)
+
+    def plain(recs):
+        e = _events(4) if recs is not None else None
+        if e: e[0].record(stream)
+        for p in Ps:
+            p.ray_setup(stream)
+        if e: e[1].record(stream)
+        for p, xq, yq in zip(Ps, xs, ys):
+            p.forward(xq, out=yq, stream=stream)
+        if e: e[2].record(stream)
+        for p, yq, zq in zip(Ps, ys, zs):
+            p.adjoint(yq, out=zq, stream=stream)
+        if e: e[3].record(stream)
+        if recs is not None:
+            recs.append(e)
+
+    res = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        recs, clocks, wall = _timed_loop(fn, args, flush, world, local_rank)
+        ms = parallel.max_over_ranks(float(np.mean([a.elapsed_time(d) for a, b, c, d in recs])), dev)
+        res[name] = {"ms": ms, "clocks": clocks, "wall": wall,
+                     "setup": float(np.mean([a.elapsed_time(b) for a, b, c, d in recs])),
+                     "fwd": float(np.mean([b.elapsed_time(c) for a, b, c, d in recs])),
+                     "adj": float(np.mean([c.elapsed_time(d) for a, b, c, d in recs]))}
+    ms = res["batched"]["ms"]
+    value = rays_step * world / (ms * 1e-3) / 1e9
+    xh = [t.cpu().pin_memory() for t in xs]
+    yh = [torch.empty(t.shape, pin_memory=True) for t in ys]
+    zh = [torch.empty(t.shape, pin_memory=True) for t in zs]
+    e2e = parallel.max_over_ranks(_e2e(batched, xh, xs, ys + zs, yh + zh, args, flush), dev)
+    peaks, peak_kind = _peaks()
+    rb = res["batched"]
+    dom, dom_ms = ("forward", rb["fwd"]) if rb["fwd"] >= rb["adj"] else ("adjoint", rb["adj"])
+    n_int = sum(_intersections(gq, p, sample=256) for gq, p in zip(geoms, Ps))
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = n_int * 3.0 / (dom_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "batched " + dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({peak_kind} max clock)",
+            "algorithmic_flop": n_int * 3.0, "intersections": n_int, "ms": round(dom_ms, 4)}
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random-ellipse phantoms)",
+           "config": {"workload": args.workload, "geometry": desc, "problems": n,
+                      "sides": [gq.nx for gq in geoms][:8] + ["..."], "rays_per_step": rays_step,
+                      "tile": args.tile, "plan_block": args.plan_block,
+                      "l2": "flushed between timed steps (256 MiB write)"},
+           "e2e": {"value": round(rays_step * world / (e2e * 1e-3) / 1e9, 4), "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(t.numel() for t in xs) * 4),
+                   "d2h_bytes_per_step": int(sum(t.numel() for t in ys + zs) * 4), "ms_per_step": round(e2e, 4)},
+           # per step: 2 x 64 setup kernels, the batched forward, the adjoint's zero fill and
+           # the batched adjoint
+           "gpu_launches": args.steps * (2 * n + 3),
+           "kernel_ms": {"ray_setup": round(rb["setup"], 4), "forward": round(rb["fwd"], 4),
+                         "adjoint": round(rb["adj"], 4)},
+           "plain": {"value": round(rays_step * world / (res["plain"]["ms"] * 1e-3) / 1e9, 4),
+                     "ms_per_step": round(res["plain"]["ms"], 4),
+                     "kernel_ms": {"forward": round(res["plain"]["fwd"], 4), "adjoint": round(res["plain"]["adj"], 4)}},
+           "clocks": rb["clocks"], "roofline": roof, "wall_s": round(rb["wall"], 3)}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_uneven(geoms, xs, budget_s=args.cpu_budget)
+    fwd_plan.close()
+    adj_plan.close()
+    for p in Ps:
+        p.close()
     return out
 
 
@@ -263,11 +480,11 @@ def cpu_baseline(g, x_np, budget_s=15.0):
     from oracle import oracle as O
 
     f64 = x_np.reshape(x_np.shape[0], -1).astype(np.float64)
-    views = np.arange(0, g.n_views, 180)  # 4 views: probe the rate
+    views = np.arange(0, g.n_views, max(1, g.n_views // 4))[:4]  # probe the rate
     t0 = time.perf_counter()
     rays = _oracle_step(O, g, f64, views)
     dt = time.perf_counter() - t0
-    n = int(max(4, min(g.n_views, 4 * budget_s / max(dt, 1e-3))))
+    n = int(max(len(views), min(g.n_views, len(views) * budget_s / max(dt, 1e-3))))
     views = np.linspace(0, g.n_views - 1, n).round().astype(np.int64)
     t0 = time.perf_counter()
     rays = _oracle_step(O, g, f64, views)
@@ -277,49 +494,98 @@ def cpu_baseline(g, x_np, budget_s=15.0):
                       f"in float64 ({rays} rays, {dt:.1f} s)"}
 
 
+def _uneven_sample(O, geoms, imgs, n_views):
+    rays = 0
+    for gq, xq in zip(geoms, imgs):
+        views = np.linspace(0, gq.n_views - 1, n_views).round().astype(np.int64)
+        rays += _oracle_step(O, gq, xq.reshape(1, -1).astype(np.float64), views)
+    return rays
+
+
+def cpu_baseline_uneven(geoms, xs, budget_s=15.0):
+    from oracle import oracle as O
+
+    imgs = [t.cpu().numpy() for t in xs]
+    t0 = time.perf_counter()
+    _uneven_sample(O, geoms, imgs, 2)
+    dt = time.perf_counter() - t0
+    nv = int(max(2, min(geoms[0].n_views, 2 * budget_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    rays = _uneven_sample(O, geoms, imgs, nv)
+    dt = time.perf_counter() - t0
+    return {"value": round(rays / dt / 1e9, 9), "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{nv} of 720 views of each of the {len(geoms)} problems, forward+adjoint in float64 "
+                      f"({rays} rays, {dt:.1f} s)"}
+
+
 def run_reference(args, rank, world):
     from oracle import oracle as O
     from paper_2006_00686_gb300 import inputs
 
-    g = inputs.fan2d_512()
-    B = inputs.FAN2D_BATCH
-    x = inputs.phantom_batch(g, B, 10, seed0=200).numpy()
-    f64 = x.reshape(B, -1).astype(np.float64)
-    n_views = max(2, int(args.ref_views))
+    builder, B, n_shapes, seed, desc = WORKLOADS[args.workload]
+    if builder is None:
+        geoms = inputs.fans_uneven(B)
+        imgs = [inputs.phantom(gq, n_shapes, seed + q).numpy() for q, gq in enumerate(geoms)]
+        n_views = max(1, int(args.ref_views) // 8)
+
+        def sample(k):
+            return _uneven_sample(O, geoms, imgs, n_views)
+        what = f"{n_views} of 720 views of each of the {B} problems per step, forward+adjoint in float64"
+        config = {"workload": args.workload, "geometry": desc, "problems": B}
+    else:
+        g = getattr(inputs, builder)()
+        if B > 1:
+            x = inputs.phantom_batch(g, B, n_shapes, seed0=seed).numpy()
+        else:
+            x = inputs.phantom(g, n_shapes, seed).numpy()[None]
+        f64 = x.reshape(B, -1).astype(np.float64)
+        n_views = max(1, min(g.n_views, int(args.ref_views) if g.is3d is False else max(1, int(args.ref_views) // 8)))
+
+        def sample(k):
+            views = (np.arange(n_views) * (g.n_views // n_views) + k) % g.n_views
+            return _oracle_step(O, g, f64, views)
+        what = f"{n_views} of {g.n_views} views per step, all {B} images, forward+adjoint in float64"
+        config = _config({"sample": what}) if args.workload == "fan2d_512x16" else {
+            "workload": args.workload, "geometry": desc, "image": list(g.image_shape()), "views": g.n_views,
+            "detector": [g.n_rows, g.n_cols], "batch_per_gpu": B, "sample": what}
     times, rays = [], 0
     for k in range(args.warmup + args.steps):
-        views = (np.arange(n_views) * (g.n_views // n_views) + k) % g.n_views
         t0 = time.perf_counter()
-        rays = _oracle_step(O, g, f64, views)
+        rays = sample(k)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
     ms = 1e3 * float(np.mean(times))
     value = rays / (ms * 1e-3) / 1e9
-    sample = f"{n_views} of {g.n_views} views per step, all {B} images, forward+adjoint in float64"
     return {"impl": "reference", "metric": METRIC, "value": round(value, 9), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random-ellipse phantoms)",
-            "config": _config({"sample": sample}),
+            "config": config,
             "cpu_baseline": {"value": round(value, 9), "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": what},
             "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 100; 5 for the 3D scans)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--adjoint", default="gather", choices=["gather", "scatter"])
-    ap.add_argument("--chunk", type=int, default=16)
+    ap.add_argument("--workload", default="fan2d_512x16", choices=sorted(WORKLOADS))
+    ap.add_argument("--adjoint", default=None, choices=["gather", "scatter"],
+                    help="adjoint method (default: gather in 2D, scatter in 3D)")
+    ap.add_argument("--chunk", type=int, default=0, help="images per thread of the batched path")
     ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--tile", type=int, default=0, help="rays per work item of the persistent batch")
+    ap.add_argument("--plan-block", type=int, default=0, help="threads per CTA of the persistent batch")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-views", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.steps is None:
+        args.steps = 5 if args.workload in ("par3d_256_tilt", "cone_512", "helix_512x256") else 100
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

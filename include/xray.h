@@ -100,9 +100,13 @@ typedef struct {
     int32_t block;         /* threads per block of the ray kernels (64..256, multiple of 32) */
     int32_t batch_chunk;   /* images walked together by one thread (1, 2, 4, 8 or 16);
                               1 also disables the batched paths */
-    int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER */
-    int32_t path;          /* batched path for 2D scans and batches >= 4: XR_PATH_TILED,
-                              XR_PATH_INTERLEAVED or XR_PATH_RAY (one thread per ray) */
+    int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER; XR_ADJ_AUTO (the default):
+                              the gather on the 2D quad-plane path, the scatter elsewhere */
+    int32_t path;          /* 2D scans, batches >= 4: XR_PATH_TILED, XR_PATH_INTERLEAVED or
+                              XR_PATH_RAY (one thread per ray, several images per thread).
+                              3D scans: XR_PATH_RAY keeps the one-thread-per-ray kernels on
+                              the caller's layout; any other value takes the 3D fast path
+                              when a workspace is reserved */
 } xr_tuning;
 
 enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
@@ -129,13 +133,18 @@ void xr_geometry_destroy(xr_geometry *g);
 xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
 
 /* Reserve the handle's workspace for batches of up to max_batch images (allocates on the
- * handle's device and synchronises it; do this outside stream capture).  With a workspace,
- * xr_project and the gather adjoint take the batched fast path for batches of 4 or more:
- * the images (or sinograms) of each chunk of 16 are first interleaved so that one unit's
- * values sit in one 64-byte line, in two spatial orders (x fastest and y fastest), and each
- * ray is walked by 4 lanes that own 4 images each.  Without a workspace, or for larger
- * batches, the calls use the one-thread-per-ray kernels (same results).
+ * handle's device and synchronises it; do this outside stream capture).
+ * 2D scans: with a workspace, xr_project and the adjoint take the batched fast path for
+ * batches of 4 or more: the images (or sinograms) of each chunk of 16 are first
+ * interleaved so that one unit's values sit in one 64-byte line, in two spatial orders
+ * (x fastest and y fastest), and one thread walks each ray for up to 16 images.
  * Workspace bytes: 4 * padded_batch * (2 * (nx+4)(ny+4)nz + n_rays).
+ * 3D scans: the workspace is one [nz][nx][ny] copy of a volume (4 * n_units bytes, any
+ * batch); each image is copied into it and every ray reads whichever of the two layouts
+ * has its warp's neighbouring rays in neighbouring words; the scatter adjoint uses it as a
+ * second accumulator.
+ * Without a workspace, or for larger batches, the calls use the one-thread-per-ray kernels
+ * on the caller's layout (same lengths).
  * Errors: XR_ERR_NULL, XR_ERR_BATCH, XR_ERR_ALLOC, XR_ERR_CUDA. */
 xr_status xr_reserve(xr_geometry *g, int32_t max_batch);
 

@@ -74,8 +74,7 @@ __global__ void __launch_bounds__(256) project_kernel(const RayRec *__restrict__
     vis.nb = min(BC, batch - b0);
 #pragma unroll
     for (int b = 0; b < BC; ++b) vis.acc[b] = 0.f;
-    Walk W;
-    if (walk_setup(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, W)) walk(W, vis);
+    walk_ray(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, vis);
 #pragma unroll
     for (int b = 0; b < BC; ++b)
         if (b < vis.nb) sino[(b0 + b) * sino_bs + r] = vis.acc[b];
@@ -101,8 +100,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const RayRec *__restrict__
         any |= vis.g[b] != 0.f;
     }
     if (!any) return;
-    Walk W;
-    if (walk_setup(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, W)) walk(W, vis);
+    walk_ray(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, vis);
 }
 
 template <int BC>
@@ -259,8 +257,7 @@ __global__ void ray_units_kernel(const RayRec *__restrict__ rays, int64_t n_rays
         return;
     }
     ExportVisitor vis{idx + (int64_t)q * cap, len + (int64_t)q * cap, cap, 0};
-    Walk W;
-    if (walk_setup(rays[id], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, W)) walk(W, vis);
+    walk_ray(rays[id], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, vis);
     count[q] = vis.n;
 }
 
@@ -308,7 +305,6 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchItem *__restric
         for (int q = threadIdx.x; q < tile; q += blockDim.x) {
             const int64_t r = first + q;
             if (r >= P.n_rays) break;
-            Walk W;
             const int64_t sy = P.nx, sz = (int64_t)P.nx * P.ny;
             if (!ADJ) {
                 FwdVisitor<1> vis;
@@ -316,7 +312,7 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchItem *__restric
                 vis.bs = 0;
                 vis.nb = 1;
                 vis.acc[0] = 0.f;
-                if (walk_setup(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, W)) walk(W, vis);
+                walk_ray(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, P.three, vis);
                 P.sino[r] = vis.acc[0];
             } else {
                 ScatterVisitor<1> vis;
@@ -324,7 +320,7 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchItem *__restric
                 vis.bs = 0;
                 vis.nb = 1;
                 vis.g[0] = __ldg(P.sino + r);
-                if (vis.g[0] != 0.f && walk_setup(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, W)) walk(W, vis);
+                if (vis.g[0] != 0.f) walk_ray(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, P.three, vis);
             }
         }
     }

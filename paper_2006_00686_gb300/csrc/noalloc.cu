@@ -92,7 +92,7 @@ extern "C" xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t
         it.nx = g->params.nx;
         it.ny = g->params.ny;
         it.nz = g->params.nz;
-        it.pad = 0;
+        it.three = kind_is3d(g->params.kind);
         it.n_rays = g->n_rays;
         it.tile_begin = tiles;
         tiles += (g->n_rays + tile - 1) / tile;

@@ -25,7 +25,6 @@ static xr_status cuda_fail(cudaError_t e) { return xr_fail_cuda(e); }
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
-static bool kind_is3d(int k) { return k >= XR_PAR3D; }
 static bool kind_helical(int k) { return k == XR_HELIX || k == XR_HELIX_ARC; }
 static bool kind_divergent(int k) { return k == XR_FAN2D || k == XR_FAN2D_ARC || k >= XR_CONE; }
 static bool kind_flat(int k) { return k == XR_FAN2D || k == XR_CONE || k == XR_HELIX; }
@@ -65,6 +64,7 @@ static Grid make_grid(const xr_geometry *g)
     gr.nx = g->params.nx;
     gr.ny = g->params.ny;
     gr.nz = g->params.nz;
+    gr.three = kind_is3d(g->params.kind);
     gr.sx = 1;
     gr.sy = gr.nx;
     gr.sz = (int64_t)gr.nx * gr.ny;
@@ -135,10 +135,24 @@ static bool use_tiled(const xr_geometry *g, int batch)
 static bool use_fast(const xr_geometry *g, int batch)
 {
     // the fast kernels index one chunk of interleaved images with 32-bit offsets
-    return batch >= 4 && batch <= g->ws_batch && g->tune.batch_chunk != 1 && g->tune.path != XR_PATH_RAY &&
+    return !kind_is3d(g->params.kind) && batch >= 4 && batch <= g->ws_batch && g->tune.batch_chunk != 1 && g->tune.path != XR_PATH_RAY &&
            !use_tiled(g, batch) &&
            (int64_t)padded_units(g) * fast_chunk(batch) < ((int64_t)1 << 31) &&
            g->n_rays * fast_chunk(batch) < ((int64_t)1 << 31) && g->n_units < ((int64_t)1 << 31);
+}
+
+// 3D scans with a reserved workspace: the crossing-order walk over the image and its
+// [z][x][y] copy, one image at a time (32-bit offsets and ray ids).
+static bool use_fast3d(const xr_geometry *g)
+{
+    return kind_is3d(g->params.kind) && g->tune.path != XR_PATH_RAY && g->d_ws &&
+           g->ws_bytes >= (size_t)g->n_units * sizeof(float) && g->n_units < ((int64_t)1 << 31) &&
+           g->n_rays < ((int64_t)1 << 31);
+}
+
+static size_t reserve_bytes(const xr_geometry *g, int batch)
+{
+    return kind_is3d(g->params.kind) ? (size_t)g->n_units * sizeof(float) : fast_ws_bytes(g, batch);
 }
 
 extern "C" {
@@ -188,9 +202,11 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     g->n_units = (int64_t)p.nx * p.ny * p.nz;
     g->tune.block = 128;
     g->tune.batch_chunk = 16;
-    // measured on GB300 (fan beam 512^2 x 16, quad planes): gather 2.87 ms, vector-atomic
-    // scatter 2.94 ms; 3D scans have only the scatter.  The tuner may revise this per scan.
-    g->tune.adjoint = three ? XR_ADJ_SCATTER : XR_ADJ_GATHER;
+    // automatic: the gather on the batched quad-plane path (fan beam 512^2 x 16 on GB300:
+    // gather 2.32 ms, vector-atomic scatter 2.94 ms), the scatter elsewhere (one image: the
+    // per-pixel gather loops over every view and is many times slower).  3D scans have only
+    // the scatter.  The tuner may fix either per scan.
+    g->tune.adjoint = XR_ADJ_AUTO;
     g->tune.path = XR_PATH_INTERLEAVED;
 
     cudaError_t e = cudaGetDevice(&g->device);
@@ -280,7 +296,7 @@ xr_status xr_reserve(xr_geometry *g, int32_t max_batch)
     if (!g) return XR_ERR_NULL;
     if (max_batch < 1) return XR_ERR_BATCH;
     if (max_batch <= g->ws_batch) return XR_OK;
-    const size_t bytes = fast_ws_bytes(g, max_batch);
+    const size_t bytes = reserve_bytes(g, max_batch);
     int prev = 0;
     XR_CUDA(cudaGetDevice(&prev));
     XR_CUDA(cudaSetDevice(g->device));
@@ -350,6 +366,16 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
         XR_CUDA(launch_tile2d(g->d_rays, g->params, g->d_view_tab, d_img, d_sino, batch, 0, (cudaStream_t)stream));
         return XR_OK;
     }
+    if (use_fast3d(g)) {
+        const cudaStream_t s = (cudaStream_t)stream;
+        for (int b = 0; b < batch; ++b) {
+            const float *img = d_img + (size_t)b * g->n_units;
+            XR_CUDA(launch_transpose_xy(img, g->d_ws, g->params.nx, g->params.ny, g->params.nz, s));
+            XR_CUDA(launch_project3d(g->d_rays, g->n_rays, g->params.nx, g->params.ny, g->params.nz, img, g->d_ws,
+                                     d_sino + (size_t)b * g->n_rays, g->tune.block, s));
+        }
+        return XR_OK;
+    }
     if (use_fast(g, batch)) {
         // quad planes, one thread per ray for plane_nq(g) * 4 images
         const int Q = (batch + 3) / 4;
@@ -376,6 +402,9 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if (batch < 1) return XR_ERR_BATCH;
     if (!aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
     if (method == XR_ADJ_AUTO) method = g->tune.adjoint;
+    if (method == XR_ADJ_AUTO)
+        method = (!kind_is3d(g->params.kind) && !use_tiled(g, batch) && use_fast(g, batch)) ? XR_ADJ_GATHER
+                                                                                          : XR_ADJ_SCATTER;
     const int chunk = pick_chunk(g, batch);
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
     const cudaStream_t s = (cudaStream_t)stream;
@@ -395,6 +424,13 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         return XR_OK;
     }
     if (method != XR_ADJ_SCATTER) return XR_ERR_ARG;
+    if (use_fast3d(g)) {
+        for (int b = 0; b < batch; ++b)
+            XR_CUDA(launch_scatter3d(g->d_rays, g->n_rays, g->params.nx, g->params.ny, g->params.nz,
+                                     d_sino + (size_t)b * g->n_rays, d_img + (size_t)b * g->n_units, g->d_ws,
+                                     g->tune.block, s));
+        return XR_OK;
+    }
     if (use_tiled(g, batch)) {
         if ((batch + 3) / 4 > 65535) return XR_ERR_SIZE;
         XR_CUDA(launch_tile2d(g->d_rays, g->params, g->d_view_tab, d_sino, d_img, batch, 1, s));
@@ -472,7 +508,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         items[i].nx = g->params.nx;
         items[i].ny = g->params.ny;
         items[i].nz = g->params.nz;
-        items[i].pad = 0;
+        items[i].three = kind_is3d(g->params.kind);
         items[i].n_rays = g->n_rays;
         items[i].tile_begin = tiles;
         tiles += (g->n_rays + tile - 1) / tile;

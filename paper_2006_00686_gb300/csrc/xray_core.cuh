@@ -228,6 +228,175 @@ __device__ __forceinline__ void walk(const Walk &W, V &vis)
     else if (W.nact == 1) walk_run<1>(W, vis);
 }
 
+// ---------------------------------------------------------------------------------------
+// The 3D walk in crossing order.
+//
+// For a voxel, C_low is the largest of its three entering planes' t and C_up the smallest
+// of its three leaving planes' t (eq. conditions_3D_1).  Visiting the voxels in the order
+// the ray crosses planes gives both directly: C_low is the last plane crossed and C_up
+// the nearest plane ahead, one per axis.  So the walk keeps, per axis, the t of the
+// current voxel's leaving plane, takes the smallest, emits C_up - C_low when positive
+// (the condition C_low < C_up: a tie of two planes gives a voxel of zero length, which is
+// skipped), and steps that axis.  Every plane t is the same fused multiply-add
+// (plane index - o) * (1/w) + (-frac/w) as in the slab walk, so each (ray, voxel) length
+// is one well-defined float and the set of voxels is exactly those with C_low < C_up.
+// An axis with w = 0 keeps its fixed index and never crosses a plane (t = +inf).
+// ---------------------------------------------------------------------------------------
+
+template <class Off>
+struct Dda {
+    float t0, t1, t2;     // t of the current voxel's leaving plane per axis (+inf: inactive)
+    float q0, q1, q2;     // that plane's index minus the integer foot point, per axis
+    float s0, s1, s2;     // +1 or -1: direction of travel per axis
+    float i0, b0, i1, b1, i2, b2;  // plane t = fma(q, i, b)
+    int r0, r1, r2;       // voxels left along each axis before the ray leaves the volume
+    Off d0, d1, d2;       // signed offset step per axis
+    Off off;              // offset of the current voxel
+    float tcur;           // C_low of the current voxel
+};
+
+// Axis setup: plane constants and box entry/exit; false when the ray misses this axis's
+// slab (inactive axis with its fixed index outside the grid).
+__device__ __forceinline__ bool dda_axis(float w, float f, int o, int N, float &inv, float &b, float &tin,
+                                         float &tout)
+{
+    if (w == 0.f) {
+        inv = 0.f;
+        b = 0.f;
+        return (unsigned)o < (unsigned)N;
+    }
+    inv = __frcp_rn(w);
+    b = __fmul_rn(-f, inv);
+    const float ta = __fmaf_rn((float)(0 - o), inv, b);
+    const float tb = __fmaf_rn((float)(N - o), inv, b);
+    tin = fmaxf(tin, fminf(ta, tb));
+    tout = fminf(tout, fmaxf(ta, tb));
+    return true;
+}
+
+// The voxel of this axis containing the start of the walk (just after tin), its leaving
+// plane and the voxels left.  Unit n of the axis spans planes n and n + 1.
+template <class Off>
+__device__ __forceinline__ void dda_start(float w, float f, int o, int N, float inv, float b, float tin, Off stride,
+                                          float &t, float &q, float &s, int &rem, Off &d, Off &off)
+{
+    if (w == 0.f) {
+        t = INFINITY;
+        q = 0.f;
+        s = 0.f;
+        rem = 0;
+        d = 0;
+        off += (Off)o * stride;
+        return;
+    }
+    int n = (int)floorf(__fmaf_rn(w, tin, f)) + o;
+    if (w > 0.f) {
+        // want t(n) <= tin < t(n + 1)
+#pragma unroll
+        for (int it = 0; it < 2; ++it)
+            if (__fmaf_rn((float)(n + 1 - o), inv, b) <= tin) ++n;
+#pragma unroll
+        for (int it = 0; it < 2; ++it)
+            if (__fmaf_rn((float)(n - o), inv, b) > tin) --n;
+        n = min(max(n, 0), N - 1);
+        q = (float)(n + 1 - o);
+        s = 1.f;
+        rem = N - 1 - n;
+        d = stride;
+    } else {
+        // planes ordered the other way: want t(n + 1) <= tin < t(n)
+#pragma unroll
+        for (int it = 0; it < 2; ++it)
+            if (__fmaf_rn((float)(n - o), inv, b) <= tin) --n;
+#pragma unroll
+        for (int it = 0; it < 2; ++it)
+            if (__fmaf_rn((float)(n + 1 - o), inv, b) > tin) ++n;
+        n = min(max(n, 0), N - 1);
+        q = (float)(n - o);
+        s = -1.f;
+        rem = n;
+        d = -stride;
+    }
+    t = __fmaf_rn(q, inv, b);
+    off += (Off)n * stride;
+}
+
+// Prepare the walk; false when the ray crosses no voxel.
+template <class Off>
+__device__ __forceinline__ bool dda_setup(const RayRec &r, int nx, int ny, int nz, Off sx, Off sy, Off sz,
+                                          Dda<Off> &D)
+{
+    if (r.flags & RAY_MISS) return false;
+    if (r.w0 == 0.f && r.w1 == 0.f && r.w2 == 0.f) return false;
+    float tin = -INFINITY, tout = INFINITY;
+    if (!dda_axis(r.w0, r.f0, r.o0, nx, D.i0, D.b0, tin, tout)) return false;
+    if (!dda_axis(r.w1, r.f1, r.o1, ny, D.i1, D.b1, tin, tout)) return false;
+    if (!dda_axis(r.w2, r.f2, r.o2, nz, D.i2, D.b2, tin, tout)) return false;
+    if (!(tin < tout)) return false;
+    D.off = 0;
+    dda_start(r.w0, r.f0, r.o0, nx, D.i0, D.b0, tin, sx, D.t0, D.q0, D.s0, D.r0, D.d0, D.off);
+    dda_start(r.w1, r.f1, r.o1, ny, D.i1, D.b1, tin, sy, D.t1, D.q1, D.s1, D.r1, D.d1, D.off);
+    dda_start(r.w2, r.f2, r.o2, nz, D.i2, D.b2, tin, sz, D.t2, D.q2, D.s2, D.r2, D.d2, D.off);
+    D.tcur = tin;
+    return true;
+}
+
+// One voxel: its length (<= 0: not crossed) and offset; then step to the next voxel.
+// Returns false once the ray has left the volume (the returned voxel is still valid).
+// Every step that does not return false uses up one of r0 + r1 + r2, so the walk ends.
+template <class Off>
+__device__ __forceinline__ bool dda_step(Dda<Off> &D, Off &off, float &l)
+{
+    const float tn = fminf(D.t0, fminf(D.t1, D.t2));
+    l = __fsub_rn(tn, D.tcur);
+    off = D.off;
+    D.tcur = fmaxf(D.tcur, tn);
+    const bool c0 = D.t0 == tn, c1 = !c0 && D.t1 == tn, c2 = !c0 && !c1;
+    const int rem = c0 ? D.r0 : (c1 ? D.r1 : D.r2);
+    if (rem == 0) return false;
+    D.r0 -= c0;
+    D.r1 -= c1;
+    D.r2 -= c2;
+    D.off += c0 ? D.d0 : (c1 ? D.d1 : D.d2);
+    D.q0 += c0 ? D.s0 : 0.f;
+    D.q1 += c1 ? D.s1 : 0.f;
+    D.q2 += c2 ? D.s2 : 0.f;
+    const float n0 = __fmaf_rn(D.q0, D.i0, D.b0), n1 = __fmaf_rn(D.q1, D.i1, D.b1),
+                n2 = __fmaf_rn(D.q2, D.i2, D.b2);
+    D.t0 = c0 ? n0 : D.t0;
+    D.t1 = c1 ? n1 : D.t1;
+    D.t2 = c2 ? n2 : D.t2;
+    return true;
+}
+
+// Walk the ray: vis(offset, length) for every voxel with C_low < C_up, in crossing order.
+template <class Off, class V>
+__device__ __forceinline__ void dda_run(Dda<Off> &D, V &vis)
+{
+    for (;;) {
+        Off off;
+        float l;
+        const bool more = dda_step(D, off, l);
+        if (l > 0.f) vis(off, l);
+        if (!more) break;
+    }
+}
+
+// Either walk, by the scan's dimension: the slab walk for 2D scans, the crossing-order
+// walk for 3D scans.
+template <class V>
+__device__ __forceinline__ void walk_ray(const RayRec &r, int nx, int ny, int nz, int64_t sx, int64_t sy,
+                                         int64_t sz, bool three, V &vis)
+{
+    if (three) {
+        Dda<int64_t> D;
+        if (dda_setup<int64_t>(r, nx, ny, nz, sx, sy, sz, D)) dda_run(D, vis);
+    } else {
+        Walk W;
+        if (walk_setup(r, nx, ny, nz, sx, sy, sz, W)) walk(W, vis);
+    }
+}
+
 // Length of unit (i, j, k) exactly as walk_run computes it, or 0 when the walk does not
 // visit it.  Used by the unit-driven (gather) adjoint.
 __device__ __forceinline__ float walk_unit_length(const Walk &W, int i, int j, int k)

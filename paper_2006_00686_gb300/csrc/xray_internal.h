@@ -23,8 +23,11 @@ struct GeoParams {
 // Image extents and layout strides passed to the ray kernels.
 struct Grid {
     int nx, ny, nz;
+    int three;           // 1: a 3D scan (crossing-order walk), 0: 2D (slab walk)
     int64_t sx, sy, sz;  // element strides of i, j, k
 };
+
+inline bool kind_is3d(int k) { return k >= XR_PAR3D; }
 
 // Per detector sample: the parts of the ray parameters that depend on the detector only
 // (2D: s and cos/sin of gamma; 3D: s1, the detector part of s2, cos/sin of alpha and beta).
@@ -64,7 +67,7 @@ struct BatchItem {
     const float *img;
     float *sino;
     int nx, ny, nz;
-    int pad;
+    int three;  // 1: a 3D scan
     int64_t n_rays;
     int64_t tile_begin;  // first global tile index of this problem
 };
@@ -105,6 +108,14 @@ cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoP
 cudaError_t launch_tile2d(const RayRec *rays, const GeoParams &g, const float *vt, const float *in, float *out,
                           int batch, int adjoint, cudaStream_t s);
 size_t gather_rec_bytes();
+// Fast path for 3D scans (fast3d.cu): one thread per ray with the crossing-order walk,
+// reading the caller's image or its [z][x][y] copy by the ray's direction.
+cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_project3d(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *img,
+                             const float *imgT, float *sino, int block, cudaStream_t s);
+// Zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
+cudaError_t launch_scatter3d(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *sino,
+                             float *out, float *accT, int block, cudaStream_t s);
 cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
                                 const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
                                 cudaStream_t s);

@@ -185,7 +185,12 @@ class Projector:
         raise XRayError(f"{name} has shape {tuple(t.shape)}, expected {unit_shape} or (B,)+{unit_shape}")
 
     def _maybe_reserve(self, b: int):
-        if b >= 4 and b > self.reserved and self.auto_reserve and not torch.cuda.is_current_stream_capturing():
+        if not self.auto_reserve or torch.cuda.is_current_stream_capturing():
+            return
+        if self.geom.is3d:
+            if self.reserved < 1:  # one volume copy serves every batch size
+                self.reserve(1)
+        elif b >= 4 and b > self.reserved:
             self.reserve(b)
 
     def forward(self, img: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
