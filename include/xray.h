@@ -107,9 +107,15 @@ typedef struct {
                               3D scans: XR_PATH_RAY keeps the one-thread-per-ray kernels on
                               the caller's layout; any other value takes the 3D fast path
                               when a workspace is reserved */
+    int32_t order;         /* 3D fast path: the order threads take rays in.  XR_ORDER_VIEW:
+                              [view][row][col]; XR_ORDER_ROW: (row, view, col), so the rays in
+                              flight share detector rows across views; XR_ORDER_AUTO (the
+                              default): ROW for circular cones, VIEW otherwise */
 } xr_tuning;
 
 enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
+
+enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2 };
 
 /* Batched paths.  TILED: a CTA stages a 32x32 tile of up to 16 images in shared memory and
  * walks every ray of a group of views through it (2D scans).  INTERLEAVED: images are

@@ -150,6 +150,16 @@ static bool use_fast3d(const xr_geometry *g)
            g->n_rays < ((int64_t)1 << 31);
 }
 
+// Ray order of the 3D fast path: row-major for circular cones (a detector row crosses one
+// slab of z in every view), the ray order otherwise (a helix moves through z view by view;
+// a parallel scan's views each cross the whole volume).
+static int row_major(const xr_geometry *g)
+{
+    if (g->tune.order == XR_ORDER_ROW) return 1;
+    if (g->tune.order == XR_ORDER_VIEW) return 0;
+    return (g->params.kind == XR_CONE || g->params.kind == XR_CONE_ARC) ? 1 : 0;
+}
+
 static size_t reserve_bytes(const xr_geometry *g, int batch)
 {
     return kind_is3d(g->params.kind) ? (size_t)g->n_units * sizeof(float) : fast_ws_bytes(g, batch);
@@ -208,6 +218,7 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     // the scatter.  The tuner may fix either per scan.
     g->tune.adjoint = XR_ADJ_AUTO;
     g->tune.path = XR_PATH_INTERLEAVED;
+    g->tune.order = XR_ORDER_AUTO;
 
     cudaError_t e = cudaGetDevice(&g->device);
     const size_t n_det = (size_t)p.n_rows * p.n_cols;
@@ -342,6 +353,8 @@ xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
     if (t->adjoint && t->adjoint != XR_ADJ_SCATTER && t->adjoint != XR_ADJ_GATHER) return XR_ERR_ARG;
     if (t->adjoint == XR_ADJ_GATHER && kind_is3d(g->params.kind)) return XR_ERR_ARG;
     if (t->path < 0 || t->path > XR_PATH_RAY) return XR_ERR_ARG;
+    if (t->order < 0 || t->order > XR_ORDER_ROW) return XR_ERR_ARG;
+    if (t->order) g->tune.order = t->order;
     if (t->path) g->tune.path = t->path;
     if (t->block) g->tune.block = t->block;
     if (t->batch_chunk) g->tune.batch_chunk = t->batch_chunk;
@@ -371,7 +384,7 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
         for (int b = 0; b < batch; ++b) {
             const float *img = d_img + (size_t)b * g->n_units;
             XR_CUDA(launch_transpose_xy(img, g->d_ws, g->params.nx, g->params.ny, g->params.nz, s));
-            XR_CUDA(launch_project3d(g->d_rays, g->n_rays, g->params.nx, g->params.ny, g->params.nz, img, g->d_ws,
+            XR_CUDA(launch_project3d(g->d_rays, g->params, g->n_rays, row_major(g), img, g->d_ws,
                                      d_sino + (size_t)b * g->n_rays, g->tune.block, s));
         }
         return XR_OK;
@@ -426,9 +439,8 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if (method != XR_ADJ_SCATTER) return XR_ERR_ARG;
     if (use_fast3d(g)) {
         for (int b = 0; b < batch; ++b)
-            XR_CUDA(launch_scatter3d(g->d_rays, g->n_rays, g->params.nx, g->params.ny, g->params.nz,
-                                     d_sino + (size_t)b * g->n_rays, d_img + (size_t)b * g->n_units, g->d_ws,
-                                     g->tune.block, s));
+            XR_CUDA(launch_scatter3d(g->d_rays, g->params, g->n_rays, row_major(g), d_sino + (size_t)b * g->n_rays,
+                                     d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, s));
         return XR_OK;
     }
     if (use_tiled(g, batch)) {

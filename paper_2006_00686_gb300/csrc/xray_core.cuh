@@ -241,6 +241,12 @@ __device__ __forceinline__ void walk(const Walk &W, V &vis)
 // (plane index - o) * (1/w) + (-frac/w) as in the slab walk, so each (ray, voxel) length
 // is one well-defined float and the set of voxels is exactly those with C_low < C_up.
 // An axis with w = 0 keeps its fixed index and never crosses a plane (t = +inf).
+//
+// The walk ends at tout, the box's exit (the nearest of the three exit planes, computed
+// by the same expression as that plane's t in the walk).  Every voxel entered before tout
+// lies inside the grid: an index leaves its range only by crossing its axis's exit plane,
+// at a t >= tout.  From then on the clamped C_up = min(..., tout) equals C_low and every
+// length is 0, so nothing outside the grid is ever read or written.
 // ---------------------------------------------------------------------------------------
 
 template <class Off>
@@ -249,10 +255,10 @@ struct Dda {
     float q0, q1, q2;     // that plane's index minus the integer foot point, per axis
     float s0, s1, s2;     // +1 or -1: direction of travel per axis
     float i0, b0, i1, b1, i2, b2;  // plane t = fma(q, i, b)
-    int r0, r1, r2;       // voxels left along each axis before the ray leaves the volume
     Off d0, d1, d2;       // signed offset step per axis
     Off off;              // offset of the current voxel
     float tcur;           // C_low of the current voxel
+    float tout;           // exit from the grid
 };
 
 // Axis setup: plane constants and box entry/exit; false when the ray misses this axis's
@@ -274,17 +280,16 @@ __device__ __forceinline__ bool dda_axis(float w, float f, int o, int N, float &
     return true;
 }
 
-// The voxel of this axis containing the start of the walk (just after tin), its leaving
-// plane and the voxels left.  Unit n of the axis spans planes n and n + 1.
+// The voxel of this axis containing the start of the walk (just after tin) and its
+// leaving plane.  Unit n of the axis spans planes n and n + 1.
 template <class Off>
 __device__ __forceinline__ void dda_start(float w, float f, int o, int N, float inv, float b, float tin, Off stride,
-                                          float &t, float &q, float &s, int &rem, Off &d, Off &off)
+                                          float &t, float &q, float &s, Off &d, Off &off)
 {
     if (w == 0.f) {
         t = INFINITY;
         q = 0.f;
         s = 0.f;
-        rem = 0;
         d = 0;
         off += (Off)o * stride;
         return;
@@ -301,7 +306,6 @@ __device__ __forceinline__ void dda_start(float w, float f, int o, int N, float 
         n = min(max(n, 0), N - 1);
         q = (float)(n + 1 - o);
         s = 1.f;
-        rem = N - 1 - n;
         d = stride;
     } else {
         // planes ordered the other way: want t(n + 1) <= tin < t(n)
@@ -314,7 +318,6 @@ __device__ __forceinline__ void dda_start(float w, float f, int o, int N, float 
         n = min(max(n, 0), N - 1);
         q = (float)(n - o);
         s = -1.f;
-        rem = n;
         d = -stride;
     }
     t = __fmaf_rn(q, inv, b);
@@ -334,51 +337,52 @@ __device__ __forceinline__ bool dda_setup(const RayRec &r, int nx, int ny, int n
     if (!dda_axis(r.w2, r.f2, r.o2, nz, D.i2, D.b2, tin, tout)) return false;
     if (!(tin < tout)) return false;
     D.off = 0;
-    dda_start(r.w0, r.f0, r.o0, nx, D.i0, D.b0, tin, sx, D.t0, D.q0, D.s0, D.r0, D.d0, D.off);
-    dda_start(r.w1, r.f1, r.o1, ny, D.i1, D.b1, tin, sy, D.t1, D.q1, D.s1, D.r1, D.d1, D.off);
-    dda_start(r.w2, r.f2, r.o2, nz, D.i2, D.b2, tin, sz, D.t2, D.q2, D.s2, D.r2, D.d2, D.off);
+    dda_start(r.w0, r.f0, r.o0, nx, D.i0, D.b0, tin, sx, D.t0, D.q0, D.s0, D.d0, D.off);
+    dda_start(r.w1, r.f1, r.o1, ny, D.i1, D.b1, tin, sy, D.t1, D.q1, D.s1, D.d1, D.off);
+    dda_start(r.w2, r.f2, r.o2, nz, D.i2, D.b2, tin, sz, D.t2, D.q2, D.s2, D.d2, D.off);
     D.tcur = tin;
+    D.tout = tout;
     return true;
 }
 
-// One voxel: its length (<= 0: not crossed) and offset; then step to the next voxel.
-// Returns false once the ray has left the volume (the returned voxel is still valid).
-// Every step that does not return false uses up one of r0 + r1 + r2, so the walk ends.
+// Upper bound on the steps of one ray: one per voxel, at most nx + ny + nz + 1.
+__device__ __forceinline__ int dda_max_steps(int nx, int ny, int nz) { return nx + ny + nz + 2; }
+
+// One voxel: its length (0 once past the exit) and offset; then step to the next voxel.
+// Returns the axis stepped (0, 1, 2; 3 once past the exit).
 template <class Off>
-__device__ __forceinline__ bool dda_step(Dda<Off> &D, Off &off, float &l)
+__device__ __forceinline__ int dda_step(Dda<Off> &D, Off &off, float &l)
 {
-    const float tn = fminf(D.t0, fminf(D.t1, D.t2));
+    const float tn = fminf(fminf(D.t0, D.t1), fminf(D.t2, D.tout));
     l = __fsub_rn(tn, D.tcur);
     off = D.off;
     D.tcur = fmaxf(D.tcur, tn);
-    const bool c0 = D.t0 == tn, c1 = !c0 && D.t1 == tn, c2 = !c0 && !c1;
-    const int rem = c0 ? D.r0 : (c1 ? D.r1 : D.r2);
-    if (rem == 0) return false;
-    D.r0 -= c0;
-    D.r1 -= c1;
-    D.r2 -= c2;
-    D.off += c0 ? D.d0 : (c1 ? D.d1 : D.d2);
-    D.q0 += c0 ? D.s0 : 0.f;
-    D.q1 += c1 ? D.s1 : 0.f;
-    D.q2 += c2 ? D.s2 : 0.f;
-    const float n0 = __fmaf_rn(D.q0, D.i0, D.b0), n1 = __fmaf_rn(D.q1, D.i1, D.b1),
-                n2 = __fmaf_rn(D.q2, D.i2, D.b2);
-    D.t0 = c0 ? n0 : D.t0;
-    D.t1 = c1 ? n1 : D.t1;
-    D.t2 = c2 ? n2 : D.t2;
-    return true;
+    const bool c0 = D.t0 == tn, c1 = !c0 && D.t1 == tn, c2 = !c0 && !c1 && D.t2 == tn;
+    D.off += c0 ? D.d0 : (c1 ? D.d1 : (c2 ? D.d2 : (Off)0));
+    if (c0) {
+        D.q0 += D.s0;
+        D.t0 = __fmaf_rn(D.q0, D.i0, D.b0);
+    }
+    if (c1) {
+        D.q1 += D.s1;
+        D.t1 = __fmaf_rn(D.q1, D.i1, D.b1);
+    }
+    if (c2) {
+        D.q2 += D.s2;
+        D.t2 = __fmaf_rn(D.q2, D.i2, D.b2);
+    }
+    return c0 ? 0 : (c1 ? 1 : (c2 ? 2 : 3));
 }
 
 // Walk the ray: vis(offset, length) for every voxel with C_low < C_up, in crossing order.
 template <class Off, class V>
-__device__ __forceinline__ void dda_run(Dda<Off> &D, V &vis)
+__device__ __forceinline__ void dda_run(Dda<Off> &D, int max_steps, V &vis)
 {
-    for (;;) {
+    for (int k = 0; k < max_steps && D.tcur < D.tout; ++k) {
         Off off;
         float l;
-        const bool more = dda_step(D, off, l);
+        dda_step(D, off, l);
         if (l > 0.f) vis(off, l);
-        if (!more) break;
     }
 }
 
@@ -390,7 +394,7 @@ __device__ __forceinline__ void walk_ray(const RayRec &r, int nx, int ny, int nz
 {
     if (three) {
         Dda<int64_t> D;
-        if (dda_setup<int64_t>(r, nx, ny, nz, sx, sy, sz, D)) dda_run(D, vis);
+        if (dda_setup<int64_t>(r, nx, ny, nz, sx, sy, sz, D)) dda_run(D, dda_max_steps(nx, ny, nz), vis);
     } else {
         Walk W;
         if (walk_setup(r, nx, ny, nz, sx, sy, sz, W)) walk(W, vis);

@@ -111,11 +111,12 @@ size_t gather_rec_bytes();
 // Fast path for 3D scans (fast3d.cu): one thread per ray with the crossing-order walk,
 // reading the caller's image or its [z][x][y] copy by the ray's direction.
 cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int nz, cudaStream_t s);
-cudaError_t launch_project3d(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *img,
-                             const float *imgT, float *sino, int block, cudaStream_t s);
+// row_major: threads run over (row, view, col) instead of the ray order.
+cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
+                             const float *img, const float *imgT, float *sino, int block, cudaStream_t s);
 // Zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
-cudaError_t launch_scatter3d(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *sino,
-                             float *out, float *accT, int block, cudaStream_t s);
+cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
+                             const float *sino, float *out, float *accT, int block, cudaStream_t s);
 cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
                                 const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
                                 cudaStream_t s);

@@ -70,19 +70,32 @@ def _time(fn, reps: int, budget_s: float) -> float:
 
 def projector_candidates(g, batch: int) -> list:
     out = []
+    if g.is3d:
+        # the volume-copy path in either ray order, then the caller's layout
+        for order in (X.XR_ORDER_VIEW, X.XR_ORDER_ROW):
+            for block in (128, 256):
+                out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=X.XR_ADJ_SCATTER, block=block,
+                                order=order))
+        out.append(dict(path=X.XR_PATH_RAY, batch_chunk=min(16, max(1, batch)), adjoint=X.XR_ADJ_SCATTER,
+                        block=128, order=X.XR_ORDER_VIEW))
+        return out
     if batch >= 4:
         for chunk in (16, 8, 4):
             if chunk > 4 * ((batch + 3) // 4) and chunk != 4:
                 continue
-            for adj in ((X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER) if not g.is3d else (X.XR_ADJ_SCATTER,)):
+            for adj in (X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER):
                 out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=chunk, adjoint=adj, block=128))
-        if not g.is3d:
-            out.append(dict(path=X.XR_PATH_TILED, batch_chunk=16, adjoint=X.XR_ADJ_SCATTER, block=128))
+        out.append(dict(path=X.XR_PATH_TILED, batch_chunk=16, adjoint=X.XR_ADJ_SCATTER, block=128))
     for block in (128, 256):
-        for adj in ((X.XR_ADJ_SCATTER, X.XR_ADJ_GATHER) if not g.is3d else (X.XR_ADJ_SCATTER,)):
+        for adj in (X.XR_ADJ_SCATTER, X.XR_ADJ_GATHER):
             out.append(dict(path=X.XR_PATH_RAY, batch_chunk=1 if batch < 4 else min(16, batch), adjoint=adj,
                             block=block))
     return out
+
+
+def _apply(P, c):
+    P.set_tuning(block=c["block"], batch_chunk=c["batch_chunk"], adjoint=c["adjoint"], path=c["path"],
+                 order=c.get("order", 0))
 
 
 def tune_projector(P: "X.Projector", batch: int, cache_path: str | None = None, reps: int = 5,
@@ -94,26 +107,25 @@ def tune_projector(P: "X.Projector", batch: int, cache_path: str | None = None, 
     cache = _load(cache_path)
     if key in cache:
         best = cache[key]
-        P.set_tuning(block=best["block"], batch_chunk=best["batch_chunk"], adjoint=best["adjoint"],
-                     path=best["path"])
+        _apply(P, best)
         return best
     dev = P.device
     if x is None:
         x = torch.rand(g.image_shape(batch if batch > 1 else None), device=dev)
     y = torch.empty(g.sino_shape(batch if batch > 1 else None), device=dev)
     z = torch.empty_like(x)
-    if batch >= 4:
-        P.reserve(batch)
+    if batch >= 4 or g.is3d:
+        P.reserve(max(batch, 1))
     results = []
     for c in projector_candidates(g, batch):
-        P.set_tuning(block=c["block"], batch_chunk=c["batch_chunk"], adjoint=c["adjoint"], path=c["path"])
+        _apply(P, c)
         f_ms = _time(lambda: P.forward(x, out=y), reps, budget_s)
         a_ms = _time(lambda: P.adjoint(y, out=z), reps, budget_s)
         results.append(dict(c, forward_ms=f_ms, adjoint_ms=a_ms))
         if verbose:
             print("tune", key, results[-1], flush=True)
     best = min(results, key=lambda r: r["forward_ms"] + r["adjoint_ms"])
-    P.set_tuning(block=best["block"], batch_chunk=best["batch_chunk"], adjoint=best["adjoint"], path=best["path"])
+    _apply(P, best)
     cache = _load(cache_path)
     cache[key] = best
     _store(cache_path, cache)

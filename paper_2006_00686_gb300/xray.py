@@ -18,6 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libxray.so")
 
 XR_ADJ_AUTO, XR_ADJ_SCATTER, XR_ADJ_GATHER = 0, 1, 2
+XR_ORDER_AUTO, XR_ORDER_VIEW, XR_ORDER_ROW = 0, 1, 2
 XR_PATH_AUTO, XR_PATH_TILED, XR_PATH_INTERLEAVED, XR_PATH_RAY = 0, 1, 2, 3
 
 
@@ -46,7 +47,7 @@ class _Info(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("batch_chunk", ctypes.c_int32), ("adjoint", ctypes.c_int32),
-                ("path", ctypes.c_int32)]
+                ("path", ctypes.c_int32), ("order", ctypes.c_int32)]
 
 
 class _Problem(ctypes.Structure):
@@ -159,14 +160,15 @@ class Projector:
             pass
 
     # -- tuning ---------------------------------------------------------------------------
-    def set_tuning(self, block: int = 0, batch_chunk: int = 0, adjoint: int = 0, path: int = 0):
-        t = _Tuning(block, batch_chunk, adjoint, path)
+    def set_tuning(self, block: int = 0, batch_chunk: int = 0, adjoint: int = 0, path: int = 0, order: int = 0):
+        t = _Tuning(block, batch_chunk, adjoint, path, order)
         _check(lib().xr_set_tuning(self._h, ctypes.byref(t)), "xr_set_tuning")
 
     def tuning(self) -> dict:
         t = _Tuning()
         _check(lib().xr_get_tuning(self._h, ctypes.byref(t)), "xr_get_tuning")
-        return {"block": t.block, "batch_chunk": t.batch_chunk, "adjoint": t.adjoint, "path": t.path}
+        return {"block": t.block, "batch_chunk": t.batch_chunk, "adjoint": t.adjoint, "path": t.path,
+                "order": t.order}
 
     def reserve(self, max_batch: int):
         """Reserve the batched fast path's workspace (allocates; not during graph capture)."""
