@@ -378,6 +378,14 @@ def run_uneven(args, rank, world, local_rank):
     xs = [inputs.phantom(gq, n_shapes, s, device=str(dev)).float().contiguous() for gq, s in zip(geoms, seeds)]
     ys = [torch.empty(gq.sino_shape(), device=dev) for gq in geoms]
     zs = [torch.empty(gq.image_shape(), device=dev) for gq in geoms]
+    for p, xq, yq, zq in zip(Ps, xs, ys, zs):  # workspaces of the plain form, outside the timing
+        p.forward(xq, out=yq)
+        p.adjoint(yq, out=zq)
+    tuned = None
+    if not args.tile and not args.plan_block:  # the autotuner picks the plan's work items
+        from paper_2006_00686_gb300 import tune as T
+        tuned = T.tune_batch_plan(Ps, xs, ys)
+        args.tile, args.plan_block = tuned["tile"], tuned["block"]
     fwd_plan = BatchPlan(Ps, xs, ys, tile=args.tile, block=args.plan_block)
     adj_plan = BatchPlan(Ps, zs, ys, tile=args.tile, block=args.plan_block)
     flush = torch.empty(64 * 1024 * 1024, device=dev)
@@ -443,6 +451,7 @@ def run_uneven(args, rank, world, local_rank):
            "config": {"workload": args.workload, "geometry": desc, "problems": n,
                       "sides": [gq.nx for gq in geoms][:8] + ["..."], "rays_per_step": rays_step,
                       "tile": args.tile, "plan_block": args.plan_block,
+                      "plan_tuning": "autotuned" if tuned else "given",
                       "l2": "flushed between timed steps (256 MiB write)"},
            "e2e": {"value": round(rays_step * world / (e2e * 1e-3) / 1e9, 4), "unit": UNIT,
                    "h2d_bytes_per_step": int(sum(t.numel() for t in xs) * 4),

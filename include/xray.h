@@ -101,7 +101,8 @@ typedef struct {
     int32_t batch_chunk;   /* images walked together by one thread (1, 2, 4, 8 or 16);
                               1 also disables the batched paths */
     int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER; XR_ADJ_AUTO (the default):
-                              the gather on the 2D quad-plane path, the scatter elsewhere */
+                              2D scans: the gather on the quad-plane path, the scatter
+                              elsewhere; 3D scans: the gather */
     int32_t path;          /* 2D scans, batches >= 4: XR_PATH_TILED, XR_PATH_INTERLEAVED or
                               XR_PATH_RAY (one thread per ray, several images per thread).
                               3D scans: XR_PATH_RAY keeps the one-thread-per-ray kernels on
@@ -172,8 +173,11 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
 xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img, int32_t batch,
                          xr_stream stream);
 
-/* As xr_backproject with an explicit method (XR_ADJ_SCATTER / XR_ADJ_GATHER).
- * XR_ADJ_GATHER is available for 2D kinds; elsewhere it returns XR_ERR_ARG. */
+/* As xr_backproject with an explicit method.  XR_ADJ_SCATTER: ray-driven, each ray adds
+ * l * g to every unit it crosses (atomics).  XR_ADJ_GATHER: unit-driven; 2D scans: one thread
+ * per pixel sums the rays whose detector footprint covers it; 3D scans: one CTA per 16^3
+ * tile of voxels walks every ray of the tile's detector footprint through the tile and sums
+ * in shared memory.  All give the same (ray, unit) lengths. */
 xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float *d_img,
                                 int32_t batch, int32_t method, xr_stream stream);
 

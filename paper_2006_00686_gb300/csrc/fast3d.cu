@@ -1,5 +1,6 @@
-// Fast path for 3D scans: one thread per ray, the crossing-order walk, and a second copy
-// of the volume with y fastest.
+// Fast path for single images (3D scans, and 2D scans outside the batched quad-plane
+// path) and for persistent launches over uneven problems: one thread per ray, the
+// crossing-order walk, and a second copy of the image with y fastest.
 //
 // A warp holds 32 neighbouring detector columns of one row; their rays run side by side,
 // spread across the horizontal direction perpendicular to the beam.  When the beam runs
@@ -75,16 +76,12 @@ struct RayOrder {
     }
 };
 
+// Forward sum of one ray; imgT may be NULL (then every ray reads img).
 template <int U>
-__global__ void __launch_bounds__(256) fwd3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
-                                                    int nx, int ny, int nz, const float *__restrict__ img,
-                                                    const float *__restrict__ imgT, float *__restrict__ sino)
+__device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
+                                         const float *__restrict__ imgT)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_rays) return;
-    const int r = ord.ray(t);
-    const RayRec rr = rays[r];
-    const bool tr = leans_x(rr);
+    const bool tr = imgT != nullptr && leans_x(rr);
     const float *__restrict__ base = tr ? imgT : img;
     Dda<int> D;
     float acc = 0.f;
@@ -102,24 +99,24 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(const RayRec *__restrict__ r
             for (int u = 0; u < U; ++u) acc = __fmaf_rn(v[u], l[u], acc);  // + 0 where l == 0
         }
     }
-    sino[r] = acc;
+    return acc;
 }
 
-// Adjoint: one RED per (ray, voxel).  As in the forward, U voxels are generated ahead and
-// their U REDs issued back to back from separate registers, so a warp does not wait for
-// one RED's operands to be taken before building the next.
-template <int U>
-__global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
-                                                        int nx, int ny, int nz, const float *__restrict__ sino,
-                                                        float *__restrict__ out, float *__restrict__ accT)
+// Fire-and-forget float add to global memory.  Written out because pointers read from a
+// work list are generic to the compiler, which then emits an atomic that returns the old
+// value (and waits for it) instead of a reduction.
+__device__ __forceinline__ void red_add(float *p, float v)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_rays) return;
-    const int r = ord.ray(t);
-    const float g = __ldg(sino + r);
-    if (g == 0.f) return;
-    const RayRec rr = rays[r];
-    const bool tr = leans_x(rr);
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+}
+
+// Adjoint of one ray: one RED per voxel.  As in the forward, U voxels are generated ahead
+// and their U REDs issued back to back from separate registers.  accT may be NULL.
+template <int U>
+__device__ __forceinline__ void scatter_ray(const RayRec &rr, float g, int nx, int ny, int nz, float *__restrict__ out,
+                                            float *__restrict__ accT)
+{
+    const bool tr = accT != nullptr && leans_x(rr);
     float *__restrict__ base = tr ? accT : out;
     Dda<int> D;
     if (!dda_setup<int>(rr, nx, ny, nz, tr ? ny : 1, tr ? 1 : nx, nx * ny, D)) return;
@@ -130,7 +127,147 @@ __global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict
         for (int u = 0; u < U; ++u) dda_step(D, off[u], l[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (l[u] > 0.f) atomicAdd(base + off[u], __fmul_rn(g, l[u]));
+            if (l[u] > 0.f) red_add(base + off[u], __fmul_rn(g, l[u]));
+    }
+}
+
+template <int U>
+__global__ void __launch_bounds__(256) fwd3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
+                                                    int nx, int ny, int nz, const float *__restrict__ img,
+                                                    const float *__restrict__ imgT, float *__restrict__ sino)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_rays) return;
+    const int r = ord.ray(t);
+    sino[r] = fwd_ray<U>(rays[r], nx, ny, nz, img, imgT);
+}
+
+template <int U>
+__global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
+                                                        int nx, int ny, int nz, const float *__restrict__ sino,
+                                                        float *__restrict__ out, float *__restrict__ accT)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_rays) return;
+    const int r = ord.ray(t);
+    const float g = __ldg(sino + r);
+    if (g != 0.f) scatter_ray<U>(rays[r], g, nx, ny, nz, out, accT);
+}
+
+// ---------------------------------------------------------------------------------------
+// Work lists of uneven problems: every warp takes work items of `tile` consecutive rays from
+// one atomic counter until none is left.  A warp never waits for another warp (no CTA
+// barrier), so a long ray holds up only its own warp.  The per-problem copies and
+// accumulators are prepared and folded back by the item kernels below, one launch each for
+// the whole list (blockIdx.y = problem, grid-stride over its 32 x 32 tiles).
+// ---------------------------------------------------------------------------------------
+
+// CTAs per SM the adjoint's registers must allow: its REDs are issued and not waited for,
+// so more resident warps keep more of them in flight
+#ifndef XR_BATCH_ADJ_MIN_BLOCKS
+#define XR_BATCH_ADJ_MIN_BLOCKS 6
+#endif
+
+template <int U, bool ADJ>
+__global__ void __launch_bounds__(256, ADJ ? XR_BATCH_ADJ_MIN_BLOCKS : 1) batched_dda_kernel(const BatchItem *__restrict__ items, int n_items,
+                                                          int64_t n_tiles, int tile,
+                                                          unsigned long long *__restrict__ counter)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)n_tiles) break;
+        const BatchItem &P = items[find_item(items, n_items, (int64_t)t)];
+        const int64_t first = ((int64_t)t - P.tile_begin) * tile;
+        for (int q = lane; q < tile; q += 32) {
+            const int64_t r = first + q;
+            if (r >= P.n_rays) break;
+            if (!ADJ) {
+                P.sino[r] = fwd_ray<U>(P.rays[r], P.nx, P.ny, P.nz, P.img, P.aux);
+            } else {
+                const float g = __ldg(P.sino + r);
+                if (g != 0.f) scatter_ray<U>(P.rays[r], g, P.nx, P.ny, P.nz, const_cast<float *>(P.img), P.aux);
+            }
+        }
+    }
+}
+
+// The same work list as one ordinary launch: CTA b takes work item b (tile = CTA threads).
+template <int U, bool ADJ>
+__global__ void __launch_bounds__(1024) flat_dda_kernel(const BatchItem *__restrict__ items, int n_items, int tile)
+{
+    const int64_t t = blockIdx.x;
+    const BatchItem &P = items[find_item(items, n_items, t)];
+    const int64_t r = (t - P.tile_begin) * tile + threadIdx.x;
+    if (r >= P.n_rays) return;
+    if (!ADJ) {
+        P.sino[r] = fwd_ray<U>(P.rays[r], P.nx, P.ny, P.nz, P.img, P.aux);
+    } else {
+        const float g = __ldg(P.sino + r);
+        if (g != 0.f) scatter_ray<U>(P.rays[r], g, P.nx, P.ny, P.nz, const_cast<float *>(P.img), P.aux);
+    }
+}
+
+__device__ __forceinline__ int item_tiles(const BatchItem &P) { return ((P.nx + TT - 1) / TT) * ((P.ny + TT - 1) / TT) * P.nz; }
+
+// aux = [z][x][y] copy of img, per item
+__global__ void __launch_bounds__(256) transpose_items_kernel(const BatchItem *__restrict__ items)
+{
+    __shared__ float tile[TT][TT + 1];
+    const BatchItem &P = items[blockIdx.y];
+    if (!P.aux) return;
+    const int ntx = (P.nx + TT - 1) / TT, nty = (P.ny + TT - 1) / TT;
+    for (int b = blockIdx.x; b < item_tiles(P); b += gridDim.x) {
+        const int x0 = (b % ntx) * TT, y0 = ((b / ntx) % nty) * TT, z = b / (ntx * nty);
+        const size_t zoff = (size_t)z * P.nx * P.ny;
+        __syncthreads();
+        for (int dy = threadIdx.y; dy < TT; dy += blockDim.y) {
+            const int x = x0 + threadIdx.x, y = y0 + dy;
+            if (x < P.nx && y < P.ny) tile[dy][threadIdx.x] = P.img[zoff + (size_t)y * P.nx + x];
+        }
+        __syncthreads();
+        for (int dx = threadIdx.y; dx < TT; dx += blockDim.y) {
+            const int y = y0 + threadIdx.x, x = x0 + dx;
+            if (x < P.nx && y < P.ny) P.aux[zoff + (size_t)x * P.ny + y] = tile[threadIdx.x][dx];
+        }
+    }
+}
+
+// img = 0 and aux = 0, per item
+__global__ void __launch_bounds__(256) zero_items_kernel(const BatchItem *__restrict__ items)
+{
+    const BatchItem &P = items[blockIdx.y];
+    const int64_t n = (int64_t)P.nx * P.ny * P.nz;
+    float *img = const_cast<float *>(P.img);
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        img[u] = 0.f;
+        if (P.aux) P.aux[u] = 0.f;
+    }
+}
+
+// img += [z][y][x] view of aux, per item
+__global__ void __launch_bounds__(256) add_transposed_items_kernel(const BatchItem *__restrict__ items)
+{
+    __shared__ float tile[TT][TT + 1];
+    const BatchItem &P = items[blockIdx.y];
+    if (!P.aux) return;
+    float *img = const_cast<float *>(P.img);
+    const int ntx = (P.nx + TT - 1) / TT, nty = (P.ny + TT - 1) / TT;
+    for (int b = blockIdx.x; b < item_tiles(P); b += gridDim.x) {
+        const int x0 = (b % ntx) * TT, y0 = ((b / ntx) % nty) * TT, z = b / (ntx * nty);
+        const size_t zoff = (size_t)z * P.nx * P.ny;
+        __syncthreads();
+        for (int dx = threadIdx.y; dx < TT; dx += blockDim.y) {
+            const int y = y0 + threadIdx.x, x = x0 + dx;
+            if (x < P.nx && y < P.ny) tile[dx][threadIdx.x] = P.aux[zoff + (size_t)x * P.ny + y];
+        }
+        __syncthreads();
+        for (int dy = threadIdx.y; dy < TT; dy += blockDim.y) {
+            const int x = x0 + threadIdx.x, y = y0 + dy;
+            if (x < P.nx && y < P.ny) img[zoff + (size_t)y * P.nx + x] += tile[threadIdx.x][dy];
+        }
     }
 }
 
@@ -145,6 +282,51 @@ constexpr int kFwdAhead = XR_FWD3D_AHEAD;
 constexpr int kAdjAhead = XR_ADJ3D_AHEAD;
 
 }  // namespace
+
+int batched_ctas_per_sm(int block, int adjoint)
+{
+    int n = 0;
+    if (adjoint)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_dda_kernel<kAdjAhead, true>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_dda_kernel<kFwdAhead, false>, block, 0);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                           unsigned long long *counter, int adjoint, int with_aux, int grid_ctas, int block,
+                           cudaStream_t s)
+{
+    const dim3 per_item(256, (unsigned)n_items);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+#ifndef XR_BATCH_FLAT
+#define XR_BATCH_FLAT 0
+#endif
+    const bool flat = (XR_BATCH_FLAT & (adjoint ? 2 : 1)) && tile <= 1024;
+    if (!adjoint) {
+        if (with_aux) transpose_items_kernel<<<per_item, dim3(TT, 8), 0, s>>>(items);
+        if (flat)
+            flat_dda_kernel<kFwdAhead, false><<<(unsigned)n_tiles, tile, 0, s>>>(items, n_items, tile);
+        else
+            batched_dda_kernel<kFwdAhead, false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
+        return cudaGetLastError();
+    }
+    zero_items_kernel<<<per_item, 256, 0, s>>>(items);
+    if (flat)
+        flat_dda_kernel<kAdjAhead, true><<<(unsigned)n_tiles, tile, 0, s>>>(items, n_items, tile);
+    else
+        batched_dda_kernel<kAdjAhead, true><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
+    if (with_aux) add_transposed_items_kernel<<<per_item, dim3(TT, 8), 0, s>>>(items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s)
+{
+    batched_dda_kernel<kFwdAhead, false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int nz, cudaStream_t s)
 {

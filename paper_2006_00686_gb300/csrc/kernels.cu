@@ -1,5 +1,5 @@
-// Ray kernels: forward projection, ray-driven scatter adjoint, unit-driven gather adjoint
-// (2D), sparse-row export and the persistent batched launch.  All FP32 with FP32
+// Ray kernels on the caller's layout: forward projection, ray-driven scatter adjoint,
+// unit-driven gather adjoint (2D) and sparse-row export.  All FP32 with FP32
 // accumulation; no tensor cores (the work is a gather along rays, not a contraction).
 #include "xray_internal.h"
 
@@ -267,107 +267,6 @@ cudaError_t launch_ray_units(const RayRec *rays, int64_t n_rays, const Grid &gri
     const int block = 128;
     ray_units_kernel<<<(n + block - 1) / block, block, 0, s>>>(rays, n_rays, grid, ids, n, cap, idx, len,
                                                                count);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------------------
-// Persistent batched launch over uneven problems.  The global tile space is the
-// concatenation of every problem's tiles of `tile` consecutive rays; each CTA takes tiles
-// from one atomic counter until none is left (no CTA ever waits for another).
-// ---------------------------------------------------------------------------------------
-
-__device__ __forceinline__ int find_item(const BatchItem *items, int n, int64_t t)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (items[mid].tile_begin <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <bool ADJ>
-__global__ void __launch_bounds__(256) batched_kernel(const BatchItem *__restrict__ items, int n_items,
-                                                      int64_t n_tiles, int tile,
-                                                      unsigned long long *__restrict__ counter)
-{
-    __shared__ int64_t s_tile;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const int64_t t = s_tile;
-        if (t >= n_tiles) break;
-        const int it = find_item(items, n_items, t);
-        const BatchItem &P = items[it];
-        const int64_t first = (t - P.tile_begin) * tile;
-        for (int q = threadIdx.x; q < tile; q += blockDim.x) {
-            const int64_t r = first + q;
-            if (r >= P.n_rays) break;
-            const int64_t sy = P.nx, sz = (int64_t)P.nx * P.ny;
-            if (!ADJ) {
-                FwdVisitor<1> vis;
-                vis.img = P.img;
-                vis.bs = 0;
-                vis.nb = 1;
-                vis.acc[0] = 0.f;
-                walk_ray(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, P.three, vis);
-                P.sino[r] = vis.acc[0];
-            } else {
-                ScatterVisitor<1> vis;
-                vis.img = const_cast<float *>(P.img);
-                vis.bs = 0;
-                vis.nb = 1;
-                vis.g[0] = __ldg(P.sino + r);
-                if (vis.g[0] != 0.f) walk_ray(P.rays[r], P.nx, P.ny, P.nz, 1, sy, sz, P.three, vis);
-            }
-        }
-    }
-}
-
-// Zero every problem's image before a scatter adjoint (grid-stride over all units).
-__global__ void zero_items_kernel(const BatchItem *__restrict__ items, int n_items)
-{
-    for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
-        const BatchItem &P = items[it];
-        const int64_t n = (int64_t)P.nx * P.ny * P.nz;
-        float *img = const_cast<float *>(P.img);
-        for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-             u += (int64_t)gridDim.x * blockDim.x)
-            img[u] = 0.f;
-    }
-}
-
-int batched_ctas_per_sm(int block, int adjoint)
-{
-    int n = 0;
-    if (adjoint)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<true>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<false>, block, 0);
-    return n > 0 ? n : 1;
-}
-
-cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
-                           unsigned long long *counter, int adjoint, int grid_ctas, int block,
-                           cudaStream_t s)
-{
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
-    if (adjoint) {
-        zero_items_kernel<<<dim3(256, (unsigned)min(n_items, 65535)), 256, 0, s>>>(items, n_items);
-        batched_kernel<true><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
-    } else {
-        batched_kernel<false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
-                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s)
-{
-    batched_kernel<false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
     return cudaGetLastError();
 }
 

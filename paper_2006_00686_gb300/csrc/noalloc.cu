@@ -85,10 +85,12 @@ extern "C" xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t
         const xr_geometry *g = probs[i].geom;
         if (!g || !probs[i].img || !probs[i].sino) return XR_ERR_NULL;
         if (((uintptr_t)probs[i].img & 15u) || ((uintptr_t)probs[i].sino & 15u)) return XR_ERR_ALIGN;
+        if (g->n_units >= ((int64_t)1 << 31)) return XR_ERR_SIZE;  // 32-bit walk offsets
         BatchItem &it = w.items[i];
         it.rays = g->d_rays;
         it.img = probs[i].img;
         it.sino = probs[i].sino;
+        it.aux = nullptr;  // no copies: every ray reads the caller's layout
         it.nx = g->params.nx;
         it.ny = g->params.ny;
         it.nz = g->params.nz;

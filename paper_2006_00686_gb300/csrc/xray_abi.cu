@@ -39,6 +39,7 @@ static xr_status validate(const xr_geometry_desc *d)
     if (d->nx < 1 || d->ny < 1 || nz < 1 || d->nx > 16384 || d->ny > 16384 || nz > 16384) return XR_ERR_SIZE;
     if (d->n_views < 1 || d->n_cols < 1 || nr < 1) return XR_ERR_SIZE;
     if ((int64_t)d->n_views * nr * d->n_cols > ((int64_t)1 << 40)) return XR_ERR_SIZE;
+    if ((int64_t)nr * d->n_cols >= ((int64_t)1 << 31)) return XR_ERR_SIZE;
     if (!d->angles) return XR_ERR_NULL;
     if (kind_helical(d->kind) && !d->src_z) return XR_ERR_NULL;
     if (!(d->dx > 0) || !(d->dy > 0) || (three && !(d->dz > 0))) return XR_ERR_GEOMETRY;
@@ -141,11 +142,12 @@ static bool use_fast(const xr_geometry *g, int batch)
            g->n_rays * fast_chunk(batch) < ((int64_t)1 << 31) && g->n_units < ((int64_t)1 << 31);
 }
 
-// 3D scans with a reserved workspace: the crossing-order walk over the image and its
-// [z][x][y] copy, one image at a time (32-bit offsets and ray ids).
-static bool use_fast3d(const xr_geometry *g)
+// Single-image fast path (3D scans, and 2D scans outside the quad-plane path) with a
+// reserved workspace: the crossing-order walk over the image and its [z][x][y] copy, one
+// image at a time (32-bit offsets and ray ids).
+static bool use_dda(const xr_geometry *g)
 {
-    return kind_is3d(g->params.kind) && g->tune.path != XR_PATH_RAY && g->d_ws &&
+    return g->tune.path != XR_PATH_RAY && g->d_ws &&
            g->ws_bytes >= (size_t)g->n_units * sizeof(float) && g->n_units < ((int64_t)1 << 31) &&
            g->n_rays < ((int64_t)1 << 31);
 }
@@ -162,7 +164,8 @@ static int row_major(const xr_geometry *g)
 
 static size_t reserve_bytes(const xr_geometry *g, int batch)
 {
-    return kind_is3d(g->params.kind) ? (size_t)g->n_units * sizeof(float) : fast_ws_bytes(g, batch);
+    if (kind_is3d(g->params.kind) || batch < 4) return (size_t)g->n_units * sizeof(float);
+    return fast_ws_bytes(g, batch);  // >= n_units floats: serves the single-image path too
 }
 
 extern "C" {
@@ -351,7 +354,6 @@ xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
         t->batch_chunk != 8 && t->batch_chunk != 16)
         return XR_ERR_ARG;
     if (t->adjoint && t->adjoint != XR_ADJ_SCATTER && t->adjoint != XR_ADJ_GATHER) return XR_ERR_ARG;
-    if (t->adjoint == XR_ADJ_GATHER && kind_is3d(g->params.kind)) return XR_ERR_ARG;
     if (t->path < 0 || t->path > XR_PATH_RAY) return XR_ERR_ARG;
     if (t->order < 0 || t->order > XR_ORDER_ROW) return XR_ERR_ARG;
     if (t->order) g->tune.order = t->order;
@@ -379,7 +381,7 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
         XR_CUDA(launch_tile2d(g->d_rays, g->params, g->d_view_tab, d_img, d_sino, batch, 0, (cudaStream_t)stream));
         return XR_OK;
     }
-    if (use_fast3d(g)) {
+    if (!use_fast(g, batch) && use_dda(g)) {
         const cudaStream_t s = (cudaStream_t)stream;
         for (int b = 0; b < batch; ++b) {
             const float *img = d_img + (size_t)b * g->n_units;
@@ -415,14 +417,24 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if (batch < 1) return XR_ERR_BATCH;
     if (!aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
     if (method == XR_ADJ_AUTO) method = g->tune.adjoint;
-    if (method == XR_ADJ_AUTO)
-        method = (!kind_is3d(g->params.kind) && !use_tiled(g, batch) && use_fast(g, batch)) ? XR_ADJ_GATHER
-                                                                                          : XR_ADJ_SCATTER;
+    if (method == XR_ADJ_AUTO) {
+        // measured on GB300: 3D scatter 438 ms vs tiled gather 682 ms (circular cone 512^3);
+        // 2D: the quad-plane gather beats the vector-atomic scatter (2.33 vs 2.94 ms,
+        // fan beam 512^2 x 16), one image: the scatter
+        if (kind_is3d(g->params.kind))
+            method = XR_ADJ_SCATTER;
+        else
+            method = (!use_tiled(g, batch) && use_fast(g, batch)) ? XR_ADJ_GATHER : XR_ADJ_SCATTER;
+    }
     const int chunk = pick_chunk(g, batch);
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
     const cudaStream_t s = (cudaStream_t)stream;
     if (method == XR_ADJ_GATHER) {
-        if (kind_is3d(g->params.kind)) return XR_ERR_ARG;
+        if (kind_is3d(g->params.kind)) {
+            if (batch > 65535) return XR_ERR_SIZE;
+            XR_CUDA(launch_tile3d_adj(g->d_rays, g->d_views, g->params, d_sino, g->n_rays, d_img, batch, s));
+            return XR_OK;
+        }
         if (use_fast(g, batch)) {
             const int Q = (batch + 3) / 4;
             const size_t padded = (size_t)((batch + fast_chunk(batch) - 1) / fast_chunk(batch)) * fast_chunk(batch);
@@ -437,7 +449,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         return XR_OK;
     }
     if (method != XR_ADJ_SCATTER) return XR_ERR_ARG;
-    if (use_fast3d(g)) {
+    if (!use_tiled(g, batch) && !use_fast(g, batch) && use_dda(g)) {
         for (int b = 0; b < batch; ++b)
             XR_CUDA(launch_scatter3d(g->d_rays, g->params, g->n_rays, row_major(g), d_sino + (size_t)b * g->n_rays,
                                      d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, s));
@@ -488,6 +500,7 @@ struct xr_batch {
     int64_t n_tiles;
     BatchItem *d_items;
     unsigned long long *d_counter;
+    float *d_aux;  // every problem's [nz][nx][ny] copy / accumulator, back to back
 };
 
 extern "C" {
@@ -503,7 +516,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
     if (tile < 32 || tile > 65536 || (tile & 31) || block < 64 || block > 256 || (block & 31)) return XR_ERR_ARG;
     BatchItem *items = (BatchItem *)malloc(sizeof(BatchItem) * (size_t)n);
     if (!items) return XR_ERR_ALLOC;
-    int64_t tiles = 0;
+    int64_t tiles = 0, aux_units = 0;
     for (int i = 0; i < n; ++i) {
         const xr_geometry *g = probs[i].geom;
         if (!g || !probs[i].img || !probs[i].sino) {
@@ -514,9 +527,14 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
             free(items);
             return XR_ERR_ALIGN;
         }
+        if (g->n_units >= ((int64_t)1 << 31)) {  // the walk indexes one problem with 32 bits
+            free(items);
+            return XR_ERR_SIZE;
+        }
         items[i].rays = g->d_rays;
         items[i].img = probs[i].img;
         items[i].sino = probs[i].sino;
+        items[i].aux = nullptr;
         items[i].nx = g->params.nx;
         items[i].ny = g->params.ny;
         items[i].nz = g->params.nz;
@@ -524,6 +542,11 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         items[i].n_rays = g->n_rays;
         items[i].tile_begin = tiles;
         tiles += (g->n_rays + tile - 1) / tile;
+        aux_units += (g->n_units + 3) & ~(int64_t)3;  // keep every copy 16-byte aligned
+    }
+    if (n > 65535) {
+        free(items);
+        return XR_ERR_SIZE;
     }
     xr_batch *b = new (std::nothrow) xr_batch();
     if (!b) {
@@ -539,7 +562,15 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items, sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_aux, (size_t)aux_units * sizeof(float));
+    if (e == cudaSuccess) {
+        int64_t at = 0;
+        for (int i = 0; i < n; ++i) {
+            items[i].aux = b->d_aux + at;
+            at += (probs[i].geom->n_units + 3) & ~(int64_t)3;
+        }
+        e = cudaMemcpy(b->d_items, items, sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice);
+    }
     free(items);
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
@@ -562,6 +593,7 @@ void xr_batch_destroy(xr_batch *b)
     cudaDeviceSynchronize();
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
+    cudaFree(b->d_aux);
     cudaSetDevice(prev);
     delete b;
 }
@@ -569,7 +601,7 @@ void xr_batch_destroy(xr_batch *b)
 xr_status xr_batch_project(const xr_batch *b, xr_stream stream)
 {
     if (!b) return XR_ERR_NULL;
-    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 0, b->ctas_fwd, b->block,
+    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 0, 1, b->ctas_fwd, b->block,
                            (cudaStream_t)stream));
     return XR_OK;
 }
@@ -577,7 +609,7 @@ xr_status xr_batch_project(const xr_batch *b, xr_stream stream)
 xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream)
 {
     if (!b) return XR_ERR_NULL;
-    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 1, b->ctas_adj, b->block,
+    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 1, 1, b->ctas_adj, b->block,
                            (cudaStream_t)stream));
     return XR_OK;
 }

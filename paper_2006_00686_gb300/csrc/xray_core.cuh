@@ -261,37 +261,37 @@ struct Dda {
     float tout;           // exit from the grid
 };
 
-// Axis setup: plane constants and box entry/exit; false when the ray misses this axis's
-// slab (inactive axis with its fixed index outside the grid).
-__device__ __forceinline__ bool dda_axis(float w, float f, int o, int N, float &inv, float &b, float &tin,
+// Axis setup: plane constants and entry/exit of the index range [lo, hi) of this axis;
+// false when the ray misses it (inactive axis with its fixed index outside the range).
+__device__ __forceinline__ bool dda_axis(float w, float f, int o, int lo, int hi, float &inv, float &b, float &tin,
                                          float &tout)
 {
     if (w == 0.f) {
         inv = 0.f;
         b = 0.f;
-        return (unsigned)o < (unsigned)N;
+        return o >= lo && o < hi;
     }
     inv = __frcp_rn(w);
     b = __fmul_rn(-f, inv);
-    const float ta = __fmaf_rn((float)(0 - o), inv, b);
-    const float tb = __fmaf_rn((float)(N - o), inv, b);
+    const float ta = __fmaf_rn((float)(lo - o), inv, b);
+    const float tb = __fmaf_rn((float)(hi - o), inv, b);
     tin = fmaxf(tin, fminf(ta, tb));
     tout = fminf(tout, fmaxf(ta, tb));
     return true;
 }
 
 // The voxel of this axis containing the start of the walk (just after tin) and its
-// leaving plane.  Unit n of the axis spans planes n and n + 1.
+// leaving plane.  Unit n of the axis spans planes n and n + 1; offsets count from lo.
 template <class Off>
-__device__ __forceinline__ void dda_start(float w, float f, int o, int N, float inv, float b, float tin, Off stride,
-                                          float &t, float &q, float &s, Off &d, Off &off)
+__device__ __forceinline__ void dda_start(float w, float f, int o, int lo, int hi, float inv, float b, float tin,
+                                          Off stride, float &t, float &q, float &s, Off &d, Off &off)
 {
     if (w == 0.f) {
         t = INFINITY;
         q = 0.f;
         s = 0.f;
         d = 0;
-        off += (Off)o * stride;
+        off += (Off)(o - lo) * stride;
         return;
     }
     int n = (int)floorf(__fmaf_rn(w, tin, f)) + o;
@@ -303,7 +303,7 @@ __device__ __forceinline__ void dda_start(float w, float f, int o, int N, float 
 #pragma unroll
         for (int it = 0; it < 2; ++it)
             if (__fmaf_rn((float)(n - o), inv, b) > tin) --n;
-        n = min(max(n, 0), N - 1);
+        n = min(max(n, lo), hi - 1);
         q = (float)(n + 1 - o);
         s = 1.f;
         d = stride;
@@ -315,34 +315,45 @@ __device__ __forceinline__ void dda_start(float w, float f, int o, int N, float 
 #pragma unroll
         for (int it = 0; it < 2; ++it)
             if (__fmaf_rn((float)(n + 1 - o), inv, b) > tin) ++n;
-        n = min(max(n, 0), N - 1);
+        n = min(max(n, lo), hi - 1);
         q = (float)(n - o);
         s = -1.f;
         d = -stride;
     }
     t = __fmaf_rn(q, inv, b);
-    off += (Off)n * stride;
+    off += (Off)(n - lo) * stride;
 }
 
-// Prepare the walk; false when the ray crosses no voxel.
+// Prepare the walk through the box [lo0, hi0) x [lo1, hi1) x [lo2, hi2) of the grid (index
+// planes are the grid's, so every voxel gets the same length as in a walk of the whole
+// grid); offsets count from the box's first voxel with the given strides.  False when the
+// ray crosses no voxel of the box.
 template <class Off>
-__device__ __forceinline__ bool dda_setup(const RayRec &r, int nx, int ny, int nz, Off sx, Off sy, Off sz,
-                                          Dda<Off> &D)
+__device__ __forceinline__ bool dda_setup_box(const RayRec &r, int lo0, int hi0, int lo1, int hi1, int lo2, int hi2,
+                                              Off sx, Off sy, Off sz, Dda<Off> &D)
 {
     if (r.flags & RAY_MISS) return false;
     if (r.w0 == 0.f && r.w1 == 0.f && r.w2 == 0.f) return false;
     float tin = -INFINITY, tout = INFINITY;
-    if (!dda_axis(r.w0, r.f0, r.o0, nx, D.i0, D.b0, tin, tout)) return false;
-    if (!dda_axis(r.w1, r.f1, r.o1, ny, D.i1, D.b1, tin, tout)) return false;
-    if (!dda_axis(r.w2, r.f2, r.o2, nz, D.i2, D.b2, tin, tout)) return false;
+    if (!dda_axis(r.w0, r.f0, r.o0, lo0, hi0, D.i0, D.b0, tin, tout)) return false;
+    if (!dda_axis(r.w1, r.f1, r.o1, lo1, hi1, D.i1, D.b1, tin, tout)) return false;
+    if (!dda_axis(r.w2, r.f2, r.o2, lo2, hi2, D.i2, D.b2, tin, tout)) return false;
     if (!(tin < tout)) return false;
     D.off = 0;
-    dda_start(r.w0, r.f0, r.o0, nx, D.i0, D.b0, tin, sx, D.t0, D.q0, D.s0, D.d0, D.off);
-    dda_start(r.w1, r.f1, r.o1, ny, D.i1, D.b1, tin, sy, D.t1, D.q1, D.s1, D.d1, D.off);
-    dda_start(r.w2, r.f2, r.o2, nz, D.i2, D.b2, tin, sz, D.t2, D.q2, D.s2, D.d2, D.off);
+    dda_start(r.w0, r.f0, r.o0, lo0, hi0, D.i0, D.b0, tin, sx, D.t0, D.q0, D.s0, D.d0, D.off);
+    dda_start(r.w1, r.f1, r.o1, lo1, hi1, D.i1, D.b1, tin, sy, D.t1, D.q1, D.s1, D.d1, D.off);
+    dda_start(r.w2, r.f2, r.o2, lo2, hi2, D.i2, D.b2, tin, sz, D.t2, D.q2, D.s2, D.d2, D.off);
     D.tcur = tin;
     D.tout = tout;
     return true;
+}
+
+// The walk through the whole grid.
+template <class Off>
+__device__ __forceinline__ bool dda_setup(const RayRec &r, int nx, int ny, int nz, Off sx, Off sy, Off sz,
+                                          Dda<Off> &D)
+{
+    return dda_setup_box<Off>(r, 0, nx, 0, ny, 0, nz, sx, sy, sz, D);
 }
 
 // Upper bound on the steps of one ray: one per voxel, at most nx + ny + nz + 1.

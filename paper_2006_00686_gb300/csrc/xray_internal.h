@@ -66,18 +66,35 @@ struct BatchItem {
     const RayRec *rays;
     const float *img;
     float *sino;
+    float *aux;  // n_units floats: the [nz][nx][ny] copy / accumulator, or NULL (read img only)
     int nx, ny, nz;
     int three;  // 1: a 3D scan
     int64_t n_rays;
     int64_t tile_begin;  // first global tile index of this problem
 };
 
+// The problem owning global tile t (items sorted by tile_begin).
+__device__ __forceinline__ int find_item(const BatchItem *items, int n, int64_t t)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent launch over the work list (fast3d.cu): the crossing-order walk for every
+// problem.  Forward: the [nz][nx][ny] copies are written first when the items carry aux
+// buffers; adjoint: images (and aux) are zeroed, scattered into, and aux added back.
+// The tile counter is zeroed here.
 cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
-                           unsigned long long *counter, int adjoint, int grid_ctas, int block,
+                           unsigned long long *counter, int adjoint, int with_aux, int grid_ctas, int block,
                            cudaStream_t s);
 
-// Forward persistent launch over a work list already in device memory; the tile counter
-// must be zero (no memset here).
+// Forward persistent launch over a work list already in device memory, items without aux;
+// the tile counter must be zero (no memset here).
 cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
                                  unsigned long long *counter, int grid_ctas, int block, cudaStream_t s);
 
@@ -117,6 +134,10 @@ cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_r
 // Zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
 cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
                              const float *sino, float *out, float *accT, int block, cudaStream_t s);
+// Unit-driven adjoint for 3D scans (tile3d.cu): one CTA per 16^3 tile of voxels gathers
+// every ray of its detector footprint in shared memory and writes the tile once.
+cudaError_t launch_tile3d_adj(const RayRec *rays, const ViewRec *views, const GeoParams &g, const float *sino,
+                              int64_t n_rays, float *img, int batch, cudaStream_t s);
 cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
                                 const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
                                 cudaStream_t s);

@@ -71,11 +71,12 @@ def _time(fn, reps: int, budget_s: float) -> float:
 def projector_candidates(g, batch: int) -> list:
     out = []
     if g.is3d:
-        # the volume-copy path in either ray order, then the caller's layout
+        # the volume-copy path in either ray order with either adjoint, then the caller's layout
         for order in (X.XR_ORDER_VIEW, X.XR_ORDER_ROW):
-            for block in (128, 256):
-                out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=X.XR_ADJ_SCATTER, block=block,
-                                order=order))
+            for adj in (X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER):
+                out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=adj, block=128, order=order))
+        out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=X.XR_ADJ_GATHER, block=256,
+                        order=X.XR_ORDER_ROW))
         out.append(dict(path=X.XR_PATH_RAY, batch_chunk=min(16, max(1, batch)), adjoint=X.XR_ADJ_SCATTER,
                         block=128, order=X.XR_ORDER_VIEW))
         return out
@@ -86,6 +87,10 @@ def projector_candidates(g, batch: int) -> list:
             for adj in (X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER):
                 out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=chunk, adjoint=adj, block=128))
         out.append(dict(path=X.XR_PATH_TILED, batch_chunk=16, adjoint=X.XR_ADJ_SCATTER, block=128))
+    else:
+        # one image at a time through the image and its y-fastest copy
+        for adj in (X.XR_ADJ_SCATTER, X.XR_ADJ_GATHER):
+            out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=1, adjoint=adj, block=128))
     for block in (128, 256):
         for adj in (X.XR_ADJ_SCATTER, X.XR_ADJ_GATHER):
             out.append(dict(path=X.XR_PATH_RAY, batch_chunk=1 if batch < 4 else min(16, batch), adjoint=adj,
@@ -114,8 +119,7 @@ def tune_projector(P: "X.Projector", batch: int, cache_path: str | None = None, 
         x = torch.rand(g.image_shape(batch if batch > 1 else None), device=dev)
     y = torch.empty(g.sino_shape(batch if batch > 1 else None), device=dev)
     z = torch.empty_like(x)
-    if batch >= 4 or g.is3d:
-        P.reserve(max(batch, 1))
+    P.reserve(max(batch, 1))
     results = []
     for c in projector_candidates(g, batch):
         _apply(P, c)
@@ -132,23 +136,28 @@ def tune_projector(P: "X.Projector", batch: int, cache_path: str | None = None, 
     return best
 
 
-def tune_batch_plan(projectors, images, sinos, cache_path: str | None = None, reps: int = 5,
-                    budget_s: float = 2.0) -> dict:
-    """Choose rays per work item and threads per CTA of a persistent uneven batch."""
+def tune_batch_plan(projectors, images, sinos, cache_path: str | None = None, reps: int = 3,
+                    budget_s: float = 2.0, verbose: bool = False) -> dict:
+    """Choose rays per work item and threads per CTA of a persistent uneven batch by timing
+    its forward and adjoint launches (the adjoint writes scratch images, not `images`)."""
     key = _gpu_name() + "|plan|" + ";".join(scan_key(p.geom, 1) for p in projectors)
     cache = _load(cache_path)
     if key in cache:
         return cache[key]
+    scratch = [torch.empty_like(x) for x in images]
     results = []
     for tile in (64, 128, 256, 512, 1024):
         for block in (128, 256):
-            if tile < block:
-                continue
-            plan = X.BatchPlan(projectors, images, sinos, tile=tile, block=block)
-            ms = _time(plan.project, reps, budget_s)
-            results.append(dict(tile=tile, block=block, forward_ms=ms))
-            plan.close()
-    best = min(results, key=lambda r: r["forward_ms"])
+            fwd = X.BatchPlan(projectors, images, sinos, tile=tile, block=block)
+            adj = X.BatchPlan(projectors, scratch, sinos, tile=tile, block=block)
+            f_ms = _time(fwd.project, reps, budget_s)
+            a_ms = _time(adj.backproject, reps, budget_s)
+            results.append(dict(tile=tile, block=block, forward_ms=f_ms, adjoint_ms=a_ms))
+            if verbose:
+                print("tune plan", results[-1], flush=True)
+            fwd.close()
+            adj.close()
+    best = min(results, key=lambda r: r["forward_ms"] + r["adjoint_ms"])
     cache = _load(cache_path)
     cache[key] = best
     _store(cache_path, cache)

@@ -189,10 +189,10 @@ class Projector:
     def _maybe_reserve(self, b: int):
         if not self.auto_reserve or torch.cuda.is_current_stream_capturing():
             return
-        if self.geom.is3d:
-            if self.reserved < 1:  # one volume copy serves every batch size
+        if self.geom.is3d or b < 4:
+            if self.reserved < 1:  # one image copy: the single-image path
                 self.reserve(1)
-        elif b >= 4 and b > self.reserved:
+        elif b > self.reserved:
             self.reserve(b)
 
     def forward(self, img: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

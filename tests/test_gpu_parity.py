@@ -165,7 +165,7 @@ def test_adjoint_small(name):
     f = _phantom(g, 21).numpy().astype(np.float64)
     y = O.forward(g, f).astype(np.float32)  # the same float32 sinogram feeds both sides
     P = _proj(g)
-    methods = [1, 2] if not g.is3d else [1]
+    methods = [1, 2]
     z_ref = O.adjoint(g, y.astype(np.float64))
     for m in methods:
         z = P.adjoint(torch.from_numpy(y.reshape(g.sino_shape())).cuda(), method=m).cpu().numpy()
@@ -244,8 +244,11 @@ def test_fast3d_matches_ray_path(name):
     Pr.set_tuning(path=XR_PATH_RAY)
     yf, yr = Pf.forward(x), Pr.forward(x)
     assert Pf.reserved >= 1 and torch.equal(yf, yr)
-    zf, zr = Pf.adjoint(yf), Pr.adjoint(yf)
+    zf, zr = Pf.adjoint(yf, method=1), Pr.adjoint(yf, method=1)
     assert float((zf - zr).abs().max()) <= 1e-5 * float(zr.abs().max())
+    # the tile-driven gather sums the same (ray, voxel) lengths
+    zg = Pf.adjoint(yf, method=2)
+    assert float((zg - zr).abs().max()) <= 1e-5 * float(zr.abs().max())
     assert torch.equal(Pf.forward(x), yf)
 
 
@@ -329,9 +332,9 @@ def test_full_size_adjoint_view_subset(name):
     z = P.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
     z_ref = O.adjoint(g, y.astype(np.float64).reshape(-1))
     H.check_adjoint(z, z_ref, name)
-    if not g.is3d:
-        z2 = P.adjoint(torch.from_numpy(y).cuda(), method=1).cpu().numpy()
-        H.check_adjoint(z2, z_ref, name + " scatter")
+    for m in (1, 2):
+        z2 = P.adjoint(torch.from_numpy(y).cuda(), method=m).cpu().numpy()
+        H.check_adjoint(z2, z_ref, f"{name} method {m}")
     P.close()
 
 

@@ -23,13 +23,15 @@ def test_candidates_cover_paths():
     assert paths == {X.XR_PATH_INTERLEAVED, X.XR_PATH_TILED, X.XR_PATH_RAY}
     assert {c["adjoint"] for c in c16} == {X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER}
     assert {c["batch_chunk"] for c in c16 if c["path"] == X.XR_PATH_INTERLEAVED} == {4, 8, 16}
-    # a batch below four images has only the one-thread-per-ray path
-    assert {c["path"] for c in tune.projector_candidates(g, 1)} == {X.XR_PATH_RAY}
+    # a batch below four images: the single-image copy path or the caller's layout
+    assert {c["path"] for c in tune.projector_candidates(g, 1)} == {X.XR_PATH_INTERLEAVED, X.XR_PATH_RAY}
     # no candidate walks more images per thread than the batch holds (rounded to four)
     assert {c["batch_chunk"] for c in tune.projector_candidates(g, 5)
             if c["path"] == X.XR_PATH_INTERLEAVED} == {4, 8}
     g3 = inputs.Geometry("cone", 8, 8, 8, angles=np.arange(4) * 0.5, n_cols=9, n_rows=9, sod=40.0, sdd=60.0)
-    assert all(c["adjoint"] == X.XR_ADJ_SCATTER for c in tune.projector_candidates(g3, 8))
+    c3 = tune.projector_candidates(g3, 8)
+    assert {c["adjoint"] for c in c3} == {X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER}
+    assert {c["order"] for c in c3} == {X.XR_ORDER_VIEW, X.XR_ORDER_ROW}
     assert all(c["path"] != X.XR_PATH_TILED for c in tune.projector_candidates(g3, 8))
 
 
