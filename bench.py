@@ -271,7 +271,13 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_kind = _peaks()
     fwd, adj = float(np.mean(fwd_ms)), float(np.mean(adj_ms))
     dom, dom_ms = ("forward", fwd) if fwd >= adj else ("adjoint", adj)
-    method = "gather" if P.tuning()["adjoint"] == XR_ADJ_GATHER else "scatter"
+    # the method the library's automatic choice takes: the gather on the 2D quad-plane path
+    # (batches of 4 or more), the scatter elsewhere
+    adj = P.tuning()["adjoint"]
+    if adj == 0:
+        method = "gather" if (not g.is3d and B >= 4) else "scatter"
+    else:
+        method = "gather" if adj == XR_ADJ_GATHER else "scatter"
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
     # forward and gather kernels, from one ncu capture of this workload
     traffic = None
@@ -283,17 +289,18 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if args.workload == "fan2d_512x16":
         config = _config({"adjoint": method, "batch_chunk": P.tuning()["batch_chunk"], "block": args.block})
-        # per step: detector setup, ray setup, image interleave, forward walk, then either
-        # the scatter walk + its de-interleave (two accumulator memsets are not kernels)
-        # or the sinogram interleave + gather
-        launches = 6
+        # per step: detector setup, ray setup, the gather's per-ray constants, image
+        # interleave, forward walk, then either the scatter walk + its de-interleave (two
+        # accumulator memsets are not kernels) or the sinogram interleave + gather
+        launches = 7
     else:
         config = {"workload": args.workload, "geometry": desc, "image": list(g.image_shape()),
                   "views": g.n_views, "detector": [g.n_rows, g.n_cols], "batch_per_gpu": B, "adjoint": method,
                   "l2": "flushed between timed steps (256 MiB write)"}
-        # detector setup, ray setup, forward walk, adjoint walk (the scatter's zero fill is
-        # a memset, not a kernel)
-        launches = 4
+        # detector setup, ray setup (2D: and the gather's per-ray constants), then per image:
+        # the y-fastest copy, the forward walk, the scatter walk and the fold of the transposed
+        # accumulator (zero fills are memsets)
+        launches = (2 if g.is3d else 3) + 4 * B
         if args.workload == "par3d_256_tilt":
             extra = _autograd_and_sirt(P, x, y, args)
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -456,9 +463,10 @@ def run_uneven(args, rank, world, local_rank):
            "e2e": {"value": round(rays_step * world / (e2e * 1e-3) / 1e9, 4), "unit": UNIT,
                    "h2d_bytes_per_step": int(sum(t.numel() for t in xs) * 4),
                    "d2h_bytes_per_step": int(sum(t.numel() for t in ys + zs) * 4), "ms_per_step": round(e2e, 4)},
-           # per step: 2 x 64 setup kernels, the batched forward, the adjoint's zero fill and
-           # the batched adjoint
-           "gpu_launches": args.steps * (2 * n + 3),
+           # per step: 3 x 64 setup kernels (detector, ray, gather constants); the copies and the
+           # persistent forward; the zero fill, the persistent adjoint and the fold of the
+           # transposed accumulators
+           "gpu_launches": args.steps * (3 * n + 5),
            "kernel_ms": {"ray_setup": round(rb["setup"], 4), "forward": round(rb["fwd"], 4),
                          "adjoint": round(rb["adj"], 4)},
            "plain": {"value": round(rays_step * world / (res["plain"]["ms"] * 1e-3) / 1e9, 4),

@@ -155,9 +155,7 @@ __device__ __noinline__ void scatter_rows_general(int oB, int NB, int sgB, float
         const float tb0 = __fmaf_rn(q + (float)sgB, invB, bB);
         const float tb1 = __fmaf_rn(q + (float)(1 - sgB), invB, bB);
         const float l = __fsub_rn(fminf(thi, tb1), fmaxf(tlo, tb0));
-        if (l > 0.f)
-            atomicAdd(reinterpret_cast<float4 *>(const_cast<float *>(base + (int64_t)jg * sB)),
-                      make_float4(g.x * l, g.y * l, g.z * l, g.w * l));
+        if (l > 0.f) red_add4(const_cast<float *>(base + (int64_t)jg * sB), g.x * l, g.y * l, g.z * l, g.w * l);
     }
 }
 
@@ -167,7 +165,7 @@ struct Il4ScatterVisitor {
     float4 g;
     __device__ __forceinline__ void operator()(int64_t off, float l)
     {
-        atomicAdd(reinterpret_cast<float4 *>(il + off), make_float4(g.x * l, g.y * l, g.z * l, g.w * l));
+        red_add4(il + off, g.x * l, g.y * l, g.z * l, g.w * l);
     }
 };
 
@@ -195,9 +193,7 @@ template <bool ADJ>
 __device__ __forceinline__ void unit_op(const float *p, bool on, float l, float4 &acc)
 {
     if (ADJ) {
-        if (on && l > 0.f)
-            atomicAdd(reinterpret_cast<float4 *>(const_cast<float *>(p)),
-                      make_float4(acc.x * l, acc.y * l, acc.z * l, acc.w * l));
+        if (on && l > 0.f) red_add4(const_cast<float *>(p), acc.x * l, acc.y * l, acc.z * l, acc.w * l);
     } else {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         fma4(acc, on ? __ldg(reinterpret_cast<const float4 *>(p)) : z, l);

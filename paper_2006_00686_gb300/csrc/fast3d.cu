@@ -102,14 +102,6 @@ __device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int n
     return acc;
 }
 
-// Fire-and-forget float add to global memory.  Written out because pointers read from a
-// work list are generic to the compiler, which then emits an atomic that returns the old
-// value (and waits for it) instead of a reduction.
-__device__ __forceinline__ void red_add(float *p, float v)
-{
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
-}
-
 // Adjoint of one ray: one RED per voxel.  As in the forward, U voxels are generated ahead
 // and their U REDs issued back to back from separate registers.  accT may be NULL.
 template <int U>

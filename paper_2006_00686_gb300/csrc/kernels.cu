@@ -35,7 +35,7 @@ struct ScatterVisitor {
     {
 #pragma unroll
         for (int b = 0; b < BC; ++b)
-            if (b < nb && g[b] != 0.f) atomicAdd(img + b * bs + off, __fmul_rn(g[b], l));
+            if (b < nb && g[b] != 0.f) red_add(img + b * bs + off, __fmul_rn(g[b], l));
     }
 };
 

@@ -1,4 +1,4 @@
-// Per-geometry ray setup, double precision, in two kernels.
+// Per-geometry ray setup in two kernels.
 //
 // The paper maps every scan to parallel-beam ray parameters by its transformation formulas
 // (eq. 2Dparalleltofan, eq. 2Dparalleltofan_2, eq. equiangular_cone_beam,
@@ -6,28 +6,81 @@
 // eq. Helical_cone_beam_equispaced).  Their angles split into a part that depends only on
 // the detector sample (gamma; alpha and beta) and the view angle, which enters as a sum
 // (phi = gamma + alpha_v - pi/2, phi1 = phi'_1 + alpha):
-//   * det_setup_kernel: per detector sample, the transcendental part (atan, sqrt, sin,
-//     cos) -- s, s1, the detector part of s2, and cos/sin of gamma, alpha, beta;
+//   * det_setup_kernel: per detector sample, in double precision, the transcendental part
+//     (atan, sqrt, sin, cos) -- s, s1, the detector part of s2, and cos/sin of gamma, alpha,
+//     beta -- stored as float pairs;
 //   * ray_setup_kernel: per ray, cos/sin of the summed angle by the angle-sum identities,
 //     the ray point and direction (eq. direction_normal; eq. 3Dparallel_direction,
 //     theta_1, theta_2), the foot point closest to the image centre and the index-space
-//     record the walk uses (see xray_core.cuh).  Multiply-adds only.
+//     record the walk uses (see xray_core.cuh).
+// The per-ray arithmetic runs on float pairs (hi + lo) with the error-free transformations
+// of Dekker (1971) and Knuth (TAOCP vol. 2, 4.2.2): a product's rounding error is recovered
+// with one FMA, a sum's with the two-sum sequence.  That keeps about 48 significant bits --
+// the foot point's fraction needs about 37 -- on the FP32 pipes.  Products and sums of exact
+// values (axis-parallel rays, integer detector offsets) stay exact, so the fixed indices of
+// on-grid rays are found as with exact arithmetic.
 // The view part (cos/sin of the view angle, source height H) comes from the host.
 #include "xray_internal.h"
 
 namespace xr {
 
+// ---- float-pair arithmetic (round-to-nearest intrinsics: no contraction or reordering)
+
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ DF quick_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = two_sum(a.hi, b.hi);
+    const DF t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ bool df_is_zero(DF a) { return a.hi == 0.f && a.lo == 0.f; }
+
 // Snap cos/sin pairs within 1e-12 of a multiple of pi/2 to exact 0 and +-1, so that
 // axis-parallel and in-plane rays are recognised as such.
-__device__ __forceinline__ void snap(double &c, double &s)
+__device__ __forceinline__ void snap(DF &c, DF &s)
 {
-    if (fabs(c) < 1e-12) {
-        c = 0.0;
-        s = s > 0.0 ? 1.0 : -1.0;
-    } else if (fabs(s) < 1e-12) {
-        s = 0.0;
-        c = c > 0.0 ? 1.0 : -1.0;
+    if (fabsf(c.hi) < 1e-12f) {
+        c = DF{0.f, 0.f};
+        s = DF{s.hi > 0.f ? 1.f : -1.f, 0.f};
+    } else if (fabsf(s.hi) < 1e-12f) {
+        s = DF{0.f, 0.f};
+        c = DF{c.hi > 0.f ? 1.f : -1.f, 0.f};
     }
+}
+
+__device__ __forceinline__ DF to_df(double x)
+{
+    const float hi = __double2float_rn(x);
+    return DF{hi, __double2float_rn(x - (double)hi)};
 }
 
 __global__ void det_setup_kernel(GeoParams g, DetRec *__restrict__ out)
@@ -38,79 +91,74 @@ __global__ void det_setup_kernel(GeoParams g, DetRec *__restrict__ out)
     const double u = (c - 0.5 * (g.n_cols - 1)) * g.du + g.u0;
     const double w = (row - 0.5 * (g.n_rows - 1)) * g.dv + g.v0;
     const double D = g.sod;
-    DetRec R;
-    R.s1 = u;
-    R.s2 = w;
-    R.ca = 1.0;
-    R.sa = 0.0;
-    R.cb = 1.0;
-    R.sb = 0.0;
+    double s1 = u, s2 = w, ca = 1.0, sa = 0.0, cb = 1.0, sb = 0.0;
     switch (g.kind) {
     case XR_FAN2D: {  // eq. 2Dparalleltofan_2: t on the line through the origin
         const double t = u * g.sod / g.sdd;
         const double gam = atan(t / D);
-        R.s1 = D * t / sqrt(D * D + t * t);
-        sincos(gam, &R.sa, &R.ca);
+        s1 = D * t / sqrt(D * D + t * t);
+        sincos(gam, &sa, &ca);
         break;
     }
     case XR_FAN2D_ARC:  // eq. 2Dparalleltofan: u is gamma
-        R.s1 = D * sin(u);
-        sincos(u, &R.sa, &R.ca);
+        s1 = D * sin(u);
+        sincos(u, &sa, &ca);
         break;
     case XR_CONE:
     case XR_HELIX: {  // eq. equispaced_cone_beam (+ Helical_cone_beam_equispaced, H added per view)
         const double t = u * g.sod / g.sdd, h = w * g.sod / g.sdd;
         const double alpha = atan(t / D);
         const double beta = atan(h / sqrt(D * D + t * t));
-        sincos(alpha, &R.sa, &R.ca);
-        sincos(beta, &R.sb, &R.cb);
-        R.s1 = D * R.sa;
-        R.s2 = h * R.ca * R.ca * R.cb;
+        sincos(alpha, &sa, &ca);
+        sincos(beta, &sb, &cb);
+        s1 = D * sa;
+        s2 = h * ca * ca * cb;
         break;
     }
     case XR_CONE_ARC:
     case XR_HELIX_ARC:  // eq. equiangular_cone_beam (+ Helical_cone_beam_equiangular)
-        sincos(u, &R.sa, &R.ca);
-        sincos(w, &R.sb, &R.cb);
-        R.s1 = D * R.sa;
-        R.s2 = D * R.ca * R.sb;
+        sincos(u, &sa, &ca);
+        sincos(w, &sb, &cb);
+        s1 = D * sa;
+        s2 = D * ca * sb;
         break;
     default:  // parallel beams: s = u (2D); s1 = u, s2 = w (3D)
         break;
     }
+    DetRec R;
+    R.s1 = to_df(s1);
+    R.s2 = to_df(s2);
+    R.ca = to_df(ca);
+    R.sa = to_df(sa);
+    R.cb = to_df(cb);
+    R.sb = to_df(sb);
     out[d] = R;
 }
 
-__global__ void ray_setup_kernel(GeoParams g, const ViewRec *__restrict__ views,
-                                 const DetRec *__restrict__ det, RayRec *__restrict__ out, int64_t n_rays)
+// One ray: view v, detector sample d.
+__device__ __forceinline__ RayRec ray_record(const GeoParams &g, const SetupDF &K, const ViewDF &V, const DetRec &R)
 {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
-    const int64_t ndet = (int64_t)g.n_rows * g.n_cols;
-    const int v = (int)(r / ndet);
-    const DetRec R = det[r - (int64_t)v * ndet];
-    const ViewRec V = views[v];
-
-    double P[3], T[3];
+    DF P[3], T[3];
+    const DF zero{0.f, 0.f};
     if (g.kind <= XR_FAN2D_ARC) {
-        double cp, sp;
+        DF cp, sp;
         if (g.kind == XR_PAR2D) {
             cp = V.c1;  // phi = angles[v]
             sp = V.s1;
         } else {
             // phi = gamma + alpha - pi/2: cos(phi) = sin(gamma + alpha), sin(phi) = -cos(gamma + alpha)
-            cp = R.sa * V.c1 + R.ca * V.s1;
-            sp = R.sa * V.s1 - R.ca * V.c1;
+            cp = df_add(df_mul(R.sa, V.c1), df_mul(R.ca, V.s1));
+            sp = df_sub(df_mul(R.sa, V.s1), df_mul(R.ca, V.c1));
         }
         snap(cp, sp);
         T[0] = cp;
         T[1] = sp;
-        T[2] = 0.0;
-        P[0] = -R.s1 * sp;
-        P[1] = R.s1 * cp;
-        P[2] = g.cz;
+        T[2] = zero;
+        P[0] = df_neg(df_mul(R.s1, sp));
+        P[1] = df_mul(R.s1, cp);
+        P[2] = K.cz;
     } else {
-        double c1, sn1, c2, sn2, s1 = R.s1, s2 = R.s2;
+        DF c1, sn1, c2, sn2, s2 = R.s2;
         if (g.kind == XR_PAR3D) {
             c1 = V.c1;
             sn1 = V.s1;
@@ -118,62 +166,69 @@ __global__ void ray_setup_kernel(GeoParams g, const ViewRec *__restrict__ views,
             sn2 = V.s2;
         } else {
             // phi1 = phi'_1 + alpha, phi2 = beta
-            c1 = V.c1 * R.ca - V.s1 * R.sa;
-            sn1 = V.s1 * R.ca + V.c1 * R.sa;
+            c1 = df_sub(df_mul(V.c1, R.ca), df_mul(V.s1, R.sa));
+            sn1 = df_add(df_mul(V.s1, R.ca), df_mul(V.c1, R.sa));
             c2 = R.cb;
             sn2 = R.sb;
-            s2 += V.H * R.cb;
+            s2 = df_add(s2, df_mul(V.H, R.cb));
         }
         snap(c1, sn1);
         snap(c2, sn2);
-        T[0] = c2 * c1;
-        T[1] = c2 * sn1;
+        T[0] = df_mul(c2, c1);
+        T[1] = df_mul(c2, sn1);
         T[2] = sn2;
-        P[0] = -s1 * sn1 - s2 * sn2 * c1;
-        P[1] = s1 * c1 - s2 * sn2 * sn1;
-        P[2] = s2 * c2;
+        const DF s2sn2 = df_mul(s2, sn2);
+        P[0] = df_neg(df_add(df_mul(R.s1, sn1), df_mul(s2sn2, c1)));
+        P[1] = df_sub(df_mul(R.s1, c1), df_mul(s2sn2, sn1));
+        P[2] = df_mul(s2, c2);
     }
     // Foot point: the point of the line closest to the image centre.
-    const double tf = (g.cx - P[0]) * T[0] + (g.cy - P[1]) * T[1] + (g.cz - P[2]) * T[2];
-    for (int a = 0; a < 3; ++a) P[a] += (T[a] == 0.0 ? 0.0 : tf * T[a]);
+    const DF tf = df_add(df_add(df_mul(df_sub(K.cx, P[0]), T[0]), df_mul(df_sub(K.cy, P[1]), T[1])),
+                         df_mul(df_sub(K.cz, P[2]), T[2]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (!df_is_zero(T[a])) P[a] = df_add(P[a], df_mul(tf, T[a]));
 
-    // Index space: u_x grows with i, u_y with j (y falls), u_z with k (z falls).  The
-    // reciprocal spacings come from the host; whether the ray enters the image is decided by
-    // the walk's own box test.
+    // Index space: u_x grows with i, u_y with j (y falls), u_z with k (z falls).  Whether
+    // the ray enters the image is decided by the walk's own box test.
     const int N[3] = {g.nx, g.ny, g.nz};
-    const double o[3] = {(P[0] - (g.cx - 0.5 * g.nx * g.dx)) * g.inv_dx,
-                         ((g.cy + 0.5 * g.ny * g.dy) - P[1]) * g.inv_dy,
-                         ((g.cz + 0.5 * g.nz * g.dz) - P[2]) * g.inv_dz};
-    const double wd[3] = {T[0] * g.inv_dx, -T[1] * g.inv_dy, -T[2] * g.inv_dz};
+    const DF o[3] = {df_mul(df_sub(P[0], K.x0), K.idx), df_mul(df_sub(K.y1, P[1]), K.idy),
+                     df_mul(df_sub(K.z1, P[2]), K.idz)};
+    const DF wd[3] = {df_mul(T[0], K.idx), df_neg(df_mul(T[1], K.idy)), df_neg(df_mul(T[2], K.idz))};
 
     RayRec rec;
     int flags = 0;
     float wf[3], ff[3];
     int oi[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (wd[a] == 0.0) {
+        // floor of hi + lo, and the fraction left
+        float fl = floorf(o[a].hi);
+        if (o[a].hi == fl && o[a].lo < 0.f) fl -= 1.f;
+        const bool below = o[a].hi < 0.f || (o[a].hi == 0.f && o[a].lo < 0.f);
+        if (df_is_zero(wd[a])) {
             // Fixed index: unit n holds u in [n, n+1]; a ray on the plane u = n (two
             // candidates) takes the bigger index (Section 4.1), the far edge u = N the last.
             wf[a] = 0.f;
             ff[a] = 0.f;
-            if (o[a] >= 0.0 && o[a] <= N[a]) {
-                oi[a] = min((int)floor(o[a]), N[a] - 1);
+            const bool above = o[a].hi > (float)N[a] || (o[a].hi == (float)N[a] && o[a].lo > 0.f);
+            if (!below && !above) {
+                oi[a] = min((int)fl, N[a] - 1);
             } else {
                 oi[a] = -1;
                 flags |= RAY_MISS;
             }
         } else {
-            double fl = floor(o[a]);
-            float fr = (float)(o[a] - fl);
+            float fr = __fadd_rn(__fsub_rn(o[a].hi, fl), o[a].lo);
             if (fr >= 1.0f) {
                 fr = 0.0f;
-                fl += 1.0;
+                fl += 1.f;
             }
-            wf[a] = (float)wd[a];
+            wf[a] = __fadd_rn(wd[a].hi, wd[a].lo);
             ff[a] = fr;
-            if (fabs(fl) > 32000.0) {
+            if (fabsf(fl) > 32000.f) {
                 flags |= RAY_MISS;
-                fl = 0.0;
+                fl = 0.f;
             }
             oi[a] = (int)fl;
         }
@@ -188,7 +243,29 @@ __global__ void ray_setup_kernel(GeoParams g, const ViewRec *__restrict__ views,
     rec.o1 = (int16_t)oi[1];
     rec.o2 = (int16_t)oi[2];
     rec.flags = (int16_t)flags;
-    out[r] = rec;
+    return rec;
+}
+
+// blockIdx.y = view (when the views fit the grid's y extent), x: detector samples.
+__global__ void ray_setup_kernel(GeoParams g, SetupDF K, const ViewDF *__restrict__ views,
+                                 const DetRec *__restrict__ det, RayRec *__restrict__ out)
+{
+    const int ndet = g.n_rows * g.n_cols;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndet) return;
+    const int v = blockIdx.y;
+    out[(int64_t)v * ndet + d] = ray_record(g, K, views[v], det[d]);
+}
+
+// The same over a 1D grid, for scans with more views than the grid's y extent.
+__global__ void ray_setup_flat_kernel(GeoParams g, SetupDF K, const ViewDF *__restrict__ views,
+                                      const DetRec *__restrict__ det, RayRec *__restrict__ out, int64_t n_rays)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int64_t ndet = (int64_t)g.n_rows * g.n_cols;
+    const int64_t v = r / ndet;
+    out[r] = ray_record(g, K, views[v], det[r - v * ndet]);
 }
 
 cudaError_t launch_det_setup(const GeoParams &g, DetRec *d_det, cudaStream_t s)
@@ -198,13 +275,34 @@ cudaError_t launch_det_setup(const GeoParams &g, DetRec *d_det, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_setup(const GeoParams &g, const ViewRec *d_views, const DetRec *d_det, RayRec *d_rays,
-                             int64_t n_rays, cudaStream_t s)
+cudaError_t launch_ray_setup(const GeoParams &g, const SetupDF &c, const ViewDF *d_views, const DetRec *d_det,
+                             RayRec *d_rays, int64_t n_rays, cudaStream_t s)
 {
     const int block = 128;
-    const int64_t grid = (n_rays + block - 1) / block;
-    ray_setup_kernel<<<(unsigned)grid, block, 0, s>>>(g, d_views, d_det, d_rays, n_rays);
+    const int64_t ndet = (int64_t)g.n_rows * g.n_cols;
+    if (g.n_views <= 65535) {
+        const dim3 grid((unsigned)((ndet + block - 1) / block), (unsigned)g.n_views);
+        ray_setup_kernel<<<grid, block, 0, s>>>(g, c, d_views, d_det, d_rays);
+    } else {
+        ray_setup_flat_kernel<<<(unsigned)((n_rays + block - 1) / block), block, 0, s>>>(g, c, d_views, d_det, d_rays,
+                                                                                        n_rays);
+    }
     return cudaGetLastError();
+}
+
+SetupDF make_setup_df(const GeoParams &g)
+{
+    SetupDF K;
+    K.cx = df_from_double(g.cx);
+    K.cy = df_from_double(g.cy);
+    K.cz = df_from_double(g.cz);
+    K.x0 = df_from_double(g.cx - 0.5 * g.nx * g.dx);
+    K.y1 = df_from_double(g.cy + 0.5 * g.ny * g.dy);
+    K.z1 = df_from_double(g.cz + 0.5 * g.nz * g.dz);
+    K.idx = df_from_double(g.inv_dx);
+    K.idy = df_from_double(g.inv_dy);
+    K.idz = df_from_double(g.inv_dz);
+    return K;
 }
 
 }  // namespace xr

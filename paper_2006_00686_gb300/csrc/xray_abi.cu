@@ -226,6 +226,7 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     cudaError_t e = cudaGetDevice(&g->device);
     const size_t n_det = (size_t)p.n_rows * p.n_cols;
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views, (size_t)p.n_views * sizeof(ViewRec));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_views_df, (size_t)p.n_views * sizeof(ViewDF));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_det, n_det * sizeof(DetRec));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
     if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_view_tab, (size_t)p.n_views * 8 * sizeof(float));
@@ -255,6 +256,22 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
             vr[v].H = kind_helical(desc->kind) ? desc->src_z[v] : 0.0;
         }
         e = cudaMemcpy(g->d_views, vr, (size_t)p.n_views * sizeof(ViewRec), cudaMemcpyHostToDevice);
+        ViewDF *vd = (ViewDF *)calloc((size_t)p.n_views, sizeof(ViewDF));
+        if (!vd) {
+            free(vr);
+            xr_geometry_destroy(g);
+            return XR_ERR_ALLOC;
+        }
+        for (int v = 0; v < p.n_views; ++v) {
+            vd[v].c1 = df_from_double(vr[v].c1);
+            vd[v].s1 = df_from_double(vr[v].s1);
+            vd[v].c2 = df_from_double(vr[v].c2);
+            vd[v].s2 = df_from_double(vr[v].s2);
+            vd[v].H = df_from_double(vr[v].H);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->d_views_df, vd, (size_t)p.n_views * sizeof(ViewDF), cudaMemcpyHostToDevice);
+        free(vd);
         free(vr);
     }
     if (e == cudaSuccess && !three) {
@@ -268,7 +285,8 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
         free(vt);
     }
     if (e == cudaSuccess) e = launch_det_setup(p, g->d_det, nullptr);
-    if (e == cudaSuccess) e = launch_ray_setup(p, g->d_views, g->d_det, g->d_rays, g->n_rays, nullptr);
+    g->setup_df = make_setup_df(p);
+    if (e == cudaSuccess) e = launch_ray_setup(p, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays, nullptr);
     if (e == cudaSuccess && g->d_grec) e = launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
@@ -287,6 +305,7 @@ void xr_geometry_destroy(xr_geometry *g)
     cudaSetDevice(g->device);
     cudaDeviceSynchronize();
     cudaFree(g->d_views);
+    cudaFree(g->d_views_df);
     cudaFree(g->d_det);
     cudaFree(g->d_rays);
     cudaFree(g->d_view_tab);
@@ -300,7 +319,8 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream)
 {
     if (!g) return XR_ERR_NULL;
     XR_CUDA(launch_det_setup(g->params, g->d_det, (cudaStream_t)stream));
-    XR_CUDA(launch_ray_setup(g->params, g->d_views, g->d_det, g->d_rays, g->n_rays, (cudaStream_t)stream));
+    XR_CUDA(launch_ray_setup(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays,
+                             (cudaStream_t)stream));
     if (g->d_grec) XR_CUDA(launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, (cudaStream_t)stream));
     return XR_OK;
 }
@@ -338,7 +358,7 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
     if (!g || !info) return XR_ERR_NULL;
     info->n_rays = g->n_rays;
     info->n_units = g->n_units;
-    info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * (8 * 4 + sizeof(ViewRec)) +
+    info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * (8 * 4 + sizeof(ViewRec) + sizeof(ViewDF)) +
                         (int64_t)g->params.n_rows * g->params.n_cols * (int64_t)sizeof(DetRec) +
                         (g->d_grec ? g->n_rays * (int64_t)gather_rec_bytes() : 0) + (int64_t)g->ws_bytes;
     info->is3d = kind_is3d(g->params.kind);

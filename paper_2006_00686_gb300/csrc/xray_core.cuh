@@ -43,6 +43,22 @@ static_assert(sizeof(RayRec) == 32, "RayRec layout");
 
 enum { RAY_MISS = 1 };
 
+// Fire-and-forget float add to global memory.  Written out because a pointer read from a
+// struct or a work list is generic to the compiler, which then emits an atomic that returns
+// the old value (and waits for it) instead of a reduction.
+__device__ __forceinline__ void red_add(float *p, float v)
+{
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+}
+
+// The same for four consecutive floats (16-byte aligned): one 128-bit vector reduction.
+__device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+
 template <class T>
 __device__ __forceinline__ T sel3(int a, T x, T y, T z)
 {

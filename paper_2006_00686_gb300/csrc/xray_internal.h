@@ -29,10 +29,24 @@ struct Grid {
 
 inline bool kind_is3d(int k) { return k >= XR_PAR3D; }
 
+// A float pair hi + lo with |lo| <= ulp(hi) / 2: about 48 significant bits, computed on the
+// FP32 pipes (GB300's FP64 rate is a small fraction of its FP32 rate).
+struct DF {
+    float hi, lo;
+};
+
+inline DF df_from_double(double x)
+{
+    DF r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
 // Per detector sample: the parts of the ray parameters that depend on the detector only
 // (2D: s and cos/sin of gamma; 3D: s1, the detector part of s2, cos/sin of alpha and beta).
 struct DetRec {
-    double s1, s2, ca, sa, cb, sb;
+    DF s1, s2, ca, sa, cb, sb;
 };
 
 // Per view: cos/sin of the view angle (PAR3D: of phi1 and phi2) and the source height.
@@ -40,9 +54,22 @@ struct ViewRec {
     double c1, s1, c2, s2, H, pad0, pad1, pad2;
 };
 
+// The same per view, as float pairs, for the ray setup.
+struct ViewDF {
+    DF c1, s1, c2, s2, H, pad;
+};
+
+// Scan constants of the ray setup, as float pairs: the image centre, the planes i = 0,
+// j = 0, k = 0 (x0 = cx - nx dx / 2, y1 = cy + ny dy / 2, z1 = cz + nz dz / 2) and 1/d.
+struct SetupDF {
+    DF cx, cy, cz, x0, y1, z1, idx, idy, idz;
+};
+
+SetupDF make_setup_df(const GeoParams &g);
+
 cudaError_t launch_det_setup(const GeoParams &g, DetRec *d_det, cudaStream_t s);
-cudaError_t launch_ray_setup(const GeoParams &g, const ViewRec *d_views, const DetRec *d_det, RayRec *d_rays,
-                             int64_t n_rays, cudaStream_t s);
+cudaError_t launch_ray_setup(const GeoParams &g, const SetupDF &c, const ViewDF *d_views, const DetRec *d_det,
+                             RayRec *d_rays, int64_t n_rays, cudaStream_t s);
 
 cudaError_t launch_project(const RayRec *rays, int64_t n_rays, const Grid &grid, const float *img,
                            int64_t img_bs, float *sino, int64_t sino_bs, int batch, int chunk,
@@ -153,8 +180,10 @@ struct xr_geometry {
     xr::GeoParams params;
     int device;
     int64_t n_rays, n_units;
-    xr::ViewRec *d_views;  // per view (host-computed cos/sin of the view angles)
-    xr::DetRec *d_det;     // per detector sample (det_setup_kernel)
+    xr::ViewRec *d_views;    // per view (host-computed cos/sin of the view angles)
+    xr::ViewDF *d_views_df;  // the same as float pairs
+    xr::SetupDF setup_df;    // scan constants of the ray setup
+    xr::DetRec *d_det;       // per detector sample (det_setup_kernel)
     xr::RayRec *d_rays;
     float *d_view_tab;   // per view: 2D gather footprint data (8 floats)
     void *d_grec;        // per ray: plane constants of the 2D gather
