@@ -273,11 +273,11 @@ def run_ours(args, rank, world, local_rank):
     dom, dom_ms = ("forward", fwd) if fwd >= adj else ("adjoint", adj)
     # the method the library's automatic choice takes: the gather on the 2D quad-plane path
     # (batches of 4 or more), the scatter elsewhere
-    adj = P.tuning()["adjoint"]
-    if adj == 0:
+    adj_mode = P.tuning()["adjoint"]
+    if adj_mode == 0:
         method = "gather" if (not g.is3d and B >= 4) else "scatter"
     else:
-        method = "gather" if adj == XR_ADJ_GATHER else "scatter"
+        method = "gather" if adj_mode == XR_ADJ_GATHER else "scatter"
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
     # forward and gather kernels, from one ncu capture of this workload
     traffic = None
