@@ -188,6 +188,13 @@ def _e2e(step, host_in, dev_in, dev_out, host_out, args, flush):
     return float(np.mean(out))
 
 
+def _l2_peak():
+    """Measured L2 read bandwidth (GB/s): a 64 MiB buffer read 20 times per launch with
+    128-bit L2-only loads (xr_read_probe), best of 5 launches."""
+    from paper_2006_00686_gb300.xray import read_bandwidth
+    return read_bandwidth(64 << 20, 20, 5)
+
+
 def _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic):
     # The path is bound by neither HBM (for the 2D workloads the images and sinograms stay
     # in L2) nor tensor cores: every unit costs scalar FP32 work.  "alu": achieved =
@@ -200,14 +207,19 @@ def _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic):
     mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     compulsory = 4.0 * (g.n_units + g.n_rays) * B
+    gather = 4.0 * n_int * B
+    gather_gbs = gather / (dom_ms * 1e-3) / 1e9
+    l2_peak = _l2_peak()
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({peak_kind} max clock)",
             "algorithmic_flop": flop, "intersections_per_image": n_int, "ms": round(dom_ms, 4),
             "hbm": {"compulsory_bytes": compulsory, "achieved_gbs": round(compulsory / (dom_ms * 1e-3) / 1e9, 1),
-                    "gather_bytes": 4.0 * n_int * B,
-                    "gather_gbs": round(4.0 * n_int * B / (dom_ms * 1e-3) / 1e9, 1),
-                    "peak_gbs": peaks["hbm_gbs"]}}
+                    "peak_gbs": peaks["hbm_gbs"], "frac": round(compulsory / (dom_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
+            # the gather along rays as bytes: 4 B per (ray, unit, image), served from L1/L2
+            "l2": {"algorithmic_bytes": gather, "achieved_gbs": round(gather_gbs, 1), "peak_gbs": round(l2_peak, 1),
+                   "frac": round(gather_gbs / l2_peak, 4),
+                   "peak_source": "measured: xr_read_probe, 64 MiB read 20x per launch, L2-only loads"}}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -361,8 +373,27 @@ def _autograd_and_sirt(P, x, y, args):
     e.record()
     e.synchronize()
     sirt_ms = a.elapsed_time(e) / n
+    # ordered-subset SIRT (8 interleaved view subsets) and Tikhonov CGLS on the same scan
+    os = recon.OSSIRT(P.geom, b, 8)
+    os.sweep()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(n):
+        os.sweep()
+    e.record()
+    e.synchronize()
+    os_ms = a.elapsed_time(e) / n
+    os.close()
+    recon.cgls(P, b, 2, lam=1.0)
+    torch.cuda.synchronize()
+    a.record()
+    recon.cgls(P, b, n, lam=1.0)
+    e.record()
+    e.synchronize()
+    cg_ms = a.elapsed_time(e) / n  # one CGLS iteration: a forward, an adjoint and 3 reductions
     rays = P.geom.n_rays
-    return {"autograd_fwd_bwd_ms": round(ad_ms, 3),
+    return {"os_sirt_sweep_ms": round(os_ms, 3), "cgls_iter_ms": round(cg_ms, 3),
+            "autograd_fwd_bwd_ms": round(ad_ms, 3),
             "autograd_grays_s": round(rays / (ad_ms * 1e-3) / 1e9, 4),
             "sirt_iter_ms_graph": round(sirt_ms, 3),
             "sirt_grays_s": round(rays / (sirt_ms * 1e-3) / 1e9, 4)}

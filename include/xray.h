@@ -65,6 +65,9 @@ typedef enum {
     XR_CONE_ARC = 5,   /* equiangular circular cone: u, v are the angles alpha, beta (eq. equiangular_cone_beam) */
     XR_HELIX = 6,      /* equispaced helical cone: src_z[v] = H (eq. Helical_cone_beam_equispaced) */
     XR_HELIX_ARC = 7,  /* equiangular helical cone (eq. Helical_cone_beam_equiangular) */
+    XR_RAYS2D = 8,     /* a list of rays given by their parameters: angles[2r], angles[2r+1] = s, phi
+                          (Section 4.3, Adaptability); n_views = number of rays */
+    XR_RAYS3D = 9,     /* a list of rays: angles[4r .. 4r+3] = s1, s2, phi1, phi2 (Section 4.3) */
 } xr_kind;
 
 /* Scan description.  Host memory; the library copies what it needs during
@@ -77,8 +80,9 @@ typedef struct {
     int32_t nx, ny, nz;            /* image size (2D: nz = 1); each in [1, 16384] */
     double dx, dy, dz;             /* unit spacing (> 0) */
     double cx, cy, cz;             /* image centre (Section 4.2) */
-    int32_t n_views, n_rows, n_cols; /* detector (2D: n_rows = 1) */
-    const double *angles;          /* [n_views] (XR_PAR3D: [n_views][2]) */
+    int32_t n_views, n_rows, n_cols; /* detector (2D: n_rows = 1; ray lists: n_rows = n_cols = 1) */
+    const double *angles;          /* [n_views] (XR_PAR3D: [n_views][2]; XR_RAYS2D: [n_rays][2];
+                                      XR_RAYS3D: [n_rays][4]) */
     const double *src_z;           /* [n_views] source heights H for helical kinds, else NULL */
     double du, dv, u0, v0;         /* detector sampling */
     double sod, sdd;               /* source-origin and source-detector distances (fan/cone) */
@@ -173,7 +177,8 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
 xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img, int32_t batch,
                          xr_stream stream);
 
-/* As xr_backproject with an explicit method.  XR_ADJ_SCATTER: ray-driven, each ray adds
+/* As xr_backproject with an explicit method (ray lists have no detector to gather over: the
+ * scatter only, XR_ADJ_GATHER returns XR_ERR_ARG).  XR_ADJ_SCATTER: ray-driven, each ray adds
  * l * g to every unit it crosses (atomics).  XR_ADJ_GATHER: unit-driven; 2D scans: one thread
  * per pixel sums the rays whose detector footprint covers it; 3D scans: one CTA per 16^3
  * tile of voxels walks every ray of the tile's detector footprint through the tile and sums
@@ -235,6 +240,15 @@ xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream);
 #define XR_NOALLOC_MAX_PROBLEMS 256
 xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t n, int32_t tile,
                                      xr_stream stream);
+
+/* Read-bandwidth probe (measurement only; the paper has no counterpart).  Reads the device
+ * buffer d_buf of n_floats floats (a multiple of 4, 16-byte aligned) `reps` times with 128-bit
+ * loads that are cached in L2 only, on a grid of every SM's resident CTAs, and writes one float
+ * per thread to d_sink (device, sink_floats >= SMs x resident CTAs x 256).  Timed with events on
+ * `stream`, bytes / time is the L2 read bandwidth when the buffer fits L2.
+ * Errors: XR_ERR_NULL, XR_ERR_SIZE, XR_ERR_ALIGN, XR_ERR_CUDA. */
+xr_status xr_read_probe(const float *d_buf, int64_t n_floats, int32_t reps, float *d_sink,
+                        int32_t sink_floats, xr_stream stream);
 
 /* Text of a status code (static storage). */
 const char *xr_status_string(xr_status s);

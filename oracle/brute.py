@@ -61,6 +61,19 @@ def ray_of(g, ray: int):
         else:
             d = math.cos(u) * e_c + math.sin(u) * e_t  # u is the fan angle
         p = S
+    elif k == "rays2d":
+        # the ray with normal distance s and direction (cos phi, sin phi) (eq. direction_normal)
+        sv, phi = float(ang[v][0]), float(ang[v][1])
+        c, s = _cs(phi)
+        p = np.array([-sv * s, sv * c, 0.0])
+        d = np.array([c, s, 0.0])
+    elif k == "rays3d":
+        # p = s1 theta_1 + s2 theta_2, direction theta (eq. 3Dparallel_direction, theta_1, theta_2)
+        s1v, s2v, f1, f2 = (float(x) for x in ang[v])
+        c1, s1 = _cs(f1)
+        c2, s2 = _cs(f2)
+        d = np.array([c2 * c1, c2 * s1, s2])
+        p = s1v * np.array([-s1, c1, 0.0]) + s2v * np.array([-s2 * c1, -s2 * s1, c2])
     elif k == "par3d":
         c1, s1 = _cs(float(ang[v][0]))
         c2, s2 = _cs(float(ang[v][1]))
@@ -111,7 +124,7 @@ def _axis_intervals(b, p, d, n, lower_first):
 def lengths(g, p, d) -> np.ndarray:
     """Exact intersection length with every unit, shape image_shape (2D: [ny, nx])."""
     bx, by, bz = _bounds(g)
-    three = g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc")
+    three = g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc", "rays3d")
     lx0, lx1, mx = _axis_intervals(bx, p[0], d[0], g.nx, True)
     ly0, ly1, my = _axis_intervals(by, p[1], d[1], g.ny, False)
     if three:
@@ -142,7 +155,7 @@ def box_chord(g, p, d) -> float:
     """Length of the line inside the image box (slab method on one box)."""
     lo = np.array([g.cx - g.nx * g.dx / 2, g.cy - g.ny * g.dy / 2, g.cz - g.nz * g.dz / 2])
     hi = np.array([g.cx + g.nx * g.dx / 2, g.cy + g.ny * g.dy / 2, g.cz + g.nz * g.dz / 2])
-    three = g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc")
+    three = g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc", "rays3d")
     t0, t1 = -np.inf, np.inf
     for a in range(3 if three else 2):
         if d[a] == 0.0:
@@ -156,7 +169,7 @@ def box_chord(g, p, d) -> float:
 
 def sampled_lengths(g, p, d, h: float = 1e-3) -> np.ndarray:
     """Midpoint sampling of the line at spacing h inside the box; per-unit error <= 2h."""
-    three = g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc")
+    three = g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc", "rays3d")
     lo = np.array([g.cx - g.nx * g.dx / 2, g.cy - g.ny * g.dy / 2, g.cz - g.nz * g.dz / 2])
     hi = np.array([g.cx + g.nx * g.dx / 2, g.cy + g.ny * g.dy / 2, g.cz + g.nz * g.dz / 2])
     R = float(np.linalg.norm(hi - lo)) + float(np.linalg.norm(p - 0.5 * (lo + hi)))

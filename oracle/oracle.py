@@ -17,7 +17,7 @@ SRC = os.path.join(HERE, "xray_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 KIND_IDS = {"par2d": 0, "fan2d": 1, "fan2d_arc": 2, "par3d": 3, "cone": 4, "cone_arc": 5,
-            "helix": 6, "helix_arc": 7}
+            "helix": 6, "helix_arc": 7, "rays2d": 8, "rays3d": 9}
 
 
 def build(force: bool = False) -> str:

@@ -11,7 +11,8 @@
  *   1. ray parameters from the scan: eq. 2Dparalleltofan (equiangular fan),
  *      eq. 2Dparalleltofan_2 (equispaced fan), eq. equiangular_cone_beam,
  *      eq. equispaced_cone_beam, eq. Helical_cone_beam_equiangular,
- *      eq. Helical_cone_beam_equispaced;
+ *      eq. Helical_cone_beam_equispaced; a ray list gives each ray's parallel-beam
+ *      parameters directly (Section 4.3, Adaptability);
  *   2. the ray symmetries that bring a 2D ray to phi in [0, pi) (Section 2.2.1) and a 3D ray
  *      to (phi1, phi2) in [0, 2pi) x [0, pi/2] (Section 3.2.1);
  *   3. the ray point and direction: eq. direction_normal (2D), eq. 3Dparallel_direction,
@@ -63,7 +64,7 @@
 #endif
 
 enum { K_PAR2D = 0, K_FAN2D = 1, K_FAN2D_ARC = 2, K_PAR3D = 3, K_CONE = 4, K_CONE_ARC = 5,
-       K_HELIX = 6, K_HELIX_ARC = 7 };
+       K_HELIX = 6, K_HELIX_ARC = 7, K_RAYS2D = 8, K_RAYS3D = 9 };
 
 typedef struct {
     int kind;
@@ -71,13 +72,14 @@ typedef struct {
     double dx, dy, dz;
     double cx, cy, cz;
     int n_views, n_rows, n_cols;
-    const double *angles; /* n_views, or 2*n_views (phi1, phi2) for parallel 3D */
+    const double *angles; /* n_views, or 2*n_views (phi1, phi2) for parallel 3D; ray lists:
+                             (s, phi) per ray (2D) or (s1, s2, phi1, phi2) per ray (3D) */
     const double *src_z;  /* n_views for helical kinds, else NULL */
     double du, dv, u0, v0;
     double sod, sdd;
 } orc_geom;
 
-static int is3d(const orc_geom *g) { return g->kind >= K_PAR3D; }
+static int is3d(const orc_geom *g) { return g->kind >= K_PAR3D && g->kind != K_RAYS2D; }
 
 /* ---------------------------------------------------------------------------------------
  * Unit lists and the optional trace of intermediate quantities
@@ -295,6 +297,13 @@ static double det_v(const orc_geom *g, long r) { return (r - 0.5 * (g->n_rows - 
 /* 2D: (s, phi) of ray (view v, column c) */
 static void params_2d(const orc_geom *g, long v, long c, double *s, double *phi)
 {
+    if (g->kind == K_RAYS2D) {
+        /* a ray given by its own parameters (Section 4.3: any ray set whose parameters are
+         * known) */
+        *s = g->angles[2 * v];
+        *phi = g->angles[2 * v + 1];
+        return;
+    }
     const double u = det_u(g, c), a = g->angles[v], D = g->sod;
     if (g->kind == K_PAR2D) {
         *s = u;
@@ -315,6 +324,13 @@ static void params_2d(const orc_geom *g, long v, long c, double *s, double *phi)
 static void params_3d(const orc_geom *g, long v, long r, long c, double *s1, double *s2,
                       double *phi1, double *phi2)
 {
+    if (g->kind == K_RAYS3D) {
+        *s1 = g->angles[4 * v];
+        *s2 = g->angles[4 * v + 1];
+        *phi1 = g->angles[4 * v + 2];
+        *phi2 = g->angles[4 * v + 3];
+        return;
+    }
     const double u = det_u(g, c), w = det_v(g, r), D = g->sod;
     const int helical = (g->kind == K_HELIX || g->kind == K_HELIX_ARC);
     const double H = helical ? g->src_z[v] : 0.0;

@@ -1,0 +1,49 @@
+// Read-bandwidth probe: the denominator of the L2 roofline the benchmark reports next to the
+// FP32 one.  A buffer small enough to stay in L2 is read `reps` times with 128-bit loads by a
+// grid of (SMs x resident CTAs); one float per thread is written so the loads are not dropped.
+#include "xray_internal.h"
+
+namespace xr {
+namespace {
+
+__global__ void __launch_bounds__(256) read_probe_kernel(const float4 *__restrict__ buf, int64_t n4, int reps,
+                                                         float *__restrict__ sink)
+{
+    float acc = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r) {
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += stride) {
+            const float4 v = __ldcg(buf + k);  // cached in L2 only: every pass is an L2 read
+            acc += (v.x + v.y) + (v.z + v.w);
+        }
+    }
+    sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+}  // namespace
+}  // namespace xr
+
+#define PROBE_CUDA(call)                              \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return xr_fail_cuda(e_); \
+    } while (0)
+
+extern "C" xr_status xr_read_probe(const float *d_buf, int64_t n_floats, int32_t reps, float *d_sink,
+                                   int32_t sink_floats, xr_stream stream)
+{
+    using namespace xr;
+    if (!d_buf || !d_sink) return XR_ERR_NULL;
+    if (n_floats < 4 || reps < 1 || (n_floats & 3)) return XR_ERR_SIZE;
+    if (((uintptr_t)d_buf & 15u) != 0) return XR_ERR_ALIGN;
+    int dev = 0, sms = 0, per_sm = 0;
+    PROBE_CUDA(cudaGetDevice(&dev));
+    PROBE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PROBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, read_probe_kernel, 256, 0));
+    const int grid = sms * (per_sm > 0 ? per_sm : 1);
+    if ((int64_t)grid * 256 > sink_floats) return XR_ERR_SIZE;
+    read_probe_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4 *>(d_buf), n_floats / 4,
+                                                              reps, d_sink);
+    PROBE_CUDA(cudaGetLastError());
+    return XR_OK;
+}

@@ -12,7 +12,8 @@
 //   * ray_setup_kernel: per ray, cos/sin of the summed angle by the angle-sum identities,
 //     the ray point and direction (eq. direction_normal; eq. 3Dparallel_direction,
 //     theta_1, theta_2), the foot point closest to the image centre and the index-space
-//     record the walk uses (see xray_core.cuh).
+//     record the walk uses (see xray_core.cuh).  A ray list carries each ray's parameters
+//     in its per-view record (Section 4.3: the method needs nothing but them).
 // The per-ray arithmetic runs on float pairs (hi + lo) with the error-free transformations
 // of Dekker (1971) and Knuth (TAOCP vol. 2, 4.2.2): a product's rounding error is recovered
 // with one FMA, a sum's with the two-sum sequence.  That keeps about 48 significant bits --
@@ -140,11 +141,12 @@ __device__ __forceinline__ RayRec ray_record(const GeoParams &g, const SetupDF &
 {
     DF P[3], T[3];
     const DF zero{0.f, 0.f};
-    if (g.kind <= XR_FAN2D_ARC) {
-        DF cp, sp;
-        if (g.kind == XR_PAR2D) {
+    if (g.kind <= XR_FAN2D_ARC || g.kind == XR_RAYS2D) {
+        DF cp, sp, sv = R.s1;
+        if (g.kind == XR_PAR2D || g.kind == XR_RAYS2D) {
             cp = V.c1;  // phi = angles[v]
             sp = V.s1;
+            if (g.kind == XR_RAYS2D) sv = V.H;  // the ray's own s
         } else {
             // phi = gamma + alpha - pi/2: cos(phi) = sin(gamma + alpha), sin(phi) = -cos(gamma + alpha)
             cp = df_add(df_mul(R.sa, V.c1), df_mul(R.ca, V.s1));
@@ -154,16 +156,20 @@ __device__ __forceinline__ RayRec ray_record(const GeoParams &g, const SetupDF &
         T[0] = cp;
         T[1] = sp;
         T[2] = zero;
-        P[0] = df_neg(df_mul(R.s1, sp));
-        P[1] = df_mul(R.s1, cp);
+        P[0] = df_neg(df_mul(sv, sp));
+        P[1] = df_mul(sv, cp);
         P[2] = K.cz;
     } else {
-        DF c1, sn1, c2, sn2, s2 = R.s2;
-        if (g.kind == XR_PAR3D) {
+        DF c1, sn1, c2, sn2, s1 = R.s1, s2 = R.s2;
+        if (g.kind == XR_PAR3D || g.kind == XR_RAYS3D) {
             c1 = V.c1;
             sn1 = V.s1;
             c2 = V.c2;
             sn2 = V.s2;
+            if (g.kind == XR_RAYS3D) {  // the ray's own s1, s2
+                s1 = V.H;
+                s2 = V.pad;
+            }
         } else {
             // phi1 = phi'_1 + alpha, phi2 = beta
             c1 = df_sub(df_mul(V.c1, R.ca), df_mul(V.s1, R.sa));
@@ -178,8 +184,8 @@ __device__ __forceinline__ RayRec ray_record(const GeoParams &g, const SetupDF &
         T[1] = df_mul(c2, sn1);
         T[2] = sn2;
         const DF s2sn2 = df_mul(s2, sn2);
-        P[0] = df_neg(df_add(df_mul(R.s1, sn1), df_mul(s2sn2, c1)));
-        P[1] = df_sub(df_mul(R.s1, c1), df_mul(s2sn2, sn1));
+        P[0] = df_neg(df_add(df_mul(s1, sn1), df_mul(s2sn2, c1)));
+        P[1] = df_sub(df_mul(s1, c1), df_mul(s2sn2, sn1));
         P[2] = df_mul(s2, c2);
     }
     // Foot point: the point of the line closest to the image centre.

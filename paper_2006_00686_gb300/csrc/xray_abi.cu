@@ -26,16 +26,20 @@ static xr_status cuda_fail(cudaError_t e) { return xr_fail_cuda(e); }
     } while (0)
 
 static bool kind_helical(int k) { return k == XR_HELIX || k == XR_HELIX_ARC; }
-static bool kind_divergent(int k) { return k == XR_FAN2D || k == XR_FAN2D_ARC || k >= XR_CONE; }
+static bool kind_divergent(int k)
+{
+    return k == XR_FAN2D || k == XR_FAN2D_ARC || (k >= XR_CONE && k <= XR_HELIX_ARC);
+}
 static bool kind_flat(int k) { return k == XR_FAN2D || k == XR_CONE || k == XR_HELIX; }
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 static xr_status validate(const xr_geometry_desc *d)
 {
     if (!d) return XR_ERR_NULL;
-    if (d->kind < XR_PAR2D || d->kind > XR_HELIX_ARC) return XR_ERR_KIND;
-    const bool three = kind_is3d(d->kind);
-    const int nz = three ? d->nz : 1, nr = three ? d->n_rows : 1;
+    if (d->kind < XR_PAR2D || d->kind > XR_RAYS3D) return XR_ERR_KIND;
+    const bool three = kind_is3d(d->kind), list = kind_is_list(d->kind);
+    const int nz = three ? d->nz : 1, nr = (three && !list) ? d->n_rows : 1;
+    if (list && (d->n_cols != 1 || (three && d->n_rows != 1))) return XR_ERR_SIZE;
     if (d->nx < 1 || d->ny < 1 || nz < 1 || d->nx > 16384 || d->ny > 16384 || nz > 16384) return XR_ERR_SIZE;
     if (d->n_views < 1 || d->n_cols < 1 || nr < 1) return XR_ERR_SIZE;
     if ((int64_t)d->n_views * nr * d->n_cols > ((int64_t)1 << 40)) return XR_ERR_SIZE;
@@ -43,7 +47,7 @@ static xr_status validate(const xr_geometry_desc *d)
     if (!d->angles) return XR_ERR_NULL;
     if (kind_helical(d->kind) && !d->src_z) return XR_ERR_NULL;
     if (!(d->dx > 0) || !(d->dy > 0) || (three && !(d->dz > 0))) return XR_ERR_GEOMETRY;
-    if (!(d->du > 0) || (three && !(d->dv > 0))) return XR_ERR_GEOMETRY;
+    if (!list && (!(d->du > 0) || (three && !(d->dv > 0)))) return XR_ERR_GEOMETRY;
     if (kind_divergent(d->kind)) {
         if (!(d->sod > 0)) return XR_ERR_GEOMETRY;
         if (kind_flat(d->kind) && !(d->sdd > 0)) return XR_ERR_GEOMETRY;
@@ -77,6 +81,10 @@ static void fill_view_table(const xr_geometry_desc *d, float *vt)
 {
     for (int v = 0; v < d->n_views; ++v) {
         double e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (kind_is_list(d->kind)) {  // no detector: the gathers do not take ray lists
+            for (int k = 0; k < 8; ++k) vt[8 * v + k] = 0.f;
+            continue;
+        }
         const double a = d->angles[v];
         if (d->kind == XR_PAR2D) {
             e[0] = -sin(a);  // s = -x sin(phi) + y cos(phi)
@@ -130,7 +138,7 @@ static int plane_nq(const xr_geometry *g, int batch)
 // Tiled path: 2D scans, batches of 4 or more (no workspace needed).
 static bool use_tiled(const xr_geometry *g, int batch)
 {
-    return !kind_is3d(g->params.kind) && batch >= 4 && g->tune.batch_chunk != 1 && g->tune.path == XR_PATH_TILED;
+    return !kind_is3d(g->params.kind) && !kind_is_list(g->params.kind) && batch >= 4 && g->tune.batch_chunk != 1 && g->tune.path == XR_PATH_TILED;
 }
 
 static bool use_fast(const xr_geometry *g, int batch)
@@ -180,6 +188,12 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     if (!g) return XR_ERR_ALLOC;
     g->desc = *desc;
     const bool three = kind_is3d(desc->kind);
+    if (kind_is_list(desc->kind)) {
+        g->desc.n_rows = 1;
+        g->desc.n_cols = 1;
+        g->desc.du = g->desc.dv = 1.0;
+        g->desc.u0 = g->desc.v0 = 0.0;
+    }
     if (!three) {
         g->desc.nz = 1;
         g->desc.n_rows = 1;
@@ -195,17 +209,17 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     p.nz = g->desc.nz;
     p.n_views = desc->n_views;
     p.n_rows = g->desc.n_rows;
-    p.n_cols = desc->n_cols;
+    p.n_cols = g->desc.n_cols;
     p.dx = desc->dx;
     p.dy = desc->dy;
     p.dz = g->desc.dz;
     p.cx = desc->cx;
     p.cy = desc->cy;
     p.cz = desc->cz;
-    p.du = desc->du;
+    p.du = g->desc.du;
     p.dv = g->desc.dv;
-    p.u0 = desc->u0;
-    p.v0 = three ? desc->v0 : 0.0;
+    p.u0 = g->desc.u0;
+    p.v0 = three ? g->desc.v0 : 0.0;
     p.sod = desc->sod;
     p.sdd = desc->sdd;
     p.inv_dx = 1.0 / p.dx;
@@ -246,6 +260,22 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
             return XR_ERR_ALLOC;
         }
         for (int v = 0; v < p.n_views; ++v) {
+            if (desc->kind == XR_RAYS2D) {  // (s, phi)
+                vr[v].c1 = cos(desc->angles[2 * v + 1]);
+                vr[v].s1 = sin(desc->angles[2 * v + 1]);
+                vr[v].H = desc->angles[2 * v];
+                continue;
+            }
+            if (desc->kind == XR_RAYS3D) {  // (s1, s2, phi1, phi2)
+                const double *q = desc->angles + 4 * (size_t)v;
+                vr[v].c1 = cos(q[2]);
+                vr[v].s1 = sin(q[2]);
+                vr[v].c2 = cos(q[3]);
+                vr[v].s2 = sin(q[3]);
+                vr[v].H = q[0];
+                vr[v].pad0 = q[1];
+                continue;
+            }
             const double a = desc->kind == XR_PAR3D ? desc->angles[2 * v] : desc->angles[v];
             vr[v].c1 = cos(a);
             vr[v].s1 = sin(a);
@@ -268,6 +298,7 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
             vd[v].c2 = df_from_double(vr[v].c2);
             vd[v].s2 = df_from_double(vr[v].s2);
             vd[v].H = df_from_double(vr[v].H);
+            vd[v].pad = df_from_double(vr[v].pad0);
         }
         if (e == cudaSuccess)
             e = cudaMemcpy(g->d_views_df, vd, (size_t)p.n_views * sizeof(ViewDF), cudaMemcpyHostToDevice);
@@ -437,6 +468,10 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if (batch < 1) return XR_ERR_BATCH;
     if (!aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
     if (method == XR_ADJ_AUTO) method = g->tune.adjoint;
+    if (kind_is_list(g->params.kind)) {
+        if (method == XR_ADJ_GATHER) return XR_ERR_ARG;
+        method = XR_ADJ_SCATTER;
+    }
     if (method == XR_ADJ_AUTO) {
         // measured on GB300: 3D scatter 438 ms vs tiled gather 682 ms (circular cone 512^3);
         // 2D: the quad-plane gather beats the vector-atomic scatter (2.33 vs 2.94 ms,

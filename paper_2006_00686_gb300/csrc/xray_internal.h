@@ -27,7 +27,8 @@ struct Grid {
     int64_t sx, sy, sz;  // element strides of i, j, k
 };
 
-inline bool kind_is3d(int k) { return k >= XR_PAR3D; }
+inline bool kind_is3d(int k) { return k >= XR_PAR3D && k != XR_RAYS2D; }
+inline bool kind_is_list(int k) { return k == XR_RAYS2D || k == XR_RAYS3D; }
 
 // A float pair hi + lo with |lo| <= ulp(hi) / 2: about 48 significant bits, computed on the
 // FP32 pipes (GB300's FP64 rate is a small fraction of its FP32 rate).
@@ -50,11 +51,12 @@ struct DetRec {
 };
 
 // Per view: cos/sin of the view angle (PAR3D: of phi1 and phi2) and the source height.
+// Ray lists (one ray per view): cos/sin of phi (phi1, phi2) and, in H and pad0, s (s1, s2).
 struct ViewRec {
     double c1, s1, c2, s2, H, pad0, pad1, pad2;
 };
 
-// The same per view, as float pairs, for the ray setup.
+// The same per view, as float pairs, for the ray setup (ray lists: s or s1 in H, s2 in pad).
 struct ViewDF {
     DF c1, s1, c2, s2, H, pad;
 };

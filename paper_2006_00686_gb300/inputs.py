@@ -43,8 +43,11 @@ KINDS = {
     "cone_arc": 5,
     "helix": 6,
     "helix_arc": 7,
+    "rays2d": 8,  # a list of rays, each given by its parameters (s, phi)
+    "rays3d": 9,  # a list of rays, each given by its parameters (s1, s2, phi1, phi2)
 }
-KINDS_3D = ("par3d", "cone", "cone_arc", "helix", "helix_arc")
+KINDS_3D = ("par3d", "cone", "cone_arc", "helix", "helix_arc", "rays3d")
+RAY_LISTS = {"rays2d": 2, "rays3d": 4}  # parameters per ray
 
 
 @dataclass
@@ -61,7 +64,7 @@ class Geometry:
     cx: float = 0.0
     cy: float = 0.0
     cz: float = 0.0
-    angles: np.ndarray = None  # float64 [n_views] (par3d: [n_views, 2])
+    angles: np.ndarray = None  # float64 [n_views] (par3d: [n_views, 2]; ray lists: [n_rays, 2 or 4])
     src_z: np.ndarray = None  # float64 [n_views], helical kinds only
     n_cols: int = 1
     n_rows: int = 1
@@ -80,6 +83,10 @@ class Geometry:
             self.src_z = np.ascontiguousarray(np.asarray(self.src_z, dtype=np.float64))
         if not self.is3d:
             self.nz, self.n_rows = 1, 1
+        if self.kind in RAY_LISTS:
+            # one "view" per ray, one detector sample each
+            self.angles = self.angles.reshape(-1, RAY_LISTS[self.kind])
+            self.n_rows, self.n_cols = 1, 1
 
     @property
     def kind_id(self) -> int:

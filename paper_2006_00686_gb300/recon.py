@@ -1,11 +1,14 @@
-"""Reconstruction loops on top of the projector: SIRT and gradient-descent least squares.
+"""Reconstruction loops on top of the projector: SIRT, ordered-subset SIRT, Tikhonov-regularised
+least squares by CGLS, and gradient-descent least squares through autograd.
 
-Both only compose the CUDA forward and adjoint (through the C ABI) with elementwise torch
-operations on the device.  The SIRT iteration can be captured once in a CUDA graph and
-replayed.
+All of them only compose the CUDA forward and adjoint (through the C ABI) with elementwise
+torch operations on the device -- the reconstruction use the paper's method is built for
+(Section 1: iterative methods need the transform and its adjoint many times).  The SIRT
+iteration can be captured once in a CUDA graph and replayed.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from .xray import Projector, project
@@ -88,3 +91,79 @@ def lsq_gradient_descent(proj: Projector, b: torch.Tensor, n_iter: int, step: fl
         with torch.no_grad():
             x -= step * x.grad
     return x.detach(), losses
+
+
+def subset_views(n_views: int, n_subsets: int) -> list:
+    """Interleaved view subsets: subset s holds views s, s + S, s + 2S, ... (each subset spans
+    the whole angular range)."""
+    return [np.arange(s, n_views, n_subsets, dtype=np.int64) for s in range(n_subsets)]
+
+
+class OSSIRT:
+    """Ordered-subset SIRT: one sweep applies, subset by subset,
+    x <- x + relax * C_s A_s^T R_s (b_s - A_s x), with A_s the transform restricted to the
+    views of subset s and R_s, C_s its inverse row and column sums.  Each subset is a
+    Projector of its own (a view subset of the scan), so every update runs the CUDA kernels."""
+
+    def __init__(self, geom, b: torch.Tensor, n_subsets: int, relax: float = 1.0):
+        self.geom, self.relax = geom, float(relax)
+        self.subsets = subset_views(geom.n_views, n_subsets)
+        dev = b.device
+        sino = b.reshape(geom.n_views, -1)
+        self.P, self.b, self.R, self.C = [], [], [], []
+        for idx in self.subsets:
+            g = geom.subset_views(idx)
+            P = Projector(g)
+            bs = sino[torch.from_numpy(idx).to(dev)].reshape(g.sino_shape()).contiguous()
+            row = P.forward(torch.ones(g.image_shape(), device=dev))
+            col = P.adjoint(torch.ones(g.sino_shape(), device=dev))
+            self.P.append(P)
+            self.b.append(bs)
+            self.R.append(torch.where(row > 0, 1.0 / row.clamp_min(1e-30), torch.zeros_like(row)))
+            self.C.append(torch.where(col > 0, 1.0 / col.clamp_min(1e-30), torch.zeros_like(col)))
+        self.x = torch.zeros(geom.image_shape(), device=dev)
+
+    def sweep(self):
+        for P, b, R, C in zip(self.P, self.b, self.R, self.C):
+            r = (b - P.forward(self.x)) * R
+            self.x.addcmul_(C, P.adjoint(r), value=self.relax)
+
+    def run(self, n_sweeps: int):
+        for _ in range(n_sweeps):
+            self.sweep()
+        return self.x
+
+    def close(self):
+        for P in self.P:
+            P.close()
+
+
+def cgls(proj: Projector, b: torch.Tensor, n_iter: int, lam: float = 0.0, x0: torch.Tensor | None = None):
+    """Tikhonov-regularised least squares, min ||A x - b||^2 + lam ||x||^2, by CGLS (conjugate
+    gradients on (A^T A + lam I) x = A^T b without forming A^T A).  Returns x and the norms
+    ||A^T (b - A x) - lam x|| of the normal-equation residual per iteration (float64
+    reductions)."""
+    g = proj.geom
+    x = torch.zeros(g.image_shape(), device=b.device) if x0 is None else x0.clone()
+    r = b - proj.forward(x)
+    s = proj.adjoint(r) - lam * x
+    p = s.clone()
+    gamma = float((s.double() ** 2).sum())
+    norms = [gamma ** 0.5]
+    for _ in range(n_iter):
+        if gamma == 0.0:
+            break
+        q = proj.forward(p)
+        delta = float((q.double() ** 2).sum()) + lam * float((p.double() ** 2).sum())
+        if delta <= 0.0:
+            break
+        alpha = gamma / delta
+        x.add_(p, alpha=alpha)
+        r.sub_(q, alpha=alpha)
+        s = proj.adjoint(r) - lam * x
+        gamma_new = float((s.double() ** 2).sum())
+        p.mul_(gamma_new / gamma).add_(s)
+        gamma = gamma_new
+        norms.append(gamma ** 0.5)
+    return x, norms
+

@@ -73,6 +73,7 @@ SIGNATURES = {
     "xr_batch_project": (_I32, [_VP, _VP]),
     "xr_batch_backproject": (_I32, [_VP, _VP]),
     "xr_project_batched_noalloc": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _VP]),
+    "xr_read_probe": (_I32, [_VP, ctypes.c_int64, _I32, _VP, _I32, _VP]),
     "xr_status_string": (ctypes.c_char_p, [_I32]),
     "xr_last_cuda_error": (_I32, []),
     "xr_version": (_I32, []),
@@ -294,3 +295,28 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def read_bandwidth(n_bytes: int = 64 << 20, reps: int = 20, trials: int = 5) -> float:
+    """Measured read bandwidth (GB/s) of a device buffer of n_bytes read `reps` times per
+    launch (the L2 read bandwidth when the buffer fits L2): best of `trials` event-timed
+    launches after one warm-up."""
+    n = (n_bytes // 16) * 4
+    buf = torch.ones(n, device="cuda")
+    sink = torch.empty(1 << 22, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def launch():
+        _check(lib().xr_read_probe(_ptr(buf), n, reps, _ptr(sink), sink.numel(), _stream(stream)), "xr_read_probe")
+
+    launch()
+    best = 0.0
+    for _ in range(trials):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        launch()
+        b.record(stream)
+        b.synchronize()
+        best = max(best, 4.0 * n * reps / (a.elapsed_time(b) * 1e-3) / 1e9)
+    return best
+

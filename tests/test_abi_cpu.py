@@ -65,7 +65,10 @@ def _desc(X, **kw):
 
 
 @pytest.mark.parametrize("kw,code", [
-    (dict(kind=9), 3),                      # XR_ERR_KIND
+    (dict(kind=10), 3),                     # XR_ERR_KIND
+    (dict(kind=-1), 3),
+    (dict(kind=8, n_cols=9), 2),            # a ray list has one sample per "view"
+    (dict(kind=9, nz=4, n_rows=2, n_cols=1), 2),
     (dict(nx=0), 2),                        # XR_ERR_SIZE
     (dict(n_cols=0), 2),
     (dict(nx=20000), 2),

@@ -45,6 +45,16 @@ def _rand_geom(kind, rng):
     kw = dict(nx=nx, ny=ny, nz=nz, dx=rng.uniform(0.6, 1.4), dy=rng.uniform(0.6, 1.4), dz=rng.uniform(0.6, 1.4),
               cx=rng.uniform(-2, 2), cy=rng.uniform(-2, 2), cz=rng.uniform(-2, 2))
     nv = 7
+    if kind in ("rays2d", "rays3d"):
+        # rays given by their parameters, spread over the image's bounding circle
+        half = 0.5 * math.sqrt((nx * kw["dx"]) ** 2 + (ny * kw["dy"]) ** 2 + (nz * kw["dz"]) ** 2)
+        n = 900
+        if kind == "rays2d":
+            ang = np.stack([rng.uniform(-half, half, n), rng.uniform(-pi, 3 * pi, n)], axis=1)
+        else:
+            ang = np.stack([rng.uniform(-half, half, n), rng.uniform(-half, half, n), rng.uniform(-pi, 3 * pi, n),
+                            rng.uniform(-pi, pi, n)], axis=1)
+        return Geometry(kind, angles=ang, **kw)
     if kind == "par2d":
         return Geometry(kind, angles=rng.uniform(-pi, 3 * pi, nv), n_cols=41, du=rng.uniform(0.5, 1.5), **kw)
     if kind == "fan2d":
@@ -102,6 +112,47 @@ def test_unit_sets_special_rays(offset):
             v = r // (g.n_rows * g.n_cols)
             if np.all(np.isclose(np.mod(dirs[v], pi / 2), 0.0) | np.isclose(np.mod(dirs[v], pi / 2), pi / 2)):
                 np.testing.assert_array_equal(np.sort(rows_gpu[q][0]), rows_ref[q][0])
+
+
+@pytest.mark.parametrize("kind", ["rays2d", "rays3d"])
+def test_ray_list_forward_adjoint_dot(kind):
+    # random ray lists (Section 4.3): forward and scatter adjoint vs the oracle, dot test
+    rng = np.random.default_rng(31)
+    if kind == "rays2d":
+        g0 = Geometry("rays2d", 48, 40, dx=0.9, dy=1.1, cx=0.5, cy=-0.3, angles=np.zeros((1, 2)))
+        half = 0.5 * math.hypot(48 * 0.9, 40 * 1.1)
+        ang = np.stack([rng.uniform(-half, half, 20000), rng.uniform(0, 2 * pi, 20000)], axis=1)
+    else:
+        g0 = Geometry("rays3d", 24, 20, 16, dx=0.9, dy=1.1, dz=1.0, cx=0.5, cy=-0.3, cz=0.2, angles=np.zeros((1, 4)))
+        half = 0.5 * math.sqrt((24 * 0.9) ** 2 + (20 * 1.1) ** 2 + 16 ** 2)
+        ang = np.stack([rng.uniform(-half, half, 20000), rng.uniform(-half, half, 20000),
+                        rng.uniform(0, 2 * pi, 20000), rng.uniform(-pi / 2, pi / 2, 20000)], axis=1)
+    g = Geometry(kind, g0.nx, g0.ny, g0.nz, dx=g0.dx, dy=g0.dy, dz=g0.dz, cx=g0.cx, cy=g0.cy, cz=g0.cz, angles=ang)
+    P = _proj(g)
+    f = _phantom(g, 17)
+    y = P.forward(f.cuda()).cpu().numpy().reshape(-1)
+    f64 = f.numpy().astype(np.float64).reshape(-1)
+    H.check_rays(g, y, O.forward(g, f64), O.forward(g, np.abs(f64)), float(np.abs(f64).max()), kind)
+    yin = rng.random(g.n_rays).astype(np.float32)
+    z = P.adjoint(torch.from_numpy(yin.reshape(g.sino_shape())).cuda()).cpu().numpy().reshape(-1)
+    H.check_adjoint(z, O.adjoint(g, yin.astype(np.float64)), kind)
+    with pytest.raises(Exception):
+        P.adjoint(torch.from_numpy(yin.reshape(g.sino_shape())).cuda(), method=2)  # no detector to gather over
+    x = torch.from_numpy(rng.random(g.image_shape(), dtype=np.float32)).cuda()
+    yv = torch.from_numpy(yin.reshape(g.sino_shape())).cuda()
+    lhs = float((P.forward(x).double() * yv.double()).sum())
+    rhs = float((x.double() * P.adjoint(yv).double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_ray_list_of_cone_parameters_reproduces_the_cone():
+    g = H.cone_small(32, 12)
+    params = np.stack([O.ray_params(g, r) for r in range(g.n_rays)])
+    gl = Geometry("rays3d", g.nx, g.ny, g.nz, dx=g.dx, dy=g.dy, dz=g.dz, cx=g.cx, cy=g.cy, cz=g.cz, angles=params)
+    f = _phantom(g, 5).cuda()
+    yc = _proj(g).forward(f).reshape(-1)
+    yl = _proj(gl).forward(f).reshape(-1)
+    assert float((yc - yl).abs().max()) <= 1e-5 * float(yc.abs().max())
 
 
 def test_ambiguity_examples_on_gpu():

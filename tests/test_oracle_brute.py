@@ -218,3 +218,56 @@ def test_uniform_disc_converges_to_chord():
     g.u0, g.du = 0.0, 1.0
     got = np.array([O.forward(Geometry("par2d", n, n, angles=[0.37], n_cols=1, u0=v), f)[0] for v in s])
     np.testing.assert_allclose(got, 2 * np.sqrt(R * R - s * s), atol=3.0)
+
+
+# ---------------------------------------------------------------------------------------
+# Ray lists: rays given by their own parameters (Section 4.3)
+# ---------------------------------------------------------------------------------------
+
+def _ray_list(kind, rng, n=40):
+    nx, ny = int(rng.integers(2, 9)), int(rng.integers(2, 9))
+    kw = dict(nx=nx, ny=ny, dx=rng.uniform(0.5, 1.5), dy=rng.uniform(0.5, 1.5), cx=rng.uniform(-1, 1),
+              cy=rng.uniform(-1, 1))
+    half = 0.5 * math.hypot(nx * kw["dx"], ny * kw["dy"])
+    if kind == "rays2d":
+        ang = np.stack([rng.uniform(-half - 1, half + 1, n), rng.uniform(-3 * pi, 3 * pi, n)], axis=1)
+        return Geometry(kind, angles=ang, **kw)
+    nz = int(rng.integers(2, 7))
+    kw.update(nz=nz, dz=rng.uniform(0.5, 1.5), cz=rng.uniform(-1, 1))
+    ang = np.stack([rng.uniform(-half - 1, half + 1, n), rng.uniform(-half - 1, half + 1, n),
+                    rng.uniform(-3 * pi, 3 * pi, n), rng.uniform(-2 * pi, 2 * pi, n)], axis=1)
+    return Geometry(kind, angles=ang, **kw)
+
+
+@pytest.mark.parametrize("kind", ["rays2d", "rays3d"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ray_lists_vs_brute_force(kind, seed):
+    g = _ray_list(kind, np.random.default_rng(100 + seed))
+    for r in range(g.n_rays):
+        _check_ray(g, r)
+
+
+def test_ray_lists_special_rays():
+    # on grid lines, axis-parallel, diagonal, every quadrant: the ambiguity rule applies
+    ang2 = [[1.0, 0.0], [0.0, pi / 2], [3.0, 0.0], [-3.0, pi / 2], [0.5, pi / 4], [2.0, pi], [-1.0, 3 * pi / 2],
+            [0.0, 0.0], [1.5, -pi / 2]]
+    g = Geometry("rays2d", 6, 6, angles=ang2)
+    for r in range(g.n_rays):
+        _check_ray(g, r)
+    ang3 = [[1.0, 1.0, 0.0, 0.0], [0.0, 0.0, pi / 2, 0.0], [-0.5, math.sqrt(2), 0.0, pi / 4],
+            [1.0, -1.0, pi / 2, pi / 2], [0.3, 0.2, pi / 4, pi / 4], [2.0, 0.0, pi, -pi / 2]]
+    g3 = Geometry("rays3d", 4, 4, 4, angles=ang3)
+    for r in range(g3.n_rays):
+        _check_ray(g3, r)
+
+
+@pytest.mark.parametrize("scan", ["fan2d", "cone"])
+def test_ray_list_of_a_scans_parameters_is_that_scan(scan):
+    # the parameters of a scan's own rays, given as a list, reproduce the scan exactly
+    rng = np.random.default_rng(7)
+    g = _rand_geom(scan, rng)
+    params = np.stack([O.ray_params(g, r) for r in range(g.n_rays)])
+    gl = Geometry("rays2d" if scan == "fan2d" else "rays3d", g.nx, g.ny, g.nz, dx=g.dx, dy=g.dy, dz=g.dz,
+                  cx=g.cx, cy=g.cy, cz=g.cz, angles=params)
+    f = rng.random(g.n_units)
+    np.testing.assert_array_equal(O.forward(gl, f), O.forward(g, f))
