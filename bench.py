@@ -134,6 +134,8 @@ WORKLOADS = {
                       "736x64 flat detector, sod 600, sdd 1100"),
     "fans_uneven_64": (None, 64, 10, 500, "64 uneven 2D fans (sides 128..1024, seed 5), one persistent "
                        "launch each for forward and adjoint"),
+    "fan2d_512x16_atten": ("fan2d_512", 16, 10, 200, "attenuated transform (exponential attenuation of a "
+                           "0.02 + 0.05 x ellipse-phantom map) on the 512^2 x 16 fan scan"),
 }
 
 
@@ -252,14 +254,23 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
 
+    atten = args.workload.endswith("_atten")
+    mu = (0.02 + 0.05 * inputs.phantom(g, 4, 900, device=str(dev))).float().contiguous() if atten else None
+
     def step(recs):
         e = _events(4) if recs is not None else None
         if e: e[0].record(stream)
         P.ray_setup(stream)
         if e: e[1].record(stream)
-        P.forward(x, out=y, stream=stream)
+        if atten:
+            P.forward_attenuated(x, mu, out=y, stream=stream)
+        else:
+            P.forward(x, out=y, stream=stream)
         if e: e[2].record(stream)
-        P.adjoint(y, out=z, stream=stream)
+        if atten:
+            P.adjoint_attenuated(y, mu, out=z, stream=stream)
+        else:
+            P.adjoint(y, out=z, stream=stream)
         if e: e[3].record(stream)
         if recs is not None:
             recs.append(e)
@@ -299,7 +310,11 @@ def run_ours(args, rank, world, local_rank):
     roof = _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic)
 
     extra = {}
-    if args.workload == "fan2d_512x16":
+    if atten:
+        config = _config({"workload": args.workload, "geometry": desc, "adjoint": "scatter (attenuated)"})
+        # detector setup, ray setup, gather constants, the attenuated forward and adjoint
+        launches = 5
+    elif args.workload == "fan2d_512x16":
         config = _config({"adjoint": method, "batch_chunk": P.tuning()["batch_chunk"], "block": args.block})
         # per step: detector setup, ray setup, the gather's per-ray constants, image
         # interleave, forward walk, then either the scatter walk + its de-interleave (two

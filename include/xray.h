@@ -186,6 +186,21 @@ xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img
 xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float *d_img,
                                 int32_t batch, int32_t method, xr_stream stream);
 
+/* Attenuated transform: the generalized Radon transform of eq. generalizedRadontransform
+ * with the exponential attenuation weight of the SPECT case (Section 1),
+ * Phi(theta, x, t) = exp(-int_t^inf mu(x + s theta) ds), for an attenuation image d_mu
+ * ([n_units] float32, device, one map for the whole batch).  With f and mu constant on each
+ * unit, ray r gives sino[b][r] = sum over its units k (in the order the ray crosses them) of
+ * img[b][I_k] * exp(-A_k) * E_k, where A_k is the attenuation between unit k and the ray's far
+ * end (towards +theta, the ray's own direction) and E_k = (1 - exp(-mu_k l_k)) / mu_k (l_k when
+ * mu_k = 0).  Same layouts, alignment and errors as xr_project; one thread per ray on the
+ * caller's layout (two walks per ray: the total attenuation, then the weights).
+ * xr_backproject_attenuated is its exact transpose (overwrites d_img). */
+xr_status xr_project_attenuated(const xr_geometry *g, const float *d_mu, const float *d_img, float *d_sino,
+                                int32_t batch, xr_stream stream);
+xr_status xr_backproject_attenuated(const xr_geometry *g, const float *d_mu, const float *d_sino, float *d_img,
+                                    int32_t batch, xr_stream stream);
+
 /* Sparse rows of the projection matrix (Algorithm 1/2 "Output", Section 4.2): for each of
  * the n rays listed in d_rays (device int64 ray ids), the units it crosses with positive
  * length, written in visiting order to d_idx[q*cap ...] (1D index I, int64) and

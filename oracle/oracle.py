@@ -64,6 +64,11 @@ def lib():
                                      ctypes.c_int, ctypes.c_int]
         _lib.orc_adjoint.argtypes = [P(_Geom), c_double_p, c_double_p, c_long_p, ctypes.c_long,
                                      ctypes.c_int, ctypes.c_int]
+        for name in ("orc_forward_attenuated", "orc_adjoint_attenuated"):
+            fn = getattr(_lib, name)
+            fn.argtypes = [P(_Geom), c_double_p, c_double_p, c_double_p, c_long_p, ctypes.c_long, ctypes.c_int,
+                           ctypes.c_int]
+            fn.restype = ctypes.c_int
         _lib.orc_max_threads.restype = ctypes.c_int
     return _lib
 
@@ -164,3 +169,41 @@ def adjoint(g, sino, rays=None, threads: int | None = None) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("oracle unit list overflow")
     return out[0] if single else out
+
+
+def forward_attenuated(g, mu, img, rays=None, threads: int | None = None) -> np.ndarray:
+    """Attenuated forward projection in float64 (exponential weight of the attenuation map
+    ``mu`` along each ray, integrated towards +theta)."""
+    s, keep = _geom(g)
+    m = np.ascontiguousarray(np.asarray(mu, dtype=np.float64).reshape(-1))
+    f = np.asarray(img, dtype=np.float64)
+    single = f.size == n_units(g)
+    f = np.ascontiguousarray(f.reshape(1, -1) if single else f.reshape(f.shape[0], n_units(g)))
+    batch = f.shape[0]
+    r, rp = _rays_arg(rays)
+    nr = n_rays(g) if r is None else r.size
+    out = np.zeros((batch, nr))
+    rc = lib().orc_forward_attenuated(ctypes.byref(s), _dptr(m), _dptr(f), _dptr(out), rp, nr, batch,
+                                      threads or max_threads())
+    if rc != 0:
+        raise RuntimeError("oracle unit list overflow")
+    return out[0] if single else out
+
+
+def adjoint_attenuated(g, mu, sino, rays=None, threads: int | None = None) -> np.ndarray:
+    """Adjoint of forward_attenuated in float64."""
+    s, keep = _geom(g)
+    m = np.ascontiguousarray(np.asarray(mu, dtype=np.float64).reshape(-1))
+    r, rp = _rays_arg(rays)
+    nr = n_rays(g) if r is None else r.size
+    y = np.asarray(sino, dtype=np.float64)
+    single = y.size == nr
+    y = np.ascontiguousarray(y.reshape(1 if single else y.shape[0], nr))
+    batch = y.shape[0]
+    out = np.zeros((batch, n_units(g)))
+    rc = lib().orc_adjoint_attenuated(ctypes.byref(s), _dptr(m), _dptr(y), _dptr(out), rp, nr, batch,
+                                      threads or max_threads())
+    if rc != 0:
+        raise RuntimeError("oracle unit list overflow")
+    return out[0] if single else out
+

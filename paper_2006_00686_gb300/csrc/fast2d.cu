@@ -755,8 +755,14 @@ __device__ __forceinline__ float gather_len(const float4 ga, const float4 gb, fl
     return __fsub_rn(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)));
 }
 
+// CTAs per SM the gather's registers must allow (16 accumulators and two bins' prefetched
+// values per thread with 4 planes)
+#ifndef XR_GATHER_MIN_BLOCKS
+#define XR_GATHER_MIN_BLOCKS(NQ) ((NQ) >= 4 ? 2 : 3)
+#endif
+
 template <int NQ, int KIND>
-__global__ void __launch_bounds__(256, NQ >= 4 ? 2 : 3) gather_plane_kernel(const RayRec *__restrict__ rays,
+__global__ void __launch_bounds__(256, XR_GATHER_MIN_BLOCKS(NQ)) gather_plane_kernel(const RayRec *__restrict__ rays,
                                                               const GatherRec *__restrict__ grec, GeoParams g,
                                                               const float *__restrict__ vt,
                                                               const float4 *__restrict__ sil, int64_t n_rays,

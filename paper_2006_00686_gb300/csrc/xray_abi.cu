@@ -536,6 +536,34 @@ xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img
     return xr_backproject_method(g, d_sino, d_img, batch, XR_ADJ_AUTO, stream);
 }
 
+xr_status xr_project_attenuated(const xr_geometry *g, const float *d_mu, const float *d_img, float *d_sino,
+                                int32_t batch, xr_stream stream)
+{
+    if (!g || !d_mu || !d_img || !d_sino) return XR_ERR_NULL;
+    if (batch < 1) return XR_ERR_BATCH;
+    if (!aligned16(d_mu) || !aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
+    const int chunk = pick_chunk(g, batch);
+    if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
+    XR_CUDA(launch_attenuated(false, g->d_rays, g->n_rays, make_grid(g), d_mu, d_img, d_sino, g->n_units, batch,
+                              chunk, g->tune.block, (cudaStream_t)stream));
+    return XR_OK;
+}
+
+xr_status xr_backproject_attenuated(const xr_geometry *g, const float *d_mu, const float *d_sino, float *d_img,
+                                    int32_t batch, xr_stream stream)
+{
+    if (!g || !d_mu || !d_img || !d_sino) return XR_ERR_NULL;
+    if (batch < 1) return XR_ERR_BATCH;
+    if (!aligned16(d_mu) || !aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
+    const int chunk = pick_chunk(g, batch);
+    if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
+    const cudaStream_t s = (cudaStream_t)stream;
+    XR_CUDA(cudaMemsetAsync(d_img, 0, (size_t)g->n_units * batch * sizeof(float), s));
+    XR_CUDA(launch_attenuated(true, g->d_rays, g->n_rays, make_grid(g), d_mu, d_sino, d_img, g->n_units, batch,
+                              chunk, g->tune.block, s));
+    return XR_OK;
+}
+
 xr_status xr_ray_units(const xr_geometry *g, const int64_t *d_rays, int32_t n, int32_t cap, int64_t *d_idx,
                        float *d_len, int32_t *d_count, xr_stream stream)
 {

@@ -167,6 +167,11 @@ cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_r
 // every ray of its detector footprint in shared memory and writes the tile once.
 cudaError_t launch_tile3d_adj(const RayRec *rays, const ViewRec *views, const GeoParams &g, const float *sino,
                               int64_t n_rays, float *img, int batch, cudaStream_t s);
+// Attenuated transform (atten.cu): one thread per ray, `chunk` images per thread; in/out
+// in the caller's layout ([batch][units] / [batch][rays]); the adjoint adds into out.
+cudaError_t launch_attenuated(bool adjoint, const RayRec *rays, int64_t n_rays, const Grid &grid, const float *mu,
+                              const float *in, float *out, int64_t n_units, int batch, int chunk, int block,
+                              cudaStream_t s);
 cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
                                 const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
                                 cudaStream_t s);

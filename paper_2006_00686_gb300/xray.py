@@ -74,6 +74,8 @@ SIGNATURES = {
     "xr_batch_backproject": (_I32, [_VP, _VP]),
     "xr_project_batched_noalloc": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _VP]),
     "xr_read_probe": (_I32, [_VP, ctypes.c_int64, _I32, _VP, _I32, _VP]),
+    "xr_project_attenuated": (_I32, [_VP, _VP, _VP, _VP, _I32, _VP]),
+    "xr_backproject_attenuated": (_I32, [_VP, _VP, _VP, _VP, _I32, _VP]),
     "xr_status_string": (ctypes.c_char_p, [_I32]),
     "xr_last_cuda_error": (_I32, []),
     "xr_version": (_I32, []),
@@ -222,6 +224,39 @@ class Projector:
 
     __call__ = forward
 
+    def forward_attenuated(self, img: torch.Tensor, mu: torch.Tensor, out: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+        """Attenuated transform (exponential attenuation of the map ``mu`` towards each ray's
+        far end) of one image or a batch."""
+        _need_cuda(img, "img")
+        _need_cuda(mu, "mu")
+        if tuple(mu.shape) != self.geom.image_shape():
+            raise XRayError(f"mu has shape {tuple(mu.shape)}, expected {self.geom.image_shape()}")
+        b = self._batch_of(img, self.geom.image_shape(), "img")
+        shape = self.geom.sino_shape(b if b else None)
+        if out is None:
+            out = torch.empty(shape, device=img.device, dtype=torch.float32)
+        _need_cuda(out, "out")
+        _check(lib().xr_project_attenuated(self._h, _ptr(mu), _ptr(img), _ptr(out), max(b, 1), _stream(stream)),
+               "xr_project_attenuated")
+        return out
+
+    def adjoint_attenuated(self, sino: torch.Tensor, mu: torch.Tensor, out: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+        """The exact transpose of forward_attenuated."""
+        _need_cuda(sino, "sino")
+        _need_cuda(mu, "mu")
+        if tuple(mu.shape) != self.geom.image_shape():
+            raise XRayError(f"mu has shape {tuple(mu.shape)}, expected {self.geom.image_shape()}")
+        b = self._batch_of(sino, self.geom.sino_shape(), "sino")
+        shape = self.geom.image_shape(b if b else None)
+        if out is None:
+            out = torch.empty(shape, device=sino.device, dtype=torch.float32)
+        _need_cuda(out, "out")
+        _check(lib().xr_backproject_attenuated(self._h, _ptr(mu), _ptr(sino), _ptr(out), max(b, 1),
+                                               _stream(stream)), "xr_backproject_attenuated")
+        return out
+
     def ray_units(self, rays, cap: int | None = None):
         """Sparse rows for the given ray ids: list of (unit indices int64, lengths float32)
         per ray, in visiting order."""
@@ -258,6 +293,25 @@ class XRayFunction(torch.autograd.Function):
 def project(x: torch.Tensor, proj: Projector) -> torch.Tensor:
     """Differentiable forward projection."""
     return XRayFunction.apply(x, proj)
+
+
+class AttenuatedXRayFunction(torch.autograd.Function):
+    """y = A_mu x (the attenuated transform for a fixed attenuation map mu); backward is its
+    transpose on the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, mu: torch.Tensor, proj: Projector):
+        ctx.proj, ctx.mu = proj, mu
+        return proj.forward_attenuated(x.contiguous(), mu)
+
+    @staticmethod
+    def backward(ctx, gy: torch.Tensor):
+        return ctx.proj.adjoint_attenuated(gy.contiguous(), ctx.mu), None, None
+
+
+def project_attenuated(x: torch.Tensor, mu: torch.Tensor, proj: Projector) -> torch.Tensor:
+    """Differentiable attenuated forward projection (gradient with respect to x)."""
+    return AttenuatedXRayFunction.apply(x, mu, proj)
 
 
 class BatchPlan:
