@@ -665,10 +665,12 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import __graft_entry__
-    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2006_00686_gb300", "libxray.so")):
+    if rank == 0:  # one process builds (or finds the build current); the others wait for it
         __graft_entry__.build()
     if world > 1:
         torch.distributed.barrier()
+    if rank != 0:
+        __graft_entry__.build()  # up to date by now: only checks and imports
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
