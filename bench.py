@@ -168,26 +168,59 @@ def _timed_loop(step, args, flush, world, local_rank):
     return recs, clk.summary(), wall
 
 
-def _e2e(step, host_in, dev_in, dev_out, host_out, args, flush):
-    """Mean ms of one step with the pinned H2D copies of its inputs and the D2H copies of
-    its results inside the timed region."""
+def _e2e(sets, args, flush):
+    """Mean ms per step of the end-to-end loop: every step copies its inputs host -> device
+    (pinned), runs, and copies its results device -> host.  Host-to-device and
+    device-to-host copies run on two more streams with two buffer sets, so the copies of
+    steps k + 1 and k - 1 overlap step k's kernels; each step waits for its own inputs, and a
+    buffer set is refilled only after its previous results were copied out.  The whole
+    K-step loop is timed, from the first copy in to the last copy out.
+    sets: two dicts with step() (launches on the current stream), host_in, dev_in, dev_out,
+    host_out."""
     import torch
-    stream = torch.cuda.current_stream()
-    out = []
-    for k in range(args.warmup + args.steps):
-        flush.fill_(1.0)
-        a, b = _events(2)
-        a.record(stream)
-        for d, h in zip(dev_in, host_in):
-            d.copy_(h, non_blocking=True)
-        step(None)
-        for h, d in zip(host_out, dev_out):
-            h.copy_(d, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        if k >= args.warmup:
-            out.append(a.elapsed_time(b))
-    return float(np.mean(out))
+    comp = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    n = len(sets)
+    h2d = [torch.cuda.Event() for _ in range(n)]
+    done = [torch.cuda.Event() for _ in range(n)]
+    d2h = [torch.cuda.Event() for _ in range(n)]
+    for e in done + d2h:
+        e.record(comp)
+
+    def copy_in(k):
+        i = k % n
+        s_in.wait_event(done[i])  # the set's previous step no longer reads its inputs
+        with torch.cuda.stream(s_in):
+            for d, h in zip(sets[i]["dev_in"], sets[i]["host_in"]):
+                d.copy_(h, non_blocking=True)
+        h2d[i].record(s_in)
+
+    def run(K, start=None):
+        if start is not None:
+            start.record(s_in)
+        copy_in(0)
+        for k in range(K):
+            i = k % n
+            if k + 1 < K:
+                copy_in(k + 1)  # prefetch the next step's inputs
+            comp.wait_event(h2d[i])
+            comp.wait_event(d2h[i])  # the set's previous results are out
+            flush.fill_(1.0)  # L2 flushed before every step, inside the timed loop
+            sets[i]["step"]()
+            done[i].record(comp)
+            s_out.wait_event(done[i])
+            with torch.cuda.stream(s_out):
+                for h, d in zip(sets[i]["host_out"], sets[i]["dev_out"]):
+                    h.copy_(d, non_blocking=True)
+            d2h[i].record(s_out)
+
+    run(args.warmup)
+    torch.cuda.synchronize()
+    a, b = _events(2)
+    run(args.steps, start=a)
+    b.record(s_out)
+    b.synchronize()
+    return a.elapsed_time(b) / args.steps
 
 
 def _l2_peak():
@@ -257,23 +290,27 @@ def run_ours(args, rank, world, local_rank):
     atten = args.workload.endswith("_atten")
     mu = (0.02 + 0.05 * inputs.phantom(g, 4, 900, device=str(dev))).float().contiguous() if atten else None
 
-    def step(recs):
-        e = _events(4) if recs is not None else None
-        if e: e[0].record(stream)
-        P.ray_setup(stream)
-        if e: e[1].record(stream)
-        if atten:
-            P.forward_attenuated(x, mu, out=y, stream=stream)
-        else:
-            P.forward(x, out=y, stream=stream)
-        if e: e[2].record(stream)
-        if atten:
-            P.adjoint_attenuated(y, mu, out=z, stream=stream)
-        else:
-            P.adjoint(y, out=z, stream=stream)
-        if e: e[3].record(stream)
-        if recs is not None:
-            recs.append(e)
+    def make_step(xb, yb, zb):
+        def step(recs=None):
+            e = _events(4) if recs is not None else None
+            if e: e[0].record(stream)
+            P.ray_setup(stream)
+            if e: e[1].record(stream)
+            if atten:
+                P.forward_attenuated(xb, mu, out=yb, stream=stream)
+            else:
+                P.forward(xb, out=yb, stream=stream)
+            if e: e[2].record(stream)
+            if atten:
+                P.adjoint_attenuated(yb, mu, out=zb, stream=stream)
+            else:
+                P.adjoint(yb, out=zb, stream=stream)
+            if e: e[3].record(stream)
+            if recs is not None:
+                recs.append(e)
+        return step
+
+    step = make_step(x, y, z)
 
     recs, clocks, wall = _timed_loop(step, args, flush, world, local_rank)
     setup_ms = [a.elapsed_time(b) for a, b, c, d in recs]
@@ -287,9 +324,11 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the C ABI with host buffers: pinned H2D of the images, the step,
     # D2H of the sinograms and the adjoint images, all inside the timed region
     x_h = x.cpu().pin_memory()
-    y_h = torch.empty(y.shape, pin_memory=True)
-    z_h = torch.empty(z.shape, pin_memory=True)
-    e2e = parallel.max_over_ranks(_e2e(step, [x_h], [x], [y, z], [y_h, z_h], args, flush), dev)
+    sets = []
+    for xb, yb, zb in ((x, y, z), (x.clone(), torch.empty_like(y), torch.empty_like(z))):
+        sets.append({"step": make_step(xb, yb, zb), "host_in": [x_h], "dev_in": [xb], "dev_out": [yb, zb],
+                     "host_out": [torch.empty(yb.shape, pin_memory=True), torch.empty(zb.shape, pin_memory=True)]})
+    e2e = parallel.max_over_ranks(_e2e(sets, args, flush), dev)
 
     peaks, peak_kind = _peaks()
     fwd, adj = float(np.mean(fwd_ms)), float(np.mean(adj_ms))
@@ -336,7 +375,9 @@ def run_ours(args, rank, world, local_rank):
            "config": config,
            "e2e": {"value": round(rays_step * world / (e2e * 1e-3) / 1e9, 4), "unit": UNIT,
                    "h2d_bytes_per_step": int(x.numel() * 4),
-                   "d2h_bytes_per_step": int(y.numel() * 4 + z.numel() * 4), "ms_per_step": round(e2e, 4)},
+                   "d2h_bytes_per_step": int(y.numel() * 4 + z.numel() * 4), "ms_per_step": round(e2e, 4),
+                   "method": "pinned copies in and out on two more streams, two buffer sets, L2 flushed "
+                             "per step, whole loop timed"},
            "gpu_launches": args.steps * launches,
            "kernel_ms": {"ray_setup": round(float(np.mean(setup_ms)), 4), "forward": round(fwd, 4),
                          "adjoint": round(adj, 4)},
@@ -483,10 +524,29 @@ def run_uneven(args, rank, world, local_rank):
                      "adj": float(np.mean([c.elapsed_time(d) for a, b, c, d in recs]))}
     ms = res["batched"]["ms"]
     value = rays_step * world / (ms * 1e-3) / 1e9
+    # end to end: two buffer sets, each with its own pair of plans (plans hold their buffers)
     xh = [t.cpu().pin_memory() for t in xs]
-    yh = [torch.empty(t.shape, pin_memory=True) for t in ys]
-    zh = [torch.empty(t.shape, pin_memory=True) for t in zs]
-    e2e = parallel.max_over_ranks(_e2e(batched, xh, xs, ys + zs, yh + zh, args, flush), dev)
+    xs1 = [t.clone() for t in xs]
+    ys1 = [torch.empty_like(t) for t in ys]
+    zs1 = [torch.empty_like(t) for t in zs]
+    plans1 = (BatchPlan(Ps, xs1, ys1, tile=args.tile, block=args.plan_block),
+              BatchPlan(Ps, zs1, ys1, tile=args.tile, block=args.plan_block))
+
+    def batched_on(fp, ap):
+        def step():
+            for p in Ps:
+                p.ray_setup(stream)
+            fp.project(stream)
+            ap.backproject(stream)
+        return step
+
+    sets = []
+    for (fp, ap), xb, yb, zb in (((fwd_plan, adj_plan), xs, ys, zs), (plans1, xs1, ys1, zs1)):
+        sets.append({"step": batched_on(fp, ap), "host_in": xh, "dev_in": xb, "dev_out": yb + zb,
+                     "host_out": [torch.empty(t.shape, pin_memory=True) for t in yb + zb]})
+    e2e = parallel.max_over_ranks(_e2e(sets, args, flush), dev)
+    for pl in plans1:
+        pl.close()
     peaks, peak_kind = _peaks()
     rb = res["batched"]
     dom, dom_ms = ("forward", rb["fwd"]) if rb["fwd"] >= rb["adj"] else ("adjoint", rb["adj"])
@@ -508,7 +568,9 @@ def run_uneven(args, rank, world, local_rank):
                       "l2": "flushed between timed steps (256 MiB write)"},
            "e2e": {"value": round(rays_step * world / (e2e * 1e-3) / 1e9, 4), "unit": UNIT,
                    "h2d_bytes_per_step": int(sum(t.numel() for t in xs) * 4),
-                   "d2h_bytes_per_step": int(sum(t.numel() for t in ys + zs) * 4), "ms_per_step": round(e2e, 4)},
+                   "d2h_bytes_per_step": int(sum(t.numel() for t in ys + zs) * 4), "ms_per_step": round(e2e, 4),
+                   "method": "pinned copies in and out on two more streams, two buffer sets, L2 flushed "
+                             "per step, whole loop timed"},
            # per step: 3 x 64 setup kernels (detector, ray, gather constants); the copies and the
            # persistent forward; the zero fill, the persistent adjoint and the fold of the
            # transposed accumulators
