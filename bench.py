@@ -351,8 +351,9 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if atten:
         config = _config({"workload": args.workload, "geometry": desc, "adjoint": "scatter (attenuated)"})
-        # detector setup, ray setup, gather constants, the attenuated forward and adjoint
-        launches = 5
+        # detector setup, ray setup, gather constants; forward: image planes, the map's two
+        # padded copies, the walk; adjoint: the map's copies, the walk, the de-interleave
+        launches = 9
     elif args.workload == "fan2d_512x16":
         config = _config({"adjoint": method, "batch_chunk": P.tuning()["batch_chunk"], "block": args.block})
         # per step: detector setup, ray setup, the gather's per-ray constants, image

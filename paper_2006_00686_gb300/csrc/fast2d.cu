@@ -548,6 +548,15 @@ cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int
     return cudaGetLastError();
 }
 
+cudaError_t launch_deinterleave_sum(const float *acc0, const float *acc1, int batch, int nx, int ny, int nz, int Bp,
+                                    float *img, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    deinterleave_sum_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)((batch + Bp - 1) / Bp)), 256, 0, s>>>(
+        acc0, acc1, batch, nx, ny, nz, Bp, img);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, cudaStream_t s)
 {
     gather_prep_kernel<<<(unsigned)((n_rays + 255) / 256), 256, 0, s>>>(rays, n_rays,

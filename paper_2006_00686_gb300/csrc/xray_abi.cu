@@ -536,16 +536,36 @@ xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img
     return xr_backproject_method(g, d_sino, d_img, batch, XR_ADJ_AUTO, stream);
 }
 
+// Attenuated transform of a 2D batch on the interleaved layouts: the batched fast path's
+// workspace, with room after the two image copies for the map's two padded copies.
+static bool use_atten_planes(const xr_geometry *g, int batch)
+{
+    if (kind_is3d(g->params.kind) || !use_fast(g, batch)) return false;
+    const size_t padded = (size_t)((batch + fast_chunk(batch) - 1) / fast_chunk(batch)) * fast_chunk(batch);
+    return 2 * padded_units(g) <= padded * (size_t)g->n_rays && g->n_rays < ((int64_t)1 << 31);
+}
+
 xr_status xr_project_attenuated(const xr_geometry *g, const float *d_mu, const float *d_img, float *d_sino,
                                 int32_t batch, xr_stream stream)
 {
     if (!g || !d_mu || !d_img || !d_sino) return XR_ERR_NULL;
     if (batch < 1) return XR_ERR_BATCH;
     if (!aligned16(d_mu) || !aligned16(d_img) || !aligned16(d_sino)) return XR_ERR_ALIGN;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (use_atten_planes(g, batch)) {
+        const size_t padded = (size_t)((batch + fast_chunk(batch) - 1) / fast_chunk(batch)) * fast_chunk(batch);
+        float *il0 = g->d_ws, *il1 = g->d_ws + padded * padded_units(g);
+        float *mu0 = g->d_ws + 2 * padded * padded_units(g), *mu1 = mu0 + padded_units(g);
+        XR_CUDA(launch_interleave_planes(d_img, batch, g->params.nx, g->params.ny, 1, il0, il1, s));
+        XR_CUDA(launch_mu_layouts(d_mu, g->params.nx, g->params.ny, mu0, mu1, s));
+        XR_CUDA(launch_atten_plane_fwd(g->d_rays, g->n_rays, g->params.nx, g->params.ny, il0, il1, mu0, mu1, d_sino,
+                                       batch, plane_nq(g, batch), s));
+        return XR_OK;
+    }
     const int chunk = pick_chunk(g, batch);
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
     XR_CUDA(launch_attenuated(false, g->d_rays, g->n_rays, make_grid(g), d_mu, d_img, d_sino, g->n_units, batch,
-                              chunk, g->tune.block, (cudaStream_t)stream));
+                              chunk, g->tune.block, s));
     return XR_OK;
 }
 
@@ -558,6 +578,17 @@ xr_status xr_backproject_attenuated(const xr_geometry *g, const float *d_mu, con
     const int chunk = pick_chunk(g, batch);
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
     const cudaStream_t s = (cudaStream_t)stream;
+    if (use_atten_planes(g, batch)) {
+        const int Bp = fast_chunk(batch);
+        const size_t padded = (size_t)((batch + Bp - 1) / Bp) * Bp;
+        float *acc0 = g->d_ws, *acc1 = g->d_ws + padded * padded_units(g);
+        float *mu0 = g->d_ws + 2 * padded * padded_units(g), *mu1 = mu0 + padded_units(g);
+        XR_CUDA(launch_mu_layouts(d_mu, g->params.nx, g->params.ny, mu0, mu1, s));
+        XR_CUDA(launch_atten_plane_adj(g->d_rays, g->n_rays, g->params.nx, g->params.ny, acc0, acc1,
+                                       padded * padded_units(g) * sizeof(float), mu0, mu1, d_sino, d_img, batch, Bp,
+                                       s));
+        return XR_OK;
+    }
     XR_CUDA(cudaMemsetAsync(d_img, 0, (size_t)g->n_units * batch * sizeof(float), s));
     XR_CUDA(launch_attenuated(true, g->d_rays, g->n_rays, make_grid(g), d_mu, d_sino, d_img, g->n_units, batch,
                               chunk, g->tune.block, s));

@@ -167,6 +167,18 @@ cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_r
 // every ray of its detector footprint in shared memory and writes the tile once.
 cudaError_t launch_tile3d_adj(const RayRec *rays, const ViewRec *views, const GeoParams &g, const float *sino,
                               int64_t n_rays, float *img, int batch, cudaStream_t s);
+cudaError_t launch_deinterleave_sum(const float *acc0, const float *acc1, int batch, int nx, int ny, int nz, int Bp,
+                                    float *img, cudaStream_t s);
+
+// Attenuated transform of 2D batches on the interleaved layouts (atten2d.cu).
+cudaError_t launch_mu_layouts(const float *mu, int nx, int ny, float *mu0, float *mu1, cudaStream_t s);
+cudaError_t launch_atten_plane_fwd(const RayRec *rays, int64_t n_rays, int nx, int ny, const float *il0,
+                                   const float *il1, const float *mu0, const float *mu1, float *sino, int batch,
+                                   int nq, cudaStream_t s);
+cudaError_t launch_atten_plane_adj(const RayRec *rays, int64_t n_rays, int nx, int ny, float *acc0, float *acc1,
+                                   size_t acc_bytes, const float *mu0, const float *mu1, const float *sino,
+                                   float *img, int batch, int Bp, cudaStream_t s);
+
 // Attenuated transform (atten.cu): one thread per ray, `chunk` images per thread; in/out
 // in the caller's layout ([batch][units] / [batch][rays]); the adjoint adds into out.
 cudaError_t launch_attenuated(bool adjoint, const RayRec *rays, int64_t n_rays, const Grid &grid, const float *mu,

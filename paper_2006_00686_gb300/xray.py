@@ -233,6 +233,7 @@ class Projector:
         if tuple(mu.shape) != self.geom.image_shape():
             raise XRayError(f"mu has shape {tuple(mu.shape)}, expected {self.geom.image_shape()}")
         b = self._batch_of(img, self.geom.image_shape(), "img")
+        self._maybe_reserve(b)
         shape = self.geom.sino_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=img.device, dtype=torch.float32)
@@ -249,6 +250,7 @@ class Projector:
         if tuple(mu.shape) != self.geom.image_shape():
             raise XRayError(f"mu has shape {tuple(mu.shape)}, expected {self.geom.image_shape()}")
         b = self._batch_of(sino, self.geom.sino_shape(), "sino")
+        self._maybe_reserve(b)
         shape = self.geom.image_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=sino.device, dtype=torch.float32)

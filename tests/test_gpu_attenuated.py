@@ -89,3 +89,34 @@ def test_attenuated_dot_product_and_autograd(name):
     ref = P.adjoint_attenuated(yv, mu)
     assert float((xr.grad - ref).abs().max()) <= 1e-6 * float(ref.abs().max())
     P.close()
+
+
+@pytest.mark.parametrize("batch", [4, 5, 16, 20])
+@pytest.mark.parametrize("name", ["fan2d_96", "rays2d"])
+def test_attenuated_batched_planes(name, batch):
+    # 2D batches on the interleaved layouts against the oracle and against the caller's-layout
+    # kernels (the same weights: equal up to the order of the reductions)
+    from paper_2006_00686_gb300.xray import Projector, XR_PATH_RAY
+    g = SCANS[name]()
+    P = Projector(g)
+    P.reserve(batch)
+    mu = _mu(g, 8).cuda()
+    f = torch.stack([inputs.phantom(g, 6, 60 + b) for b in range(batch)])
+    y = P.forward_attenuated(f.cuda(), mu)
+    m64 = mu.double().cpu().numpy().reshape(-1)
+    f64 = f.double().numpy().reshape(batch, -1)
+    y_ref = O.forward_attenuated(g, m64, f64)
+    scale = O.forward(g, np.abs(f64))
+    yh = y.cpu().numpy().reshape(batch, -1)
+    for b in range(batch):
+        H.check_rays(g, yh[b], y_ref[b], scale[b], float(np.abs(f64[b]).max()), f"{name}[{b}]")
+    z = P.adjoint_attenuated(y, mu).cpu().numpy().reshape(batch, -1)
+    z_ref = O.adjoint_attenuated(g, m64, yh.astype(np.float64))
+    for b in range(batch):
+        H.check_adjoint(z[b], z_ref[b], f"{name}[{b}] adjoint")
+    Pr = Projector(g)
+    Pr.set_tuning(path=XR_PATH_RAY)
+    yr = Pr.forward_attenuated(f.cuda(), mu)
+    assert float((yr - y).abs().max()) <= 1e-5 * float(y.abs().max())
+    P.close()
+    Pr.close()

@@ -389,6 +389,28 @@ def test_full_size_adjoint_view_subset(name):
     P.close()
 
 
+def test_bench_configuration_full_size_fan_x16():
+    # the benchmark's own launch configuration (16 images, quad planes, gather adjoint) at
+    # full size, every ray and every pixel against the oracle
+    g = inputs.fan2d_512()
+    P = _proj(g)
+    f = inputs.phantom_batch(g, 16, 10, 200)
+    y = P.forward(f.cuda())
+    z = P.adjoint(y)
+    assert P.tuning()["path"] == 2 and P.reserved >= 16
+    f64 = f.numpy().astype(np.float64).reshape(16, -1)
+    y_ref = O.forward(g, f64)
+    scale = O.forward(g, np.abs(f64))
+    yh = y.cpu().numpy().reshape(16, -1)
+    for b in range(16):
+        H.check_rays(g, yh[b], y_ref[b], scale[b], float(np.abs(f64[b]).max()), f"fan x16 [{b}]")
+    z_ref = O.adjoint(g, yh.astype(np.float64))
+    zh = z.cpu().numpy().reshape(16, -1)
+    for b in range(16):
+        H.check_adjoint(zh[b], z_ref[b], f"fan x16 adjoint [{b}]")
+    P.close()
+
+
 @pytest.mark.parametrize("path", ["tiled", "interleaved"])
 def test_calls_do_not_interfere(path):
     # a forward after an adjoint (which shares the handle's workspace) gives the same result
