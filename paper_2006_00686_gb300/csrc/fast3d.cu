@@ -76,10 +76,11 @@ struct RayOrder {
     }
 };
 
-// Forward sum of one ray; imgT may be NULL (then every ray reads img).
-template <int U>
-__device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
-                                         const float *__restrict__ imgT)
+// Forward sum of one ray; imgT may be NULL (then every ray reads img).  SKIP: an axis the
+// ray does not cross (w = 0), left out of every step, or 0.
+template <int U, int SKIP>
+__device__ __forceinline__ float fwd_ray_t(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
+                                           const float *__restrict__ imgT)
 {
     const bool tr = imgT != nullptr && leans_x(rr);
     const float *__restrict__ base = tr ? imgT : img;
@@ -91,7 +92,7 @@ __device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int n
             int off[U];
             float l[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) dda_step(D, off[u], l[u]);
+            for (int u = 0; u < U; ++u) dda_step_t<SKIP>(D, off[u], l[u]);
             float v[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) v[u] = l[u] > 0.f ? __ldg(base + off[u]) : 0.f;
@@ -102,11 +103,22 @@ __device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int n
     return acc;
 }
 
+// Rays of 2D scans and of single-tilt-axis scans keep one index fixed: their walk leaves
+// that axis out (the same voxels and lengths, fewer instructions per step).
+template <int U>
+__device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
+                                         const float *__restrict__ imgT)
+{
+    if (rr.w2 == 0.f) return fwd_ray_t<U, 2>(rr, nx, ny, nz, img, imgT);
+    if (rr.w1 == 0.f) return fwd_ray_t<U, 1>(rr, nx, ny, nz, img, imgT);
+    return fwd_ray_t<U, 0>(rr, nx, ny, nz, img, imgT);
+}
+
 // Adjoint of one ray: one RED per voxel.  As in the forward, U voxels are generated ahead
 // and their U REDs issued back to back from separate registers.  accT may be NULL.
-template <int U>
-__device__ __forceinline__ void scatter_ray(const RayRec &rr, float g, int nx, int ny, int nz, float *__restrict__ out,
-                                            float *__restrict__ accT)
+template <int U, int SKIP>
+__device__ __forceinline__ void scatter_ray_t(const RayRec &rr, float g, int nx, int ny, int nz,
+                                              float *__restrict__ out, float *__restrict__ accT)
 {
     const bool tr = accT != nullptr && leans_x(rr);
     float *__restrict__ base = tr ? accT : out;
@@ -116,11 +128,20 @@ __device__ __forceinline__ void scatter_ray(const RayRec &rr, float g, int nx, i
         int off[U];
         float l[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) dda_step(D, off[u], l[u]);
+        for (int u = 0; u < U; ++u) dda_step_t<SKIP>(D, off[u], l[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (l[u] > 0.f) red_add(base + off[u], __fmul_rn(g, l[u]));
     }
+}
+
+template <int U>
+__device__ __forceinline__ void scatter_ray(const RayRec &rr, float g, int nx, int ny, int nz, float *__restrict__ out,
+                                            float *__restrict__ accT)
+{
+    if (rr.w2 == 0.f) scatter_ray_t<U, 2>(rr, g, nx, ny, nz, out, accT);
+    else if (rr.w1 == 0.f) scatter_ray_t<U, 1>(rr, g, nx, ny, nz, out, accT);
+    else scatter_ray_t<U, 0>(rr, g, nx, ny, nz, out, accT);
 }
 
 template <int U>

@@ -401,6 +401,43 @@ __device__ __forceinline__ int dda_step(Dda<Off> &D, Off &off, float &l)
     return c0 ? 0 : (c1 ? 1 : (c2 ? 2 : 3));
 }
 
+// The same step for a ray whose axis SKIP (1 or 2) has w = 0: that axis's leaving t is +inf
+// and never the smallest, so leaving it out of the minimum and the selects changes nothing in
+// the (offset, length) sequence -- it only saves the instructions.
+template <int SKIP, class Off>
+__device__ __forceinline__ void dda_step_skip(Dda<Off> &D, Off &off, float &l)
+{
+    static_assert(SKIP == 1 || SKIP == 2, "axis left out");
+    const float ta = D.t0, tb = SKIP == 2 ? D.t1 : D.t2;
+    const float tn = fminf(fminf(ta, tb), D.tout);
+    l = __fsub_rn(tn, D.tcur);
+    off = D.off;
+    D.tcur = fmaxf(D.tcur, tn);
+    const bool c0 = ta == tn, cb = !c0 && tb == tn;
+    D.off += c0 ? D.d0 : (cb ? (SKIP == 2 ? D.d1 : D.d2) : (Off)0);
+    if (c0) {
+        D.q0 += D.s0;
+        D.t0 = __fmaf_rn(D.q0, D.i0, D.b0);
+    }
+    if (cb) {
+        if (SKIP == 2) {
+            D.q1 += D.s1;
+            D.t1 = __fmaf_rn(D.q1, D.i1, D.b1);
+        } else {
+            D.q2 += D.s2;
+            D.t2 = __fmaf_rn(D.q2, D.i2, D.b2);
+        }
+    }
+}
+
+// dda_step with the axes the ray may cross fixed at compile time: SKIP = 0 keeps all three.
+template <int SKIP, class Off>
+__device__ __forceinline__ void dda_step_t(Dda<Off> &D, Off &off, float &l)
+{
+    if (SKIP == 0) dda_step(D, off, l);
+    else dda_step_skip<SKIP == 0 ? 1 : SKIP>(D, off, l);
+}
+
 // Walk the ray: vis(offset, length) for every voxel with C_low < C_up, in crossing order.
 template <class Off, class V>
 __device__ __forceinline__ void dda_run(Dda<Off> &D, int max_steps, V &vis)
