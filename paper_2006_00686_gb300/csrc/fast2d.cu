@@ -1,19 +1,18 @@
-// Batched fast path for rays with at most two active axes (every 2D scan, and 3D rays
-// that stay in one coordinate plane), for batches of 4 or more images.
+// Batched fast path for 2D scans (rays with at most two active axes), batches of 4 or more.
 //
-// Layout.  The images of one batch chunk (Bp = 4 * LPR images) are interleaved so that the
-// Bp values of one unit are contiguous (64 bytes for Bp = 16), in two spatial orders:
-//   IL0 = [nz][ny+2P][nx+2P][Bp]  (x fastest)  used by warps whose rays are driven along y,
-//   IL1 = [nz][nx+2P][ny+2P][Bp]  (y fastest)  used by warps whose rays are driven along x,
-// so that the rays of a warp -- neighbouring detector bins, which sit on neighbouring
-// units of the minor axis at every driving step -- read neighbouring 64-byte chunks.
+// Two layouts of the batch, both in two bordered spatial orders (IL0: x fastest, IL1:
+// y fastest), so that the rays of a warp -- neighbouring detector bins, which sit on
+// neighbouring units of the minor axis at every driving step -- touch neighbouring memory:
+//   * quad planes [Q][ny+2P][nx+2P][4] (second half of this file): plane q holds images
+//     4q..4q+3 as one float4 per unit; the forward (one thread per ray) and the gather adjoint
+//     (one thread per pixel) run on it;
+//   * Bp-interleaved [chunk][...][Bp] (Bp = 4 * LPR images of one chunk contiguous, 64 bytes
+//     for Bp = 16): the accumulators of the ray-driven scatter adjoint, which adds with
+//     128-bit vector reductions.
 // A border of P = 2 zero units surrounds the image in x and y: the walk visits driving
 // slabs one beyond the image's extent, where the minor index can leave the image by at
 // most two, so every row the kernel can touch is valid memory and holds zero outside the
 // image -- no per-unit range test is needed.
-//
-// Mapping.  LPR lanes cooperate on one ray; each lane owns 4 images and loads them as one
-// float4.  A warp holds 32/LPR rays that step through the driving index in lockstep.
 //
 // Slab step (2D form of the walk in xray_core.cuh).  Between driving planes m and m+1 the
 // ray moves from row jc = floor(u_B(m)) to row jn = floor(u_B(m+1)); if they differ it
@@ -34,41 +33,8 @@
 namespace xr {
 
 // ---------------------------------------------------------------------------------------
-// Interleave: user images [B][nz][ny][nx] -> IL0 / IL1 of chunk c ([chunk][...][Bp])
+// Layout conversions
 // ---------------------------------------------------------------------------------------
-
-__global__ void interleave_images_kernel(const float *__restrict__ img, int batch, int nx, int ny, int nz,
-                                         int Bp, float *__restrict__ il0, float *__restrict__ il1)
-{
-    // the grid covers the padded units: the zero border is rewritten on every call
-    const int px = nx + 2 * XR_IL_PAD, py = ny + 2 * XR_IL_PAD;
-    const int64_t np = (int64_t)px * py * nz;  // padded units per image
-    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= np) return;
-    const int chunk = blockIdx.y;
-    const int ip = (int)(u % px);
-    const int64_t rest = u / px;
-    const int jp = (int)(rest % py);
-    const int k = (int)(rest / py);
-    const int i = ip - XR_IL_PAD, j = jp - XR_IL_PAD;
-    const bool inside = i >= 0 && i < nx && j >= 0 && j < ny;
-    const int64_t n = (int64_t)nx * ny * nz;
-    const int64_t uu = inside ? ((int64_t)k * ny + j) * nx + i : 0;
-    const int64_t o0 = ((int64_t)chunk * np + u) * Bp;
-    const int64_t o1 = ((int64_t)chunk * np + ((int64_t)k * px + ip) * py + jp) * Bp;
-    for (int b4 = 0; b4 < Bp; b4 += 4) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int b = chunk * Bp + b4;
-        if (inside) {
-            v.x = (b + 0 < batch) ? __ldg(img + (int64_t)(b + 0) * n + uu) : 0.f;
-            v.y = (b + 1 < batch) ? __ldg(img + (int64_t)(b + 1) * n + uu) : 0.f;
-            v.z = (b + 2 < batch) ? __ldg(img + (int64_t)(b + 2) * n + uu) : 0.f;
-            v.w = (b + 3 < batch) ? __ldg(img + (int64_t)(b + 3) * n + uu) : 0.f;
-        }
-        *reinterpret_cast<float4 *>(il0 + o0 + b4) = v;
-        *reinterpret_cast<float4 *>(il1 + o1 + b4) = v;
-    }
-}
 
 // Adjoint accumulators -> user images: img[b][u] = IL0 + IL1 at unit u (interiors only).
 __global__ void deinterleave_sum_kernel(const float *__restrict__ il0, const float *__restrict__ il1, int batch,
@@ -200,8 +166,9 @@ __device__ __forceinline__ void unit_op(const float *p, bool on, float l, float4
     }
 }
 
-// ADJ = false: forward, il0/il1 are the interleaved images, sino the output.
-// ADJ = true: adjoint (scatter), sino is the input and il0/il1 the zeroed accumulators.
+// LPR lanes cooperate on one ray, each owning 4 images.  ADJ = true (the one launched): the
+// scatter adjoint, sino the input and il0/il1 the zeroed Bp-interleaved accumulators.
+// ADJ = false walks the same way as a forward on Bp-interleaved images.
 template <int LPR, bool ADJ>
 __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const RayRec *__restrict__ rays, int64_t n_rays,
                                                            int nx, int ny, int nz, const float *__restrict__ il0,
@@ -383,125 +350,9 @@ __global__ void gather_prep_kernel(const RayRec *__restrict__ rays, int64_t n_ra
     out[r] = g;
 }
 
-template <int NB4, int KIND>  // Bp = 4 * NB4 images; KIND: XR_PAR2D, XR_FAN2D or XR_FAN2D_ARC
-__global__ void __launch_bounds__(256) gather_fast2_kernel(const RayRec *__restrict__ rays,
-                                                           const GatherRec *__restrict__ grec, GeoParams g,
-                                                           const float *__restrict__ vt,
-                                                           const float *__restrict__ sil, int64_t n_rays,
-                                                           float *__restrict__ img, int batch)
-{
-    constexpr int Bp = 4 * NB4;
-    // 32-bit indexing throughout (the host admits this path only when n_rays * Bp < 2^31)
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & 3;
-    const int pix = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2);
-    const int n_pix = g.nx * g.ny;
-    const bool live = pix < n_pix;
-    const int i = live ? pix % g.nx : 0, j = live ? pix / g.nx : 0;
-    const int chunk = blockIdx.y;
-    const int nr = (int)n_rays;
-    const float4 *S4 = reinterpret_cast<const float4 *>(sil) + chunk * NB4 * nr;
-    const float4 *G4 = reinterpret_cast<const float4 *>(grec);
-    const float4 *V4 = reinterpret_cast<const float4 *>(vt);
-    float acc[Bp];
-#pragma unroll
-    for (int b = 0; b < Bp; ++b) acc[b] = 0.f;
-    // pixel centre and half extents
-    const float xc = (float)(g.cx + (i + 0.5 - 0.5 * g.nx) * g.dx);
-    const float yc = (float)(g.cy + (0.5 * g.ny - j - 0.5) * g.dy);
-    const float hx = (float)(0.5 * g.dx), hy = (float)(0.5 * g.dy);
-    const float half = 0.5f * (float)(g.n_cols - 1);
-    const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0, sdd = (float)g.sdd;
-    const float fi = (float)i, fj = (float)j;
-    const int ncols = g.n_cols, nviews = live ? g.n_views : 0;
-    for (int v = 0, vbase = 0; v < nviews; ++v, vbase += ncols) {
-        // the same view record for every lane of the warp: one broadcast load
-        const float4 e0 = __ldg(V4 + 2 * v);
-        const float4 e1 = __ldg(V4 + 2 * v + 1);
-        float umin, umax;
-        if (KIND == XR_PAR2D) {
-            const float uc = e0.x * xc + e0.y * yc, hw = fabsf(e0.x) * hx + fabsf(e0.y) * hy;
-            umin = uc - hw;
-            umax = uc + hw;
-        } else {
-            const float rx = xc - e0.x, ry = yc - e0.y;
-            const float depth = rx * e0.z + ry * e0.w, lat = rx * e1.x + ry * e1.y;
-            const float dd = fabsf(e0.z) * hx + fabsf(e0.w) * hy, dl = fabsf(e1.x) * hx + fabsf(e1.y) * hy;
-            // footprint bounds only: an approximate reciprocal is enough (a 1e-3 bin margin follows)
-            const float r1 = __fdividef(1.0f, depth - dd), r2 = __fdividef(1.0f, depth + dd);
-            const float lo = lat - dl, hi = lat + dl;
-            const float a = fminf(lo * r1, lo * r2), b = fmaxf(hi * r1, hi * r2);
-            if (KIND == XR_FAN2D) {
-                umin = sdd * a;
-                umax = sdd * b;
-            } else {
-                umin = atanf(a);
-                umax = atanf(b);
-            }
-        }
-        // bin range; clamped before the round-up / round-down adds that turn floats into ints
-        const float c0f = fminf(fmaxf((umin - u0) * inv_du + half - 1e-3f, -1.0f), 4.0e6f);
-        const float c1f = fminf(fmaxf((umax - u0) * inv_du + half + 1e-3f, -1.0f), 4.0e6f);
-        const int c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
-        const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, ncols - 1);
-        for (int c = c0 + sub; c <= c1; c += 4) {
-            const int r = vbase + c;
-            const float4 ga = __ldg(G4 + 2 * r);
-            const float4 gb = __ldg(G4 + 2 * r + 1);
-            const int flags = __float_as_int(gb.z);
-            float l = 0.f;
-            if (flags == 0) {
-                // ga = (inv_x, b_x, inv_y, b_y), gb = (ox, oy, flags, -)
-                const float qx = fi - gb.x, qy = fj - gb.y;
-                const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
-                const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
-                l = __fsub_rn(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)));
-            } else if (flags == 2) {
-                Walk W;
-                if (walk_setup(rays[r], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
-                    l = walk_unit_length(W, i, j, 0);
-            }
-            if (l > 0.f) {
-#pragma unroll
-                for (int b4 = 0; b4 < NB4; ++b4) {
-                    const float4 s = __ldg(S4 + b4 * nr + r);
-                    acc[4 * b4 + 0] = __fmaf_rn(s.x, l, acc[4 * b4 + 0]);
-                    acc[4 * b4 + 1] = __fmaf_rn(s.y, l, acc[4 * b4 + 1]);
-                    acc[4 * b4 + 2] = __fmaf_rn(s.z, l, acc[4 * b4 + 2]);
-                    acc[4 * b4 + 3] = __fmaf_rn(s.w, l, acc[4 * b4 + 3]);
-                }
-            }
-        }
-    }
-    // reduce over the 4 lanes of the pixel
-#pragma unroll
-    for (int b = 0; b < Bp; ++b) {
-        acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 1);
-        acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 2);
-    }
-    if (live) {
-        // lane `sub` stores images sub, sub + 4, ... of this chunk
-#pragma unroll
-        for (int b = 0; b < Bp; ++b) {
-            const int bb = chunk * Bp + b;
-            if ((b & 3) == sub && bb < batch) img[(int64_t)bb * n_pix + pix] = acc[b];  // once per pixel
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------------------
-
-cudaError_t launch_interleave_images(const float *img, int batch, int nx, int ny, int nz, int Bp, float *il0,
-                                     float *il1, cudaStream_t s)
-{
-    const int64_t np = (int64_t)(nx + 2 * XR_IL_PAD) * (ny + 2 * XR_IL_PAD) * nz;
-    const int chunks = (batch + Bp - 1) / Bp;
-    interleave_images_kernel<<<dim3((unsigned)((np + 255) / 256), chunks), 256, 0, s>>>(img, batch, nx, ny, nz, Bp,
-                                                                                       il0, il1);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,
                                    cudaStream_t s)
@@ -509,19 +360,6 @@ cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays,
     const int chunks = (batch + Bp - 1) / Bp;
     interleave_sino_kernel<<<dim3((unsigned)((n_rays + 255) / 256), chunks), 256, 0, s>>>(sino, batch, n_rays,
                                                                                          Bp, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_project_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
-                                 const float *il1, int Bp, float *sino, int batch, int block, cudaStream_t s)
-{
-    const int lpr = Bp / 4;
-    const int64_t threads = n_rays * lpr;
-    const int64_t warps = (threads + 31) / 32;
-    const dim3 grid((unsigned)((warps * 32 + block - 1) / block), (unsigned)((batch + Bp - 1) / Bp));
-    if (lpr == 4) fwd_fast2_kernel<4, false><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
-    else if (lpr == 2) fwd_fast2_kernel<2, false><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
-    else fwd_fast2_kernel<1, false><<<grid, block, 0, s>>>(rays, n_rays, nx, ny, nz, il0, il1, Bp, sino, batch);
     return cudaGetLastError();
 }
 
@@ -565,26 +403,6 @@ cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, c
 }
 
 size_t gather_rec_bytes() { return sizeof(GatherRec); }
-
-cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
-                                const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
-                                cudaStream_t s)
-{
-    const int64_t n_pix = (int64_t)g.nx * g.ny;
-    const dim3 grid((unsigned)((n_pix * 4 + block - 1) / block), (unsigned)((batch + Bp - 1) / Bp));
-    const GatherRec *G = reinterpret_cast<const GatherRec *>(grec);
-#define XR_GATHER_LAUNCH(K)                                                                                   \
-    do {                                                                                                      \
-        if (Bp == 16) gather_fast2_kernel<4, K><<<grid, block, 0, s>>>(rays, G, g, vt, sil, n_rays, img, batch); \
-        else if (Bp == 8) gather_fast2_kernel<2, K><<<grid, block, 0, s>>>(rays, G, g, vt, sil, n_rays, img, batch); \
-        else gather_fast2_kernel<1, K><<<grid, block, 0, s>>>(rays, G, g, vt, sil, n_rays, img, batch);     \
-    } while (0)
-    if (g.kind == XR_PAR2D) XR_GATHER_LAUNCH(XR_PAR2D);
-    else if (g.kind == XR_FAN2D) XR_GATHER_LAUNCH(XR_FAN2D);
-    else XR_GATHER_LAUNCH(XR_FAN2D_ARC);
-#undef XR_GATHER_LAUNCH
-    return cudaGetLastError();
-}
 
 }  // namespace xr
 

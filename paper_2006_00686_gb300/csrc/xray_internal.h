@@ -130,12 +130,8 @@ cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_
 int batched_ctas_per_sm(int block, int adjoint);
 
 // Batched fast path for rays with at most two active axes (fast2d.cu).
-cudaError_t launch_interleave_images(const float *img, int batch, int nx, int ny, int nz, int Bp, float *il0,
-                                     float *il1, cudaStream_t s);
 cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,
                                    cudaStream_t s);
-cudaError_t launch_project_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
-                                 const float *il1, int Bp, float *sino, int batch, int block, cudaStream_t s);
 cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, float *acc0,
                                  float *acc1, size_t acc_bytes, int Bp, const float *sino, float *img, int batch,
                                  int block, cudaStream_t s);
@@ -184,9 +180,6 @@ cudaError_t launch_atten_plane_adj(const RayRec *rays, int64_t n_rays, int nx, i
 cudaError_t launch_attenuated(bool adjoint, const RayRec *rays, int64_t n_rays, const Grid &grid, const float *mu,
                               const float *in, float *out, int64_t n_units, int batch, int chunk, int block,
                               cudaStream_t s);
-cudaError_t launch_gather_fast2(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
-                                const float *sil, int64_t n_rays, float *img, int batch, int Bp, int block,
-                                cudaStream_t s);
 
 }  // namespace xr
 
