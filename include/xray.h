@@ -26,7 +26,8 @@
  * Errors: every call returns an xr_status and never aborts or exits.  After XR_ERR_CUDA,
  * xr_last_cuda_error() returns the CUDA error code seen by the calling thread.
  * Thread safety: calls on different handles may run concurrently; calls on one handle
- * must not.
+ * must not, and work launched through one handle on different streams must not overlap in
+ * time (the handle's workspace holds the interleaved copies and accumulators of the call).
  */
 #ifndef XRAY_H
 #define XRAY_H
