@@ -164,6 +164,17 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info);
 xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t);
 xr_status xr_get_tuning(const xr_geometry *g, xr_tuning *t);
 
+/* Autotuning (the paper has no counterpart).  Times every candidate tuning of the handle --
+ * batched path, images per thread, adjoint method, ray order -- on forward + adjoint of
+ * images and sinograms of ones, for the batch size the workspace is reserved for (1 without
+ * a reservation; the call reserves it), on a stream of its own, and keeps the fastest.
+ * cache_path (may be NULL): a text file with one line per scan and GPU; a scan found there
+ * is set without timing anything, a new result is appended.  Allocates and synchronises the
+ * handle's device: not for stream capture.
+ * Errors: XR_ERR_NULL, XR_ERR_TUNE (no candidate ran, or the cache could not be written),
+ * XR_ERR_ALLOC, XR_ERR_CUDA. */
+xr_status xr_tune(xr_geometry *g, const char *cache_path);
+
 /* Forward projection (eq. Xray_transform_image): for b < batch and every ray r,
  * sino[b][r] = sum over units I crossed by r of img[b][I] * l_I(r).
  * d_img: [batch][n_units] float32, d_sino: [batch][n_rays] float32 (overwritten).
@@ -201,6 +212,14 @@ xr_status xr_project_attenuated(const xr_geometry *g, const float *d_mu, const f
                                 int32_t batch, xr_stream stream);
 xr_status xr_backproject_attenuated(const xr_geometry *g, const float *d_mu, const float *d_sino, float *d_img,
                                     int32_t batch, xr_stream stream);
+
+/* Device error word of the handle (the paper has no counterpart): bits or-ed in by the
+ * handle's kernels since the last call, then cleared.  XR_DEVERR_WALK_BOUND: a ray's walk on
+ * the single-image fast path reached its step bound (nx + ny + nz + 2 units) before the
+ * image box's exit -- a ray record inconsistent with the grid; its sum is then incomplete.
+ * Synchronises the handle's device.  Errors: XR_ERR_NULL, XR_ERR_CUDA. */
+enum { XR_DEVERR_WALK_BOUND = 1 };
+xr_status xr_get_device_error(const xr_geometry *g, int32_t *code);
 
 /* Sparse rows of the projection matrix (Algorithm 1/2 "Output", Section 4.2): for each of
  * the n rays listed in d_rays (device int64 ray ids), the units it crosses with positive
@@ -244,7 +263,7 @@ xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream);
  * cannot afford the synchronisation of an allocation).  Same result as xr_batch_project on
  * the same problems, but the work list and tile counter live in one fixed array in device
  * memory that the library reserves on every device that loads it, until the process exits
- * (XR_NOALLOC_MAX_PROBLEMS work-list entries, about 14 KiB).  The caller still passes and
+ * (XR_NOALLOC_MAX_PROBLEMS work-list entries, about 16 KiB).  The caller still passes and
  * owns every image and sinogram.
  * The first call on a device looks up the array's device address (once, with that device
  * current); make that first call before any stream capture.  Each call rewrites the work
@@ -256,6 +275,17 @@ xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream);
 #define XR_NOALLOC_MAX_PROBLEMS 256
 xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t n, int32_t tile,
                                      xr_stream stream);
+
+/* One-call batched forward and adjoint over uneven problems (the paper has no counterpart:
+ * batching is a systems form of its per-ray method).  Same work list, capacity
+ * (XR_NOALLOC_MAX_PROBLEMS), no-allocation property and concurrency rule as
+ * xr_project_batched_noalloc, with work items of 256 rays.  xr_project_batched writes every
+ * problem's sino from its img; xr_backproject_batched overwrites every problem's img with
+ * the adjoint of its sino (a zero fill, then one persistent scatter launch; the problems'
+ * images are the only accumulators, so it is slower than a plan's backproject, which keeps
+ * a second layout).  Errors: as xr_project_batched_noalloc. */
+xr_status xr_project_batched(const xr_problem *probs, int32_t n, xr_stream stream);
+xr_status xr_backproject_batched(const xr_problem *probs, int32_t n, xr_stream stream);
 
 /* Read-bandwidth probe (measurement only; the paper has no counterpart).  Reads the device
  * buffer d_buf of n_floats floats (a multiple of 4, 16-byte aligned) `reps` times with 128-bit

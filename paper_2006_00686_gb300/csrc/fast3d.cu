@@ -80,7 +80,7 @@ struct RayOrder {
 // ray does not cross (w = 0), left out of every step, or 0.
 template <int U, int SKIP>
 __device__ __forceinline__ float fwd_ray_t(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
-                                           const float *__restrict__ imgT)
+                                           const float *__restrict__ imgT, int *err)
 {
     const bool tr = imgT != nullptr && leans_x(rr);
     const float *__restrict__ base = tr ? imgT : img;
@@ -99,6 +99,7 @@ __device__ __forceinline__ float fwd_ray_t(const RayRec &rr, int nx, int ny, int
 #pragma unroll
             for (int u = 0; u < U; ++u) acc = __fmaf_rn(v[u], l[u], acc);  // + 0 where l == 0
         }
+        if (err && D.tcur < D.tout) atomicOr(err, XR_DEVERR_WALK_BOUND);
     }
     return acc;
 }
@@ -107,18 +108,18 @@ __device__ __forceinline__ float fwd_ray_t(const RayRec &rr, int nx, int ny, int
 // that axis out (the same voxels and lengths, fewer instructions per step).
 template <int U>
 __device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
-                                         const float *__restrict__ imgT)
+                                         const float *__restrict__ imgT, int *err = nullptr)
 {
-    if (rr.w2 == 0.f) return fwd_ray_t<U, 2>(rr, nx, ny, nz, img, imgT);
-    if (rr.w1 == 0.f) return fwd_ray_t<U, 1>(rr, nx, ny, nz, img, imgT);
-    return fwd_ray_t<U, 0>(rr, nx, ny, nz, img, imgT);
+    if (rr.w2 == 0.f) return fwd_ray_t<U, 2>(rr, nx, ny, nz, img, imgT, err);
+    if (rr.w1 == 0.f) return fwd_ray_t<U, 1>(rr, nx, ny, nz, img, imgT, err);
+    return fwd_ray_t<U, 0>(rr, nx, ny, nz, img, imgT, err);
 }
 
 // Adjoint of one ray: one RED per voxel.  As in the forward, U voxels are generated ahead
 // and their U REDs issued back to back from separate registers.  accT may be NULL.
 template <int U, int SKIP>
 __device__ __forceinline__ void scatter_ray_t(const RayRec &rr, float g, int nx, int ny, int nz,
-                                              float *__restrict__ out, float *__restrict__ accT)
+                                              float *__restrict__ out, float *__restrict__ accT, int *err)
 {
     const bool tr = accT != nullptr && leans_x(rr);
     float *__restrict__ base = tr ? accT : out;
@@ -133,38 +134,39 @@ __device__ __forceinline__ void scatter_ray_t(const RayRec &rr, float g, int nx,
         for (int u = 0; u < U; ++u)
             if (l[u] > 0.f) red_add(base + off[u], __fmul_rn(g, l[u]));
     }
+    if (err && D.tcur < D.tout) atomicOr(err, XR_DEVERR_WALK_BOUND);
 }
 
 template <int U>
 __device__ __forceinline__ void scatter_ray(const RayRec &rr, float g, int nx, int ny, int nz, float *__restrict__ out,
-                                            float *__restrict__ accT)
+                                            float *__restrict__ accT, int *err = nullptr)
 {
-    if (rr.w2 == 0.f) scatter_ray_t<U, 2>(rr, g, nx, ny, nz, out, accT);
-    else if (rr.w1 == 0.f) scatter_ray_t<U, 1>(rr, g, nx, ny, nz, out, accT);
-    else scatter_ray_t<U, 0>(rr, g, nx, ny, nz, out, accT);
+    if (rr.w2 == 0.f) scatter_ray_t<U, 2>(rr, g, nx, ny, nz, out, accT, err);
+    else if (rr.w1 == 0.f) scatter_ray_t<U, 1>(rr, g, nx, ny, nz, out, accT, err);
+    else scatter_ray_t<U, 0>(rr, g, nx, ny, nz, out, accT, err);
 }
 
 template <int U>
 __global__ void __launch_bounds__(256) fwd3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
                                                     int nx, int ny, int nz, const float *__restrict__ img,
-                                                    const float *__restrict__ imgT, float *__restrict__ sino)
+                                                    const float *__restrict__ imgT, float *__restrict__ sino, int *err)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_rays) return;
     const int r = ord.ray(t);
-    sino[r] = fwd_ray<U>(rays[r], nx, ny, nz, img, imgT);
+    sino[r] = fwd_ray<U>(rays[r], nx, ny, nz, img, imgT, err);
 }
 
 template <int U>
 __global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
                                                         int nx, int ny, int nz, const float *__restrict__ sino,
-                                                        float *__restrict__ out, float *__restrict__ accT)
+                                                        float *__restrict__ out, float *__restrict__ accT, int *err)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_rays) return;
     const int r = ord.ray(t);
     const float g = __ldg(sino + r);
-    if (g != 0.f) scatter_ray<U>(rays[r], g, nx, ny, nz, out, accT);
+    if (g != 0.f) scatter_ray<U>(rays[r], g, nx, ny, nz, out, accT, err);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -354,16 +356,16 @@ static RayOrder make_order(const GeoParams &g, int row_major)
 }
 
 cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
-                             const float *img, const float *imgT, float *sino, int block, cudaStream_t s)
+                             const float *img, const float *imgT, float *sino, int block, int *err, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
     fwd3d_kernel<kFwdAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, row_major), g.nx, g.ny, g.nz,
-                                                     img, imgT, sino);
+                                                     img, imgT, sino, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
-                             const float *sino, float *out, float *accT, int block, cudaStream_t s)
+                             const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s)
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const size_t bytes = (size_t)nx * ny * nz * sizeof(float);
@@ -372,7 +374,7 @@ cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_r
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
     scatter3d_kernel<kAdjAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, row_major), nx, ny, nz, sino, out,
-                                              accT);
+                                              accT, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((nx + TT - 1) / TT), (unsigned)((ny + TT - 1) / TT), (unsigned)nz);

@@ -1,5 +1,6 @@
 // xr_project_batched_noalloc: the batched forward projection for callers that cannot
-// allocate device memory.
+// allocate device memory (and xr_project_batched / xr_backproject_batched, the one-call
+// forward and adjoint over the same fixed work-list array).
 //
 // Some callers cannot call cudaMalloc at the point where they need a projection: code
 // running while a stream is captured in global mode (where cudaMalloc is refused), hosts
@@ -70,8 +71,27 @@ cudaError_t scratch_on_current_device(unsigned char **out)
 
 }  // namespace
 
+// Uploads the work list into the scratch array and launches the forward (adjoint = 0) or
+// the zero fill and the adjoint (adjoint = 1) over it.
+static xr_status noalloc_launch(const xr_problem *probs, int32_t n, int32_t tile, int adjoint, xr_stream stream);
+
 extern "C" xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t n, int32_t tile,
                                                 xr_stream stream)
+{
+    return noalloc_launch(probs, n, tile, 0, stream);
+}
+
+extern "C" xr_status xr_project_batched(const xr_problem *probs, int32_t n, xr_stream stream)
+{
+    return noalloc_launch(probs, n, 0, 0, stream);
+}
+
+extern "C" xr_status xr_backproject_batched(const xr_problem *probs, int32_t n, xr_stream stream)
+{
+    return noalloc_launch(probs, n, 0, 1, stream);
+}
+
+static xr_status noalloc_launch(const xr_problem *probs, int32_t n, int32_t tile, int adjoint, xr_stream stream)
 {
     if (!probs) return XR_ERR_NULL;
     if (n < 1) return XR_ERR_SIZE;
@@ -109,10 +129,12 @@ extern "C" xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t
     const int block = 256;
     noalloc_upload_kernel<<<1, 256, 0, s>>>(w, scratch);
     e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = launch_batched_items(reinterpret_cast<const BatchItem *>(scratch + kCounterBytes), n, tiles, tile,
-                                 reinterpret_cast<unsigned long long *>(scratch), sms * batched_ctas_per_sm(block, 0),
-                                 block, s);
+    const BatchItem *items = reinterpret_cast<const BatchItem *>(scratch + kCounterBytes);
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(scratch);
+    if (e == cudaSuccess && !adjoint)
+        e = launch_batched_items(items, n, tiles, tile, counter, sms * batched_ctas_per_sm(block, 0), block, s);
+    if (e == cudaSuccess && adjoint)  // zero fill, then the scatter straight into the images
+        e = launch_batched(items, n, tiles, tile, counter, 1, 0, sms * batched_ctas_per_sm(block, 1), block, s);
     if (e != cudaSuccess) return xr_fail_cuda(e);
     return XR_OK;
 }

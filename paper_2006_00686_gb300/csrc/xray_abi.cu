@@ -243,6 +243,8 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views_df, (size_t)p.n_views * sizeof(ViewDF));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_det, n_det * sizeof(DetRec));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(int));
     if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_view_tab, (size_t)p.n_views * 8 * sizeof(float));
     if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_grec, (size_t)g->n_rays * gather_rec_bytes());
     if (e != cudaSuccess) {
@@ -342,6 +344,7 @@ void xr_geometry_destroy(xr_geometry *g)
     cudaFree(g->d_view_tab);
     cudaFree(g->d_grec);
     cudaFree(g->d_ws);
+    cudaFree(g->d_err);
     cudaSetDevice(prev);
     delete g;
 }
@@ -438,7 +441,7 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
             const float *img = d_img + (size_t)b * g->n_units;
             XR_CUDA(launch_transpose_xy(img, g->d_ws, g->params.nx, g->params.ny, g->params.nz, s));
             XR_CUDA(launch_project3d(g->d_rays, g->params, g->n_rays, row_major(g), img, g->d_ws,
-                                     d_sino + (size_t)b * g->n_rays, g->tune.block, s));
+                                     d_sino + (size_t)b * g->n_rays, g->tune.block, g->d_err, s));
         }
         return XR_OK;
     }
@@ -507,7 +510,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if (!use_tiled(g, batch) && !use_fast(g, batch) && use_dda(g)) {
         for (int b = 0; b < batch; ++b)
             XR_CUDA(launch_scatter3d(g->d_rays, g->params, g->n_rays, row_major(g), d_sino + (size_t)b * g->n_rays,
-                                     d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, s));
+                                     d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, g->d_err, s));
         return XR_OK;
     }
     if (use_tiled(g, batch)) {
@@ -592,6 +595,20 @@ xr_status xr_backproject_attenuated(const xr_geometry *g, const float *d_mu, con
     XR_CUDA(cudaMemsetAsync(d_img, 0, (size_t)g->n_units * batch * sizeof(float), s));
     XR_CUDA(launch_attenuated(true, g->d_rays, g->n_rays, make_grid(g), d_mu, d_sino, d_img, g->n_units, batch,
                               chunk, g->tune.block, s));
+    return XR_OK;
+}
+
+xr_status xr_get_device_error(const xr_geometry *g, int32_t *code)
+{
+    if (!g || !code) return XR_ERR_NULL;
+    int prev = 0, h = 0;
+    XR_CUDA(cudaGetDevice(&prev));
+    XR_CUDA(cudaSetDevice(g->device));
+    cudaError_t e = cudaMemcpy(&h, g->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(int));
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *code = h;
     return XR_OK;
 }
 

@@ -154,11 +154,12 @@ size_t gather_rec_bytes();
 // reading the caller's image or its [z][x][y] copy by the ray's direction.
 cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int nz, cudaStream_t s);
 // row_major: threads run over (row, view, col) instead of the ray order.
+// err: the handle's device error word (XR_DEVERR_* bits are or-ed in), or NULL.
 cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
-                             const float *img, const float *imgT, float *sino, int block, cudaStream_t s);
+                             const float *img, const float *imgT, float *sino, int block, int *err, cudaStream_t s);
 // Zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
 cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
-                             const float *sino, float *out, float *accT, int block, cudaStream_t s);
+                             const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s);
 // Unit-driven adjoint for 3D scans (tile3d.cu): one CTA per 16^3 tile of voxels gathers
 // every ray of its detector footprint in shared memory and writes the tile once.
 cudaError_t launch_tile3d_adj(const RayRec *rays, const ViewRec *views, const GeoParams &g, const float *sino,
@@ -200,6 +201,7 @@ struct xr_geometry {
     float *d_view_tab;   // per view: 2D gather footprint data (8 floats)
     void *d_grec;        // per ray: plane constants of the 2D gather
     float *d_ws;         // workspace of the batched fast path (interleaved copies)
+    int *d_err;          // device error word (XR_DEVERR_* bits)
     size_t ws_bytes;
     int ws_batch;        // largest batch the workspace holds (0: none reserved)
     xr_tuning tune;

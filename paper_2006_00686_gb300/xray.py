@@ -74,6 +74,10 @@ SIGNATURES = {
     "xr_batch_backproject": (_I32, [_VP, _VP]),
     "xr_project_batched_noalloc": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _VP]),
     "xr_read_probe": (_I32, [_VP, ctypes.c_int64, _I32, _VP, _I32, _VP]),
+    "xr_project_batched": (_I32, [ctypes.POINTER(_Problem), _I32, _VP]),
+    "xr_backproject_batched": (_I32, [ctypes.POINTER(_Problem), _I32, _VP]),
+    "xr_tune": (_I32, [_VP, ctypes.c_char_p]),
+    "xr_get_device_error": (_I32, [_VP, ctypes.POINTER(_I32)]),
     "xr_project_attenuated": (_I32, [_VP, _VP, _VP, _VP, _I32, _VP]),
     "xr_backproject_attenuated": (_I32, [_VP, _VP, _VP, _VP, _I32, _VP]),
     "xr_status_string": (ctypes.c_char_p, [_I32]),
@@ -172,6 +176,18 @@ class Projector:
         _check(lib().xr_get_tuning(self._h, ctypes.byref(t)), "xr_get_tuning")
         return {"block": t.block, "batch_chunk": t.batch_chunk, "adjoint": t.adjoint, "path": t.path,
                 "order": t.order}
+
+    def tune(self, cache_path: str | None = None) -> dict:
+        """Time the candidate tunings in the library (xr_tune) for the reserved batch size and
+        keep the fastest; cache_path: a text cache shared across processes."""
+        _check(lib().xr_tune(self._h, None if cache_path is None else os.fsencode(cache_path)), "xr_tune")
+        return self.tuning()
+
+    def device_error(self) -> int:
+        """The handle's device error word since the last call (0: none), then cleared."""
+        code = ctypes.c_int32(0)
+        _check(lib().xr_get_device_error(self._h, ctypes.byref(code)), "xr_get_device_error")
+        return int(code.value)
 
     def reserve(self, max_batch: int):
         """Reserve the batched fast path's workspace (allocates; not during graph capture)."""
