@@ -245,10 +245,13 @@ def _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic):
     gather = 4.0 * n_int * B
     gather_gbs = gather / (dom_ms * 1e-3) / 1e9
     l2_peak = _l2_peak()
+    from paper_2006_00686_gb300.xray import fma_throughput
+    fma_meas = fma_throughput()
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({peak_kind} max clock)",
             "algorithmic_flop": flop, "intersections_per_image": n_int, "ms": round(dom_ms, 4),
+            "fp32_fma_measured_tflops": round(fma_meas, 2),
             "hbm": {"compulsory_bytes": compulsory, "achieved_gbs": round(compulsory / (dom_ms * 1e-3) / 1e9, 1),
                     "peak_gbs": peaks["hbm_gbs"], "frac": round(compulsory / (dom_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
             # the gather along rays as bytes: 4 B per (ray, unit, image), served from L1/L2

@@ -296,6 +296,13 @@ xr_status xr_backproject_batched(const xr_problem *probs, int32_t n, xr_stream s
 xr_status xr_read_probe(const float *d_buf, int64_t n_floats, int32_t reps, float *d_sink,
                         int32_t sink_floats, xr_stream stream);
 
+/* FP32 FMA probe (measurement only; the paper has no counterpart): every SM's resident CTAs
+ * run 8 independent fused multiply-add chains per thread for `iters` steps and write one
+ * float per thread to d_sink (sink_floats >= SMs x resident CTAs x 256); *flop receives the
+ * FLOP count (2 per FMA) of the launch, to be divided by its event-timed duration.
+ * Errors: XR_ERR_NULL, XR_ERR_SIZE, XR_ERR_CUDA. */
+xr_status xr_fma_probe(int32_t iters, float *d_sink, int32_t sink_floats, int64_t *flop, xr_stream stream);
+
 /* Text of a status code (static storage). */
 const char *xr_status_string(xr_status s);
 

@@ -20,6 +20,23 @@ __global__ void __launch_bounds__(256) read_probe_kernel(const float4 *__restric
     sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+// FP32 FMA throughput: 8 independent chains per thread, `iters` steps each, written once.
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, float *__restrict__ sink)
+{
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    const float m = 0.999999f, c = 1e-7f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = __fmaf_rn(a[k], m, c);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += a[k];
+    sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 }  // namespace
 }  // namespace xr
 
@@ -47,3 +64,21 @@ extern "C" xr_status xr_read_probe(const float *d_buf, int64_t n_floats, int32_t
     PROBE_CUDA(cudaGetLastError());
     return XR_OK;
 }
+
+extern "C" xr_status xr_fma_probe(int32_t iters, float *d_sink, int32_t sink_floats, int64_t *flop, xr_stream stream)
+{
+    using namespace xr;
+    if (!d_sink || !flop) return XR_ERR_NULL;
+    if (iters < 1) return XR_ERR_SIZE;
+    int dev = 0, sms = 0, per_sm = 0;
+    PROBE_CUDA(cudaGetDevice(&dev));
+    PROBE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PROBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_probe_kernel, 256, 0));
+    const int grid = sms * (per_sm > 0 ? per_sm : 1);
+    if ((int64_t)grid * 256 > sink_floats) return XR_ERR_SIZE;
+    fma_probe_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(iters, d_sink);
+    PROBE_CUDA(cudaGetLastError());
+    *flop = (int64_t)grid * 256 * 8 * 2 * (int64_t)iters;
+    return XR_OK;
+}
+

@@ -74,6 +74,7 @@ SIGNATURES = {
     "xr_batch_backproject": (_I32, [_VP, _VP]),
     "xr_project_batched_noalloc": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _VP]),
     "xr_read_probe": (_I32, [_VP, ctypes.c_int64, _I32, _VP, _I32, _VP]),
+    "xr_fma_probe": (_I32, [_I32, _VP, _I32, ctypes.POINTER(ctypes.c_int64), _VP]),
     "xr_project_batched": (_I32, [ctypes.POINTER(_Problem), _I32, _VP]),
     "xr_backproject_batched": (_I32, [ctypes.POINTER(_Problem), _I32, _VP]),
     "xr_tune": (_I32, [_VP, ctypes.c_char_p]),
@@ -390,5 +391,28 @@ def read_bandwidth(n_bytes: int = 64 << 20, reps: int = 20, trials: int = 5) -> 
         b.record(stream)
         b.synchronize()
         best = max(best, 4.0 * n * reps / (a.elapsed_time(b) * 1e-3) / 1e9)
+    return best
+
+
+def fma_throughput(iters: int = 20000, trials: int = 5) -> float:
+    """Measured FP32 FMA throughput (TFLOP/s, 2 FLOP per FMA): best of `trials` event-timed
+    launches of xr_fma_probe after one warm-up."""
+    sink = torch.empty(1 << 22, device="cuda")
+    stream = torch.cuda.current_stream()
+    flop = ctypes.c_int64(0)
+
+    def launch():
+        _check(lib().xr_fma_probe(iters, _ptr(sink), sink.numel(), ctypes.byref(flop), _stream(stream)),
+               "xr_fma_probe")
+
+    launch()
+    best = 0.0
+    for _ in range(trials):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        launch()
+        b.record(stream)
+        b.synchronize()
+        best = max(best, flop.value / (a.elapsed_time(b) * 1e-3) / 1e12)
     return best
 

@@ -88,3 +88,16 @@ def test_device_error_word_stays_clear(X):
     P.adjoint(y)
     assert P.device_error() == 0
     P.close()
+
+
+def test_measurement_probes_report_plausible_peaks(X):
+    # FP32 FMA: positive and not above the count of FP32 lanes at the maximum SM clock
+    # (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s; 10 % for clock reporting)
+    props = torch.cuda.get_device_properties(0)
+    lanes_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    fma = X.fma_throughput(iters=2000, trials=2)
+    assert 0.05 * lanes_peak < fma < 1.1 * lanes_peak
+    # L2-only reads of a buffer that fits L2: above the HBM copy rate is expected, far above
+    # 100 TB/s would mean the probe did not read
+    bw = X.read_bandwidth(16 << 20, 4, 2)
+    assert 100.0 < bw < 100_000.0
