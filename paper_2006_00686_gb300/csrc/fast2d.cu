@@ -324,30 +324,29 @@ __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const
 // pixel's footprint bins of each view and all Bp images, then reduce.
 // ---------------------------------------------------------------------------------------
 
-// Per-ray plane constants of both in-plane axes: t(plane q of axis a) = fma(q - o_a, inv_a, b_a).
-struct __align__(16) GatherRec {
-    float inv_x, b_x, inv_y, b_y;
-    float ox, oy;  // integer parts of the foot point (as floats, exact)
-    int flags;     // 1: the ray misses, 2: the ray is parallel to an axis (general path)
-    int pad;
-};
-static_assert(sizeof(GatherRec) == 32, "GatherRec layout");
+// Per-ray plane constants of both in-plane axes, t(plane q of axis a) = fma(q - o_a, inv_a, b_a),
+// stored as two arrays so that a warp's loads of neighbouring rays are contiguous:
+//     GA[r] = (inv_x, b_x, inv_y, b_y)   16 B
+//     GB[r] = (o_x, o_y)                 8 B, the integer parts of the foot point (exact floats)
+// A ray that misses the image, or is parallel to an axis, has inv_x == 0 or inv_y == 0 (a
+// missing ray all zeros); those take the walk's own unit length.
+constexpr size_t kGatherRecBytes = sizeof(float4) + sizeof(float2);
 
-__global__ void gather_prep_kernel(const RayRec *__restrict__ rays, int64_t n_rays, GatherRec *__restrict__ out)
+__global__ void gather_prep_kernel(const RayRec *__restrict__ rays, int64_t n_rays, float4 *__restrict__ ga,
+                                   float2 *__restrict__ gb)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     const RayRec R = rays[r];
-    GatherRec g;
-    g.flags = (R.flags & RAY_MISS) ? 1 : ((R.w0 == 0.f || R.w1 == 0.f) ? 2 : 0);
-    g.inv_x = R.w0 != 0.f ? __frcp_rn(R.w0) : 0.f;
-    g.b_x = __fmul_rn(-R.f0, g.inv_x);
-    g.inv_y = R.w1 != 0.f ? __frcp_rn(R.w1) : 0.f;
-    g.b_y = __fmul_rn(-R.f1, g.inv_y);
-    g.ox = (float)R.o0;
-    g.oy = (float)R.o1;
-    g.pad = 0;
-    out[r] = g;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!(R.flags & RAY_MISS)) {
+        a.x = R.w0 != 0.f ? __frcp_rn(R.w0) : 0.f;
+        a.y = __fmul_rn(-R.f0, a.x);
+        a.z = R.w1 != 0.f ? __frcp_rn(R.w1) : 0.f;
+        a.w = __fmul_rn(-R.f1, a.z);
+    }
+    ga[r] = a;
+    gb[r] = make_float2((float)R.o0, (float)R.o1);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -397,12 +396,13 @@ cudaError_t launch_deinterleave_sum(const float *acc0, const float *acc1, int ba
 
 cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, cudaStream_t s)
 {
-    gather_prep_kernel<<<(unsigned)((n_rays + 255) / 256), 256, 0, s>>>(rays, n_rays,
-                                                                        reinterpret_cast<GatherRec *>(grec));
+    float4 *ga = reinterpret_cast<float4 *>(grec);
+    gather_prep_kernel<<<(unsigned)((n_rays + 255) / 256), 256, 0, s>>>(rays, n_rays, ga,
+                                                                        reinterpret_cast<float2 *>(ga + n_rays));
     return cudaGetLastError();
 }
 
-size_t gather_rec_bytes() { return sizeof(GatherRec); }
+size_t gather_rec_bytes() { return kGatherRecBytes; }
 
 }  // namespace xr
 
@@ -570,11 +570,10 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
 
 // Gather adjoint for 2D scans: one thread per pixel, NQ planes per thread; sil: sinogram
 // planes [Q][n_rays][4] (interleave_sino_kernel with Bp = 4 * Q, one chunk); blockIdx.y =
-// group of NQ planes.  The ray's plane constants are read first; its sinogram values only
-// when the pixel's length is positive.
-// Length of pixel (fi, fj) on ray record (ga, gb): the pixel's t-interval along x and y
-// intersected (C_up - C_low with the plane values the walk uses).
-__device__ __forceinline__ float gather_len(const float4 ga, const float4 gb, float fi, float fj)
+// group of NQ planes.
+// Length of pixel (fi, fj) on the ray with plane constants (ga, gb): the pixel's t-interval
+// along x and y intersected (C_up - C_low with the plane values the walk uses).
+__device__ __forceinline__ float gather_len(const float4 ga, const float2 gb, float fi, float fj)
 {
     const float qx = fi - gb.x, qy = fj - gb.y;
     const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
@@ -590,7 +589,7 @@ __device__ __forceinline__ float gather_len(const float4 ga, const float4 gb, fl
 
 template <int NQ, int KIND>
 __global__ void __launch_bounds__(256, XR_GATHER_MIN_BLOCKS(NQ)) gather_plane_kernel(const RayRec *__restrict__ rays,
-                                                              const GatherRec *__restrict__ grec, GeoParams g,
+                                                              const float4 *__restrict__ grec, GeoParams g,
                                                               const float *__restrict__ vt,
                                                               const float4 *__restrict__ sil, int64_t n_rays,
                                                               float *__restrict__ img, int batch)
@@ -602,7 +601,8 @@ __global__ void __launch_bounds__(256, XR_GATHER_MIN_BLOCKS(NQ)) gather_plane_ke
     const int q0 = blockIdx.y * NQ;
     const int nr = (int)n_rays;
     const float4 *S = sil + (int64_t)q0 * nr;
-    const float4 *G4 = reinterpret_cast<const float4 *>(grec);
+    const float4 *GA = grec;
+    const float2 *GB = reinterpret_cast<const float2 *>(grec + n_rays);
     const float4 *V4 = reinterpret_cast<const float4 *>(vt);
     float4 acc[NQ];
 #pragma unroll
@@ -650,23 +650,23 @@ __global__ void __launch_bounds__(256, XR_GATHER_MIN_BLOCKS(NQ)) gather_plane_ke
             const int r0 = vbase + c;
             const bool two = c + 1 <= c1;
             const int r1 = two ? r0 + 1 : r0;
-            const float4 ga0 = __ldg(G4 + 2 * r0), gb0 = __ldg(G4 + 2 * r0 + 1);
-            const float4 ga1 = __ldg(G4 + 2 * r1), gb1 = __ldg(G4 + 2 * r1 + 1);
+            const float4 ga0 = __ldg(GA + r0), ga1 = __ldg(GA + r1);
+            const float2 gb0 = __ldg(GB + r0), gb1 = __ldg(GB + r1);
             float4 s0[NQ], s1[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 s0[q] = __ldg(S + q * nr + r0);
                 s1[q] = two ? __ldg(S + q * nr + r1) : z4;
             }
-            const int f0 = __float_as_int(gb0.z), f1 = __float_as_int(gb1.z);
-            float l0 = f0 == 0 ? gather_len(ga0, gb0, fi, fj) : 0.f;
-            float l1 = (two && f1 == 0) ? gather_len(ga1, gb1, fi, fj) : 0.f;
-            if (f0 == 2 || (two && f1 == 2)) {
-                // a ray parallel to an axis: the walk's own unit length (rare)
+            const bool sp0 = ga0.x == 0.f || ga0.z == 0.f, sp1 = two && (ga1.x == 0.f || ga1.z == 0.f);
+            float l0 = sp0 ? 0.f : gather_len(ga0, gb0, fi, fj);
+            float l1 = (two && !sp1) ? gather_len(ga1, gb1, fi, fj) : 0.f;
+            if (sp0 || sp1) {
+                // a ray parallel to an axis (or one that misses): the walk's own unit length (rare)
                 Walk W;
-                if (f0 == 2 && walk_setup(rays[r0], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
+                if (sp0 && walk_setup(rays[r0], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
                     l0 = walk_unit_length(W, i, j, 0);
-                if (two && f1 == 2 && walk_setup(rays[r1], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
+                if (sp1 && walk_setup(rays[r1], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
                     l1 = walk_unit_length(W, i, j, 0);
             }
             l0 = l0 > 0.f ? l0 : 0.f;
@@ -719,7 +719,7 @@ cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoP
     const int groups = (Q + nq - 1) / nq;
     const int64_t n_pix = (int64_t)g.nx * g.ny;
     const dim3 grid((unsigned)((n_pix + 255) / 256), (unsigned)groups);
-    const GatherRec *G = reinterpret_cast<const GatherRec *>(grec);
+    const float4 *G = reinterpret_cast<const float4 *>(grec);
     const float4 *S = reinterpret_cast<const float4 *>(sil);
 #define XR_GP(NQV, K) gather_plane_kernel<NQV, K><<<grid, 256, 0, s>>>(rays, G, g, vt, S, n_rays, img, batch)
 #define XR_GP_K(K)                 \
