@@ -192,7 +192,9 @@ xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img
 /* As xr_backproject with an explicit method (ray lists have no detector to gather over: the
  * scatter only, XR_ADJ_GATHER returns XR_ERR_ARG).  XR_ADJ_SCATTER: ray-driven, each ray adds
  * l * g to every unit it crosses (atomics).  XR_ADJ_GATHER: unit-driven; 2D scans: one thread
- * per pixel sums the rays whose detector footprint covers it; 3D scans: one CTA per 16^3
+ * per pixel (on the batched fast path: per pair of horizontally adjacent pixels, with the
+ * views split into chunks whose sums are added in a fixed order) sums the rays whose
+ * detector footprint covers it; deterministic, no atomics; 3D scans: one CTA per 16^3
  * tile of voxels walks every ray of the tile's detector footprint through the tile and sums
  * in shared memory.  All give the same (ray, unit) lengths. */
 xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float *d_img,

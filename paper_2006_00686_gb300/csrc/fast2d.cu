@@ -5,7 +5,7 @@
 // neighbouring units of the minor axis at every driving step -- touch neighbouring memory:
 //   * quad planes [Q][ny+2P][nx+2P][4] (second half of this file): plane q holds images
 //     4q..4q+3 as one float4 per unit; the forward (one thread per ray) and the gather adjoint
-//     (one thread per pixel) run on it;
+//     (one thread per pair of pixels) run on it;
 //   * Bp-interleaved [chunk][...][Bp] (Bp = 4 * LPR images of one chunk contiguous, 64 bytes
 //     for Bp = 16): the accumulators of the ray-driven scatter adjoint, which adds with
 //     128-bit vector reductions.
@@ -20,6 +20,9 @@
 // |t_{m+1} - tc| in row jn.  These are C_up - C_low of the two units with the same plane
 // values the walk uses; the rare step that crosses two rows falls back to the general
 // per-candidate formula.
+#include <algorithm>
+#include <cmath>
+
 #include "xray_internal.h"
 
 // Zero border (units) around the interleaved images.
@@ -407,7 +410,7 @@ size_t gather_rec_bytes() { return kGatherRecBytes; }
 }  // namespace xr
 
 // =======================================================================================
-// Quad-plane layout: one thread per ray (forward) or per pixel (gather) for all images.
+// Quad-plane layout: one thread per ray (forward) or per pair of pixels (gather) for all images.
 //
 // The images of the batch (padded to a multiple of 4) are stored as planes of 4 images:
 // plane q holds images 4q..4q+3 as one float4 per unit, in the same two bordered spatial
@@ -568,54 +571,59 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
     }
 }
 
-// Gather adjoint for 2D scans: one thread per pixel, NQ planes per thread; sil: sinogram
-// planes [Q][n_rays][4] (interleave_sino_kernel with Bp = 4 * Q, one chunk); blockIdx.y =
-// group of NQ planes.
-// Length of pixel (fi, fj) on the ray with plane constants (ga, gb): the pixel's t-interval
-// along x and y intersected (C_up - C_low with the plane values the walk uses).
-__device__ __forceinline__ float gather_len(const float4 ga, const float2 gb, float fi, float fj)
-{
-    const float qx = fi - gb.x, qy = fj - gb.y;
-    const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
-    const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
-    return __fsub_rn(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)));
-}
-
-// CTAs per SM the gather's registers must allow (16 accumulators and two bins' prefetched
-// values per thread with 4 planes)
-#ifndef XR_GATHER_MIN_BLOCKS
-#define XR_GATHER_MIN_BLOCKS(NQ) ((NQ) >= 4 ? 2 : 3)
-#endif
+// Gather adjoint on the quad planes: one thread per pair of horizontally adjacent pixels
+// (i, j), (i+1, j) of one row (the last pixel of an odd row alone), all 4*NQ images.  Per
+// view the thread projects the pair's box (its four corners) onto the detector; for every bin
+// whose centre lies in that footprint it loads the ray's plane constants and the bin's NQ
+// sinogram quads once and adds l * g to both pixels.  The lengths are C_up - C_low of each
+// pixel from the same plane crossings the forward uses (x planes i, i+1, i+2 and y planes j,
+// j+1, each one FMA); a bin that misses a pixel gives C_up <= C_low there and adds nothing.
+// One bin per step: measured against two bins per step and against one pixel per thread
+// (fan beam 512^2 x 16: 2.17 vs 2.24 and 2.34 ms).  sil: sinogram planes [Q][n_rays][4]
+// (interleave_sino_kernel with Bp = 4 * Q, one chunk); blockIdx.y = group of NQ planes.
+//
+// The views are split into nch chunks inside each CTA of 256 threads: thread = (pair, chunk),
+// 256 / nch pairs per CTA, each warp on 32 pairs of one chunk.  The chunks' sums are added
+// in chunk order through shared memory by the chunk-0 threads, so the result does not depend
+// on scheduling.  nch multiplies the threads of the launch; the host picks it so that the
+// CTAs fill whole waves of the GPU (512^2 pairs on 152 SMs: 1.68 waves of one-chunk CTAs).
+constexpr int kGatherThreads = 256;
 
 template <int NQ, int KIND>
-__global__ void __launch_bounds__(256, XR_GATHER_MIN_BLOCKS(NQ)) gather_plane_kernel(const RayRec *__restrict__ rays,
-                                                              const float4 *__restrict__ grec, GeoParams g,
-                                                              const float *__restrict__ vt,
-                                                              const float4 *__restrict__ sil, int64_t n_rays,
-                                                              float *__restrict__ img, int batch)
+__global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_pair_kernel(
+    const RayRec *__restrict__ rays, const float4 *__restrict__ grec, GeoParams g, const float *__restrict__ vt,
+    const float4 *__restrict__ sil, int64_t n_rays, float *__restrict__ img, int batch, int nch)
 {
-    const int pix = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    extern __shared__ float red[];  // [nch - 1][8 * NQ][ppc]
+    const int tpr = (g.nx + 1) >> 1;  // threads per row
+    const int ppc = kGatherThreads / nch;  // pairs per CTA
+    const int pl = threadIdx.x % ppc, chunk = threadIdx.x / ppc;
+    const int t = (int)(blockIdx.x * ppc + pl);
+    const bool live = t < tpr * g.ny;
+    const int j = live ? t / tpr : 0, i = live ? 2 * (t - j * tpr) : 0;
+    const bool hasB = live && i + 1 < g.nx;
     const int n_pix = g.nx * g.ny;
-    const bool live = pix < n_pix;
-    const int i = live ? pix % g.nx : 0, j = live ? pix / g.nx : 0;
     const int q0 = blockIdx.y * NQ;
     const int nr = (int)n_rays;
     const float4 *S = sil + (int64_t)q0 * nr;
     const float4 *GA = grec;
     const float2 *GB = reinterpret_cast<const float2 *>(grec + n_rays);
     const float4 *V4 = reinterpret_cast<const float4 *>(vt);
-    float4 acc[NQ];
+    float4 accA[NQ], accB[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float xc = (float)(g.cx + (i + 0.5 - 0.5 * g.nx) * g.dx);
+    for (int q = 0; q < NQ; ++q) accA[q] = accB[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the pair's box: centre and half sizes
+    const int w = hasB ? 2 : 1;
+    const float xc = (float)(g.cx + (i + 0.5 * w - 0.5 * g.nx) * g.dx);
     const float yc = (float)(g.cy + (0.5 * g.ny - j - 0.5) * g.dy);
-    const float hx = (float)(0.5 * g.dx), hy = (float)(0.5 * g.dy);
+    const float hx = (float)(0.5 * w * g.dx), hy = (float)(0.5 * g.dy);
     const float half = 0.5f * (float)(g.n_cols - 1);
     const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0, sdd = (float)g.sdd;
     const float fi = (float)i, fj = (float)j;
-    const int ncols = g.n_cols, nviews = live ? g.n_views : 0;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int v = 0, vbase = 0; v < nviews; ++v, vbase += ncols) {
+    const int ncols = g.n_cols;
+    const int v0 = (int)((int64_t)chunk * g.n_views / nch);
+    const int v1 = live ? (int)((int64_t)(chunk + 1) * g.n_views / nch) : v0;
+    for (int v = v0, vbase = v0 * ncols; v < v1; ++v, vbase += ncols) {
         const float4 e0 = __ldg(V4 + 2 * v);
         const float4 e1 = __ldg(V4 + 2 * v + 1);
         float umin, umax;
@@ -624,7 +632,7 @@ __global__ void __launch_bounds__(256, XR_GATHER_MIN_BLOCKS(NQ)) gather_plane_ke
             umin = uc - hw;
             umax = uc + hw;
         } else {
-            // the projections of the pixel's four corners from the source (exact footprint)
+            // the projections of the box's four corners from the source (exact footprint)
             const float rx = xc - e0.x, ry = yc - e0.y;
             const float depth = rx * e0.z + ry * e0.w, lat = rx * e1.x + ry * e1.y;
             const float dpx = hx * e0.z, dpy = hy * e0.w, dlx = hx * e1.x, dly = hy * e1.y;
@@ -645,47 +653,88 @@ __global__ void __launch_bounds__(256, XR_GATHER_MIN_BLOCKS(NQ)) gather_plane_ke
         const float c1f = fminf(fmaxf((umax - u0) * inv_du + half + 1e-3f, -1.0f), 4.0e6f);
         const int c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
         const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, ncols - 1);
-        // two bins per step: their records and sinogram values are requested together
-        for (int c = c0; c <= c1; c += 2) {
-            const int r0 = vbase + c;
-            const bool two = c + 1 <= c1;
-            const int r1 = two ? r0 + 1 : r0;
-            const float4 ga0 = __ldg(GA + r0), ga1 = __ldg(GA + r1);
-            const float2 gb0 = __ldg(GB + r0), gb1 = __ldg(GB + r1);
-            float4 s0[NQ], s1[NQ];
+        for (int c = c0; c <= c1; ++c) {
+            const int r = vbase + c;
+            const float4 ga = __ldg(GA + r);
+            const float2 gb = __ldg(GB + r);
+            float4 sv[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                s0[q] = __ldg(S + q * nr + r0);
-                s1[q] = two ? __ldg(S + q * nr + r1) : z4;
-            }
-            const bool sp0 = ga0.x == 0.f || ga0.z == 0.f, sp1 = two && (ga1.x == 0.f || ga1.z == 0.f);
-            float l0 = sp0 ? 0.f : gather_len(ga0, gb0, fi, fj);
-            float l1 = (two && !sp1) ? gather_len(ga1, gb1, fi, fj) : 0.f;
-            if (sp0 || sp1) {
-                // a ray parallel to an axis (or one that misses): the walk's own unit length (rare)
+            for (int q = 0; q < NQ; ++q) sv[q] = __ldg(S + q * nr + r);
+            float la, lb;
+            if (ga.x != 0.f && ga.z != 0.f) {
+                // plane crossings t = fma(q - o, 1/w, -f/w): x planes i, i+1, i+2; y planes j, j+1
+                const float qx = fi - gb.x, qy = fj - gb.y;
+                const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
+                const float tx2 = __fmaf_rn(qx + 2.0f, ga.x, ga.y);
+                const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
+                const float ylo = fminf(ty0, ty1), yhi = fmaxf(ty0, ty1);
+                la = __fsub_rn(fminf(fmaxf(tx0, tx1), yhi), fmaxf(fminf(tx0, tx1), ylo));
+                lb = __fsub_rn(fminf(fmaxf(tx1, tx2), yhi), fmaxf(fminf(tx1, tx2), ylo));
+            } else {
+                // a ray parallel to an axis: the walk's own unit lengths (rare)
+                la = lb = 0.f;
                 Walk W;
-                if (sp0 && walk_setup(rays[r0], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
-                    l0 = walk_unit_length(W, i, j, 0);
-                if (sp1 && walk_setup(rays[r1], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W))
-                    l1 = walk_unit_length(W, i, j, 0);
+                if (walk_setup(rays[r], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W)) {
+                    la = walk_unit_length(W, i, j, 0);
+                    if (hasB) lb = walk_unit_length(W, i + 1, j, 0);
+                }
             }
-            l0 = l0 > 0.f ? l0 : 0.f;
-            l1 = l1 > 0.f ? l1 : 0.f;
+            la = la > 0.f ? la : 0.f;
+            lb = (hasB && lb > 0.f) ? lb : 0.f;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                fma4(acc[q], s0[q], l0);
-                fma4(acc[q], s1[q], l1);
+                fma4(accA[q], sv[q], la);
+                fma4(accB[q], sv[q], lb);
+            }
+        }
+    }
+    if (nch > 1) {
+        // chunks 1..nch-1 hand their sums to the chunk-0 thread of the same pair
+        if (chunk > 0) {
+            float *r = red + (size_t)(chunk - 1) * 8 * NQ * ppc + pl;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                r[(8 * q + 0) * ppc] = accA[q].x;
+                r[(8 * q + 1) * ppc] = accA[q].y;
+                r[(8 * q + 2) * ppc] = accA[q].z;
+                r[(8 * q + 3) * ppc] = accA[q].w;
+                r[(8 * q + 4) * ppc] = accB[q].x;
+                r[(8 * q + 5) * ppc] = accB[q].y;
+                r[(8 * q + 6) * ppc] = accB[q].z;
+                r[(8 * q + 7) * ppc] = accB[q].w;
+            }
+        }
+        __syncthreads();
+        if (chunk > 0) return;
+        for (int c = 1; c < nch; ++c) {
+            const float *r = red + (size_t)(c - 1) * 8 * NQ * ppc + pl;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                accA[q].x += r[(8 * q + 0) * ppc];
+                accA[q].y += r[(8 * q + 1) * ppc];
+                accA[q].z += r[(8 * q + 2) * ppc];
+                accA[q].w += r[(8 * q + 3) * ppc];
+                accB[q].x += r[(8 * q + 4) * ppc];
+                accB[q].y += r[(8 * q + 5) * ppc];
+                accB[q].z += r[(8 * q + 6) * ppc];
+                accB[q].w += r[(8 * q + 7) * ppc];
             }
         }
     }
     if (live) {
+        const int pix = j * g.nx + i;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int b = 4 * (q0 + q);
-            if (b + 0 < batch) img[(int64_t)(b + 0) * n_pix + pix] = acc[q].x;
-            if (b + 1 < batch) img[(int64_t)(b + 1) * n_pix + pix] = acc[q].y;
-            if (b + 2 < batch) img[(int64_t)(b + 2) * n_pix + pix] = acc[q].z;
-            if (b + 3 < batch) img[(int64_t)(b + 3) * n_pix + pix] = acc[q].w;
+            const float a4[4] = {accA[q].x, accA[q].y, accA[q].z, accA[q].w};
+            const float b4[4] = {accB[q].x, accB[q].y, accB[q].z, accB[q].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (b + k < batch) {
+                    img[(int64_t)(b + k) * n_pix + pix] = a4[k];
+                    if (hasB) img[(int64_t)(b + k) * n_pix + pix + 1] = b4[k];
+                }
+            }
         }
     }
 }
@@ -712,21 +761,51 @@ cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int
     return cudaGetLastError();
 }
 
+// View chunks per CTA of the gather: the CTAs of nch chunks take ceil(ctas / slots) waves of
+// 1/nch of the per-pair work each; take the smallest nch within 5% of the best estimate
+// (fewer chunks keep fewer views' sinogram rows in flight per SM).
+static int gather_chunks(int64_t pairs, int groups, int blocks_per_sm, int n_views)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return 1;
+    const double slots = (double)sms * blocks_per_sm;
+    double cost[4];
+    const int cand[4] = {1, 2, 4, 8};
+    double best = 1e300;
+    for (int k = 0; k < 4; ++k) {
+        cost[k] = 1e300;
+        if (cand[k] > n_views) continue;  // every chunk keeps at least one view
+        const int ppc = kGatherThreads / cand[k];
+        const double ctas = (double)((pairs + ppc - 1) / ppc) * groups;
+        cost[k] = std::ceil(ctas / slots) / cand[k];
+        best = std::min(best, cost[k]);
+    }
+    for (int k = 0; k < 4; ++k)
+        if (cost[k] <= 1.05 * best) return cand[k];
+    return 1;
+}
+
 cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
                                 const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s)
 {
     const int Q = (batch + 3) / 4;
     const int groups = (Q + nq - 1) / nq;
-    const int64_t n_pix = (int64_t)g.nx * g.ny;
-    const dim3 grid((unsigned)((n_pix + 255) / 256), (unsigned)groups);
+    const int64_t pairs = (int64_t)((g.nx + 1) / 2) * g.ny;
+    const int nch = gather_chunks(pairs, groups, nq >= 2 ? 2 : 3, g.n_views);  // 1, 2, 4 or 8
+    const int ppc = kGatherThreads / nch;
+    const dim3 grid((unsigned)((pairs + ppc - 1) / ppc), (unsigned)groups);
+    const size_t smem = (size_t)(nch - 1) * 8 * nq * ppc * sizeof(float);
     const float4 *G = reinterpret_cast<const float4 *>(grec);
     const float4 *S = reinterpret_cast<const float4 *>(sil);
-#define XR_GP(NQV, K) gather_plane_kernel<NQV, K><<<grid, 256, 0, s>>>(rays, G, g, vt, S, n_rays, img, batch)
-#define XR_GP_K(K)                 \
-    do {                           \
-        if (nq == 4) XR_GP(4, K);  \
+#define XR_GP(NQV, K) \
+    gather_pair_kernel<NQV, K><<<grid, kGatherThreads, smem, s>>>(rays, G, g, vt, S, n_rays, img, batch, nch)
+#define XR_GP_K(K)                     \
+    do {                               \
+        if (nq == 4) XR_GP(4, K);      \
         else if (nq == 2) XR_GP(2, K); \
-        else XR_GP(1, K);          \
+        else XR_GP(1, K);              \
     } while (0)
     if (g.kind == XR_PAR2D) XR_GP_K(XR_PAR2D);
     else if (g.kind == XR_FAN2D) XR_GP_K(XR_FAN2D);

@@ -312,6 +312,43 @@ def test_gather_matches_scatter_2d():
         assert np.abs(zs - zg).max() <= 1e-5 * np.abs(zs).max()
 
 
+def _odd_geom(kind, views=48):
+    # an odd number of columns (the last pixel of each row alone in its thread), anisotropic
+    # off-centre pixels, a detector offset.  The parallel scan has axis-parallel views; its
+    # offset keeps every ray at least 0.04 from a grid line, so the oracle and the kernel
+    # cannot break a tie (the bigger-index rule) differently through rounding.
+    v = np.arange(views, dtype=np.float64)
+    kw = dict(nx=101, ny=75, dx=0.9, dy=1.1, cx=3.0, cy=-2.0)
+    if kind == "par2d":
+        return Geometry(kind, angles=pi * v / 48, n_cols=170, du=0.8, u0=0.31, **kw)
+    if kind == "fan2d":
+        return Geometry(kind, angles=2 * pi * v / 48, n_cols=200, du=1.0, u0=0.7, sod=200.0, sdd=320.0, **kw)
+    return Geometry(kind, angles=2 * pi * v / 48, n_cols=200, du=0.0032, u0=0.001, sod=200.0, sdd=320.0, **kw)
+
+
+@pytest.mark.parametrize("kind,batch,views", [(k, b, 48) for k in ("par2d", "fan2d", "fan2d_arc")
+                                               for b in (4, 8, 13)] + [("fan2d", 16, v) for v in (1, 2, 3)])
+def test_gather_odd_width_against_oracle(kind, batch, views):
+    # the 2D gather (two pixels per thread, one, two or four planes of images; the views split
+    # into 8 chunks per CTA here, fewer for scans of 1-3 views) on an image of odd width,
+    # against the oracle's adjoint and the scatter
+    from paper_2006_00686_gb300.xray import XR_ADJ_GATHER, XR_ADJ_SCATTER
+    g = _odd_geom(kind, views)
+    P = _proj(g)
+    P.reserve(batch)
+    P.set_tuning(batch_chunk=16 if batch > 8 else batch)
+    rng = np.random.default_rng(batch)
+    y = torch.from_numpy(rng.uniform(0.0, 1.0, g.sino_shape(batch)).astype(np.float32)).cuda()
+    zg = P.adjoint(y, method=XR_ADJ_GATHER)
+    zs = P.adjoint(y, method=XR_ADJ_SCATTER)
+    z_ref = O.adjoint(g, y.cpu().numpy().astype(np.float64).reshape(batch, -1))
+    zh, zsh = zg.cpu().numpy().reshape(batch, -1), zs.cpu().numpy().reshape(batch, -1)
+    for b in range(batch):
+        H.check_adjoint(zh[b], z_ref[b], f"{kind}[{b}] gather")
+        H.check_adjoint(zsh[b], z_ref[b], f"{kind}[{b}] scatter")
+    P.close()
+
+
 def test_rays_that_miss_the_image_are_zero():
     g = Geometry("par2d", 16, 16, angles=[0.0, 0.7], n_cols=64, du=1.0)  # s up to +-31.5
     P = _proj(g)
