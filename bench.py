@@ -337,10 +337,11 @@ def run_ours(args, rank, world, local_rank):
     fwd, adj = float(np.mean(fwd_ms)), float(np.mean(adj_ms))
     dom, dom_ms = ("forward", fwd) if fwd >= adj else ("adjoint", adj)
     # the method the library's automatic choice takes: the gather on the 2D quad-plane path
-    # (batches of 4 or more), the scatter elsewhere
+    # (batches of 4 or more) and for single-tilt-axis scans run as 2D column problems, the
+    # scatter elsewhere
     adj_mode = P.tuning()["adjoint"]
     if adj_mode == 0:
-        method = "gather" if (not g.is3d and B >= 4) else "scatter"
+        method = "gather" if ((not g.is3d and B >= 4) or P.column_batch) else "scatter"
     else:
         method = "gather" if adj_mode == XR_ADJ_GATHER else "scatter"
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
@@ -365,12 +366,18 @@ def run_ours(args, rank, world, local_rank):
         launches = 7
     else:
         config = {"workload": args.workload, "geometry": desc, "image": list(g.image_shape()),
-                  "views": g.n_views, "detector": [g.n_rows, g.n_cols], "batch_per_gpu": B, "adjoint": method,
+                  "views": g.n_views, "detector": [g.n_rows, g.n_cols], "batch_per_gpu": B,
+                  "adjoint": method + (" (2D column problems)" if P.column_batch else ""),
                   "l2": "flushed between timed steps (256 MiB write)"}
-        # detector setup, ray setup (2D: and the gather's per-ray constants), then per image:
-        # the y-fastest copy, the forward walk, the scatter walk and the fold of the transposed
-        # accumulator (zero fills are memsets)
-        launches = (2 if g.is3d else 3) + 4 * B
+        if P.column_batch:
+            # detector setup, ray setup, the column problem's ray records and gather constants,
+            # then per image: the slice planes, the forward, the sinogram planes, the gather
+            launches = 4 + 4 * B
+        else:
+            # detector setup, ray setup (2D: and the gather's per-ray constants), then per
+            # image: the y-fastest copy, the forward walk, the scatter walk and the fold of the
+            # transposed accumulator (zero fills are memsets)
+            launches = (2 if g.is3d else 3) + 4 * B
         if args.workload == "par3d_256_tilt":
             extra = _autograd_and_sirt(P, x, y, args)
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -703,7 +710,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fan2d_512x16", choices=sorted(WORKLOADS))
     ap.add_argument("--adjoint", default=None, choices=["gather", "scatter"],
-                    help="adjoint method (default: gather in 2D, scatter in 3D)")
+                    help="adjoint method (default: the gather for 2D batches and single-tilt-axis "
+                         "parallel scans, the scatter elsewhere)")
     ap.add_argument("--chunk", type=int, default=0, help="images per thread of the batched path")
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--tile", type=int, default=0, help="rays per work item of the persistent batch")

@@ -98,6 +98,13 @@ typedef struct {
     int64_t table_bytes;   /* device bytes held by the handle (ray table) */
     int32_t is3d;
     int32_t device;        /* CUDA device the handle's tables live on */
+    int32_t column_batch;  /* 1: a 3D parallel scan whose views all have phi_1 = 0 (or all pi):
+                              every ray lies in the y-plane of its detector column (the
+                              in-plane case, Section 3.2 Case 2), and with a workspace
+                              (xr_reserve) the forward and the gather adjoint run it as a
+                              batch of 2D problems, one per column, on the 2D batched kernels.
+                              Requires distinct columns in distinct y-slices and no column
+                              plane within 1e-6 dy of a slice boundary; 0 otherwise */
 } xr_geometry_info;
 
 /* Launch tuning of a handle.  Zero fields keep the current value. */

@@ -25,8 +25,6 @@
 
 #include "xray_internal.h"
 
-// Zero border (units) around the interleaved images.
-#define XR_IL_PAD 2
 
 // Resident blocks per SM the forward kernel is compiled for (a register budget).
 #ifndef XR_FWD_MIN_BLOCKS
@@ -454,14 +452,15 @@ __global__ void interleave_planes_kernel(const float *__restrict__ img, int batc
 }
 
 // Forward: one thread per ray, NQ planes (4*NQ images) per thread; blockIdx.y = group of
-// NQ planes.  il0/il1: plane layout; sino: user layout.
+// NQ planes.  il0/il1: plane layout; sino: image b, ray r at sino[b * sb + r * sr] (the
+// user layout: sb = n_rays, sr = 1).
 template <int NQ>
 __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plane_kernel(const RayRec *__restrict__ rays,
                                                                            int64_t n_rays, int nx, int ny, int nz,
                                                                            const float4 *__restrict__ il0,
                                                                            const float4 *__restrict__ il1,
                                                                            int n_planes, float *__restrict__ sino,
-                                                                           int batch)
+                                                                           int batch, int64_t sb, int64_t sr)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q0 = blockIdx.y * NQ;
@@ -563,13 +562,14 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
         }
     }
     if (r < n_rays) {
+        float *out = sino + r * sr;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int b = 4 * (q0 + q);
-            if (b + 0 < batch) sino[(int64_t)(b + 0) * n_rays + r] = acc[q].x;
-            if (b + 1 < batch) sino[(int64_t)(b + 1) * n_rays + r] = acc[q].y;
-            if (b + 2 < batch) sino[(int64_t)(b + 2) * n_rays + r] = acc[q].z;
-            if (b + 3 < batch) sino[(int64_t)(b + 3) * n_rays + r] = acc[q].w;
+            if (b + 0 < batch) out[(int64_t)(b + 0) * sb] = acc[q].x;
+            if (b + 1 < batch) out[(int64_t)(b + 1) * sb] = acc[q].y;
+            if (b + 2 < batch) out[(int64_t)(b + 2) * sb] = acc[q].z;
+            if (b + 3 < batch) out[(int64_t)(b + 3) * sb] = acc[q].w;
         }
     }
 }
@@ -592,10 +592,25 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
 // CTAs fill whole waves of the GPU (512^2 pairs on 152 SMs: 1.68 waves of one-chunk CTAs).
 constexpr int kGatherThreads = 256;
 
+// Where image b of the gather goes: the user layout ([b][rows][nx]) when slice_of is NULL;
+// otherwise the y-slice slice_of[b] of a volume [rows][ny][nx] (slice stride nx, row stride
+// ny * nx), nothing for slice_of[b] < 0.
+struct ImgMap {
+    const int *slice_of;
+    int64_t slice_stride, row_stride;
+    __device__ __forceinline__ int64_t image(int b, int n_pix) const
+    {
+        if (!slice_of) return (int64_t)b * n_pix;
+        const int sl = __ldg(slice_of + b);
+        return sl < 0 ? -1 : (int64_t)sl * slice_stride;
+    }
+    __device__ __forceinline__ int64_t row(int nx) const { return slice_of ? row_stride : nx; }
+};
+
 template <int NQ, int KIND>
 __global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_pair_kernel(
     const RayRec *__restrict__ rays, const float4 *__restrict__ grec, GeoParams g, const float *__restrict__ vt,
-    const float4 *__restrict__ sil, int64_t n_rays, float *__restrict__ img, int batch, int nch)
+    const float4 *__restrict__ sil, int64_t n_rays, float *__restrict__ img, int batch, int nch, ImgMap om)
 {
     extern __shared__ float red[];  // [nch - 1][8 * NQ][ppc]
     const int tpr = (g.nx + 1) >> 1;  // threads per row
@@ -725,7 +740,6 @@ __global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_pair_k
         }
     }
     if (live) {
-        const int pix = j * g.nx + i;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int b = 4 * (q0 + q);
@@ -734,8 +748,11 @@ __global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_pair_k
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (b + k < batch) {
-                    img[(int64_t)(b + k) * n_pix + pix] = a4[k];
-                    if (hasB) img[(int64_t)(b + k) * n_pix + pix + 1] = b4[k];
+                    const int64_t base = om.image(b + k, n_pix);
+                    if (base < 0) continue;
+                    float *o = img + base + (int64_t)j * om.row(g.nx) + i;
+                    o[0] = a4[k];
+                    if (hasB) o[1] = b4[k];
                 }
             }
         }
@@ -752,15 +769,20 @@ cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny
 }
 
 cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
-                                 const float *il1, float *sino, int batch, int nq, cudaStream_t s)
+                                 const float *il1, float *sino, int batch, int nq, cudaStream_t s, int64_t sb,
+                                 int64_t sr)
 {
     const int Q = (batch + 3) / 4;
     const int groups = (Q + nq - 1) / nq;
     const dim3 grid((unsigned)((n_rays + 255) / 256), (unsigned)groups);
     const float4 *a = reinterpret_cast<const float4 *>(il0), *b = reinterpret_cast<const float4 *>(il1);
-    if (nq == 4) fwd_plane_kernel<4><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch);
-    else if (nq == 2) fwd_plane_kernel<2><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch);
-    else fwd_plane_kernel<1><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch);
+    if (sb < 0) {
+        sb = n_rays;
+        sr = 1;
+    }
+    if (nq == 4) fwd_plane_kernel<4><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, sb, sr);
+    else if (nq == 2) fwd_plane_kernel<2><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, sb, sr);
+    else fwd_plane_kernel<1><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, sb, sr);
     return cudaGetLastError();
 }
 
@@ -791,8 +813,10 @@ static int gather_chunks(int64_t pairs, int groups, int blocks_per_sm, int n_vie
 }
 
 cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
-                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s)
+                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s,
+                                const int *slice_of, int64_t slice_stride, int64_t row_stride)
 {
+    const ImgMap om{slice_of, slice_stride, row_stride};
     const int Q = (batch + 3) / 4;
     const int groups = (Q + nq - 1) / nq;
     const int64_t pairs = (int64_t)((g.nx + 1) / 2) * g.ny;
@@ -803,7 +827,7 @@ cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoP
     const float4 *G = reinterpret_cast<const float4 *>(grec);
     const float4 *S = reinterpret_cast<const float4 *>(sil);
 #define XR_GP(NQV, K) \
-    gather_pair_kernel<NQV, K><<<grid, kGatherThreads, smem, s>>>(rays, G, g, vt, S, n_rays, img, batch, nch)
+    gather_pair_kernel<NQV, K><<<grid, kGatherThreads, smem, s>>>(rays, G, g, vt, S, n_rays, img, batch, nch, om)
 #define XR_GP_K(K)                     \
     do {                               \
         if (nq == 4) XR_GP(4, K);      \

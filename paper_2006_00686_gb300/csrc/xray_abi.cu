@@ -5,6 +5,8 @@
 
 #include <new>
 
+#include <algorithm>
+
 #include "xray_internal.h"
 
 using namespace xr;
@@ -170,10 +172,44 @@ static int row_major(const xr_geometry *g)
     return (g->params.kind == XR_CONE || g->params.kind == XR_CONE_ARC) ? 1 : 0;
 }
 
+// Single-tilt-axis parallel scans: the column images as quad planes in both orders and the
+// sinogram planes.  Planes are padded to a multiple of 4 (the forward and the gather walk up
+// to 4 planes per thread).
+static int64_t slice_n2(const xr_geometry *g) { return (int64_t)g->params.n_views * g->params.n_rows; }
+static int64_t slice_np(const xr_geometry *g)
+{
+    return (int64_t)(g->params.nx + 2 * XR_IL_PAD) * (g->params.nz + 2 * XR_IL_PAD);
+}
+static int64_t slice_planes(const xr_geometry *g) { return (int64_t)((g->params.n_cols + 15) / 16) * 4; }
+static size_t slice_ws_bytes(const xr_geometry *g)
+{
+    return (size_t)slice_planes(g) * sizeof(float4) * (size_t)(2 * slice_np(g) + slice_n2(g));
+}
+
+// The batch-of-columns path of single-tilt-axis parallel scans (32-bit offsets in a plane,
+// 32-bit ray ids of the 2D problem).
+static bool use_slices(const xr_geometry *g)
+{
+    return g->slices.ok && g->tune.path != XR_PATH_RAY && g->d_ws && g->ws_bytes >= slice_ws_bytes(g) &&
+           slice_np(g) * 4 < ((int64_t)1 << 31) && slice_n2(g) < ((int64_t)1 << 31);
+}
+
 static size_t reserve_bytes(const xr_geometry *g, int batch)
 {
-    if (kind_is3d(g->params.kind) || batch < 4) return (size_t)g->n_units * sizeof(float);
+    if (kind_is3d(g->params.kind) || batch < 4) {
+        const size_t one = (size_t)g->n_units * sizeof(float);
+        return g->slices.ok ? std::max(one, slice_ws_bytes(g)) : one;
+    }
     return fast_ws_bytes(g, batch);  // >= n_units floats: serves the single-image path too
+}
+
+// Rebuild the 2D column problem's ray records from the 3D ray table.
+static cudaError_t slice_setup(xr_geometry *g, cudaStream_t s)
+{
+    if (!g->slices.ok) return cudaSuccess;
+    cudaError_t e = launch_slice_rays(g->d_rays, slice_n2(g), g->params.n_cols, g->slices.c_rep, g->d_rays2, s);
+    if (e == cudaSuccess) e = launch_gather_prep(g->d_rays2, slice_n2(g), g->d_grec2, s);
+    return e;
 }
 
 extern "C" {
@@ -247,6 +283,18 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(int));
     if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_view_tab, (size_t)p.n_views * 8 * sizeof(float));
     if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_grec, (size_t)g->n_rays * gather_rec_bytes());
+    if (e == cudaSuccess && three && slice_plan(desc, &g->slices)) {
+        const size_t n2 = (size_t)slice_n2(g);
+        e = cudaMalloc(&g->d_rays2, n2 * sizeof(RayRec));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_grec2, n2 * gather_rec_bytes());
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_vt2, g->slices.vt.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_slice_of, g->slices.slice_of.size() * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->d_vt2, g->slices.vt.data(), g->slices.vt.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->d_slice_of, g->slices.slice_of.data(), g->slices.slice_of.size() * sizeof(int),
+                           cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
         cudaGetLastError();
@@ -321,6 +369,7 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     g->setup_df = make_setup_df(p);
     if (e == cudaSuccess) e = launch_ray_setup(p, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays, nullptr);
     if (e == cudaSuccess && g->d_grec) e = launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, nullptr);
+    if (e == cudaSuccess) e = slice_setup(g, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
         xr_geometry_destroy(g);
@@ -345,6 +394,10 @@ void xr_geometry_destroy(xr_geometry *g)
     cudaFree(g->d_grec);
     cudaFree(g->d_ws);
     cudaFree(g->d_err);
+    cudaFree(g->d_rays2);
+    cudaFree(g->d_grec2);
+    cudaFree(g->d_vt2);
+    cudaFree(g->d_slice_of);
     cudaSetDevice(prev);
     delete g;
 }
@@ -356,6 +409,7 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream)
     XR_CUDA(launch_ray_setup(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays,
                              (cudaStream_t)stream));
     if (g->d_grec) XR_CUDA(launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, (cudaStream_t)stream));
+    XR_CUDA(slice_setup(g, (cudaStream_t)stream));
     return XR_OK;
 }
 
@@ -394,9 +448,11 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
     info->n_units = g->n_units;
     info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * (8 * 4 + sizeof(ViewRec) + sizeof(ViewDF)) +
                         (int64_t)g->params.n_rows * g->params.n_cols * (int64_t)sizeof(DetRec) +
-                        (g->d_grec ? g->n_rays * (int64_t)gather_rec_bytes() : 0) + (int64_t)g->ws_bytes;
+                        (g->d_grec ? g->n_rays * (int64_t)gather_rec_bytes() : 0) + (int64_t)g->ws_bytes +
+                        (g->slices.ok ? slice_n2(g) * (int64_t)(sizeof(RayRec) + gather_rec_bytes()) : 0);
     info->is3d = kind_is3d(g->params.kind);
     info->device = g->device;
+    info->column_batch = g->slices.ok ? 1 : 0;
     return XR_OK;
 }
 
@@ -433,6 +489,20 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
     if (use_tiled(g, batch)) {
         if ((batch + 3) / 4 > 65535) return XR_ERR_SIZE;
         XR_CUDA(launch_tile2d(g->d_rays, g->params, g->d_view_tab, d_img, d_sino, batch, 0, (cudaStream_t)stream));
+        return XR_OK;
+    }
+    if (use_slices(g)) {
+        // one 2D problem per detector column: the volume's y-slices as quad planes
+        const cudaStream_t s = (cudaStream_t)stream;
+        const GeoParams &p = g->params;
+        float *il0 = g->d_ws, *il1 = g->d_ws + 4 * slice_planes(g) * slice_np(g);
+        for (int b = 0; b < batch; ++b) {
+            XR_CUDA(launch_slice_planes(d_img + (size_t)b * g->n_units, p.nx, p.ny, p.nz, g->d_slice_of, p.n_cols,
+                                        il0, il1, s));
+            XR_CUDA(launch_project_plane(g->d_rays2, slice_n2(g), p.nx, p.nz, 1, il0, il1,
+                                         d_sino + (size_t)b * g->n_rays, p.n_cols, plane_nq(g, p.n_cols), s, 1,
+                                         p.n_cols));
+        }
         return XR_OK;
     }
     if (!use_fast(g, batch) && use_dda(g)) {
@@ -480,7 +550,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         // 2D: the quad-plane gather beats the vector-atomic scatter (2.33 vs 2.94 ms,
         // fan beam 512^2 x 16), one image: the scatter
         if (kind_is3d(g->params.kind))
-            method = XR_ADJ_SCATTER;
+            method = use_slices(g) ? XR_ADJ_GATHER : XR_ADJ_SCATTER;
         else
             method = (!use_tiled(g, batch) && use_fast(g, batch)) ? XR_ADJ_GATHER : XR_ADJ_SCATTER;
     }
@@ -488,6 +558,20 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
     const cudaStream_t s = (cudaStream_t)stream;
     if (method == XR_ADJ_GATHER) {
+        if (use_slices(g)) {
+            // one 2D gather per detector column, written into the column's y-slice
+            const GeoParams &p = g->params;
+            float *sil = g->d_ws + 8 * slice_planes(g) * slice_np(g);
+            for (int b = 0; b < batch; ++b) {
+                float *img = d_img + (size_t)b * g->n_units;
+                if (!g->slices.surjective) XR_CUDA(cudaMemsetAsync(img, 0, (size_t)g->n_units * sizeof(float), s));
+                XR_CUDA(launch_slice_sino(d_sino + (size_t)b * g->n_rays, slice_n2(g), p.n_cols, sil, s));
+                XR_CUDA(launch_gather_plane(g->d_rays2, g->d_grec2, g->slices.g2, g->d_vt2, sil, slice_n2(g), img,
+                                            p.n_cols, plane_nq(g, p.n_cols), s, g->d_slice_of, p.nx,
+                                            (int64_t)p.ny * p.nx));
+            }
+            return XR_OK;
+        }
         if (kind_is3d(g->params.kind)) {
             if (batch > 65535) return XR_ERR_SIZE;
             XR_CUDA(launch_tile3d_adj(g->d_rays, g->d_views, g->params, d_sino, g->n_rays, d_img, batch, s));

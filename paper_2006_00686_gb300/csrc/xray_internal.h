@@ -4,8 +4,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "xray.h"
 #include "xray_core.cuh"
+
+// Zero border (units) around the interleaved images of the 2D quad-plane layouts.
+#define XR_IL_PAD 2
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -140,10 +145,33 @@ cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, c
 // Quad-plane layout kernels (fast2d.cu): one thread per ray / pixel for 4*nq images.
 cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny, int nz, float *il0, float *il1,
                                      cudaStream_t s);
+// The forward writes image b, ray r at sino[b * sb + r * sr] (sb < 0: the user layout).
 cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
-                                 const float *il1, float *sino, int batch, int nq, cudaStream_t s);
+                                 const float *il1, float *sino, int batch, int nq, cudaStream_t s, int64_t sb = -1,
+                                 int64_t sr = 1);
+// The gather writes image b to the user layout, or (slice_of != NULL) to y-slice slice_of[b]
+// of a volume (pixel (i, j) of the image at slice * slice_stride + j * row_stride + i).
 cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
-                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s);
+                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s,
+                                const int *slice_of = nullptr, int64_t slice_stride = 0, int64_t row_stride = 0);
+
+// Single-tilt-axis parallel scans as batches of 2D problems, one per detector column
+// (slices.cu).  slice_of[c]: the y-slice of column c's ray plane, or -1 outside the volume;
+// c_rep: a column inside the volume (its rays give the 2D ray records); g2 and vt: the 2D
+// parallel problem in (x, z) with the rows as its detector, and its gather view table.
+struct SlicePlan {
+    bool ok = false;
+    bool surjective = false;  // every slice has a column
+    int c_rep = -1;
+    std::vector<int> slice_of;
+    std::vector<float> vt;
+    GeoParams g2{};
+};
+bool slice_plan(const xr_geometry_desc *d, SlicePlan *sp);
+cudaError_t launch_slice_rays(const RayRec *rays3, int64_t n2, int n_cols, int c_rep, RayRec *rays2, cudaStream_t s);
+cudaError_t launch_slice_planes(const float *vol, int nx, int ny, int nz, const int *slice_of, int n_img, float *il0,
+                                float *il1, cudaStream_t s);
+cudaError_t launch_slice_sino(const float *sino, int64_t n2, int n_cols, float *sil, cudaStream_t s);
 
 // Tiled forward / adjoint for 2D scans and batches (tile2d.cu); in: user-layout input,
 // out: user-layout output (cleared inside).
@@ -205,4 +233,10 @@ struct xr_geometry {
     size_t ws_bytes;
     int ws_batch;        // largest batch the workspace holds (0: none reserved)
     xr_tuning tune;
+    // single-tilt-axis parallel scans: the batch of 2D column problems (slices.cu)
+    xr::SlicePlan slices;
+    xr::RayRec *d_rays2;  // 2D ray records, n_views * n_rows
+    void *d_grec2;        // their gather records
+    float *d_vt2;         // the 2D gather's view table
+    int *d_slice_of;      // column -> slice
 };
