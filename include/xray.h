@@ -112,9 +112,10 @@ typedef struct {
     int32_t block;         /* threads per block of the ray kernels (64..256, multiple of 32) */
     int32_t batch_chunk;   /* images walked together by one thread (1, 2, 4, 8 or 16);
                               1 also disables the batched paths */
-    int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER; XR_ADJ_AUTO (the default):
-                              2D scans: the gather on the quad-plane path, the scatter
-                              elsewhere; 3D scans: the gather */
+    int32_t adjoint;       /* XR_ADJ_SCATTER or XR_ADJ_GATHER; XR_ADJ_AUTO (the default): the
+                              gather on the 2D quad-plane path and for single-tilt-axis
+                              parallel scans run as 2D column problems (column_batch), the
+                              scatter elsewhere */
     int32_t path;          /* 2D scans, batches >= 4: XR_PATH_TILED, XR_PATH_INTERLEAVED or
                               XR_PATH_RAY (one thread per ray, several images per thread).
                               3D scans: XR_PATH_RAY keeps the one-thread-per-ray kernels on

@@ -266,9 +266,10 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     g->tune.block = 128;
     g->tune.batch_chunk = 16;
     // automatic: the gather on the batched quad-plane path (fan beam 512^2 x 16 on GB300:
-    // gather 2.32 ms, vector-atomic scatter 2.94 ms), the scatter elsewhere (one image: the
-    // per-pixel gather loops over every view and is many times slower).  3D scans have only
-    // the scatter.  The tuner may fix either per scan.
+    // gather 1.97 ms, vector-atomic scatter 2.94 ms) and for single-tilt-axis parallel scans
+    // run as 2D column problems, the scatter elsewhere (one image: the per-pixel gather loops
+    // over every view and is many times slower; 3D: the tiled gather loses to the scatter).
+    // The tuner may fix either per scan.
     g->tune.adjoint = XR_ADJ_AUTO;
     g->tune.path = XR_PATH_INTERLEAVED;
     g->tune.order = XR_ORDER_AUTO;
@@ -547,8 +548,9 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     }
     if (method == XR_ADJ_AUTO) {
         // measured on GB300: 3D scatter 438 ms vs tiled gather 682 ms (circular cone 512^3);
-        // 2D: the quad-plane gather beats the vector-atomic scatter (2.33 vs 2.94 ms,
-        // fan beam 512^2 x 16), one image: the scatter
+        // single-tilt-axis scans as 2D column problems: the pair gather (C3 1.36 ms vs the 3D
+        // scatter 2.76 ms); 2D: the quad-plane gather beats the vector-atomic scatter (1.97
+        // vs 2.94 ms, fan beam 512^2 x 16), one image: the scatter
         if (kind_is3d(g->params.kind))
             method = use_slices(g) ? XR_ADJ_GATHER : XR_ADJ_SCATTER;
         else
