@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
                                                                            const float4 *__restrict__ il0,
                                                                            const float4 *__restrict__ il1,
                                                                            int n_planes, float *__restrict__ sino,
-                                                                           int batch, int64_t sb, int64_t sr)
+                                                                           int batch, int sb, int sr)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q0 = blockIdx.y * NQ;
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
         }
     }
     if (r < n_rays) {
-        float *out = sino + r * sr;
+        float *out = sino + r * (int64_t)sr;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int b = 4 * (q0 + q);
@@ -780,9 +780,11 @@ cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int
         sb = n_rays;
         sr = 1;
     }
-    if (nq == 4) fwd_plane_kernel<4><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, sb, sr);
-    else if (nq == 2) fwd_plane_kernel<2><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, sb, sr);
-    else fwd_plane_kernel<1><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, sb, sr);
+    // both strides fit 32 bits: n_rays < 2^31 and n_cols on the batched paths
+    const int isb = (int)sb, isr = (int)sr;
+    if (nq == 4) fwd_plane_kernel<4><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, isb, isr);
+    else if (nq == 2) fwd_plane_kernel<2><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, isb, isr);
+    else fwd_plane_kernel<1><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, isb, isr);
     return cudaGetLastError();
 }
 
