@@ -132,9 +132,12 @@ enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
 enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2 };
 
 /* Batched paths.  TILED: a CTA stages a 32x32 tile of up to 16 images in shared memory and
- * walks every ray of a group of views through it (2D scans).  INTERLEAVED: images are
- * interleaved per unit in device workspace (xr_reserve) and 4 lanes walk each ray.
- * RAY: one thread per ray. */
+ * walks every ray of a group of views through it (2D scans).  INTERLEAVED (the default): the
+ * images are copied into device workspace (xr_reserve) as planes of 4 images (one float4 per
+ * unit); one thread walks each ray for up to 16 images (forward), one thread gathers a pair
+ * of neighbouring pixels (XR_ADJ_GATHER), or 4 lanes per ray add with 128-bit reductions
+ * (XR_ADJ_SCATTER); for 3D scans, the single-image path with a y-fastest copy, or the column
+ * batch of single-tilt-axis scans.  RAY: one thread per ray on the caller's layout. */
 enum { XR_PATH_AUTO = 0, XR_PATH_TILED = 1, XR_PATH_INTERLEAVED = 2, XR_PATH_RAY = 3 };
 
 /* Validate `desc`, allocate the handle and its ray table on the current CUDA device and run
@@ -162,7 +165,10 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
  * 3D scans: the workspace is one [nz][nx][ny] copy of a volume (4 * n_units bytes, any
  * batch); each image is copied into it and every ray reads whichever of the two layouts
  * has its warp's neighbouring rays in neighbouring words; the scatter adjoint uses it as a
- * second accumulator.
+ * second accumulator.  Single-tilt-axis parallel scans (xr_geometry_info.column_batch)
+ * reserve the larger of that and 16 * P * (2 (nx+4)(nz+4) + n_views * n_rows) bytes,
+ * P = 4 * ceil(n_cols / 16): the column images as quad planes and the sinogram planes; when
+ * that allocation fails the single-image copy is reserved and the 3D walk runs.
  * Without a workspace, or for larger batches, the calls use the one-thread-per-ray kernels
  * on the caller's layout (same lengths).
  * Errors: XR_ERR_NULL, XR_ERR_BATCH, XR_ERR_ALLOC, XR_ERR_CUDA. */

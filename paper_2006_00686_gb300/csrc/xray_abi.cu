@@ -428,16 +428,24 @@ xr_status xr_reserve(xr_geometry *g, int32_t max_batch)
     g->d_ws = nullptr;
     g->ws_bytes = 0;
     g->ws_batch = 0;
-    cudaError_t e = cudaMalloc(&g->d_ws, bytes);
+    size_t got = bytes;
+    cudaError_t e = cudaMalloc(&g->d_ws, got);
+    const size_t one = (size_t)g->n_units * sizeof(float);
+    if (e == cudaErrorMemoryAllocation && kind_is3d(g->params.kind) && bytes > one) {
+        // the column batch's planes do not fit: keep the single-image copy (the 3D walk)
+        cudaGetLastError();
+        got = one;
+        e = cudaMalloc(&g->d_ws, got);
+    }
     // the borders of the interleaved copies stay zero: only interiors are ever written
-    if (e == cudaSuccess) e = cudaMemset(g->d_ws, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(g->d_ws, 0, got);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         cudaGetLastError();
         g->d_ws = nullptr;
         return e == cudaErrorMemoryAllocation ? XR_ERR_ALLOC : cuda_fail(e);
     }
-    g->ws_bytes = bytes;
+    g->ws_bytes = got;
     g->ws_batch = max_batch;
     return XR_OK;
 }
