@@ -191,7 +191,8 @@ static size_t slice_ws_bytes(const xr_geometry *g)
 static bool use_slices(const xr_geometry *g)
 {
     return g->slices.ok && g->tune.path != XR_PATH_RAY && g->d_ws && g->ws_bytes >= slice_ws_bytes(g) &&
-           slice_np(g) * 4 < ((int64_t)1 << 31) && slice_n2(g) < ((int64_t)1 << 31);
+           slice_np(g) * 4 < ((int64_t)1 << 31) && slice_n2(g) < ((int64_t)1 << 31) &&
+           (g->params.n_cols + 3) / 4 <= 65535;  // planes index gridDim.y
 }
 
 static size_t reserve_bytes(const xr_geometry *g, int batch)
