@@ -26,7 +26,15 @@ def _built():
 def _cases():
     v5 = np.linspace(0.1, 2 * pi, 5, endpoint=False)
     par3 = np.stack([v5, 0.3 * np.cos(v5)], axis=1)
+    # one tilt axis (phi_1 = 0): the scans run as 2D column problems; phi_2 = 0 is an
+    # axis-parallel view; no column plane lies on a slice boundary
+    tilt5 = np.stack([np.zeros(5), np.linspace(-1.0, 1.0, 5)], axis=1)
     return {
+        "tilt_1x1x1_one_column": Geometry("par3d", 1, 1, 1, angles=tilt5, n_cols=1, n_rows=3, du=0.5, dv=0.5,
+                                          u0=0.3),
+        "tilt_1x6x5_one_row": Geometry("par3d", 1, 6, 5, angles=tilt5, n_cols=6, n_rows=1, dv=0.7),
+        "tilt_7x4x1_one_view": Geometry("par3d", 7, 4, 1, angles=[[0.0, 0.4]], n_cols=4, n_rows=5, dv=0.9),
+        "tilt_5x20x6_18_columns": Geometry("par3d", 5, 20, 6, angles=tilt5, n_cols=18, n_rows=7, du=1.1, dv=1.2),
         "par2d_1x1": Geometry("par2d", 1, 1, angles=v5, n_cols=5, du=0.4),
         "par2d_1x9": Geometry("par2d", 1, 9, angles=v5, n_cols=9, du=0.7),
         "fan2d_13x1": Geometry("fan2d", 13, 1, angles=v5, n_cols=17, du=1.1, sod=40.0, sdd=60.0),
@@ -52,6 +60,7 @@ def test_degenerate_sizes(name, path, batch):
     from paper_2006_00686_gb300.xray import Projector, XR_PATH_INTERLEAVED, XR_PATH_RAY
     g = CASES[name]
     P = Projector(g)
+    assert P.column_batch == name.startswith("tilt_")
     P.set_tuning(path=XR_PATH_INTERLEAVED if path == "fast" else XR_PATH_RAY)
     rng = np.random.default_rng(len(name) + batch)
     f = rng.random((batch,) + g.image_shape()).astype(np.float32)
