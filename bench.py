@@ -348,8 +348,8 @@ def run_ours(args, rank, world, local_rank):
     # forward and gather kernels, from one ncu capture of this workload
     traffic = None
     if args.workload == "fan2d_512x16":
-        traffic = {("adjoint", "gather"): 51.6e6, ("forward", "gather"): 62.2e6,
-                   ("forward", "scatter"): 62.2e6}.get((dom, method))
+        traffic = {("adjoint", "gather"): 51.5e6, ("forward", "gather"): 62.4e6,
+                   ("forward", "scatter"): 62.4e6}.get((dom, method))
     roof = _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic)
 
     extra = {}
