@@ -13,6 +13,8 @@
 //
 // The forward walk generates U voxels (offset, length) ahead, then issues their U loads
 // together, so every thread keeps U independent loads in flight instead of one.
+#include <algorithm>
+
 #include "xray_internal.h"
 
 namespace xr {
@@ -60,18 +62,27 @@ __global__ void __launch_bounds__(256) add_transposed_kernel(const float *__rest
 // The layout a ray reads: the [z][x][y] copy when it leans along x.
 __device__ __forceinline__ bool leans_x(const RayRec &r) { return fabsf(r.w0) > fabsf(r.w1); }
 
-// Thread -> ray.  View-major: thread t is ray t ([view][row][col]).  Row-major: threads run
-// over (row, view, col), so the rays in flight at one time are one detector row in many
-// views; in a circular cone scan those rays cross one slab of z, which stays in L2 while
-// every view passes through it.
+// Thread -> ray.  View-major (mode 0): thread t is ray t ([view][row][col]).  Row-major
+// (mode 1): threads run over (row, view, col), so the rays in flight at one time are one
+// detector row in many views; in a circular cone scan those rays cross one slab of z, which
+// stays in L2 while every view passes through it.  Column-major (mode 2): threads run over
+// (view, col, row), so a warp holds 32 neighbouring rows of one detector column; in a cone
+// or helical scan those rays share the vertical plane through the source and the column and
+// sit at neighbouring heights, so with the volume stored z fastest they touch neighbouring
+// words.
 struct RayOrder {
-    int row_major;
+    int mode;
     int n_cols, n_views, n_rows;
     __device__ __forceinline__ int ray(int t) const
     {
-        if (!row_major) return t;
-        const int col = t % n_cols, rest = t / n_cols;
-        const int view = rest % n_views, row = rest / n_views;
+        if (mode == 0) return t;
+        if (mode == 1) {
+            const int col = t % n_cols, rest = t / n_cols;
+            const int view = rest % n_views, row = rest / n_views;
+            return (view * n_rows + row) * n_cols + col;
+        }
+        const int row = t % n_rows, rest = t / n_rows;
+        const int col = rest % n_cols, view = rest / n_cols;
         return (view * n_rows + row) * n_cols + col;
     }
 };
@@ -79,14 +90,12 @@ struct RayOrder {
 // Forward sum of one ray; imgT may be NULL (then every ray reads img).  SKIP: an axis the
 // ray does not cross (w = 0), left out of every step, or 0.
 template <int U, int SKIP>
-__device__ __forceinline__ float fwd_ray_t(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
-                                           const float *__restrict__ imgT, int *err)
+__device__ __forceinline__ float fwd_ray_s(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ base,
+                                           int sx, int sy, int sz, int *err)
 {
-    const bool tr = imgT != nullptr && leans_x(rr);
-    const float *__restrict__ base = tr ? imgT : img;
     Dda<int> D;
     float acc = 0.f;
-    if (dda_setup<int>(rr, nx, ny, nz, tr ? ny : 1, tr ? 1 : nx, nx * ny, D)) {
+    if (dda_setup<int>(rr, nx, ny, nz, sx, sy, sz, D)) {
         // U voxels generated ahead, then their U loads issued together
         for (int g = dda_max_steps(nx, ny, nz) / U + 1; g > 0 && D.tcur < D.tout; --g) {
             int off[U];
@@ -104,6 +113,14 @@ __device__ __forceinline__ float fwd_ray_t(const RayRec &rr, int nx, int ny, int
     return acc;
 }
 
+template <int U, int SKIP>
+__device__ __forceinline__ float fwd_ray_t(const RayRec &rr, int nx, int ny, int nz, const float *__restrict__ img,
+                                           const float *__restrict__ imgT, int *err)
+{
+    const bool tr = imgT != nullptr && leans_x(rr);
+    return fwd_ray_s<U, SKIP>(rr, nx, ny, nz, tr ? imgT : img, tr ? ny : 1, tr ? 1 : nx, nx * ny, err);
+}
+
 // Rays of 2D scans and of single-tilt-axis scans keep one index fixed: their walk leaves
 // that axis out (the same voxels and lengths, fewer instructions per step).
 template <int U>
@@ -118,13 +135,11 @@ __device__ __forceinline__ float fwd_ray(const RayRec &rr, int nx, int ny, int n
 // Adjoint of one ray: one RED per voxel.  As in the forward, U voxels are generated ahead
 // and their U REDs issued back to back from separate registers.  accT may be NULL.
 template <int U, int SKIP>
-__device__ __forceinline__ void scatter_ray_t(const RayRec &rr, float g, int nx, int ny, int nz,
-                                              float *__restrict__ out, float *__restrict__ accT, int *err)
+__device__ __forceinline__ void scatter_ray_s(const RayRec &rr, float g, int nx, int ny, int nz,
+                                              float *__restrict__ base, int sx, int sy, int sz, int *err)
 {
-    const bool tr = accT != nullptr && leans_x(rr);
-    float *__restrict__ base = tr ? accT : out;
     Dda<int> D;
-    if (!dda_setup<int>(rr, nx, ny, nz, tr ? ny : 1, tr ? 1 : nx, nx * ny, D)) return;
+    if (!dda_setup<int>(rr, nx, ny, nz, sx, sy, sz, D)) return;
     for (int k = dda_max_steps(nx, ny, nz) / U + 1; k > 0 && D.tcur < D.tout; --k) {
         int off[U];
         float l[U];
@@ -135,6 +150,14 @@ __device__ __forceinline__ void scatter_ray_t(const RayRec &rr, float g, int nx,
             if (l[u] > 0.f) red_add(base + off[u], __fmul_rn(g, l[u]));
     }
     if (err && D.tcur < D.tout) atomicOr(err, XR_DEVERR_WALK_BOUND);
+}
+
+template <int U, int SKIP>
+__device__ __forceinline__ void scatter_ray_t(const RayRec &rr, float g, int nx, int ny, int nz,
+                                              float *__restrict__ out, float *__restrict__ accT, int *err)
+{
+    const bool tr = accT != nullptr && leans_x(rr);
+    scatter_ray_s<U, SKIP>(rr, g, nx, ny, nz, tr ? accT : out, tr ? ny : 1, tr ? 1 : nx, nx * ny, err);
 }
 
 template <int U>
@@ -167,6 +190,65 @@ __global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict
     const int r = ord.ray(t);
     const float g = __ldg(sino + r);
     if (g != 0.f) scatter_ray<U>(rays[r], g, nx, ny, nz, out, accT, err);
+}
+
+// The same walks on a z-fastest copy [y][x][z] (strides nz, nx * nz, 1): the column-major
+// ray order's layout.
+template <int U>
+__global__ void __launch_bounds__(256) fwd3dz_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
+                                                     int nx, int ny, int nz, const float *__restrict__ imgZ,
+                                                     float *__restrict__ sino, int *err)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_rays) return;
+    const int r = ord.ray(t);
+    const RayRec rr = rays[r];
+    const int sx = nz, sy = nx * nz;
+    float v;
+    if (rr.w2 == 0.f) v = fwd_ray_s<U, 2>(rr, nx, ny, nz, imgZ, sx, sy, 1, err);
+    else if (rr.w1 == 0.f) v = fwd_ray_s<U, 1>(rr, nx, ny, nz, imgZ, sx, sy, 1, err);
+    else v = fwd_ray_s<U, 0>(rr, nx, ny, nz, imgZ, sx, sy, 1, err);
+    sino[r] = v;
+}
+
+template <int U>
+__global__ void __launch_bounds__(256) scatter3dz_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
+                                                         int nx, int ny, int nz, const float *__restrict__ sino,
+                                                         float *__restrict__ accZ, int *err)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_rays) return;
+    const int r = ord.ray(t);
+    const float g = __ldg(sino + r);
+    if (g == 0.f) return;
+    const RayRec rr = rays[r];
+    const int sx = nz, sy = nx * nz;
+    if (rr.w2 == 0.f) scatter_ray_s<U, 2>(rr, g, nx, ny, nz, accZ, sx, sy, 1, err);
+    else if (rr.w1 == 0.f) scatter_ray_s<U, 1>(rr, g, nx, ny, nz, accZ, sx, sy, 1, err);
+    else scatter_ray_s<U, 0>(rr, g, nx, ny, nz, accZ, sx, sy, 1, err);
+}
+
+// out[p][k] = in[k][p] for a [rows][cols] matrix (tiles of 32 x 32 through shared memory):
+// [z][y x] -> [y x][z] with rows = nz, and back with rows = nx * ny.
+__global__ void __launch_bounds__(256) transpose_rc_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                                           int64_t rows, int64_t cols)
+{
+    __shared__ float tile[TT][TT + 1];
+    const int64_t c0 = (int64_t)blockIdx.x * TT;
+    const int64_t row_tiles = (rows + TT - 1) / TT;
+    for (int64_t ty = blockIdx.y; ty < row_tiles; ty += gridDim.y) {  // gridDim.y is capped
+        const int64_t r0 = ty * TT;
+        for (int dr = threadIdx.y; dr < TT; dr += blockDim.y) {
+            const int64_t r = r0 + dr, c = c0 + threadIdx.x;
+            if (r < rows && c < cols) tile[dr][threadIdx.x] = in[r * cols + c];
+        }
+        __syncthreads();
+        for (int dc = threadIdx.y; dc < TT; dc += blockDim.y) {
+            const int64_t c = c0 + dc, r = r0 + threadIdx.x;
+            if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][dc];
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -350,30 +432,59 @@ cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int
     return cudaGetLastError();
 }
 
-static RayOrder make_order(const GeoParams &g, int row_major)
+static RayOrder make_order(const GeoParams &g, int mode)
 {
-    return RayOrder{row_major, g.n_cols, g.n_views, g.n_rows};
+    return RayOrder{mode, g.n_cols, g.n_views, g.n_rows};
 }
 
-cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
-                             const float *img, const float *imgT, float *sino, int block, int *err, cudaStream_t s)
+static cudaError_t launch_transpose_rc(const float *in, float *out, int64_t rows, int64_t cols, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
-    fwd3d_kernel<kFwdAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, row_major), g.nx, g.ny, g.nz,
-                                                     img, imgT, sino, err);
+    const dim3 grid((unsigned)((cols + TT - 1) / TT), (unsigned)std::min<int64_t>((rows + TT - 1) / TT, 65535));
+    transpose_rc_kernel<<<grid, dim3(TT, 8), 0, s>>>(in, out, rows, cols);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
+cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
+                             float *ws, float *sino, int block, int *err, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
+    cudaError_t e;
+    if (order == 2) {
+        // z-fastest copy, then the column-major walk
+        e = launch_transpose_rc(img, ws, g.nz, (int64_t)g.nx * g.ny, s);
+        if (e != cudaSuccess) return e;
+        fwd3dz_kernel<kFwdAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, 2), g.nx, g.ny, g.nz, ws,
+                                                          sino, err);
+        return cudaGetLastError();
+    }
+    e = launch_transpose_xy(img, ws, g.nx, g.ny, g.nz, s);
+    if (e != cudaSuccess) return e;
+    fwd3d_kernel<kFwdAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, order), g.nx, g.ny, g.nz,
+                                                     img, ws, sino, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order,
                              const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s)
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const size_t bytes = (size_t)nx * ny * nz * sizeof(float);
+    if (order == 2) {
+        // one z-fastest accumulator, transposed into out (every element written)
+        cudaError_t e = cudaMemsetAsync(accT, 0, bytes, s);
+        if (e != cudaSuccess) return e;
+        const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
+        scatter3dz_kernel<kAdjAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, 2), nx, ny, nz, sino,
+                                                              accT, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_transpose_rc(accT, out, (int64_t)nx * ny, nz, s);
+    }
     cudaError_t e = cudaMemsetAsync(out, 0, bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(accT, 0, bytes, s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
-    scatter3d_kernel<kAdjAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, row_major), nx, ny, nz, sino, out,
+    scatter3d_kernel<kAdjAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, order), nx, ny, nz, sino, out,
                                               accT, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

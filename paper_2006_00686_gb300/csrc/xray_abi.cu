@@ -162,14 +162,22 @@ static bool use_dda(const xr_geometry *g)
            g->n_rays < ((int64_t)1 << 31);
 }
 
-// Ray order of the 3D fast path: row-major for circular cones (a detector row crosses one
-// slab of z in every view), the ray order otherwise (a helix moves through z view by view;
-// a parallel scan's views each cross the whole volume).
-static int row_major(const xr_geometry *g)
+// Ray order of the 3D fast path (0 view, 1 row, 2 column; see launch_project3d).  Automatic,
+// measured on GB300: the forward row-major for circular cones (a detector row crosses one
+// slab of z in every view) and the ray order otherwise (a helix moves through z view by view;
+// a parallel scan's views each cross the whole volume); the scatter adjoint of cone and
+// helical scans column-major on the z-fastest copy, whose reductions from a warp's rays fall
+// on neighbouring words (cone 512^3: 400 vs 437 ms; helix: 148 vs 166 ms; their forwards
+// gain nothing, 245 vs 246 and 93 vs 88 ms).
+static int ray_order(const xr_geometry *g, bool adjoint)
 {
+    if (g->tune.order == XR_ORDER_COLUMN) return 2;
     if (g->tune.order == XR_ORDER_ROW) return 1;
     if (g->tune.order == XR_ORDER_VIEW) return 0;
-    return (g->params.kind == XR_CONE || g->params.kind == XR_CONE_ARC) ? 1 : 0;
+    const int k = g->params.kind;
+    const bool cone = k == XR_CONE || k == XR_CONE_ARC, helix = k == XR_HELIX || k == XR_HELIX_ARC;
+    if (adjoint && (cone || helix)) return 2;
+    return cone ? 1 : 0;
 }
 
 // Single-tilt-axis parallel scans: the column images as quad planes in both orders and the
@@ -475,7 +483,7 @@ xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
         return XR_ERR_ARG;
     if (t->adjoint && t->adjoint != XR_ADJ_SCATTER && t->adjoint != XR_ADJ_GATHER) return XR_ERR_ARG;
     if (t->path < 0 || t->path > XR_PATH_RAY) return XR_ERR_ARG;
-    if (t->order < 0 || t->order > XR_ORDER_ROW) return XR_ERR_ARG;
+    if (t->order < 0 || t->order > XR_ORDER_COLUMN) return XR_ERR_ARG;
     if (t->order) g->tune.order = t->order;
     if (t->path) g->tune.path = t->path;
     if (t->block) g->tune.block = t->block;
@@ -519,8 +527,7 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
         const cudaStream_t s = (cudaStream_t)stream;
         for (int b = 0; b < batch; ++b) {
             const float *img = d_img + (size_t)b * g->n_units;
-            XR_CUDA(launch_transpose_xy(img, g->d_ws, g->params.nx, g->params.ny, g->params.nz, s));
-            XR_CUDA(launch_project3d(g->d_rays, g->params, g->n_rays, row_major(g), img, g->d_ws,
+            XR_CUDA(launch_project3d(g->d_rays, g->params, g->n_rays, ray_order(g, false), img, g->d_ws,
                                      d_sino + (size_t)b * g->n_rays, g->tune.block, g->d_err, s));
         }
         return XR_OK;
@@ -604,7 +611,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     if (method != XR_ADJ_SCATTER) return XR_ERR_ARG;
     if (!use_tiled(g, batch) && !use_fast(g, batch) && use_dda(g)) {
         for (int b = 0; b < batch; ++b)
-            XR_CUDA(launch_scatter3d(g->d_rays, g->params, g->n_rays, row_major(g), d_sino + (size_t)b * g->n_rays,
+            XR_CUDA(launch_scatter3d(g->d_rays, g->params, g->n_rays, ray_order(g, true), d_sino + (size_t)b * g->n_rays,
                                      d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, g->d_err, s));
         return XR_OK;
     }

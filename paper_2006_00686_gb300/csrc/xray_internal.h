@@ -181,12 +181,15 @@ size_t gather_rec_bytes();
 // Fast path for 3D scans (fast3d.cu): one thread per ray with the crossing-order walk,
 // reading the caller's image or its [z][x][y] copy by the ray's direction.
 cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int nz, cudaStream_t s);
-// row_major: threads run over (row, view, col) instead of the ray order.
-// err: the handle's device error word (XR_DEVERR_* bits are or-ed in), or NULL.
-cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
-                             const float *img, const float *imgT, float *sino, int block, int *err, cudaStream_t s);
-// Zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
-cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int row_major,
+// order: 0 the ray order, 1 threads over (row, view, col), 2 threads over (view, col, row)
+// on a z-fastest copy.  ws: one volume of workspace (the [z][x][y] copy, or for order 2 the
+// [y][x][z] copy), written here.  err: the handle's device error word (XR_DEVERR_* bits are
+// or-ed in), or NULL.
+cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
+                             float *ws, float *sino, int block, int *err, cudaStream_t s);
+// Orders 0 and 1: zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
+// Order 2: zeroes the z-fastest accumulator accT, scatters, then writes it transposed to out.
+cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order,
                              const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s);
 // Unit-driven adjoint for 3D scans (tile3d.cu): one CTA per 16^3 tile of voxels gathers
 // every ray of its detector footprint in shared memory and writes the tile once.
