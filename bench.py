@@ -279,8 +279,9 @@ def run_ours(args, rank, world, local_rank):
     if args.chunk:
         tune["batch_chunk"] = args.chunk
     if args.order != "auto":
-        from paper_2006_00686_gb300.xray import XR_ORDER_COLUMN, XR_ORDER_ROW, XR_ORDER_VIEW
-        tune["order"] = {"view": XR_ORDER_VIEW, "row": XR_ORDER_ROW, "column": XR_ORDER_COLUMN}[args.order]
+        from paper_2006_00686_gb300.xray import XR_ORDER_COLUMN, XR_ORDER_ROW, XR_ORDER_ROWBLOCK, XR_ORDER_VIEW
+        tune["order"] = {"view": XR_ORDER_VIEW, "row": XR_ORDER_ROW, "column": XR_ORDER_COLUMN,
+                         "rowblock": XR_ORDER_ROWBLOCK}[args.order]
     P.set_tuning(block=args.block, **tune)
     seed0 = parallel.rank_seeds(rank, B, seed)[0]
     if B > 1:
@@ -371,7 +372,7 @@ def run_ours(args, rank, world, local_rank):
         config = {"workload": args.workload, "geometry": desc, "image": list(g.image_shape()),
                   "views": g.n_views, "detector": [g.n_rows, g.n_cols], "batch_per_gpu": B,
                   "adjoint": method + (" (2D column problems)" if P.column_batch else ""),
-                  "ray_order": {0: "auto", 1: "view", 2: "row", 3: "column"}[P.tuning()["order"]],
+                  "ray_order": {0: "auto", 1: "view", 2: "row", 3: "column", 4: "rowblock"}[P.tuning()["order"]],
                   "l2": "flushed between timed steps (256 MiB write)"}
         if P.column_batch:
             # detector setup, ray setup, the column problem's ray records and gather constants,
@@ -717,7 +718,7 @@ def main():
                     help="adjoint method (default: the gather for 2D batches and single-tilt-axis "
                          "parallel scans, the scatter elsewhere)")
     ap.add_argument("--chunk", type=int, default=0, help="images per thread of the batched path")
-    ap.add_argument("--order", default="auto", choices=["auto", "view", "row", "column"],
+    ap.add_argument("--order", default="auto", choices=["auto", "view", "row", "column", "rowblock"],
                     help="ray order of the 3D single-image path")
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--tile", type=int, default=0, help="rays per work item of the persistent batch")

@@ -124,9 +124,10 @@ typedef struct {
     int32_t order;         /* 3D fast path: the order threads take rays in.  XR_ORDER_VIEW:
                               [view][row][col]; XR_ORDER_ROW: (row, view, col), so the rays in
                               flight share detector rows across views; XR_ORDER_COLUMN: (view,
-                              col, row) on a z-fastest copy; XR_ORDER_AUTO (the default): the
-                              forward ROW for circular cones and VIEW otherwise, the scatter
-                              adjoint COLUMN for cone and helical scans and VIEW otherwise */
+                              col, row) on a z-fastest copy; XR_ORDER_ROWBLOCK: the same in
+                              blocks of 32 rows; XR_ORDER_AUTO (the default): ROWBLOCK for
+                              circular cones, for helices VIEW forward and COLUMN adjoint, VIEW
+                              otherwise */
 } xr_tuning;
 
 enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
@@ -135,7 +136,10 @@ enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
  * neighbouring rows of one detector column, and the rays read a z-fastest [y][x][z] copy of
  * the volume (the adjoint adds into a z-fastest accumulator): in a cone or helical scan a
  * column's rays share one vertical plane at neighbouring heights. */
-enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2, XR_ORDER_COLUMN = 3 };
+/* XR_ORDER_ROWBLOCK: as XR_ORDER_COLUMN, with the rows taken in blocks of 32 across every
+ * view and column before the next block, so that the rays in flight in a circular cone scan
+ * cross one slab of z. */
+enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2, XR_ORDER_COLUMN = 3, XR_ORDER_ROWBLOCK = 4 };
 
 /* Batched paths.  TILED: a CTA stages a 32x32 tile of up to 16 images in shared memory and
  * walks every ray of a group of views through it (2D scans).  INTERLEAVED (the default): the

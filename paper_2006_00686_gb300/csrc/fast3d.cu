@@ -69,7 +69,12 @@ __device__ __forceinline__ bool leans_x(const RayRec &r) { return fabsf(r.w0) > 
 // (view, col, row), so a warp holds 32 neighbouring rows of one detector column; in a cone
 // or helical scan those rays share the vertical plane through the source and the column and
 // sit at neighbouring heights, so with the volume stored z fastest they touch neighbouring
-// words.
+// words.  Row-blocked (mode 3): threads run over (block of 32 rows, view, col, row in the
+// block): warps as in mode 2, and the rays in flight are one block of rows in every view,
+// which in a circular cone cross one slab of z (the L2 locality of mode 1).  Threads past the
+// last row of a partial block get -1.
+constexpr int kRowBlock = 32;
+
 struct RayOrder {
     int mode;
     int n_cols, n_views, n_rows;
@@ -81,9 +86,15 @@ struct RayOrder {
             const int view = rest % n_views, row = rest / n_views;
             return (view * n_rows + row) * n_cols + col;
         }
-        const int row = t % n_rows, rest = t / n_rows;
-        const int col = rest % n_cols, view = rest / n_cols;
-        return (view * n_rows + row) * n_cols + col;
+        if (mode == 2) {
+            const int row = t % n_rows, rest = t / n_rows;
+            const int col = rest % n_cols, view = rest / n_cols;
+            return (view * n_rows + row) * n_cols + col;
+        }
+        const int rib = t % kRowBlock, rest = t / kRowBlock;
+        const int col = rest % n_cols, rest2 = rest / n_cols;
+        const int view = rest2 % n_views, row = (rest2 / n_views) * kRowBlock + rib;
+        return row < n_rows ? (view * n_rows + row) * n_cols + col : -1;
     }
 };
 
@@ -195,13 +206,14 @@ __global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict
 // The same walks on a z-fastest copy [y][x][z] (strides nz, nx * nz, 1): the column-major
 // ray order's layout.
 template <int U>
-__global__ void __launch_bounds__(256) fwd3dz_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
+__global__ void __launch_bounds__(256) fwd3dz_kernel(const RayRec *__restrict__ rays, int n_threads, RayOrder ord,
                                                      int nx, int ny, int nz, const float *__restrict__ imgZ,
                                                      float *__restrict__ sino, int *err)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_rays) return;
+    if (t >= n_threads) return;
     const int r = ord.ray(t);
+    if (r < 0) return;
     const RayRec rr = rays[r];
     const int sx = nz, sy = nx * nz;
     float v;
@@ -212,13 +224,15 @@ __global__ void __launch_bounds__(256) fwd3dz_kernel(const RayRec *__restrict__ 
 }
 
 template <int U>
-__global__ void __launch_bounds__(256) scatter3dz_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
-                                                         int nx, int ny, int nz, const float *__restrict__ sino,
-                                                         float *__restrict__ accZ, int *err)
+__global__ void __launch_bounds__(256) scatter3dz_kernel(const RayRec *__restrict__ rays, int n_threads,
+                                                         RayOrder ord, int nx, int ny, int nz,
+                                                         const float *__restrict__ sino, float *__restrict__ accZ,
+                                                         int *err)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_rays) return;
+    if (t >= n_threads) return;
     const int r = ord.ray(t);
+    if (r < 0) return;
     const float g = __ldg(sino + r);
     if (g == 0.f) return;
     const RayRec rr = rays[r];
@@ -437,6 +451,13 @@ static RayOrder make_order(const GeoParams &g, int mode)
     return RayOrder{mode, g.n_cols, g.n_views, g.n_rows};
 }
 
+// Threads of a launch in the given order (mode 3 pads the rows to whole blocks).
+static int64_t order_threads(const GeoParams &g, int64_t n_rays, int mode)
+{
+    if (mode != 3) return n_rays;
+    return (int64_t)((g.n_rows + kRowBlock - 1) / kRowBlock) * kRowBlock * g.n_cols * g.n_views;
+}
+
 static cudaError_t launch_transpose_rc(const float *in, float *out, int64_t rows, int64_t cols, cudaStream_t s)
 {
     const dim3 grid((unsigned)((cols + TT - 1) / TT), (unsigned)std::min<int64_t>((rows + TT - 1) / TT, 65535));
@@ -449,12 +470,13 @@ cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_r
 {
     const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
     cudaError_t e;
-    if (order == 2) {
-        // z-fastest copy, then the column-major walk
+    if (order >= 2) {
+        // z-fastest copy, then the column-major (or row-blocked) walk
         e = launch_transpose_rc(img, ws, g.nz, (int64_t)g.nx * g.ny, s);
         if (e != cudaSuccess) return e;
-        fwd3dz_kernel<kFwdAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, 2), g.nx, g.ny, g.nz, ws,
-                                                          sino, err);
+        const int64_t nt = order_threads(g, n_rays, order);
+        fwd3dz_kernel<kFwdAhead><<<(unsigned)((nt + block - 1) / block), block, 0, s>>>(
+            rays, (int)nt, make_order(g, order), g.nx, g.ny, g.nz, ws, sino, err);
         return cudaGetLastError();
     }
     e = launch_transpose_xy(img, ws, g.nx, g.ny, g.nz, s);
@@ -469,13 +491,13 @@ cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_r
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const size_t bytes = (size_t)nx * ny * nz * sizeof(float);
-    if (order == 2) {
+    if (order >= 2) {
         // one z-fastest accumulator, transposed into out (every element written)
         cudaError_t e = cudaMemsetAsync(accT, 0, bytes, s);
         if (e != cudaSuccess) return e;
-        const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
-        scatter3dz_kernel<kAdjAhead><<<blocks, block, 0, s>>>(rays, (int)n_rays, make_order(g, 2), nx, ny, nz, sino,
-                                                              accT, err);
+        const int64_t nt = order_threads(g, n_rays, order);
+        scatter3dz_kernel<kAdjAhead><<<(unsigned)((nt + block - 1) / block), block, 0, s>>>(
+            rays, (int)nt, make_order(g, order), nx, ny, nz, sino, accT, err);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return launch_transpose_rc(accT, out, (int64_t)nx * ny, nz, s);

@@ -162,22 +162,23 @@ static bool use_dda(const xr_geometry *g)
            g->n_rays < ((int64_t)1 << 31);
 }
 
-// Ray order of the 3D fast path (0 view, 1 row, 2 column; see launch_project3d).  Automatic,
-// measured on GB300: the forward row-major for circular cones (a detector row crosses one
-// slab of z in every view) and the ray order otherwise (a helix moves through z view by view;
-// a parallel scan's views each cross the whole volume); the scatter adjoint of cone and
-// helical scans column-major on the z-fastest copy, whose reductions from a warp's rays fall
-// on neighbouring words (cone 512^3: 400 vs 437 ms; helix: 148 vs 166 ms; their forwards
-// gain nothing, 245 vs 246 and 93 vs 88 ms).
+// Ray order of the 3D fast path (0 view, 1 row, 2 column, 3 row-blocked; see
+// launch_project3d).  Automatic, measured on GB300: circular cones row-blocked in both
+// directions (a warp's rays are neighbouring rows of one column, whose reductions fall on
+// neighbouring words of the z-fastest copy, and the rays in flight cross one slab of z:
+// cone 512^3 adjoint 341 ms vs 398 column-major and 437 row-major, forward 242 vs 246 ms);
+// helices the ray order forward (the source moves through z view by view; 88 vs 93 ms) and
+// column-major adjoint (148 vs 166 ms); the ray order otherwise.
 static int ray_order(const xr_geometry *g, bool adjoint)
 {
+    if (g->tune.order == XR_ORDER_ROWBLOCK) return 3;
     if (g->tune.order == XR_ORDER_COLUMN) return 2;
     if (g->tune.order == XR_ORDER_ROW) return 1;
     if (g->tune.order == XR_ORDER_VIEW) return 0;
     const int k = g->params.kind;
-    const bool cone = k == XR_CONE || k == XR_CONE_ARC, helix = k == XR_HELIX || k == XR_HELIX_ARC;
-    if (adjoint && (cone || helix)) return 2;
-    return cone ? 1 : 0;
+    if (k == XR_CONE || k == XR_CONE_ARC) return 3;
+    if (adjoint && (k == XR_HELIX || k == XR_HELIX_ARC)) return 2;
+    return 0;
 }
 
 // Single-tilt-axis parallel scans: the column images as quad planes in both orders and the
@@ -483,7 +484,7 @@ xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
         return XR_ERR_ARG;
     if (t->adjoint && t->adjoint != XR_ADJ_SCATTER && t->adjoint != XR_ADJ_GATHER) return XR_ERR_ARG;
     if (t->path < 0 || t->path > XR_PATH_RAY) return XR_ERR_ARG;
-    if (t->order < 0 || t->order > XR_ORDER_COLUMN) return XR_ERR_ARG;
+    if (t->order < 0 || t->order > XR_ORDER_ROWBLOCK) return XR_ERR_ARG;
     if (t->order) g->tune.order = t->order;
     if (t->path) g->tune.path = t->path;
     if (t->block) g->tune.block = t->block;

@@ -72,7 +72,7 @@ def projector_candidates(g, batch: int) -> list:
     out = []
     if g.is3d:
         # the volume-copy path in either ray order with either adjoint, then the caller's layout
-        for order in (X.XR_ORDER_VIEW, X.XR_ORDER_ROW, X.XR_ORDER_COLUMN):
+        for order in (X.XR_ORDER_VIEW, X.XR_ORDER_ROW, X.XR_ORDER_COLUMN, X.XR_ORDER_ROWBLOCK):
             for adj in (X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER):
                 out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=adj, block=128, order=order))
         out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=X.XR_ADJ_GATHER, block=256,

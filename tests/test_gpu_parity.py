@@ -283,14 +283,16 @@ def test_batched_fast_path(name, batch, path):
 
 
 @pytest.mark.parametrize("name,order", [("par3d_32_tilt", 0), ("cone_64", 0), ("helix_64x32", 0),
-                                        ("cone_64", 3), ("helix_64x32", 3)])
+                                        ("cone_64", 3), ("helix_64x32", 3), ("cone_64", 4), ("helix_64x32", 4)])
 def test_fast3d_matches_ray_path(name, order):
     # the 3D fast path (reads a y-fastest copy for x-leaning rays) and the one-thread-per-ray
     # kernels on the caller's layout walk the same voxels in the same order: bitwise equal
     # forwards, adjoints equal up to the order of the atomic additions; a forward after an
     # adjoint (both use the workspace) is unchanged
     from paper_2006_00686_gb300.xray import XR_PATH_RAY
-    # order 3 (XR_ORDER_COLUMN): threads over (view, col, row) on a z-fastest copy
+    # order 3 (XR_ORDER_COLUMN): threads over (view, col, row) on a z-fastest copy; order 4
+    # (XR_ORDER_ROWBLOCK): the same in blocks of 32 rows (helix_64x32 has 16 rows: a partial
+    # block)
     g = SMALL[name]()
     x = torch.stack([_phantom(g, 40 + b) for b in range(2)]).cuda()
     Pf, Pr = _proj(g), _proj(g)

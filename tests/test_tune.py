@@ -31,7 +31,7 @@ def test_candidates_cover_paths():
     g3 = inputs.Geometry("cone", 8, 8, 8, angles=np.arange(4) * 0.5, n_cols=9, n_rows=9, sod=40.0, sdd=60.0)
     c3 = tune.projector_candidates(g3, 8)
     assert {c["adjoint"] for c in c3} == {X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER}
-    assert {c["order"] for c in c3} == {X.XR_ORDER_VIEW, X.XR_ORDER_ROW, X.XR_ORDER_COLUMN}
+    assert {c["order"] for c in c3} == {X.XR_ORDER_VIEW, X.XR_ORDER_ROW, X.XR_ORDER_COLUMN, X.XR_ORDER_ROWBLOCK}
     assert all(c["path"] != X.XR_PATH_TILED for c in tune.projector_candidates(g3, 8))
 
 
