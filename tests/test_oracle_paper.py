@@ -116,6 +116,39 @@ def test_helix_h0_equals_circular_cone():
     np.testing.assert_array_equal(a[1], b[1])
 
 
+def test_in_plane_case2_reduces_to_2d():
+    # Section 3.2, Case 2 (eq. condition_nonzero_t_case2_3D_1): with phi_1 = 0 a 3D parallel
+    # ray lies in the plane y = s_1 and meets only the voxels of the slice holding that plane,
+    # under the 2D condition in (x, z).  So the 3D transform restricted to one detector column
+    # (s_1 = u) is the 2D parallel transform of that column's y-slice, with s = s_2 the row
+    # coordinate and phi = phi_2; the adjoint likewise.  The oracle computes the two through
+    # its separate 3D and 2D derivations.  phi_2 = 0 and pi/2 give axis-parallel rays (the
+    # closed ranges of Cases 3/4 against 2D Case 2); no column or row lies on a grid plane.
+    rng = np.random.default_rng(21)
+    nx, ny, nz = 7, 6, 5
+    dx, dy, dz, cx, cy, cz = 0.9, 1.1, 1.2, 0.4, -0.3, 0.2
+    phi2 = np.radians([-57.0, -20.0, 0.0, 33.0, 61.0, 90.0])
+    n_cols, n_rows, du, dv, u0, v0 = 5, 9, 1.3, 0.8, 0.21, 0.13
+    g3 = Geometry("par3d", nx, ny, nz, dx=dx, dy=dy, dz=dz, cx=cx, cy=cy, cz=cz,
+                  angles=np.stack([np.zeros_like(phi2), phi2], axis=1), n_cols=n_cols, n_rows=n_rows,
+                  du=du, dv=dv, u0=u0, v0=v0)
+    g2 = Geometry("par2d", nx, nz, dx=dx, dy=dz, cx=cx, cy=cz, angles=phi2, n_cols=n_rows, du=dv, u0=v0)
+    f = rng.uniform(0.0, 1.0, (nz, ny, nx))
+    sino = rng.uniform(0.0, 1.0, (len(phi2), n_rows, n_cols))
+    y3 = O.forward(g3, f.reshape(-1)).reshape(len(phi2), n_rows, n_cols)
+    z3 = O.adjoint(g3, sino.reshape(-1)).reshape(nz, ny, nx)
+    z_expect = np.zeros((nz, ny, nx))
+    for c in range(n_cols):
+        y = (c - 0.5 * (n_cols - 1)) * du + u0          # the column's plane y = s_1 = u
+        jh = (cy + 0.5 * ny * dy - y) / dy               # its slice coordinate (j counts down)
+        assert 0.0 < jh < ny and abs(jh - round(jh)) > 0.05
+        j = int(math.floor(jh))
+        y2 = O.forward(g2, f[:, j, :].reshape(-1)).reshape(len(phi2), n_rows)
+        np.testing.assert_allclose(y3[:, :, c], y2, rtol=1e-12, atol=1e-12)
+        z_expect[:, j, :] += O.adjoint(g2, sino[:, :, c].reshape(-1)).reshape(nz, nx)
+    np.testing.assert_allclose(z3, z_expect, rtol=1e-12, atol=1e-12)
+
+
 def _steps(trace, kind):
     return [r for r in trace if r[0] == kind]
 
