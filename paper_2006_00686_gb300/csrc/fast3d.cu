@@ -458,6 +458,13 @@ static int64_t order_threads(const GeoParams &g, int64_t n_rays, int mode)
     return (int64_t)((g.n_rows + kRowBlock - 1) / kRowBlock) * kRowBlock * g.n_cols * g.n_views;
 }
 
+// Thread ids are 32-bit: a row-blocked launch whose padding would pass 2^31 threads takes the
+// plain column-major order (the same rays, the same z-fastest layout).
+static int fit_order(const GeoParams &g, int64_t n_rays, int mode)
+{
+    return (mode == 3 && order_threads(g, n_rays, 3) >= ((int64_t)1 << 31)) ? 2 : mode;
+}
+
 static cudaError_t launch_transpose_rc(const float *in, float *out, int64_t rows, int64_t cols, cudaStream_t s)
 {
     const dim3 grid((unsigned)((cols + TT - 1) / TT), (unsigned)std::min<int64_t>((rows + TT - 1) / TT, 65535));
@@ -468,6 +475,7 @@ static cudaError_t launch_transpose_rc(const float *in, float *out, int64_t rows
 cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
                              float *ws, float *sino, int block, int *err, cudaStream_t s)
 {
+    order = fit_order(g, n_rays, order);
     const unsigned blocks = (unsigned)((n_rays + block - 1) / block);
     cudaError_t e;
     if (order >= 2) {
@@ -489,6 +497,7 @@ cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_r
 cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order,
                              const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s)
 {
+    order = fit_order(g, n_rays, order);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const size_t bytes = (size_t)nx * ny * nz * sizeof(float);
     if (order >= 2) {
