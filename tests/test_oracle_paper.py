@@ -149,6 +149,38 @@ def test_in_plane_case2_reduces_to_2d():
     np.testing.assert_allclose(z3, z_expect, rtol=1e-12, atol=1e-12)
 
 
+def test_cone_central_row_reduces_to_fan():
+    # The central row of a flat cone detector (h = 0, so beta = 0 and s_2 = 0 in eq.
+    # equispaced_cone_beam) holds horizontal rays in the source plane z = 0: they meet only the
+    # slice holding that plane, as the fan beam of eq. 2Dparalleltofan_2 does on the slice's
+    # image.  The cone's view angle phi'_1 (source at -D(cos phi'_1, sin phi'_1, 0)) is the fan's
+    # alpha - pi/2 (source at D(-sin alpha, cos alpha)); both detectors run along
+    # (-sin phi'_1, cos phi'_1).  Forward and adjoint, through the oracle's separate 3D and 2D
+    # formulas, with anisotropic off-centre voxels.
+    rng = np.random.default_rng(5)
+    nx, ny, nz = 9, 8, 5
+    dx, dy, dz, cx, cy, cz = 0.9, 1.1, 1.3, 0.4, -0.3, 0.45
+    phi = np.radians([0.0, 17.0, 100.0, 200.0, 290.0])
+    sod, sdd, n_cols, du, u0 = 30.0, 50.0, 15, 1.1, 0.3
+    gc = Geometry("cone", nx, ny, nz, dx=dx, dy=dy, dz=dz, cx=cx, cy=cy, cz=cz, angles=phi, n_cols=n_cols,
+                  n_rows=3, du=du, dv=0.7, u0=u0, v0=0.0, sod=sod, sdd=sdd)
+    gf = Geometry("fan2d", nx, ny, dx=dx, dy=dy, cx=cx, cy=cy, angles=phi + pi / 2, n_cols=n_cols, du=du, u0=u0,
+                  sod=sod, sdd=sdd)
+    kh = (cz + 0.5 * nz * dz) / dz  # slice coordinate of z = 0 (k counts down)
+    assert abs(kh - round(kh)) > 0.1
+    k = int(math.floor(kh))
+    f = rng.uniform(0.0, 1.0, (nz, ny, nx))
+    yc = O.forward(gc, f.reshape(-1)).reshape(len(phi), 3, n_cols)[:, 1, :]
+    yf = O.forward(gf, f[k].reshape(-1)).reshape(len(phi), n_cols)
+    np.testing.assert_allclose(yc, yf, rtol=1e-12, atol=1e-12)
+    sino = np.zeros((len(phi), 3, n_cols))
+    sino[:, 1, :] = rng.uniform(0.0, 1.0, (len(phi), n_cols))
+    zc = O.adjoint(gc, sino.reshape(-1)).reshape(nz, ny, nx)
+    z_expect = np.zeros((nz, ny, nx))
+    z_expect[k] = O.adjoint(gf, sino[:, 1, :].reshape(-1)).reshape(ny, nx)
+    np.testing.assert_allclose(zc, z_expect, rtol=1e-12, atol=1e-12)
+
+
 def _steps(trace, kind):
     return [r for r in trace if r[0] == kind]
 
