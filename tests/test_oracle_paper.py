@@ -149,22 +149,25 @@ def test_in_plane_case2_reduces_to_2d():
     np.testing.assert_allclose(z3, z_expect, rtol=1e-12, atol=1e-12)
 
 
-def test_cone_central_row_reduces_to_fan():
+@pytest.mark.parametrize("cone,fan,du,u0", [("cone", "fan2d", 1.1, 0.3), ("cone_arc", "fan2d_arc", 0.02, 0.004)])
+def test_cone_central_row_reduces_to_fan(cone, fan, du, u0):
     # The central row of a flat cone detector (h = 0, so beta = 0 and s_2 = 0 in eq.
     # equispaced_cone_beam) holds horizontal rays in the source plane z = 0: they meet only the
     # slice holding that plane, as the fan beam of eq. 2Dparalleltofan_2 does on the slice's
     # image.  The cone's view angle phi'_1 (source at -D(cos phi'_1, sin phi'_1, 0)) is the fan's
     # alpha - pi/2 (source at D(-sin alpha, cos alpha)); both detectors run along
-    # (-sin phi'_1, cos phi'_1).  Forward and adjoint, through the oracle's separate 3D and 2D
-    # formulas, with anisotropic off-centre voxels.
+    # (-sin phi'_1, cos phi'_1).  Flat (eq. equispaced_cone_beam vs 2Dparalleltofan_2) and
+    # equiangular (eq. equiangular_cone_beam vs 2Dparalleltofan, du in radians) detectors;
+    # forward and adjoint, through the oracle's separate 3D and 2D formulas, with anisotropic
+    # off-centre voxels.
     rng = np.random.default_rng(5)
     nx, ny, nz = 9, 8, 5
     dx, dy, dz, cx, cy, cz = 0.9, 1.1, 1.3, 0.4, -0.3, 0.45
     phi = np.radians([0.0, 17.0, 100.0, 200.0, 290.0])
-    sod, sdd, n_cols, du, u0 = 30.0, 50.0, 15, 1.1, 0.3
-    gc = Geometry("cone", nx, ny, nz, dx=dx, dy=dy, dz=dz, cx=cx, cy=cy, cz=cz, angles=phi, n_cols=n_cols,
-                  n_rows=3, du=du, dv=0.7, u0=u0, v0=0.0, sod=sod, sdd=sdd)
-    gf = Geometry("fan2d", nx, ny, dx=dx, dy=dy, cx=cx, cy=cy, angles=phi + pi / 2, n_cols=n_cols, du=du, u0=u0,
+    sod, sdd, n_cols = 30.0, 50.0, 15
+    gc = Geometry(cone, nx, ny, nz, dx=dx, dy=dy, dz=dz, cx=cx, cy=cy, cz=cz, angles=phi, n_cols=n_cols,
+                  n_rows=3, du=du, dv=0.7 * du, u0=u0, v0=0.0, sod=sod, sdd=sdd)
+    gf = Geometry(fan, nx, ny, dx=dx, dy=dy, cx=cx, cy=cy, angles=phi + pi / 2, n_cols=n_cols, du=du, u0=u0,
                   sod=sod, sdd=sdd)
     kh = (cz + 0.5 * nz * dz) / dz  # slice coordinate of z = 0 (k counts down)
     assert abs(kh - round(kh)) > 0.1
@@ -179,6 +182,37 @@ def test_cone_central_row_reduces_to_fan():
     z_expect = np.zeros((nz, ny, nx))
     z_expect[k] = O.adjoint(gf, sino[:, 1, :].reshape(-1)).reshape(ny, nx)
     np.testing.assert_allclose(zc, z_expect, rtol=1e-12, atol=1e-12)
+
+
+def test_par3d_horizontal_views_reduce_to_2d_rows():
+    # Reading R5 (phi_2 = 0 with any phi_1, not listed among the paper's cases): the foot point
+    # s_1 theta_1 + s_2 theta_2 becomes (-s_1 sin phi_1, s_1 cos phi_1, s_2) and theta is
+    # horizontal, so every detector row (s_2 = w) holds rays in the plane z = w that meet only
+    # the slice holding it, as the 2D parallel beam with phi = phi_1 and s = s_1 = u does on the
+    # slice's image.  phi_1 = 0 and pi/2 are axis-parallel views.
+    rng = np.random.default_rng(6)
+    nx, ny, nz = 9, 8, 5
+    dx, dy, dz, cx, cy, cz = 0.9, 1.1, 1.3, 0.4, -0.3, 0.45
+    phi1 = np.radians([-30.0, 0.0, 25.0, 90.0, 140.0])
+    n_rows, n_cols, du, dv, u0, v0 = 5, 11, 0.9, 1.1, 0.17, 0.23
+    g3 = Geometry("par3d", nx, ny, nz, dx=dx, dy=dy, dz=dz, cx=cx, cy=cy, cz=cz,
+                  angles=np.stack([phi1, np.zeros_like(phi1)], axis=1), n_cols=n_cols, n_rows=n_rows, du=du,
+                  dv=dv, u0=u0, v0=v0)
+    g2 = Geometry("par2d", nx, ny, dx=dx, dy=dy, cx=cx, cy=cy, angles=phi1, n_cols=n_cols, du=du, u0=u0)
+    f = rng.uniform(0.0, 1.0, (nz, ny, nx))
+    sino = rng.uniform(0.0, 1.0, (len(phi1), n_rows, n_cols))
+    y3 = O.forward(g3, f.reshape(-1)).reshape(len(phi1), n_rows, n_cols)
+    z3 = O.adjoint(g3, sino.reshape(-1)).reshape(nz, ny, nx)
+    z_expect = np.zeros((nz, ny, nx))
+    for r in range(n_rows):
+        z = (r - 0.5 * (n_rows - 1)) * dv + v0
+        kh = (cz + 0.5 * nz * dz - z) / dz  # the row's slice coordinate (k counts down)
+        assert 0.0 < kh < nz and abs(kh - round(kh)) > 0.1
+        k = int(math.floor(kh))
+        y2 = O.forward(g2, f[k].reshape(-1)).reshape(len(phi1), n_cols)
+        np.testing.assert_allclose(y3[:, r, :], y2, rtol=1e-12, atol=1e-12)
+        z_expect[k] += O.adjoint(g2, sino[:, r, :].reshape(-1)).reshape(ny, nx)
+    np.testing.assert_allclose(z3, z_expect, rtol=1e-12, atol=1e-12)
 
 
 def _steps(trace, kind):
