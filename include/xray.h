@@ -185,6 +185,17 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
 xr_status xr_reserve(xr_geometry *g, int32_t max_batch);
 
 xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info);
+
+/* Host-only query (no CUDA call, no allocation on the device): whether a scan description is
+ * a single-tilt-axis parallel scan that the forward and the gather adjoint run as 2D column
+ * problems (xr_geometry_info.column_batch of a handle made from it), and the y-slice of each
+ * detector column's ray plane (Section 3.2, Case 2: with phi_1 = 0 the rays of a column lie in
+ * the plane y = s_1 = u).  slice_of: n_cols int32 values written when not NULL: the slice
+ * index j (counting down in y), or -1 for a column whose plane misses the volume, and -1 for
+ * every column when the scan is not eligible.  *eligible: 1 or 0.
+ * Errors: XR_ERR_NULL (desc or eligible NULL), and the codes xr_geometry_create returns for an
+ * invalid description (XR_ERR_KIND, XR_ERR_SIZE, XR_ERR_GEOMETRY, XR_ERR_NULL). */
+xr_status xr_column_batch_plan(const xr_geometry_desc *desc, int32_t *slice_of, int32_t *eligible);
 xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t);
 xr_status xr_get_tuning(const xr_geometry *g, xr_tuning *t);
 

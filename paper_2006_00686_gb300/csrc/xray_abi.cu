@@ -475,6 +475,19 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
     return XR_OK;
 }
 
+xr_status xr_column_batch_plan(const xr_geometry_desc *desc, int32_t *slice_of, int32_t *eligible)
+{
+    if (!desc || !eligible) return XR_ERR_NULL;
+    const xr_status st = validate(desc);
+    if (st != XR_OK) return st;
+    SlicePlan sp;
+    const bool ok = kind_is3d(desc->kind) && slice_plan(desc, &sp);
+    *eligible = ok ? 1 : 0;
+    if (slice_of)
+        for (int c = 0; c < desc->n_cols; ++c) slice_of[c] = ok ? sp.slice_of[(size_t)c] : -1;
+    return XR_OK;
+}
+
 xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
 {
     if (!g || !t) return XR_ERR_NULL;

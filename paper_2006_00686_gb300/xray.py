@@ -61,6 +61,8 @@ SIGNATURES = {
     "xr_geometry_destroy": (None, [_VP]),
     "xr_ray_setup": (_I32, [_VP, _VP]),
     "xr_geometry_get_info": (_I32, [_VP, ctypes.POINTER(_Info)]),
+    "xr_column_batch_plan": (_I32, [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32)]),
     "xr_reserve": (_I32, [_VP, _I32]),
     "xr_set_tuning": (_I32, [_VP, ctypes.POINTER(_Tuning)]),
     "xr_get_tuning": (_I32, [_VP, ctypes.POINTER(_Tuning)]),
@@ -126,6 +128,29 @@ def _need_cuda(t: torch.Tensor, name: str):
         raise XRayError(f"{name} must be a contiguous float32 CUDA tensor")
 
 
+def _desc(geom: Geometry):
+    """The C description of a scan and the arrays it points into (keep them alive)."""
+    angles = np.ascontiguousarray(np.asarray(geom.angles, dtype=np.float64).reshape(-1))
+    src_z = None if geom.src_z is None else np.ascontiguousarray(geom.src_z, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    d = _Desc(KINDS[geom.kind], geom.nx, geom.ny, geom.nz, geom.dx, geom.dy, geom.dz, geom.cx, geom.cy,
+              geom.cz, geom.n_views, geom.n_rows, geom.n_cols, angles.ctypes.data_as(dp),
+              None if src_z is None else src_z.ctypes.data_as(dp),
+              geom.du, geom.dv, geom.u0, geom.v0, geom.sod, geom.sdd)
+    return d, angles, src_z
+
+
+def column_batch_plan(geom: Geometry):
+    """(eligible, slice_of): whether the library runs this scan as 2D column problems, and the
+    y-slice of each detector column (-1 outside the volume).  Host only: needs no GPU."""
+    d, _angles, _src_z = _desc(geom)
+    out = np.full(max(geom.n_cols, 1), -1, dtype=np.int32)
+    ok = ctypes.c_int32(0)
+    _check(lib().xr_column_batch_plan(ctypes.byref(d), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      ctypes.byref(ok)), "xr_column_batch_plan")
+    return bool(ok.value), out[:geom.n_cols]
+
+
 class Projector:
     """X-ray transform and adjoint of one scan on the current CUDA device."""
 
@@ -133,13 +158,7 @@ class Projector:
         if not torch.cuda.is_available():
             raise XRayError("no CUDA device: the X-ray transform runs only on the GPU")
         self.geom = geom
-        self._angles = np.ascontiguousarray(np.asarray(geom.angles, dtype=np.float64).reshape(-1))
-        self._src_z = None if geom.src_z is None else np.ascontiguousarray(geom.src_z, dtype=np.float64)
-        dp = ctypes.POINTER(ctypes.c_double)
-        d = _Desc(KINDS[geom.kind], geom.nx, geom.ny, geom.nz, geom.dx, geom.dy, geom.dz, geom.cx, geom.cy,
-                  geom.cz, geom.n_views, geom.n_rows, geom.n_cols, self._angles.ctypes.data_as(dp),
-                  None if self._src_z is None else self._src_z.ctypes.data_as(dp),
-                  geom.du, geom.dv, geom.u0, geom.v0, geom.sod, geom.sdd)
+        d, self._angles, self._src_z = _desc(geom)
         h = ctypes.c_void_p()
         torch.cuda.current_device()  # make sure the CUDA context exists
         _check(lib().xr_geometry_create(ctypes.byref(d), ctypes.byref(h)), "xr_geometry_create")

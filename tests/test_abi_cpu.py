@@ -105,3 +105,76 @@ def test_product_path_fails_loudly_without_gpu(X):
     from paper_2006_00686_gb300.inputs import par2d_64
     with pytest.raises(X.XRayError):
         X.Projector(par2d_64())
+
+
+# ---------------------------------------------------------------------------------------
+# Column batch of single-tilt-axis parallel scans: the host-side plan (no GPU needed)
+# ---------------------------------------------------------------------------------------
+
+def _tilt(nx=8, ny=6, nz=5, phi1=0.0, **kw):
+    from paper_2006_00686_gb300.inputs import Geometry
+    phi2 = np.radians([-50.0, -10.0, 30.0, 70.0])
+    ang = np.stack([np.full(4, phi1), phi2], axis=1)
+    base = dict(dx=0.9, dy=1.1, dz=1.2, cx=0.3, cy=-0.2, cz=0.1, n_cols=6, n_rows=5, du=1.1, dv=0.9, u0=0.05,
+                v0=0.1)
+    base.update(kw)
+    return Geometry("par3d", nx, ny, nz, angles=ang, **base)
+
+
+def _oracle_slices(g):
+    # the slice of every unit the oracle gives the central-row rays of each column (Section 3.2
+    # Case 2: a ray of the column meets only the slice holding its plane); -1: no unit
+    from oracle import oracle as O
+    out = []
+    for c in range(g.n_cols):
+        js = set()
+        for v in range(g.n_views):
+            idx, _ = O.ray_units(g, (v * g.n_rows + g.n_rows // 2) * g.n_cols + c)
+            js |= {int(I) // g.nx % g.ny for I in np.asarray(idx)}
+        assert len(js) <= 1, f"column {c} meets slices {js}"
+        out.append(js.pop() if js else -1)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("phi1", [0.0, math.pi])
+def test_column_batch_plan_matches_the_oracle(X, phi1):
+    g = _tilt(phi1=phi1)
+    ok, slice_of = X.column_batch_plan(g)
+    assert ok
+    np.testing.assert_array_equal(slice_of, _oracle_slices(g))
+    assert len(set(slice_of[slice_of >= 0].tolist())) == (slice_of >= 0).sum()
+
+
+def test_column_batch_plan_columns_outside_the_volume(X):
+    g = _tilt(n_cols=9, du=1.4)  # the outer columns' planes miss the 6.6-wide volume
+    ok, slice_of = X.column_batch_plan(g)
+    assert ok and (slice_of == -1).any() and (slice_of >= 0).any()
+    np.testing.assert_array_equal(slice_of, _oracle_slices(g))
+
+
+@pytest.mark.parametrize("kw", [
+    dict(du=0.5),                 # two columns per slice
+    dict(du=1.1, u0=0.0, cy=0.0, ny=6, dy=1.1, n_cols=5),  # a column plane on a slice boundary (y = 0)
+])
+def test_column_batch_plan_refuses(X, kw):
+    ok, slice_of = X.column_batch_plan(_tilt(**kw))
+    assert not ok and (slice_of == -1).all()
+
+
+def test_column_batch_plan_needs_one_tilt_axis(X):
+    from paper_2006_00686_gb300.inputs import Geometry
+    g = _tilt()
+    ang = np.array(g.angles, copy=True)
+    ang[2, 0] = 0.3
+    assert not X.column_batch_plan(Geometry("par3d", g.nx, g.ny, g.nz, angles=ang, n_cols=6, n_rows=5))[0]
+    ang[:, 0] = [0.0, math.pi, 0.0, 0.0]  # both signs of cos(phi_1): the columns swap planes
+    assert not X.column_batch_plan(Geometry("par3d", g.nx, g.ny, g.nz, angles=ang, n_cols=6, n_rows=5))[0]
+    cone = Geometry("cone", 8, 6, 5, angles=[0.1, 0.7], n_cols=6, n_rows=5, sod=40.0, sdd=60.0)
+    assert not X.column_batch_plan(cone)[0]
+
+
+def test_column_batch_plan_rejects_invalid_descriptions(X):
+    from paper_2006_00686_gb300.inputs import Geometry
+    with pytest.raises(X.XRayError):
+        X.column_batch_plan(Geometry("par3d", 8, 6, 5, dx=0.0, angles=[[0.0, 0.2]], n_cols=6, n_rows=5))
+    assert X.lib().xr_column_batch_plan(None, None, None) == 1
