@@ -1,14 +1,20 @@
-"""Benchmark: forward + adjoint X-ray transform of the 2D fan-beam workload
-(512x512 pixels, 720 views over 2*pi, 768 flat-detector bins of 1.2, source-origin 1000,
-source-detector 1500, a batch of 16 random-ellipse phantoms) on N GPUs of one node.
+"""Benchmark: forward + adjoint X-ray transform on N GPUs of one node.
 
-One step = the per-geometry ray setup + the forward projection of the 16-image batch +
-the adjoint of the resulting sinograms, every kernel launched through the C ABI.
-Metric: Grays/s = rays x images / (time of one step).  Each rank runs its own batch of 16
+Headline line: the 2D fan-beam workload (512x512 pixels, 720 views over 2*pi, 768
+flat-detector bins of 1.2, source-origin 1000, source-detector 1500, a batch of 16
+random-ellipse phantoms).  With no --workload, the same run also measures every other
+scan configuration under ``extra.per_config``: the 2D parallel beam 64^2 (CUDA-graph
+replay), the single-tilt-axis parallel beam 256^3 (with autograd and SIRT), the circular
+cone 512^3, the helical cone 512^2 x 256, and 64 uneven fans as one persistent plan
+against one launch set per problem.
+
+One step = the per-geometry ray setup + the forward projection + the adjoint of the
+resulting sinograms, every kernel launched through the C ABI.
+Metric: Grays/s = rays x images / (time of one step).  Each rank runs its own batch of
 independent images (weak scaling, no collective on the data path).
 
 ``--impl reference`` times the double-precision CPU oracle on the host cores on a bounded
-sample of the same workload (a subset of the views, all 16 images).
+sample of the same workload (a subset of the views, all images).
 """
 from __future__ import annotations
 
@@ -223,54 +229,79 @@ def _e2e(sets, args, flush):
     return a.elapsed_time(b) / args.steps
 
 
+_L2_PEAK = None
+
+
 def _l2_peak():
     """Measured L2 read bandwidth (GB/s): a 64 MiB buffer read 20 times per launch with
-    128-bit L2-only loads (xr_read_probe), best of 5 launches."""
-    from paper_2006_00686_gb300.xray import read_bandwidth
-    return read_bandwidth(64 << 20, 20, 5)
+    128-bit L2-only loads (xr_read_probe), best of 5 launches; measured once per process."""
+    global _L2_PEAK
+    if _L2_PEAK is None:
+        from paper_2006_00686_gb300.xray import read_bandwidth
+        _L2_PEAK = read_bandwidth(64 << 20, 20, 5)
+    return _L2_PEAK
 
 
-def _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic):
-    # The path is bound by neither HBM (for the 2D workloads the images and sinograms stay
-    # in L2) nor tensor cores: every unit costs scalar FP32 work.  "alu": achieved =
-    # algorithmic FP32 FLOP per launch / launch time, with per (ray, unit) intersection one
-    # subtraction for the length C_up - C_low and one FMA (2 FLOP) per image; peak = 152 SMs
-    # x 128 FP32 lanes x 2 FLOP x maximum SM clock.
-    n_int = _intersections(g, P)
-    flop = n_int * (1.0 + 2.0 * B)
-    achieved = flop / (dom_ms * 1e-3) / 1e12
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-    compulsory = 4.0 * (g.n_units + g.n_rays) * B
+def _roofline(n_int, units_bytes, B, dom, dom_ms, peaks, peak_kind, traffic, traffic_note=None):
+    """Roofline of the dominant kernel: the path is a gather (forward) or a
+    scatter (adjoint) of 4 B per (ray, unit, image) along the rays, served from L1/L2, so
+    the bound is memory, not tensor cores.  achieved = 4 B x intersections x images per
+    launch / launch time; peak = the L2 read bandwidth measured in the same run.  The
+    compulsory HBM bytes (images + sinograms) and the FP32 issue fraction are reported
+    beside it."""
     gather = 4.0 * n_int * B
-    gather_gbs = gather / (dom_ms * 1e-3) / 1e9
+    gbs = gather / (dom_ms * 1e-3) / 1e9
     l2_peak = _l2_peak()
+    flop = n_int * (1.0 + 2.0 * B)  # one subtraction per length, one FMA per image
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     from paper_2006_00686_gb300.xray import fma_throughput
-    fma_meas = fma_throughput()
-    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({peak_kind} max clock)",
-            "algorithmic_flop": flop, "intersections_per_image": n_int, "ms": round(dom_ms, 4),
-            "fp32_fma_measured_tflops": round(fma_meas, 2),
-            "hbm": {"compulsory_bytes": compulsory, "achieved_gbs": round(compulsory / (dom_ms * 1e-3) / 1e9, 1),
-                    "peak_gbs": peaks["hbm_gbs"], "frac": round(compulsory / (dom_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
-            # the gather along rays as bytes: 4 B per (ray, unit, image), served from L1/L2
-            "l2": {"algorithmic_bytes": gather, "achieved_gbs": round(gather_gbs, 1), "peak_gbs": round(l2_peak, 1),
-                   "frac": round(gather_gbs / l2_peak, 4),
-                   "peak_source": "measured: xr_read_probe, 64 MiB read 20x per launch, L2-only loads"}}
+    global _FMA
+    if "_FMA" not in globals():
+        _FMA = fma_throughput()
+    tflops = flop / (dom_ms * 1e-3) / 1e12
+    out = {"bound": "l2", "kernel": dom, "achieved": round(gbs, 1), "peak": round(l2_peak, 1), "unit": "GB/s",
+           "frac": round(gbs / l2_peak, 4), "traffic": traffic,
+           "peak_source": "measured in this run: xr_read_probe, a 64 MiB buffer read 20x per launch with "
+                          "L2-only 128-bit loads (MEASURED_PEAKS.json has no L2 figure)",
+           "algorithmic_bytes": gather, "intersections_per_image": n_int, "images": B, "ms": round(dom_ms, 4),
+           "hbm": {"compulsory_bytes": units_bytes,
+                   "achieved_gbs": round(units_bytes / (dom_ms * 1e-3) / 1e9, 1),
+                   "peak_gbs": peaks["hbm_gbs"], "peak_source": f"MEASURED_PEAKS.json ({peak_kind})",
+                   "frac": round(units_bytes / (dom_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
+           "alu": {"achieved_tflops": round(tflops, 3), "peak_tflops": round(fp32_peak, 2),
+                   "frac": round(tflops / fp32_peak, 4), "fp32_fma_measured_tflops": round(_FMA, 2),
+                   "flop": flop,
+                   "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz"}}
+    if traffic_note:
+        out["traffic_source"] = traffic_note
+    return out
 
 
-def run_ours(args, rank, world, local_rank):
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel, from the ncu captures summarised under profiles/: (workload, phase, method) ->
+# (bytes, note).  Only kernels unchanged since their capture are listed.
+TRAFFIC = {
+    ("fan2d_512x16", "adjoint", "gather"): (51.5e6, "profiles/gather_pair_fan2d_512x16.md (one launch, full size)"),
+    ("fan2d_512x16", "forward", "gather"): (62.4e6, "profiles/fwd_plane_fan2d_512x16.md (one launch, full size)"),
+}
+
+GRAPHED = ("par2d_64",)  # launch-bound steps replayed from a CUDA graph
+
+
+def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
     import torch
 
     from paper_2006_00686_gb300 import inputs, parallel
     from paper_2006_00686_gb300.xray import Projector, XR_ADJ_GATHER, XR_ADJ_SCATTER
 
-    if args.workload == "fans_uneven_64":
-        return run_uneven(args, rank, world, local_rank)
+    workload = workload or args.workload
+    cpu_budget = args.cpu_budget if cpu_budget is None else cpu_budget
+    if workload == "fans_uneven_64":
+        return run_uneven(args, rank, world, local_rank, cpu_budget)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    builder, B, n_shapes, seed, desc = WORKLOADS[args.workload]
+    builder, B, n_shapes, seed, desc = WORKLOADS[workload]
     g = getattr(inputs, builder)()
     P = Projector(g)
     tune = {}
@@ -294,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
 
-    atten = args.workload.endswith("_atten")
+    atten = workload.endswith("_atten")
     mu = (0.02 + 0.05 * inputs.phantom(g, 4, 900, device=str(dev))).float().contiguous() if atten else None
 
     def make_step(xb, yb, zb):
@@ -317,13 +348,38 @@ def run_ours(args, rank, world, local_rank):
                 recs.append(e)
         return step
 
-    step = make_step(x, y, z)
+    def graphed(step_fn):
+        """The step captured once in a CUDA graph (after an eager call that reserves the
+        workspace); each call replays it on the current stream."""
+        step_fn(None)
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            step_fn(None)
+        torch.cuda.synchronize()
 
+        def replay(recs=None):
+            e = _events(2) if recs is not None else None
+            if e: e[0].record(stream)
+            gr.replay()
+            if e: e[1].record(stream)
+            if recs is not None:
+                recs.append(e)
+        return replay
+
+    step = make_step(x, y, z)
+    use_graph = workload in GRAPHED
+
+    # per-phase kernel times from eager steps; the step time from the graph where used
     recs, clocks, wall = _timed_loop(step, args, flush, world, local_rank)
     setup_ms = [a.elapsed_time(b) for a, b, c, d in recs]
     fwd_ms = [b.elapsed_time(c) for a, b, c, d in recs]
     adj_ms = [c.elapsed_time(d) for a, b, c, d in recs]
     step_ms = [a.elapsed_time(d) for a, b, c, d in recs]
+    eager_ms = float(np.mean(step_ms))
+    if use_graph:
+        grecs, clocks, wall = _timed_loop(graphed(step), args, flush, world, local_rank)
+        step_ms = [a.elapsed_time(b) for a, b in grecs]
     ms = parallel.max_over_ranks(float(np.mean(step_ms)), dev)
     rays_step = g.n_rays * B
     value = rays_step * world / (ms * 1e-3) / 1e9
@@ -333,7 +389,9 @@ def run_ours(args, rank, world, local_rank):
     x_h = x.cpu().pin_memory()
     sets = []
     for xb, yb, zb in ((x, y, z), (x.clone(), torch.empty_like(y), torch.empty_like(z))):
-        sets.append({"step": make_step(xb, yb, zb), "host_in": [x_h], "dev_in": [xb], "dev_out": [yb, zb],
+        st = make_step(xb, yb, zb)
+        sets.append({"step": graphed(st) if use_graph else st, "host_in": [x_h], "dev_in": [xb],
+                     "dev_out": [yb, zb],
                      "host_out": [torch.empty(yb.shape, pin_memory=True), torch.empty(zb.shape, pin_memory=True)]})
     e2e = parallel.max_over_ranks(_e2e(sets, args, flush), dev)
 
@@ -348,42 +406,32 @@ def run_ours(args, rank, world, local_rank):
         method = "gather" if ((not g.is3d and B >= 4) or P.column_batch) else "scatter"
     else:
         method = "gather" if adj_mode == XR_ADJ_GATHER else "scatter"
-    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
-    # forward and gather kernels, from one ncu capture of this workload
-    traffic = None
-    if args.workload == "fan2d_512x16":
-        traffic = {("adjoint", "gather"): 51.5e6, ("forward", "gather"): 62.4e6,
-                   ("forward", "scatter"): 62.4e6}.get((dom, method))
-    roof = _roofline(g, P, B, dom, dom_ms, peaks, peak_kind, traffic)
+    traffic, note = TRAFFIC.get((workload, dom, method), (None, None))
+    n_int = _intersections(g, P)
+    roof = _roofline(n_int, 4.0 * (g.n_units + g.n_rays) * B, B, dom, dom_ms, peaks, peak_kind, traffic, note)
 
     extra = {}
     if atten:
-        config = _config({"workload": args.workload, "geometry": desc, "adjoint": "scatter (attenuated)"})
+        config = _config({"workload": workload, "geometry": desc, "adjoint": "scatter (attenuated)"})
         # detector setup, ray setup, gather constants; forward: image planes, the map's two
         # padded copies, the walk; adjoint: the map's copies, the walk, the de-interleave
         launches = 9
-    elif args.workload == "fan2d_512x16":
+    elif workload == "fan2d_512x16":
         config = _config({"adjoint": method, "batch_chunk": P.tuning()["batch_chunk"], "block": args.block})
         # per step: detector setup, ray setup, the gather's per-ray constants, image
         # interleave, forward walk, then either the scatter walk + its de-interleave (two
         # accumulator memsets are not kernels) or the sinogram interleave + gather
         launches = 7
     else:
-        config = {"workload": args.workload, "geometry": desc, "image": list(g.image_shape()),
+        config = {"workload": workload, "geometry": desc, "image": list(g.image_shape()),
                   "views": g.n_views, "detector": [g.n_rows, g.n_cols], "batch_per_gpu": B,
                   "adjoint": method + (" (2D column problems)" if P.column_batch else ""),
                   "ray_order": {0: "auto", 1: "view", 2: "row", 3: "column", 4: "rowblock"}[P.tuning()["order"]],
                   "l2": "flushed between timed steps (256 MiB write)"}
-        if P.column_batch:
-            # detector setup, ray setup, the column problem's ray records and gather constants,
-            # then per image: the slice planes, the forward, the sinogram planes, the gather
-            launches = 4 + 4 * B
-        else:
-            # detector setup, ray setup (2D: and the gather's per-ray constants), then per
-            # image: the y-fastest copy, the forward walk, the scatter walk and the fold of the
-            # transposed accumulator (zero fills are memsets)
-            launches = (2 if g.is3d else 3) + 4 * B
-        if args.workload == "par3d_256_tilt":
+        if use_graph:
+            config["cuda_graph"] = "each step replayed from one captured graph"
+        launches = _launch_count(P, g, B)
+        if workload == "par3d_256_tilt":
             extra = _autograd_and_sirt(P, x, y, args)
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -398,13 +446,27 @@ def run_ours(args, rank, world, local_rank):
            "kernel_ms": {"ray_setup": round(float(np.mean(setup_ms)), 4), "forward": round(fwd, 4),
                          "adjoint": round(adj, 4)},
            "clocks": clocks, "roofline": roof, "wall_s": round(wall, 3)}
+    if use_graph:
+        out["eager_ms_per_step"] = round(eager_ms, 4)
     if extra:
         out["extra"] = extra
     if rank == 0 and not args.no_cpu_baseline:
         xs = x if B > 1 else x[None]
-        out["cpu_baseline"] = cpu_baseline(g, xs.cpu().numpy(), budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(g, xs.cpu().numpy(), budget_s=cpu_budget)
     P.close()
     return out
+
+
+def _launch_count(P, g, B):
+    """Kernels of the repo launched per step on the single-image and column paths."""
+    if P.column_batch:
+        # detector setup, ray setup, the column problem's ray records and gather constants,
+        # then per image: the slice planes, the forward, the sinogram planes, the gather
+        return 4 + 4 * B
+    # detector setup, ray setup (2D: and the gather's per-ray constants), then per image:
+    # the layout copy, the forward walk, the scatter walk and the fold of the accumulator
+    # (zero fills are memsets)
+    return (2 if g.is3d else 3) + 4 * B
 
 
 def _autograd_and_sirt(P, x, y, args):
@@ -471,7 +533,7 @@ def _autograd_and_sirt(P, x, y, args):
             "sirt_grays_s": round(rays / (sirt_ms * 1e-3) / 1e9, 4)}
 
 
-def run_uneven(args, rank, world, local_rank):
+def run_uneven(args, rank, world, local_rank, cpu_budget=None):
     """64 uneven fans: one persistent launch for all forwards and one for all adjoints,
     against the plain form (one launch per problem and operator)."""
     import torch
@@ -481,7 +543,8 @@ def run_uneven(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    _, n, n_shapes, seed, desc = WORKLOADS[args.workload]
+    _, n, n_shapes, seed, desc = WORKLOADS["fans_uneven_64"]
+    cpu_budget = args.cpu_budget if cpu_budget is None else cpu_budget
     geoms = inputs.fans_uneven(n)
     Ps = [Projector(gq) for gq in geoms]
     seeds = parallel.rank_seeds(rank, n, seed)
@@ -566,18 +629,14 @@ def run_uneven(args, rank, world, local_rank):
     peaks, peak_kind = _peaks()
     rb = res["batched"]
     dom, dom_ms = ("forward", rb["fwd"]) if rb["fwd"] >= rb["adj"] else ("adjoint", rb["adj"])
+    # intersections of all problems (one image each), each problem's rate sampled on 256 rays
     n_int = sum(_intersections(gq, p, sample=256) for gq, p in zip(geoms, Ps))
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-    achieved = n_int * 3.0 / (dom_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "batched " + dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({peak_kind} max clock)",
-            "algorithmic_flop": n_int * 3.0, "intersections": n_int, "ms": round(dom_ms, 4)}
+    compulsory = 4.0 * sum(gq.n_units + gq.n_rays for gq in geoms)
+    roof = _roofline(n_int, compulsory, 1, "batched " + dom, dom_ms, peaks, peak_kind, None)
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random-ellipse phantoms)",
-           "config": {"workload": args.workload, "geometry": desc, "problems": n,
+           "config": {"workload": "fans_uneven_64", "geometry": desc, "problems": n,
                       "sides": [gq.nx for gq in geoms][:8] + ["..."], "rays_per_step": rays_step,
                       "tile": args.tile, "plan_block": args.plan_block,
                       "plan_tuning": "autotuned" if tuned else "given",
@@ -596,9 +655,10 @@ def run_uneven(args, rank, world, local_rank):
            "plain": {"value": round(rays_step * world / (res["plain"]["ms"] * 1e-3) / 1e9, 4),
                      "ms_per_step": round(res["plain"]["ms"], 4),
                      "kernel_ms": {"forward": round(res["plain"]["fwd"], 4), "adjoint": round(res["plain"]["adj"], 4)}},
+           "batched_over_plain": round(res["plain"]["ms"] / ms, 3),
            "clocks": rb["clocks"], "roofline": roof, "wall_s": round(rb["wall"], 3)}
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_uneven(geoms, xs, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline_uneven(geoms, xs, budget_s=cpu_budget)
     fwd_plan.close()
     adj_plan.close()
     for p in Ps:
@@ -621,15 +681,17 @@ def cpu_baseline(g, x_np, budget_s=15.0):
     from oracle import oracle as O
 
     f64 = x_np.reshape(x_np.shape[0], -1).astype(np.float64)
-    views = np.arange(0, g.n_views, max(1, g.n_views // 4))[:4]  # probe the rate
+    n_probe = 1 if g.is3d else 4  # a 3D view is ~1e6 rays
+    views = np.arange(0, g.n_views, max(1, g.n_views // n_probe))[:n_probe]  # probe the rate
     t0 = time.perf_counter()
     rays = _oracle_step(O, g, f64, views)
     dt = time.perf_counter() - t0
     n = int(max(len(views), min(g.n_views, len(views) * budget_s / max(dt, 1e-3))))
-    views = np.linspace(0, g.n_views - 1, n).round().astype(np.int64)
-    t0 = time.perf_counter()
-    rays = _oracle_step(O, g, f64, views)
-    dt = time.perf_counter() - t0
+    if n > len(views):  # else the probe is the sample
+        views = np.linspace(0, g.n_views - 1, n).round().astype(np.int64)
+        t0 = time.perf_counter()
+        rays = _oracle_step(O, g, f64, views)
+        dt = time.perf_counter() - t0
     return {"value": round(rays / dt / 1e9, 9), "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
             "sample": f"{len(views)} of {g.n_views} views, all {f64.shape[0]} images, forward+adjoint "
                       f"in float64 ({rays} rays, {dt:.1f} s)"}
@@ -707,13 +769,119 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------------------------------
+# profiling cases: single kernels on reduced scans (one warm-up pass, one timed pass), sized so
+# that one launch takes milliseconds and the volume exceeds L2 where DRAM figures matter
+#   python bench.py --case cone_384     forward, scatter and tiled-gather adjoints
+#   python bench.py --case uneven_16    16 uneven fans: plain launches, then one plan
+# ----------------------------------------------------------------------------------------
+
+def case_cone_384():
+    """Circular cone, 384^3 voxels (226 MB) spanning the 512^3 scan's field of view, 90 views,
+    512 x 384 detector of spacing 2."""
+    v = np.arange(90, dtype=np.float64)
+    s = 512 / 384
+    import torch
+
+    from paper_2006_00686_gb300 import inputs
+    from paper_2006_00686_gb300.xray import Projector
+
+    g = inputs.Geometry("cone", 384, 384, 384, dx=0.8 * s, dy=0.8 * s, dz=1.0 * s, cx=10.0, cy=-5.0, cz=3.0,
+                        angles=2 * math.pi * v / 90, n_cols=512, n_rows=384, du=2.0, dv=2.0, sod=1000.0, sdd=1500.0)
+    P = Projector(g)
+    x = inputs.phantom(g, 30, 4, device="cuda").float().contiguous()
+    y = torch.empty(g.sino_shape(), device="cuda")
+    z = torch.empty(g.image_shape(), device="cuda")
+    times = []
+    for rep in range(2):
+        e = _events(4)
+        e[0].record()
+        P.forward(x, out=y)
+        e[1].record()
+        P.adjoint(y, out=z, method=1)
+        e[2].record()
+        P.adjoint(y, out=z, method=2)
+        e[3].record()
+        e[3].synchronize()
+        times = [e[i].elapsed_time(e[i + 1]) for i in range(3)]
+    print(f"cone_384: rays {g.n_rays}, forward {times[0]:.3f} ms, scatter {times[1]:.3f} ms, "
+          f"tiled gather {times[2]:.3f} ms")
+
+
+def case_uneven_16():
+    """The first 16 of the 64 uneven fans: the plain adjoint (one launch set per problem),
+    then the same adjoints as one persistent plan."""
+    import torch
+
+    from paper_2006_00686_gb300 import inputs
+    from paper_2006_00686_gb300.xray import BatchPlan, Projector
+
+    geoms = inputs.fans_uneven()[:16]
+    Ps = [Projector(g) for g in geoms]
+    xs = [inputs.phantom(g, 10, 500 + q, device="cuda").float().contiguous() for q, g in enumerate(geoms)]
+    ys = [torch.empty(g.sino_shape(), device="cuda") for g in geoms]
+    zs = [torch.empty(g.image_shape(), device="cuda") for g in geoms]
+    for p, x, y, z in zip(Ps, xs, ys, zs):
+        p.forward(x, out=y)
+        p.adjoint(y, out=z)
+    plan = BatchPlan(Ps, zs, ys, tile=64, block=256)
+    torch.cuda.synchronize()
+    e = _events(3)
+    e[0].record()
+    for p, y, z in zip(Ps, ys, zs):
+        p.adjoint(y, out=z)
+    e[1].record()
+    plan.backproject()
+    e[2].record()
+    e[2].synchronize()
+    print(f"uneven_16: plain adjoints {e[0].elapsed_time(e[1]):.3f} ms, one plan {e[1].elapsed_time(e[2]):.3f} ms")
+
+
+CASES = {"cone_384": case_cone_384, "uneven_16": case_uneven_16}
+
+
+# the other scan configurations measured in the default run, with the same K and W (the
+# 3D scans at most PER_CONFIG_3D_STEPS timed steps) and a shorter oracle sample
+PER_CONFIG = ("par2d_64", "par3d_256_tilt", "cone_512", "helix_512x256", "fans_uneven_64")
+PER_CONFIG_3D_STEPS = 20
+PER_CONFIG_CPU_S = 5.0
+
+
+def per_config(args, rank, world, local_rank):
+    import copy
+
+    import torch
+    res = {}
+    for wl in PER_CONFIG:
+        a = copy.copy(args)
+        a.workload = wl
+        if wl in ("cone_512", "helix_512x256"):
+            a.steps = min(args.steps, PER_CONFIG_3D_STEPS)
+        if wl == "fans_uneven_64":
+            a.tile = a.plan_block = 0
+        t0 = time.perf_counter()
+        r = run_ours(a, rank, world, local_rank, workload=wl, cpu_budget=PER_CONFIG_CPU_S)
+        r["bench_wall_s"] = round(time.perf_counter() - t0, 1)
+        for k in ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data"):
+            r.pop(k, None)
+        res[wl] = r
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 100; 5 for the 3D scans)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fan2d_512x16", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="one workload only (default: the fan-beam headline plus every other scan "
+                         "configuration under extra.per_config)")
+    ap.add_argument("--no-per-config", action="store_true", help="the headline workload only")
+    ap.add_argument("--case", default=None, help="run one profiling case (%s) and exit" % ", ".join(
+        ["cone_384", "uneven_16"]))
     ap.add_argument("--adjoint", default=None, choices=["gather", "scatter"],
                     help="adjoint method (default: the gather for 2D batches and single-tilt-axis "
                          "parallel scans, the scatter elsewhere)")
@@ -728,6 +896,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    all_configs = args.workload is None and not args.no_per_config
+    if args.workload is None:
+        args.workload = "fan2d_512x16"
     if args.steps is None:
         args.steps = 5 if args.workload in ("par3d_256_tilt", "cone_512", "helix_512x256") else 100
 
@@ -742,6 +913,11 @@ def main():
         return
 
     import torch
+    if args.case:
+        import __graft_entry__
+        __graft_entry__.build()
+        CASES[args.case]()
+        return
     if world > 1:
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
@@ -753,6 +929,8 @@ def main():
     if rank != 0:
         __graft_entry__.build()  # up to date by now: only checks and imports
     out = run_ours(args, rank, world, local_rank)
+    if all_configs:
+        out.setdefault("extra", {})["per_config"] = per_config(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

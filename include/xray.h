@@ -306,9 +306,10 @@ xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream);
  * current); make that first call before any stream capture.  Each call rewrites the work
  * list and zeroes the counter, stream-ordered; calls that overlap on the GPU race on the
  * shared array, so order them (one stream, or events).
+ * Every problem's geometry must have been created on the current device.
  * tile: rays per work item (32..65536, multiple of 32; 0 = 256).
  * Errors: XR_ERR_NULL, XR_ERR_SIZE (n < 1), XR_ERR_CAPACITY (n > XR_NOALLOC_MAX_PROBLEMS),
- * XR_ERR_ARG, XR_ERR_ALIGN, XR_ERR_CUDA. */
+ * XR_ERR_ARG (tile out of range, or a geometry of another device), XR_ERR_ALIGN, XR_ERR_CUDA. */
 #define XR_NOALLOC_MAX_PROBLEMS 256
 xr_status xr_project_batched_noalloc(const xr_problem *probs, int32_t n, int32_t tile,
                                      xr_stream stream);

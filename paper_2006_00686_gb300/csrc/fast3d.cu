@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(const RayRec *__restrict__ r
                                                     int nx, int ny, int nz, const float *__restrict__ img,
                                                     const float *__restrict__ imgT, float *__restrict__ sino, int *err)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // no wrap near 2^31
     if (t >= n_rays) return;
-    const int r = ord.ray(t);
+    const int r = ord.ray((int)t);  // t < n_rays < 2^31
     sino[r] = fwd_ray<U>(rays[r], nx, ny, nz, img, imgT, err);
 }
 
@@ -196,9 +196,9 @@ __global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict
                                                         int nx, int ny, int nz, const float *__restrict__ sino,
                                                         float *__restrict__ out, float *__restrict__ accT, int *err)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // no wrap near 2^31
     if (t >= n_rays) return;
-    const int r = ord.ray(t);
+    const int r = ord.ray((int)t);  // t < n_rays < 2^31
     const float g = __ldg(sino + r);
     if (g != 0.f) scatter_ray<U>(rays[r], g, nx, ny, nz, out, accT, err);
 }
@@ -210,9 +210,9 @@ __global__ void __launch_bounds__(256) fwd3dz_kernel(const RayRec *__restrict__ 
                                                      int nx, int ny, int nz, const float *__restrict__ imgZ,
                                                      float *__restrict__ sino, int *err)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // no wrap near 2^31
     if (t >= n_threads) return;
-    const int r = ord.ray(t);
+    const int r = ord.ray((int)t);  // t < n_threads < 2^31
     if (r < 0) return;
     const RayRec rr = rays[r];
     const int sx = nz, sy = nx * nz;
@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(256) scatter3dz_kernel(const RayRec *__restric
                                                          const float *__restrict__ sino, float *__restrict__ accZ,
                                                          int *err)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // no wrap near 2^31
     if (t >= n_threads) return;
-    const int r = ord.ray(t);
+    const int r = ord.ray((int)t);  // t < n_threads < 2^31
     if (r < 0) return;
     const float g = __ldg(sino + r);
     if (g == 0.f) return;
