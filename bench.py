@@ -330,6 +330,7 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
 
     def make_step(xb, yb, zb):
         def step(recs=None):
+            stream = torch.cuda.current_stream()  # the capture stream inside graphed()
             e = _events(4) if recs is not None else None
             if e: e[0].record(stream)
             P.ray_setup(stream)
@@ -360,9 +361,9 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
 
         def replay(recs=None):
             e = _events(2) if recs is not None else None
-            if e: e[0].record(stream)
+            if e: e[0].record()
             gr.replay()
-            if e: e[1].record(stream)
+            if e: e[1].record()
             if recs is not None:
                 recs.append(e)
         return replay

@@ -125,9 +125,10 @@ typedef struct {
                               [view][row][col]; XR_ORDER_ROW: (row, view, col), so the rays in
                               flight share detector rows across views; XR_ORDER_COLUMN: (view,
                               col, row) on a z-fastest copy; XR_ORDER_ROWBLOCK: the same in
-                              blocks of 32 rows; XR_ORDER_AUTO (the default): ROWBLOCK for
-                              circular cones, for helices VIEW forward and COLUMN adjoint, VIEW
-                              otherwise */
+                              blocks of 32 rows; XR_ORDER_TRACE: the column-trace walk of cone
+                              and helical scans; XR_ORDER_AUTO (the default): TRACE where it
+                              applies, else ROWBLOCK for circular cones, for helices VIEW forward
+                              and COLUMN adjoint, VIEW otherwise */
 } xr_tuning;
 
 enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
@@ -139,7 +140,18 @@ enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
 /* XR_ORDER_ROWBLOCK: as XR_ORDER_COLUMN, with the rows taken in blocks of 32 across every
  * view and column before the next block, so that the rays in flight in a circular cone scan
  * cross one slab of z. */
-enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2, XR_ORDER_COLUMN = 3, XR_ORDER_ROWBLOCK = 4 };
+/* XR_ORDER_TRACE (cone and helical scans): the column-trace walk.  The rays of one detector
+ * column in one view lie in one vertical plane; a CTA computes that plane's xy crossings once
+ * (the (i, j) columns of voxels it crosses, in order) and its lanes, one per row, walk them in
+ * lockstep with only their own z crossings, on a z-fastest copy of the volume with a zero voxel
+ * above and below every column (workspace 4 * nx * ny * (nz + 2) bytes).  Ray records are not
+ * used: the rays are rebuilt in the kernel from per-view, per-column and per-sample tables.
+ * Applies when every row crosses at most one z plane while the plane's trace crosses one (x, y)
+ * cell (max |rise per horizontal distance| x cell diagonal < 0.99 dz), nx + ny <= 5998, and
+ * nx * ny * (nz + 2) < 2^31; XR_ORDER_AUTO takes it whenever it applies.  The adjoint is a
+ * scatter whose lanes first sum equal voxels with warp shuffles (rows closer than a voxel). */
+enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2, XR_ORDER_COLUMN = 3, XR_ORDER_ROWBLOCK = 4,
+       XR_ORDER_TRACE = 5 };
 
 /* Batched paths.  TILED: a CTA stages a 32x32 tile of up to 16 images in shared memory and
  * walks every ray of a group of views through it (2D scans).  INTERLEAVED (the default): the

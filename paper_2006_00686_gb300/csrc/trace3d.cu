@@ -1,0 +1,500 @@
+// Cone and helical scans walked column by column (circular and helical cone beams, flat and
+// equiangular detectors; eq. equispaced_cone_beam, eq. equiangular_cone_beam,
+// eq. Helical_cone_beam_equispaced, eq. Helical_cone_beam_equiangular).
+//
+// Every ray of one detector column in one view starts at the source S and ends on a vertical
+// line of the detector, so all of them lie in one vertical plane.  Measured by the horizontal
+// distance tau along that plane's trace, the rays share the x and y plane crossings: the
+// sequence of (i, j) columns of voxels the trace crosses, with the tau of each crossing, is
+// the same for every row.  Only the z crossings differ per row, and along tau each row's z
+// is linear: z(tau) = z_F + t_z tau, with t_z the row's rise per unit horizontal distance.
+// The physical length inside a voxel is the tau-length times sec = sqrt(1 + t_z^2).
+//
+// A CTA takes one (view, column) and a band of rows (one lane per row):
+//   1. the trace: the xy-plane crossings of the vertical plane inside the image box, merged
+//      in tau order -- each crossing's rank in the merge is its index plus the number of
+//      crossings of the other family before it, so every thread places its crossings
+//      independently -- into a shared list of slabs (tau at the slab's end, column offset);
+//   2. every lane walks the shared list in lockstep with the others: per slab, the voxel
+//      index at the slab's two ends is floor(u_z) at those tau (a row crosses at most one
+//      z plane per slab -- the host admits a scan only when max |t_z| x the longest slab
+//      stays below one voxel), the z plane crossed inside the slab splits it into two
+//      voxels A (entered) and B (left), and their lengths are C_up - C_low of eq.
+//      conditions_3D_1 with the slab's xy planes and the z plane as the entering and leaving
+//      planes.  A voxel with a zero length contributes nothing (the condition C_low < C_up).
+// The lanes of a warp are neighbouring rows: at every slab they touch one (i, j) column of
+// the z-fastest volume copy, at neighbouring heights, so their loads (forward) or
+// reductions (adjoint) fall on a few neighbouring sectors.  The copy has one zero voxel above
+// and below each column: a row outside the volume in z is clamped onto them, so rows that
+// enter or leave through the top or bottom face need no extra test.
+//
+// The adjoint adds g * sec * length into a z-fastest accumulator.  With AGG, lanes whose B
+// voxels coincide (rows closer than one voxel) first sum their values with a segmented
+// shuffle reduction, and only the first lane of each run issues the reduction: the rows are
+// ordered, so equal voxels are neighbouring lanes.
+//
+// Every geometric quantity of the trace and of a row is computed here from per-view,
+// per-column and per-detector-sample tables (no per-ray table): the trace in double
+// precision, the walk in float with the integer parts of the foot point kept apart.
+#include <algorithm>
+
+#include "xray_internal.h"
+
+namespace xr {
+
+namespace {
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic (rounded down) holds floor(x) in its low bits
+constexpr int kMagicBits = 0x4B400000;
+
+// floor(w) for |w| < 2^22: the float kMagic + floor(w) (exact), whose bit pattern is
+// kMagicBits + floor(w).
+__device__ __forceinline__ float magic_floor(float w) { return __fadd_rd(w, kMagic); }
+
+struct Trace {
+    float tin, tout;
+    int nslab;
+};
+
+// Number of crossings of one family (plane tau = fma(q0 + a s, inv, b), a = 0, 1, ...)
+// strictly before T, within [0, n]: an estimate from the spacing, then exact comparisons of
+// the same expressions the list is built from.
+__device__ __forceinline__ int count_before(float T, float q0, float s, float inv, float b, int n, bool or_equal)
+{
+    if (n <= 0) return 0;
+    const float t0 = __fmaf_rn(q0, inv, b);
+    const float step = fabsf(inv);
+    int k = 0;
+    if (step > 0.f) {
+        const float e = (T - t0) / step;
+        k = e < 0.f ? 0 : (e > (float)n ? n : (int)e + 1);
+    }
+    // exact: crossing k - 1 before T, crossing k not
+#pragma unroll 1
+    for (int it = 0; it < 8 && k < n; ++it) {
+        const float tk = __fmaf_rn(q0 + (float)k * s, inv, b);
+        if (or_equal ? (tk <= T) : (tk < T)) ++k;
+        else break;
+    }
+#pragma unroll 1
+    for (int it = 0; it < 8 && k > 0; ++it) {
+        const float tk = __fmaf_rn(q0 + (float)(k - 1) * s, inv, b);
+        if (or_equal ? (tk > T) : (tk >= T)) --k;
+        else break;
+    }
+    return k;
+}
+
+// The xy trace of (view, column) in index space as a ray record with a fixed z (w2 = 0):
+// u_x(tau) = o0 + f0 + w0 tau, u_y(tau) = o1 + f1 + w1 tau, tau = horizontal distance from
+// the foot point F (the trace's point closest to the image centre).  Returns false when the
+// trace misses the image.  tauF: distance of F from the source.
+__device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewRec &V, double2 cs, RayRec &r,
+                                             double &tauF)
+{
+    // horizontal direction at angle phi + alpha (angle-sum identities), source S
+    double hx = V.c1 * cs.x - V.s1 * cs.y;
+    double hy = V.s1 * cs.x + V.c1 * cs.y;
+    if (fabs(hx) < 1e-12) {
+        hx = 0.0;
+        hy = hy > 0.0 ? 1.0 : -1.0;
+    } else if (fabs(hy) < 1e-12) {
+        hy = 0.0;
+        hx = hx > 0.0 ? 1.0 : -1.0;
+    }
+    const double Sx = -T.D * V.c1, Sy = -T.D * V.s1;
+    tauF = (T.cx - Sx) * hx + (T.cy - Sy) * hy;
+    const double Fx = Sx + tauF * hx, Fy = Sy + tauF * hy;
+    // a trace farther from the centre than the image's half-diagonal misses it
+    const double dxF = Fx - T.cx, dyF = Fy - T.cy;
+    if (dxF * dxF + dyF * dyF > T.rxy2) return false;
+    const double u[2] = {(Fx - T.x0) * T.idx, (T.y1 - Fy) * T.idy};
+    const double w[2] = {hx * T.idx, -hy * T.idy};
+    const int N[2] = {T.nx, T.ny};
+    float wf[2], ff[2];
+    int oi[2];
+    int flags = 0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const double fl = floor(u[a]);
+        if (w[a] == 0.0) {
+            // the trace lies in one family of planes: the unit holding it, the bigger index on a
+            // plane, the last unit on the far edge (Section 4.1)
+            wf[a] = 0.f;
+            ff[a] = 0.f;
+            if (u[a] < 0.0 || u[a] > (double)N[a]) {
+                flags |= RAY_MISS;
+                oi[a] = 0;
+            } else {
+                oi[a] = min((int)fl, N[a] - 1);
+            }
+        } else {
+            wf[a] = (float)w[a];
+            float fr = (float)(u[a] - fl);
+            int o = (int)fl;
+            if (fr >= 1.0f) {
+                fr = 0.0f;
+                ++o;
+            }
+            ff[a] = fr;
+            oi[a] = o;
+        }
+    }
+    r.w0 = wf[0];
+    r.w1 = wf[1];
+    r.w2 = 0.f;
+    r.f0 = ff[0];
+    r.f1 = ff[1];
+    r.f2 = 0.f;
+    r.o0 = (int16_t)oi[0];
+    r.o1 = (int16_t)oi[1];
+    r.o2 = 0;
+    r.flags = (int16_t)flags;
+    return !(flags & RAY_MISS);
+}
+
+// Build the shared slab list of one trace: tend[s] = tau at the end of slab s, off[s] = the
+// z-fastest offset of its (i, j) column (i * SX + j * SY).  Slab 0 starts at tr.tin.  All
+// threads of the CTA take part; ends with a CTA barrier.
+__device__ void build_trace(const TraceGeo &T, const RayRec &r, float *tend, int *off, Trace &tr)
+{
+    const int SX = T.nz + 2, SY = T.nx * (T.nz + 2);
+    Dda<int> D;
+    tr.nslab = 0;
+    tr.tin = tr.tout = 0.f;
+    if (!dda_setup_box<int>(r, 0, T.nx, 0, T.ny, 0, 1, SX, SY, 0, D)) return;
+    tr.tin = D.tcur;
+    tr.tout = D.tout;
+    // crossings of each family strictly inside (tin, tout); the family's plane a is at
+    // fma(q + a s, inv, b)
+    const float qx = D.q0, sx = D.s0, ix = D.i0, bx = D.b0;
+    const float qy = D.q1, sy = D.s1, iy = D.i1, by = D.b1;
+    const int nxc = sx != 0.f ? count_before(D.tout, qx, sx, ix, bx, T.nx, false) : 0;
+    const int nyc = sy != 0.f ? count_before(D.tout, qy, sy, iy, by, T.ny, false) : 0;
+    const int ns = min(nxc + nyc + 1, T.max_slabs);
+    tr.nslab = ns;
+    // the start column (i0, j0) and its per-crossing steps
+    const int i0 = (D.off % SY) / SX, j0 = D.off / SY;  // D.off = i0 SX + j0 SY
+    const int di = sx > 0.f ? 1 : (sx < 0.f ? -1 : 0), dj = sy > 0.f ? 1 : (sy < 0.f ? -1 : 0);
+    // default entries (a slab list is always complete; this only keeps every offset valid)
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        tend[s] = D.tout;
+        off[s] = D.off;
+    }
+    __syncthreads();
+    auto put = [&](int rank, float t, int a, int b) {
+        if (rank < 0 || rank >= ns) return;
+        const int i = min(max(i0 + di * a, 0), T.nx - 1), j = min(max(j0 + dj * b, 0), T.ny - 1);
+        tend[rank] = t;
+        off[rank] = i * SX + j * SY;
+    };
+    for (int a = threadIdx.x; a < nxc; a += blockDim.x) {
+        const float t = __fmaf_rn(qx + (float)a * sx, ix, bx);
+        const int cy = count_before(t, qy, sy, iy, by, nyc, false);  // x first on ties
+        put(a + cy, t, a, cy);
+    }
+    for (int b = threadIdx.x; b < nyc; b += blockDim.x) {
+        const float t = __fmaf_rn(qy + (float)b * sy, iy, by);
+        const int cx = count_before(t, qx, sx, ix, bx, nxc, true);
+        put(b + cx, t, cx, b);
+    }
+    if (threadIdx.x == 0) put(ns - 1, D.tout, nxc, nyc);
+    __syncthreads();
+}
+
+// One row: u_z(tau) = oz + fz + ez tau (index space, z counting down), clamped to
+// [-0.5, nz + 0.5] so that rows outside the volume read / write the zero voxels of the
+// padded columns.
+struct Row {
+    float ez, fz, iez, bz, lo, hi, sec;
+    int cbase;  // column offset of voxel oz + m: cbase + (kMagicBits + m)
+    bool live;
+};
+
+__device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewRec &V, int view, int col, int row, double tauF)
+{
+    Row R;
+    R.live = row < T.n_rows;
+    const double tz = R.live ? T.tz[(size_t)row * T.n_cols + col] : 0.0;
+    // a row this far from the volume (2^20 voxels) cannot reach it within the trace (|u_z|
+    // changes by less than nx + ny along it); bounding u_z keeps every w below 2^22, the range
+    // of magic_floor
+    const double uz = fmin(fmax((T.z1 - (V.H + tz * tauF)) * T.idz, -1048576.0), 1048576.0);
+    float ez = (float)(-tz * T.idz);
+    if (fabsf(ez) < 1e-20f) ez = 0.f;
+    int oz;
+    float fz;
+    if (!R.live || ez == 0.f) {
+        // a horizontal row keeps one voxel: the bigger index on a plane, the last voxel on the
+        // bottom face (Section 4.1); outside the volume, the zero voxel above the column
+        oz = (!R.live || uz < 0.0 || uz > (double)T.nz) ? -1 : min((int)floor(uz), T.nz - 1);
+        fz = 0.5f;
+        ez = 0.f;
+    } else {
+        const double fl = floor(uz);
+        oz = (int)fl;
+        fz = (float)(uz - fl);
+        if (fz >= 1.0f) {
+            fz = 0.f;
+            ++oz;
+        }
+    }
+    R.ez = ez;
+    R.fz = fz;
+    R.iez = ez != 0.f ? __frcp_rn(ez) : 0.f;
+    R.bz = ez != 0.f ? __fmul_rn(-fz, R.iez) : -INFINITY;
+    R.lo = -0.5f - (float)oz;
+    R.hi = (float)(T.nz - oz) + 0.5f;
+    R.sec = R.live ? (float)sqrt(1.0 + tz * tz) : 0.f;
+    R.cbase = oz + 1 - kMagicBits;
+    return R;
+}
+
+// The voxel of the row at tau: the magic float of floor(w) (w = u_z - oz, clamped).
+__device__ __forceinline__ float row_floor(const Row &R, float tau)
+{
+    const float w = fminf(fmaxf(__fmaf_rn(R.ez, tau, R.fz), R.lo), R.hi);
+    return magic_floor(w);
+}
+
+// One slab [ta, tb] of column offset oxy: voxels A (at ta) and B (at tb), their offsets and
+// lengths (in tau).  ma / mb: the magic floats of the voxel index at ta / tb.
+__device__ __forceinline__ void slab_split(const Row &R, float ta, float tb, float ma, float mb, int oxy, int &oA,
+                                           int &oB, float &lA, float &lB)
+{
+    // the z plane crossed inside the slab: the upper of the two voxel indices (the
+    // plane between voxels m and m + 1 is u_z = m + 1 when going down, m when going up:
+    // both are max(ma, mb) with m measured from oz); no crossing puts it outside [ta, tb]
+    const float pf = fmaxf(ma, mb) - kMagic;
+    const float tx = fminf(fmaxf(__fmaf_rn(pf, R.iez, R.bz), ta), tb);
+    lA = __fsub_rn(tx, ta);
+    lB = __fsub_rn(tb, tx);
+    oA = oxy + R.cbase + __float_as_int(ma);
+    oB = oxy + R.cbase + __float_as_int(mb);
+}
+
+template <int U>
+__global__ void __launch_bounds__(128) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
+                                                        float *__restrict__ sino)
+{
+    extern __shared__ float sh[];
+    float *tend = sh;
+    int *off = reinterpret_cast<int *>(sh + T.max_slabs);
+    const int64_t cta = blockIdx.x;
+    const int col = (int)(cta % T.n_cols);
+    const int64_t rest = cta / T.n_cols;
+    const int view = (int)(rest % T.n_views), band = (int)(rest / T.n_views);
+    const ViewRec V = T.views[view];
+    RayRec r;
+    double tauF = 0.0;
+    const bool hit = trace_record(T, V, T.cols[col], r, tauF);
+    Trace tr{0.f, 0.f, 0};
+    if (hit) build_trace(T, r, tend, off, tr);  // hit is uniform over the CTA
+    const int row = band * blockDim.x + threadIdx.x;
+    if (row >= T.n_rows) return;
+    float acc = 0.f;
+    if (tr.nslab > 0) {
+        const Row R = make_row(T, V, view, col, row, tauF);
+        float ta = tr.tin, ma = row_floor(R, ta);
+        int s = 0;
+        for (; s + U <= tr.nslab; s += U) {
+            int oA[U], oB[U];
+            float lA[U], lB[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float tb = tend[s + u];
+                const float mb = row_floor(R, tb);
+                slab_split(R, ta, tb, ma, mb, off[s + u], oA[u], oB[u], lA[u], lB[u]);
+                ta = tb;
+                ma = mb;
+            }
+            float vA[U], vB[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                vA[u] = __ldg(volZ + oA[u]);
+                vB[u] = __ldg(volZ + oB[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc = __fmaf_rn(vB[u], lB[u], __fmaf_rn(vA[u], lA[u], acc));
+        }
+        for (; s < tr.nslab; ++s) {
+            const float tb = tend[s];
+            const float mb = row_floor(R, tb);
+            int oA, oB;
+            float lA, lB;
+            slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
+            acc = __fmaf_rn(__ldg(volZ + oB), lB, __fmaf_rn(__ldg(volZ + oA), lA, acc));
+            ta = tb;
+            ma = mb;
+        }
+        acc = __fmul_rn(acc, R.sec);
+    }
+    sino[((int64_t)view * T.n_rows + row) * T.n_cols + col] = acc;
+}
+
+// Segmented sum over runs of equal keys in neighbouring lanes (keys are ordered by lane):
+// the first lane of each run ends with the run's sum.  runs: an upper bound on a run's length
+// for the whole warp.
+__device__ __forceinline__ float run_sum(float v, int key, int lane, int runs)
+{
+    for (int d = 1; d < runs; d <<= 1) {
+        const float o = __shfl_down_sync(0xffffffffu, v, d);
+        const int k = __shfl_down_sync(0xffffffffu, key, d);
+        if (lane + d < 32 && k == key) v += o;
+    }
+    return v;
+}
+
+template <bool AGG>
+__global__ void __launch_bounds__(128) trace_adj_kernel(TraceGeo T, const float *__restrict__ sino,
+                                                        float *__restrict__ accZ)
+{
+    extern __shared__ float sh[];
+    float *tend = sh;
+    int *off = reinterpret_cast<int *>(sh + T.max_slabs);
+    const int64_t cta = blockIdx.x;
+    const int col = (int)(cta % T.n_cols);
+    const int64_t rest = cta / T.n_cols;
+    const int view = (int)(rest % T.n_views), band = (int)(rest / T.n_views);
+    const ViewRec V = T.views[view];
+    RayRec r;
+    double tauF = 0.0;
+    const bool hit = trace_record(T, V, T.cols[col], r, tauF);
+    Trace tr{0.f, 0.f, 0};
+    if (hit) build_trace(T, r, tend, off, tr);
+    if (tr.nslab == 0) return;  // uniform over the CTA
+    const int lane = threadIdx.x & 31;
+    const int row = band * blockDim.x + threadIdx.x;
+    const Row R = make_row(T, V, view, col, row, tauF);
+    const float g = R.live ? __ldg(sino + ((int64_t)view * T.n_rows + row) * T.n_cols + col) : 0.f;
+    const float gs = __fmul_rn(g, R.sec);
+    // longest run of lanes in one voxel: neighbouring rows are at least `pitch` apart in u_z
+    // over the whole trace (the gap is linear in tau, so its ends bound it)
+    int runs = 32;
+    if (AGG) {
+        const float w0 = __fmaf_rn(R.ez, tr.tin, R.fz) - R.lo, w1 = __fmaf_rn(R.ez, tr.tout, R.fz) - R.lo;
+        const float n0 = __shfl_down_sync(0xffffffffu, w0, 1), n1 = __shfl_down_sync(0xffffffffu, w1, 1);
+        float pitch = (lane < 31 && row + 1 < T.n_rows) ? fminf(fabsf(n0 - w0), fabsf(n1 - w1)) : INFINITY;
+        if ((n0 - w0) * (n1 - w1) <= 0.f && lane < 31 && row + 1 < T.n_rows) pitch = 0.f;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) pitch = fminf(pitch, __shfl_xor_sync(0xffffffffu, pitch, d));
+        runs = pitch > 0.04f ? min(32, 2 + (int)(1.0f / pitch)) : 32;
+    }
+    float ta = tr.tin, ma = row_floor(R, ta);
+    for (int s = 0; s < tr.nslab; ++s) {
+        const float tb = tend[s];
+        const float mb = row_floor(R, tb);
+        int oA, oB;
+        float lA, lB;
+        slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
+        if (lA > 0.f && gs != 0.f) red_add(accZ + oA, __fmul_rn(gs, lA));
+        float vB = __fmul_rn(gs, lB);
+        if (AGG) {
+            vB = run_sum(vB, oB, lane, runs);
+            const int kp = __shfl_up_sync(0xffffffffu, oB, 1);
+            if ((lane == 0 || kp != oB) && vB != 0.f) red_add(accZ + oB, vB);
+        } else if (vB != 0.f) {
+            red_add(accZ + oB, vB);
+        }
+        ta = tb;
+        ma = mb;
+    }
+}
+
+// out[p * ld + 1 + k] = in[k * cols + p] for a [rows = nz][cols = nx ny] volume, and the two
+// zero voxels out[p * ld] and out[p * ld + nz + 1] of every column (ld = nz + 2).
+__global__ void __launch_bounds__(256) to_zpad_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                                      int64_t rows, int64_t cols)
+{
+    __shared__ float tile[32][33];
+    const int64_t ld = rows + 2;
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int64_t row_tiles = (rows + 31) / 32;
+    for (int64_t ty = blockIdx.y; ty < row_tiles; ty += gridDim.y) {
+        const int64_t r0 = ty * 32;
+        for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
+            const int64_t r = r0 + dr, c = c0 + threadIdx.x;
+            if (r < rows && c < cols) tile[dr][threadIdx.x] = in[r * cols + c];
+        }
+        __syncthreads();
+        for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
+            const int64_t c = c0 + dc, r = r0 + threadIdx.x;
+            if (r < rows && c < cols) {
+                out[c * ld + 1 + r] = tile[threadIdx.x][dc];
+                if (r == 0) out[c * ld] = 0.f;
+                if (r == rows - 1) out[c * ld + rows + 1] = 0.f;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// out[k * cols + p] = acc[p * ld + 1 + k] (the padding voxels are dropped)
+__global__ void __launch_bounds__(256) from_zpad_kernel(const float *__restrict__ acc, float *__restrict__ out,
+                                                        int64_t rows, int64_t cols)
+{
+    __shared__ float tile[32][33];
+    const int64_t ld = rows + 2;
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int64_t row_tiles = (rows + 31) / 32;
+    for (int64_t ty = blockIdx.y; ty < row_tiles; ty += gridDim.y) {
+        const int64_t r0 = ty * 32;
+        for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
+            const int64_t c = c0 + dc, r = r0 + threadIdx.x;
+            if (r < rows && c < cols) tile[dc][threadIdx.x] = acc[c * ld + 1 + r];
+        }
+        __syncthreads();
+        for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
+            const int64_t r = r0 + dr, c = c0 + threadIdx.x;
+            if (r < rows && c < cols) out[r * cols + c] = tile[threadIdx.x][dr];
+        }
+        __syncthreads();
+    }
+}
+
+#ifndef XR_TRACE_AHEAD
+#define XR_TRACE_AHEAD 4
+#endif
+#ifndef XR_TRACE_AGG
+#define XR_TRACE_AGG 1
+#endif
+
+dim3 zpad_grid(int64_t rows, int64_t cols)
+{
+    return dim3((unsigned)((cols + 31) / 32), (unsigned)std::min<int64_t>((rows + 31) / 32, 65535));
+}
+
+size_t trace_smem(const TraceGeo &T) { return (size_t)T.max_slabs * (sizeof(float) + sizeof(int)); }
+
+}  // namespace
+
+size_t trace_ws_bytes(const GeoParams &g) { return (size_t)g.nx * g.ny * (size_t)(g.nz + 2) * sizeof(float); }
+
+cudaError_t launch_trace_project(const TraceGeo &T, const float *img, float *ws, float *sino, cudaStream_t s)
+{
+    const int64_t cols = (int64_t)T.nx * T.ny;
+    to_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(img, ws, T.nz, cols);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t ctas = (int64_t)T.n_cols * T.n_views * T.n_bands;
+    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, T.rows_per_cta, trace_smem(T), s>>>(T, ws, sino);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_backproject(const TraceGeo &T, const float *sino, float *img, float *ws, cudaStream_t s)
+{
+    const int64_t cols = (int64_t)T.nx * T.ny;
+    cudaError_t e = cudaMemsetAsync(ws, 0, (size_t)cols * (T.nz + 2) * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    const int64_t ctas = (int64_t)T.n_cols * T.n_views * T.n_bands;
+    if (XR_TRACE_AGG)
+        trace_adj_kernel<true><<<(unsigned)ctas, T.rows_per_cta, trace_smem(T), s>>>(T, sino, ws);
+    else
+        trace_adj_kernel<false><<<(unsigned)ctas, T.rows_per_cta, trace_smem(T), s>>>(T, sino, ws);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    from_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(ws, img, T.nz, cols);
+    return cudaGetLastError();
+}
+
+}  // namespace xr

@@ -204,13 +204,80 @@ static bool use_slices(const xr_geometry *g)
            (g->params.n_cols + 3) / 4 <= 65535;  // planes index gridDim.y
 }
 
+// The column-trace walk of cone and helical scans (workspace: the padded z-fastest copy).
+static bool use_trace(const xr_geometry *g)
+{
+    return g->trace_ok && g->tune.path != XR_PATH_RAY && g->d_ws && g->ws_bytes >= trace_ws_bytes(g->params) &&
+           (g->tune.order == XR_ORDER_AUTO || g->tune.order == XR_ORDER_TRACE);
+}
+
 static size_t reserve_bytes(const xr_geometry *g, int batch)
 {
     if (kind_is3d(g->params.kind) || batch < 4) {
-        const size_t one = (size_t)g->n_units * sizeof(float);
+        size_t one = (size_t)g->n_units * sizeof(float);
+        if (g->trace_ok) one = std::max(one, trace_ws_bytes(g->params));
         return g->slices.ok ? std::max(one, slice_ws_bytes(g)) : one;
     }
     return fast_ws_bytes(g, batch);  // >= n_units floats: serves the single-image path too
+}
+
+// Cone and helical scans: the column-trace walk's tables (per column: cos / sin of the fan
+// angle; per detector sample: the row's rise per unit horizontal distance) and whether the
+// walk applies: every row crosses at most one z plane per xy slab (a slab is at most the
+// (dx, dy) cell's diagonal long), the slab list fits 48 KiB of shared memory, and offsets of
+// the padded z-fastest copy fit 32 bits.  Flat detectors: tan(alpha) = u / sdd and
+// t_z = v / sqrt(sdd^2 + u^2) (eq. equispaced_cone_beam with t = u sod/sdd, h = v sod/sdd);
+// equiangular detectors: alpha = u, t_z = tan(v) (eq. equiangular_cone_beam).
+static bool kind_cone(int k) { return k >= XR_CONE && k <= XR_HELIX_ARC; }
+
+static bool trace_tables(const GeoParams &p, std::vector<double2> &cols, std::vector<double> &tz, TraceGeo &T)
+{
+    if (!kind_cone(p.kind)) return false;
+    const bool flat = (p.kind == XR_CONE || p.kind == XR_HELIX);
+    cols.resize((size_t)p.n_cols);
+    tz.resize((size_t)p.n_rows * p.n_cols);
+    double tzmax = 0.0;
+    for (int c = 0; c < p.n_cols; ++c) {
+        const double u = (c - 0.5 * (p.n_cols - 1)) * p.du + p.u0;
+        if (flat) {
+            const double h = sqrt(p.sdd * p.sdd + u * u);
+            cols[(size_t)c] = make_double2(p.sdd / h, u / h);
+        } else {
+            cols[(size_t)c] = make_double2(cos(u), sin(u));
+        }
+        for (int r = 0; r < p.n_rows; ++r) {
+            const double v = (r - 0.5 * (p.n_rows - 1)) * p.dv + p.v0;
+            const double t = flat ? v / sqrt(p.sdd * p.sdd + u * u) : tan(v);
+            tz[(size_t)r * p.n_cols + c] = t;
+            tzmax = std::max(tzmax, fabs(t));
+        }
+    }
+    const double slab_z = tzmax * sqrt(p.dx * p.dx + p.dy * p.dy) / p.dz;
+    if (!(slab_z < 0.99)) return false;
+    if ((int64_t)p.nx + p.ny + 2 > 6000) return false;  // 8 B per slab in 48 KiB
+    if ((int64_t)p.nx * p.ny * (p.nz + 2) >= ((int64_t)1 << 31)) return false;
+    T.nx = p.nx;
+    T.ny = p.ny;
+    T.nz = p.nz;
+    T.n_views = p.n_views;
+    T.n_rows = p.n_rows;
+    T.n_cols = p.n_cols;
+    T.rows_per_cta = p.n_rows > 64 ? 128 : (p.n_rows > 32 ? 64 : 32);
+    T.n_bands = (p.n_rows + T.rows_per_cta - 1) / T.rows_per_cta;
+    if ((int64_t)p.n_cols * p.n_views * T.n_bands >= ((int64_t)1 << 31)) return false;
+    T.max_slabs = p.nx + p.ny + 2;
+    T.x0 = p.cx - 0.5 * p.nx * p.dx;
+    T.y1 = p.cy + 0.5 * p.ny * p.dy;
+    T.z1 = p.cz + 0.5 * p.nz * p.dz;
+    T.idx = p.inv_dx;
+    T.idy = p.inv_dy;
+    T.idz = p.inv_dz;
+    T.cx = p.cx;
+    T.cy = p.cy;
+    T.D = p.sod;
+    const double rxy = 0.5 * sqrt(pow(p.nx * p.dx, 2) + pow(p.ny * p.dy, 2)) + 1e-6 * (p.dx + p.dy);
+    T.rxy2 = rxy * rxy;
+    return true;
 }
 
 // Rebuild the 2D column problem's ray records from the 3D ray table.
@@ -305,6 +372,21 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
         if (e == cudaSuccess)
             e = cudaMemcpy(g->d_slice_of, g->slices.slice_of.data(), g->slices.slice_of.size() * sizeof(int),
                            cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && three) {
+        std::vector<double2> cols;
+        std::vector<double> tz;
+        g->trace_ok = trace_tables(p, cols, tz, g->trace);
+        if (g->trace_ok) {
+            e = cudaMalloc(&g->d_tcols, cols.size() * sizeof(double2));
+            if (e == cudaSuccess) e = cudaMalloc(&g->d_tz, tz.size() * sizeof(double));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(g->d_tcols, cols.data(), cols.size() * sizeof(double2), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(g->d_tz, tz.data(), tz.size() * sizeof(double), cudaMemcpyHostToDevice);
+            g->trace.views = g->d_views;
+            g->trace.cols = g->d_tcols;
+            g->trace.tz = g->d_tz;
+        }
     }
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
@@ -409,6 +491,8 @@ void xr_geometry_destroy(xr_geometry *g)
     cudaFree(g->d_grec2);
     cudaFree(g->d_vt2);
     cudaFree(g->d_slice_of);
+    cudaFree(g->d_tcols);
+    cudaFree(g->d_tz);
     cudaSetDevice(prev);
     delete g;
 }
@@ -468,7 +552,8 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
     info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * (8 * 4 + sizeof(ViewRec) + sizeof(ViewDF)) +
                         (int64_t)g->params.n_rows * g->params.n_cols * (int64_t)sizeof(DetRec) +
                         (g->d_grec ? g->n_rays * (int64_t)gather_rec_bytes() : 0) + (int64_t)g->ws_bytes +
-                        (g->slices.ok ? slice_n2(g) * (int64_t)(sizeof(RayRec) + gather_rec_bytes()) : 0);
+                        (g->slices.ok ? slice_n2(g) * (int64_t)(sizeof(RayRec) + gather_rec_bytes()) : 0) +
+                        (g->trace_ok ? (int64_t)g->params.n_cols * (int64_t)(sizeof(double2) + g->params.n_rows * sizeof(double)) : 0);
     info->is3d = kind_is3d(g->params.kind);
     info->device = g->device;
     info->column_batch = g->slices.ok ? 1 : 0;
@@ -497,7 +582,7 @@ xr_status xr_set_tuning(xr_geometry *g, const xr_tuning *t)
         return XR_ERR_ARG;
     if (t->adjoint && t->adjoint != XR_ADJ_SCATTER && t->adjoint != XR_ADJ_GATHER) return XR_ERR_ARG;
     if (t->path < 0 || t->path > XR_PATH_RAY) return XR_ERR_ARG;
-    if (t->order < 0 || t->order > XR_ORDER_ROWBLOCK) return XR_ERR_ARG;
+    if (t->order < 0 || t->order > XR_ORDER_TRACE) return XR_ERR_ARG;
     if (t->order) g->tune.order = t->order;
     if (t->path) g->tune.path = t->path;
     if (t->block) g->tune.block = t->block;
@@ -535,6 +620,13 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
                                          d_sino + (size_t)b * g->n_rays, p.n_cols, plane_nq(g, p.n_cols), s, 1,
                                          p.n_cols));
         }
+        return XR_OK;
+    }
+    if (use_trace(g)) {
+        const cudaStream_t s = (cudaStream_t)stream;
+        for (int b = 0; b < batch; ++b)
+            XR_CUDA(launch_trace_project(g->trace, d_img + (size_t)b * g->n_units, g->d_ws,
+                                         d_sino + (size_t)b * g->n_rays, s));
         return XR_OK;
     }
     if (!use_fast(g, batch) && use_dda(g)) {
@@ -623,6 +715,12 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         return XR_OK;
     }
     if (method != XR_ADJ_SCATTER) return XR_ERR_ARG;
+    if (use_trace(g)) {
+        for (int b = 0; b < batch; ++b)
+            XR_CUDA(launch_trace_backproject(g->trace, d_sino + (size_t)b * g->n_rays, d_img + (size_t)b * g->n_units,
+                                             g->d_ws, s));
+        return XR_OK;
+    }
     if (!use_tiled(g, batch) && !use_fast(g, batch) && use_dda(g)) {
         for (int b = 0; b < batch; ++b)
             XR_CUDA(launch_scatter3d(g->d_rays, g->params, g->n_rays, ray_order(g, true), d_sino + (size_t)b * g->n_rays,

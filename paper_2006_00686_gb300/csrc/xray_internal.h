@@ -207,6 +207,23 @@ cudaError_t launch_atten_plane_adj(const RayRec *rays, int64_t n_rays, int nx, i
                                    size_t acc_bytes, const float *mu0, const float *mu1, const float *sino,
                                    float *img, int batch, int Bp, cudaStream_t s);
 
+// Cone and helical scans walked by detector column (trace3d.cu): the vertical plane of a
+// (view, column) shares its xy crossings among the column's rows.  Built at geometry creation
+// for the cone and helix kinds when every row crosses at most one z plane per xy slab.
+struct TraceGeo {
+    int nx, ny, nz, n_views, n_rows, n_cols;
+    int rows_per_cta;  // one lane per row: a CTA is one (view, column) and a band of rows
+    int n_bands;
+    int max_slabs;     // nx + ny + 2: the slab list's capacity in shared memory
+    double x0, y1, z1, idx, idy, idz, cx, cy, D, rxy2;
+    const ViewRec *views;  // cos / sin of the view angle, source height H
+    const double2 *cols;   // per detector column: cos / sin of its fan angle alpha
+    const double *tz;      // per detector sample [row][col]: rise per unit horizontal distance
+};
+size_t trace_ws_bytes(const GeoParams &g);  // the z-fastest copy with a zero voxel above and below
+cudaError_t launch_trace_project(const TraceGeo &T, const float *img, float *ws, float *sino, cudaStream_t s);
+cudaError_t launch_trace_backproject(const TraceGeo &T, const float *sino, float *img, float *ws, cudaStream_t s);
+
 // Attenuated transform (atten.cu): one thread per ray, `chunk` images per thread; in/out
 // in the caller's layout ([batch][units] / [batch][rays]); the adjoint adds into out.
 cudaError_t launch_attenuated(bool adjoint, const RayRec *rays, int64_t n_rays, const Grid &grid, const float *mu,
@@ -242,4 +259,9 @@ struct xr_geometry {
     void *d_grec2;        // their gather records
     float *d_vt2;         // the 2D gather's view table
     int *d_slice_of;      // column -> slice
+    // cone and helical scans: the column-trace walk (trace3d.cu)
+    bool trace_ok;
+    xr::TraceGeo trace;
+    double2 *d_tcols;     // per detector column (cos, sin) of the fan angle
+    double *d_tz;         // per detector sample, the row's rise per unit horizontal distance
 };

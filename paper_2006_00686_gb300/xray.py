@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libxray.so")
 
 XR_ADJ_AUTO, XR_ADJ_SCATTER, XR_ADJ_GATHER = 0, 1, 2
-XR_ORDER_AUTO, XR_ORDER_VIEW, XR_ORDER_ROW, XR_ORDER_COLUMN, XR_ORDER_ROWBLOCK = 0, 1, 2, 3, 4
+XR_ORDER_AUTO, XR_ORDER_VIEW, XR_ORDER_ROW, XR_ORDER_COLUMN, XR_ORDER_ROWBLOCK, XR_ORDER_TRACE = 0, 1, 2, 3, 4, 5
 XR_PATH_AUTO, XR_PATH_TILED, XR_PATH_INTERLEAVED, XR_PATH_RAY = 0, 1, 2, 3
 
 
