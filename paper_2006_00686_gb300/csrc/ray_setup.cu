@@ -21,68 +21,10 @@
 // values (axis-parallel rays, integer detector offsets) stay exact, so the fixed indices of
 // on-grid rays are found as with exact arithmetic.
 // The view part (cos/sin of the view angle, source height H) comes from the host.
+#include "xray_df.cuh"
 #include "xray_internal.h"
 
 namespace xr {
-
-// ---- float-pair arithmetic (round-to-nearest intrinsics: no contraction or reordering)
-
-__device__ __forceinline__ DF two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return DF{s, e};
-}
-
-// requires |a| >= |b| (or a == 0)
-__device__ __forceinline__ DF quick_two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ DF df_add(DF a, DF b)
-{
-    DF s = two_sum(a.hi, b.hi);
-    const DF t = two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = quick_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
-    return quick_two_sum(s.hi, s.lo);
-}
-
-__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
-__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
-
-__device__ __forceinline__ DF df_mul(DF a, DF b)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
-    return quick_two_sum(p, e);
-}
-
-__device__ __forceinline__ bool df_is_zero(DF a) { return a.hi == 0.f && a.lo == 0.f; }
-
-// Snap cos/sin pairs within 1e-12 of a multiple of pi/2 to exact 0 and +-1, so that
-// axis-parallel and in-plane rays are recognised as such.
-__device__ __forceinline__ void snap(DF &c, DF &s)
-{
-    if (fabsf(c.hi) < 1e-12f) {
-        c = DF{0.f, 0.f};
-        s = DF{s.hi > 0.f ? 1.f : -1.f, 0.f};
-    } else if (fabsf(s.hi) < 1e-12f) {
-        s = DF{0.f, 0.f};
-        c = DF{c.hi > 0.f ? 1.f : -1.f, 0.f};
-    }
-}
-
-__device__ __forceinline__ DF to_df(double x)
-{
-    const float hi = __double2float_rn(x);
-    return DF{hi, __double2float_rn(x - (double)hi)};
-}
 
 __global__ void det_setup_kernel(GeoParams g, DetRec *__restrict__ out)
 {

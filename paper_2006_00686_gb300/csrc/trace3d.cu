@@ -34,10 +34,12 @@
 // ordered, so equal voxels are neighbouring lanes.
 //
 // Every geometric quantity of the trace and of a row is computed here from per-view,
-// per-column and per-detector-sample tables (no per-ray table): the trace in double
-// precision, the walk in float with the integer parts of the foot point kept apart.
+// per-column and per-detector-sample tables (no per-ray table): the trace and the rows' foot
+// points in float pairs (no FP64: its rate on GB300 is a small fraction of FP32), the walk in
+// float with the integer parts of the foot point kept apart.
 #include <algorithm>
 
+#include "xray_df.cuh"
 #include "xray_internal.h"
 
 namespace xr {
@@ -88,56 +90,44 @@ __device__ __forceinline__ int count_before(float T, float q0, float s, float in
 // The xy trace of (view, column) in index space as a ray record with a fixed z (w2 = 0):
 // u_x(tau) = o0 + f0 + w0 tau, u_y(tau) = o1 + f1 + w1 tau, tau = horizontal distance from
 // the foot point F (the trace's point closest to the image centre).  Returns false when the
-// trace misses the image.  tauF: distance of F from the source.
-__device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewRec &V, double2 cs, RayRec &r,
-                                             double &tauF)
+// trace misses the image.  tauF: distance of F from the source.  Float pairs throughout (the
+// foot point's fraction needs about 37 bits).
+__device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V, float4 cs, RayRec &r, DF &tauF)
 {
     // horizontal direction at angle phi + alpha (angle-sum identities), source S
-    double hx = V.c1 * cs.x - V.s1 * cs.y;
-    double hy = V.s1 * cs.x + V.c1 * cs.y;
-    if (fabs(hx) < 1e-12) {
-        hx = 0.0;
-        hy = hy > 0.0 ? 1.0 : -1.0;
-    } else if (fabs(hy) < 1e-12) {
-        hy = 0.0;
-        hx = hx > 0.0 ? 1.0 : -1.0;
-    }
-    const double Sx = -T.D * V.c1, Sy = -T.D * V.s1;
-    tauF = (T.cx - Sx) * hx + (T.cy - Sy) * hy;
-    const double Fx = Sx + tauF * hx, Fy = Sy + tauF * hy;
+    const DF ca{cs.x, cs.y}, sa{cs.z, cs.w};
+    DF hx = df_sub(df_mul(V.c1, ca), df_mul(V.s1, sa));
+    DF hy = df_add(df_mul(V.s1, ca), df_mul(V.c1, sa));
+    snap(hx, hy);
+    const DF Sx = df_neg(df_mul(T.D, V.c1)), Sy = df_neg(df_mul(T.D, V.s1));
+    tauF = df_add(df_mul(df_sub(T.cx, Sx), hx), df_mul(df_sub(T.cy, Sy), hy));
+    const DF Fx = df_add(Sx, df_mul(tauF, hx)), Fy = df_add(Sy, df_mul(tauF, hy));
     // a trace farther from the centre than the image's half-diagonal misses it
-    const double dxF = Fx - T.cx, dyF = Fy - T.cy;
+    const float dxF = df_sub(Fx, T.cx).hi, dyF = df_sub(Fy, T.cy).hi;
     if (dxF * dxF + dyF * dyF > T.rxy2) return false;
-    const double u[2] = {(Fx - T.x0) * T.idx, (T.y1 - Fy) * T.idy};
-    const double w[2] = {hx * T.idx, -hy * T.idy};
+    const DF u[2] = {df_mul(df_sub(Fx, T.x0), T.idx), df_mul(df_sub(T.y1, Fy), T.idy)};
+    const DF w[2] = {df_mul(hx, T.idx), df_neg(df_mul(hy, T.idy))};
     const int N[2] = {T.nx, T.ny};
     float wf[2], ff[2];
     int oi[2];
     int flags = 0;
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-        const double fl = floor(u[a]);
-        if (w[a] == 0.0) {
+        if (df_is_zero(w[a])) {
             // the trace lies in one family of planes: the unit holding it, the bigger index on a
             // plane, the last unit on the far edge (Section 4.1)
             wf[a] = 0.f;
             ff[a] = 0.f;
-            if (u[a] < 0.0 || u[a] > (double)N[a]) {
-                flags |= RAY_MISS;
-                oi[a] = 0;
-            } else {
-                oi[a] = min((int)fl, N[a] - 1);
-            }
+            const bool below = u[a].hi < 0.f || (u[a].hi == 0.f && u[a].lo < 0.f);
+            const bool above = u[a].hi > (float)N[a] || (u[a].hi == (float)N[a] && u[a].lo > 0.f);
+            int fl;
+            float fr;
+            df_floor_frac(u[a], fl, fr);
+            oi[a] = (below || above) ? 0 : min(fl, N[a] - 1);
+            if (below || above) flags |= RAY_MISS;
         } else {
-            wf[a] = (float)w[a];
-            float fr = (float)(u[a] - fl);
-            int o = (int)fl;
-            if (fr >= 1.0f) {
-                fr = 0.0f;
-                ++o;
-            }
-            ff[a] = fr;
-            oi[a] = o;
+            wf[a] = __fadd_rn(w[a].hi, w[a].lo);
+            df_floor_frac(u[a], oi[a], ff[a]);
         }
     }
     r.w0 = wf[0];
@@ -211,33 +201,35 @@ struct Row {
     bool live;
 };
 
-__device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewRec &V, int view, int col, int row, double tauF)
+__device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewDF &V, int col, int row, DF tauF)
 {
     Row R;
     R.live = row < T.n_rows;
-    const double tz = R.live ? T.tz[(size_t)row * T.n_cols + col] : 0.0;
+    const float2 tzp = R.live ? T.tz[(size_t)row * T.n_cols + col] : make_float2(0.f, 0.f);
+    const DF tz{tzp.x, tzp.y};
+    DF uz = df_mul(df_sub(T.z1, df_add(V.H, df_mul(tz, tauF))), T.idz);
     // a row this far from the volume (2^20 voxels) cannot reach it within the trace (|u_z|
     // changes by less than nx + ny along it); bounding u_z keeps every w below 2^22, the range
     // of magic_floor
-    const double uz = fmin(fmax((T.z1 - (V.H + tz * tauF)) * T.idz, -1048576.0), 1048576.0);
-    float ez = (float)(-tz * T.idz);
+    if (fabsf(uz.hi) > 1048576.f) uz = DF{copysignf(1048576.f, uz.hi), 0.f};
+    const DF ezd = df_neg(df_mul(tz, T.idz));
+    float ez = __fadd_rn(ezd.hi, ezd.lo);
     if (fabsf(ez) < 1e-20f) ez = 0.f;
     int oz;
     float fz;
     if (!R.live || ez == 0.f) {
         // a horizontal row keeps one voxel: the bigger index on a plane, the last voxel on the
         // bottom face (Section 4.1); outside the volume, the zero voxel above the column
-        oz = (!R.live || uz < 0.0 || uz > (double)T.nz) ? -1 : min((int)floor(uz), T.nz - 1);
+        const bool below = uz.hi < 0.f || (uz.hi == 0.f && uz.lo < 0.f);
+        const bool above = uz.hi > (float)T.nz || (uz.hi == (float)T.nz && uz.lo > 0.f);
+        int fl;
+        float fr;
+        df_floor_frac(uz, fl, fr);
+        oz = (!R.live || below || above) ? -1 : min(fl, T.nz - 1);
         fz = 0.5f;
         ez = 0.f;
     } else {
-        const double fl = floor(uz);
-        oz = (int)fl;
-        fz = (float)(uz - fl);
-        if (fz >= 1.0f) {
-            fz = 0.f;
-            ++oz;
-        }
+        df_floor_frac(uz, oz, fz);
     }
     R.ez = ez;
     R.fz = fz;
@@ -245,7 +237,7 @@ __device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewRec &V, int
     R.bz = ez != 0.f ? __fmul_rn(-fz, R.iez) : -INFINITY;
     R.lo = -0.5f - (float)oz;
     R.hi = (float)(T.nz - oz) + 0.5f;
-    R.sec = R.live ? (float)sqrt(1.0 + tz * tz) : 0.f;
+    R.sec = R.live ? __fsqrt_rn(__fmaf_rn(tz.hi, tz.hi, 1.0f)) : 0.f;
     R.cbase = oz + 1 - kMagicBits;
     return R;
 }
@@ -284,9 +276,9 @@ __global__ void __launch_bounds__(128) trace_fwd_kernel(TraceGeo T, const float 
     const int col = (int)(cta % T.n_cols);
     const int64_t rest = cta / T.n_cols;
     const int view = (int)(rest % T.n_views), band = (int)(rest / T.n_views);
-    const ViewRec V = T.views[view];
+    const ViewDF V = T.views[view];
     RayRec r;
-    double tauF = 0.0;
+    DF tauF{0.f, 0.f};
     const bool hit = trace_record(T, V, T.cols[col], r, tauF);
     Trace tr{0.f, 0.f, 0};
     if (hit) build_trace(T, r, tend, off, tr);  // hit is uniform over the CTA
@@ -294,7 +286,7 @@ __global__ void __launch_bounds__(128) trace_fwd_kernel(TraceGeo T, const float 
     if (row >= T.n_rows) return;
     float acc = 0.f;
     if (tr.nslab > 0) {
-        const Row R = make_row(T, V, view, col, row, tauF);
+        const Row R = make_row(T, V, col, row, tauF);
         float ta = tr.tin, ma = row_floor(R, ta);
         int s = 0;
         for (; s + U <= tr.nslab; s += U) {
@@ -356,16 +348,16 @@ __global__ void __launch_bounds__(128) trace_adj_kernel(TraceGeo T, const float 
     const int col = (int)(cta % T.n_cols);
     const int64_t rest = cta / T.n_cols;
     const int view = (int)(rest % T.n_views), band = (int)(rest / T.n_views);
-    const ViewRec V = T.views[view];
+    const ViewDF V = T.views[view];
     RayRec r;
-    double tauF = 0.0;
+    DF tauF{0.f, 0.f};
     const bool hit = trace_record(T, V, T.cols[col], r, tauF);
     Trace tr{0.f, 0.f, 0};
     if (hit) build_trace(T, r, tend, off, tr);
     if (tr.nslab == 0) return;  // uniform over the CTA
     const int lane = threadIdx.x & 31;
     const int row = band * blockDim.x + threadIdx.x;
-    const Row R = make_row(T, V, view, col, row, tauF);
+    const Row R = make_row(T, V, col, row, tauF);
     const float g = R.live ? __ldg(sino + ((int64_t)view * T.n_rows + row) * T.n_cols + col) : 0.f;
     const float gs = __fmul_rn(g, R.sec);
     // longest run of lanes in one voxel: neighbouring rows are at least `pitch` apart in u_z

@@ -230,7 +230,12 @@ static size_t reserve_bytes(const xr_geometry *g, int batch)
 // equiangular detectors: alpha = u, t_z = tan(v) (eq. equiangular_cone_beam).
 static bool kind_cone(int k) { return k >= XR_CONE && k <= XR_HELIX_ARC; }
 
-static bool trace_tables(const GeoParams &p, std::vector<double2> &cols, std::vector<double> &tz, TraceGeo &T)
+// rows per CTA of the column-trace walk (32, 64 or 128; one lane per row)
+#ifndef XR_TRACE_ROWS
+#define XR_TRACE_ROWS 128
+#endif
+
+static bool trace_tables(const GeoParams &p, std::vector<float4> &cols, std::vector<float2> &tz, TraceGeo &T)
 {
     if (!kind_cone(p.kind)) return false;
     const bool flat = (p.kind == XR_CONE || p.kind == XR_HELIX);
@@ -239,16 +244,14 @@ static bool trace_tables(const GeoParams &p, std::vector<double2> &cols, std::ve
     double tzmax = 0.0;
     for (int c = 0; c < p.n_cols; ++c) {
         const double u = (c - 0.5 * (p.n_cols - 1)) * p.du + p.u0;
-        if (flat) {
-            const double h = sqrt(p.sdd * p.sdd + u * u);
-            cols[(size_t)c] = make_double2(p.sdd / h, u / h);
-        } else {
-            cols[(size_t)c] = make_double2(cos(u), sin(u));
-        }
+        const double h = sqrt(p.sdd * p.sdd + u * u);
+        const DF ca = df_from_double(flat ? p.sdd / h : cos(u)), sa = df_from_double(flat ? u / h : sin(u));
+        cols[(size_t)c] = make_float4(ca.hi, ca.lo, sa.hi, sa.lo);
         for (int r = 0; r < p.n_rows; ++r) {
             const double v = (r - 0.5 * (p.n_rows - 1)) * p.dv + p.v0;
-            const double t = flat ? v / sqrt(p.sdd * p.sdd + u * u) : tan(v);
-            tz[(size_t)r * p.n_cols + c] = t;
+            const double t = flat ? v / h : tan(v);
+            const DF d = df_from_double(t);
+            tz[(size_t)r * p.n_cols + c] = make_float2(d.hi, d.lo);
             tzmax = std::max(tzmax, fabs(t));
         }
     }
@@ -262,21 +265,21 @@ static bool trace_tables(const GeoParams &p, std::vector<double2> &cols, std::ve
     T.n_views = p.n_views;
     T.n_rows = p.n_rows;
     T.n_cols = p.n_cols;
-    T.rows_per_cta = p.n_rows > 64 ? 128 : (p.n_rows > 32 ? 64 : 32);
+    T.rows_per_cta = p.n_rows > 64 ? XR_TRACE_ROWS : (p.n_rows > 32 ? std::min(64, XR_TRACE_ROWS) : 32);
     T.n_bands = (p.n_rows + T.rows_per_cta - 1) / T.rows_per_cta;
     if ((int64_t)p.n_cols * p.n_views * T.n_bands >= ((int64_t)1 << 31)) return false;
     T.max_slabs = p.nx + p.ny + 2;
-    T.x0 = p.cx - 0.5 * p.nx * p.dx;
-    T.y1 = p.cy + 0.5 * p.ny * p.dy;
-    T.z1 = p.cz + 0.5 * p.nz * p.dz;
-    T.idx = p.inv_dx;
-    T.idy = p.inv_dy;
-    T.idz = p.inv_dz;
-    T.cx = p.cx;
-    T.cy = p.cy;
-    T.D = p.sod;
-    const double rxy = 0.5 * sqrt(pow(p.nx * p.dx, 2) + pow(p.ny * p.dy, 2)) + 1e-6 * (p.dx + p.dy);
-    T.rxy2 = rxy * rxy;
+    T.x0 = df_from_double(p.cx - 0.5 * p.nx * p.dx);
+    T.y1 = df_from_double(p.cy + 0.5 * p.ny * p.dy);
+    T.z1 = df_from_double(p.cz + 0.5 * p.nz * p.dz);
+    T.idx = df_from_double(p.inv_dx);
+    T.idy = df_from_double(p.inv_dy);
+    T.idz = df_from_double(p.inv_dz);
+    T.cx = df_from_double(p.cx);
+    T.cy = df_from_double(p.cy);
+    T.D = df_from_double(p.sod);
+    const double rxy = 0.5 * sqrt(pow(p.nx * p.dx, 2) + pow(p.ny * p.dy, 2)) * (1.0 + 1e-5) + 1e-3 * (p.dx + p.dy);
+    T.rxy2 = (float)(rxy * rxy);
     return true;
 }
 
@@ -374,16 +377,16 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
                            cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && three) {
-        std::vector<double2> cols;
-        std::vector<double> tz;
+        std::vector<float4> cols;
+        std::vector<float2> tz;
         g->trace_ok = trace_tables(p, cols, tz, g->trace);
         if (g->trace_ok) {
-            e = cudaMalloc(&g->d_tcols, cols.size() * sizeof(double2));
-            if (e == cudaSuccess) e = cudaMalloc(&g->d_tz, tz.size() * sizeof(double));
+            e = cudaMalloc(&g->d_tcols, cols.size() * sizeof(float4));
+            if (e == cudaSuccess) e = cudaMalloc(&g->d_tz, tz.size() * sizeof(float2));
             if (e == cudaSuccess)
-                e = cudaMemcpy(g->d_tcols, cols.data(), cols.size() * sizeof(double2), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(g->d_tz, tz.data(), tz.size() * sizeof(double), cudaMemcpyHostToDevice);
-            g->trace.views = g->d_views;
+                e = cudaMemcpy(g->d_tcols, cols.data(), cols.size() * sizeof(float4), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(g->d_tz, tz.data(), tz.size() * sizeof(float2), cudaMemcpyHostToDevice);
+            g->trace.views = g->d_views_df;
             g->trace.cols = g->d_tcols;
             g->trace.tz = g->d_tz;
         }
@@ -553,7 +556,7 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
                         (int64_t)g->params.n_rows * g->params.n_cols * (int64_t)sizeof(DetRec) +
                         (g->d_grec ? g->n_rays * (int64_t)gather_rec_bytes() : 0) + (int64_t)g->ws_bytes +
                         (g->slices.ok ? slice_n2(g) * (int64_t)(sizeof(RayRec) + gather_rec_bytes()) : 0) +
-                        (g->trace_ok ? (int64_t)g->params.n_cols * (int64_t)(sizeof(double2) + g->params.n_rows * sizeof(double)) : 0);
+                        (g->trace_ok ? (int64_t)g->params.n_cols * (int64_t)(sizeof(float4) + g->params.n_rows * sizeof(float2)) : 0);
     info->is3d = kind_is3d(g->params.kind);
     info->device = g->device;
     info->column_batch = g->slices.ok ? 1 : 0;

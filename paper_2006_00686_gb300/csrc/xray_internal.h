@@ -215,10 +215,11 @@ struct TraceGeo {
     int rows_per_cta;  // one lane per row: a CTA is one (view, column) and a band of rows
     int n_bands;
     int max_slabs;     // nx + ny + 2: the slab list's capacity in shared memory
-    double x0, y1, z1, idx, idy, idz, cx, cy, D, rxy2;
-    const ViewRec *views;  // cos / sin of the view angle, source height H
-    const double2 *cols;   // per detector column: cos / sin of its fan angle alpha
-    const double *tz;      // per detector sample [row][col]: rise per unit horizontal distance
+    DF x0, y1, z1, idx, idy, idz, cx, cy, D;  // planes i = 0, j = 0, k = 0; 1/d; centre; sod
+    float rxy2;            // squared xy half-diagonal of the image (with a small margin)
+    const ViewDF *views;   // cos / sin of the view angle, source height H
+    const float4 *cols;    // per detector column: cos / sin of its fan angle alpha (float pairs)
+    const float2 *tz;      // per detector sample [row][col]: rise per unit horizontal distance
 };
 size_t trace_ws_bytes(const GeoParams &g);  // the z-fastest copy with a zero voxel above and below
 cudaError_t launch_trace_project(const TraceGeo &T, const float *img, float *ws, float *sino, cudaStream_t s);
@@ -262,6 +263,6 @@ struct xr_geometry {
     // cone and helical scans: the column-trace walk (trace3d.cu)
     bool trace_ok;
     xr::TraceGeo trace;
-    double2 *d_tcols;     // per detector column (cos, sin) of the fan angle
-    double *d_tz;         // per detector sample, the row's rise per unit horizontal distance
+    float4 *d_tcols;      // per detector column (cos, sin) of the fan angle, float pairs
+    float2 *d_tz;         // per detector sample, the row's rise per unit horizontal distance
 };
