@@ -141,15 +141,15 @@ enum { XR_ADJ_AUTO = 0, XR_ADJ_SCATTER = 1, XR_ADJ_GATHER = 2 };
  * view and column before the next block, so that the rays in flight in a circular cone scan
  * cross one slab of z. */
 /* XR_ORDER_TRACE (cone and helical scans): the column-trace walk.  The rays of one detector
- * column in one view lie in one vertical plane; a CTA computes that plane's xy crossings once
- * (the (i, j) columns of voxels it crosses, in order) and its lanes, one per row, walk them in
- * lockstep with only their own z crossings, on a z-fastest copy of the volume with a zero voxel
- * above and below every column (workspace 4 * nx * ny * (nz + 2) bytes).  Ray records are not
- * used: the rays are rebuilt in the kernel from per-view, per-column and per-sample tables.
- * Applies when every row crosses at most one z plane while the plane's trace crosses one (x, y)
- * cell (max |rise per horizontal distance| x cell diagonal < 0.99 dz), nx + ny <= 5998, and
- * nx * ny * (nz + 2) < 2^31; XR_ORDER_AUTO takes it whenever it applies.  The adjoint is a
- * scatter whose lanes first sum equal voxels with warp shuffles (rows closer than a voxel). */
+ * column in one view lie in one vertical plane; a warp computes that plane's xy crossings once
+ * (the (i, j) columns of voxels it crosses, in order) and its lanes, one per row of a block of
+ * 32, walk them in lockstep with only their own z crossings, on a z-fastest copy of the volume
+ * with a zero voxel above and below every column (workspace 4 * nx * ny * (nz + 2) bytes).  Ray
+ * records are not used: the rays are rebuilt in the kernel from per-view, per-column and
+ * per-sample tables.  Applies when every row crosses at most one z plane while the plane's
+ * trace crosses one (x, y) cell (max |rise per horizontal distance| x cell diagonal < 0.99 dz)
+ * and nx * ny * (nz + 2) < 2^31; XR_ORDER_AUTO takes it whenever it applies.  The adjoint is a
+ * ray-driven scatter (one reduction per row and voxel). */
 enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2, XR_ORDER_COLUMN = 3, XR_ORDER_ROWBLOCK = 4,
        XR_ORDER_TRACE = 5 };
 

@@ -10,28 +10,36 @@
 // is linear: z(tau) = z_F + t_z tau, with t_z the row's rise per unit horizontal distance.
 // The physical length inside a voxel is the tau-length times sec = sqrt(1 + t_z^2).
 //
-// A CTA takes one (view, column) and a band of rows (one lane per row):
+// A warp takes one (view, column) and a block of 32 rows (one lane per row):
 //   1. the trace: the xy-plane crossings of the vertical plane inside the image box, merged
-//      in tau order -- each crossing's rank in the merge is its index plus the number of
-//      crossings of the other family before it, so every thread places its crossings
-//      independently -- into a shared list of slabs (tau at the slab's end, column offset);
-//   2. every lane walks the shared list in lockstep with the others: per slab, the voxel
+//      in tau order into slabs (tau at the slab's end, column offset), laid out in chunks of
+//      64 slots in the warp's shared memory.  Each lane places the crossings of its own
+//      share of a chunk's tau range: a crossing's slot is its index plus the number of
+//      crossings of the other family before it, counted exactly, so the lanes need no
+//      communication beyond the chunk's first rank;
+//   2. every lane walks the chunk's slabs in lockstep with the others: per slab, the voxel
 //      index at the slab's two ends is floor(u_z) at those tau (a row crosses at most one
 //      z plane per slab -- the host admits a scan only when max |t_z| x the longest slab
 //      stays below one voxel), the z plane crossed inside the slab splits it into two
 //      voxels A (entered) and B (left), and their lengths are C_up - C_low of eq.
 //      conditions_3D_1 with the slab's xy planes and the z plane as the entering and leaving
 //      planes.  A voxel with a zero length contributes nothing (the condition C_low < C_up).
+// Warps run in the order (row block, view, column), so the rays in flight are one block of 32
+// rows in a few views: a thin slab of the volume that L2 holds (a band of 128 rows kept ~40 %
+// of a 512^3 cone volume in flight and read it from DRAM ~27 times per launch).
 // The lanes of a warp are neighbouring rows: at every slab they touch one (i, j) column of
 // the z-fastest volume copy, at neighbouring heights, so their loads (forward) or
 // reductions (adjoint) fall on a few neighbouring sectors.  The copy has one zero voxel above
 // and below each column: a row outside the volume in z is clamped onto them, so rows that
 // enter or leave through the top or bottom face need no extra test.
 //
-// The adjoint adds g * sec * length into a z-fastest accumulator.  With AGG, lanes whose B
-// voxels coincide (rows closer than one voxel) first sum their values with a segmented
-// shuffle reduction, and only the first lane of each run issues the reduction: the rows are
-// ordered, so equal voxels are neighbouring lanes.
+// The adjoint adds g * sec * length into a z-fastest accumulator with one reduction per
+// (row, voxel).  XR_TRACE_AGG=1 builds the warp-aggregated form instead: lanes whose B voxels
+// coincide (rows closer than one voxel) first sum their values with a segmented shuffle
+// reduction, and only the first lane of each run reduces (the rows are ordered, so equal
+// voxels are neighbouring lanes).  Measured on GB300 it lost: the shuffles doubled the
+// kernel's instructions while the reductions of a warp already fall on a few neighbouring
+// sectors (circular cone 512^3: 494 vs 241 ms; helix 512^2 x 256: 219 vs 82 ms).
 //
 // Every geometric quantity of the trace and of a row is computed here from per-view,
 // per-column and per-detector-sample tables (no per-ray table): the trace and the rows' foot
@@ -53,24 +61,16 @@ constexpr int kMagicBits = 0x4B400000;
 // kMagicBits + floor(w).
 __device__ __forceinline__ float magic_floor(float w) { return __fadd_rd(w, kMagic); }
 
-struct Trace {
-    float tin, tout;
-    int nslab;
-};
-
 // Number of crossings of one family (plane tau = fma(q0 + a s, inv, b), a = 0, 1, ...)
-// strictly before T, within [0, n]: an estimate from the spacing, then exact comparisons of
-// the same expressions the list is built from.
-__device__ __forceinline__ int count_before(float T, float q0, float s, float inv, float b, int n, bool or_equal)
+// strictly before T (or_equal: at or before T), within [0, n]: an estimate from the family's
+// rate (crossings per unit tau, |w|), then exact comparisons of the same expressions the slab
+// list is built from.
+__device__ __forceinline__ int count_before(float T, float q0, float s, float inv, float b, float rate, int n,
+                                            bool or_equal)
 {
     if (n <= 0) return 0;
-    const float t0 = __fmaf_rn(q0, inv, b);
-    const float step = fabsf(inv);
-    int k = 0;
-    if (step > 0.f) {
-        const float e = (T - t0) / step;
-        k = e < 0.f ? 0 : (e > (float)n ? n : (int)e + 1);
-    }
+    const float e = (T - __fmaf_rn(q0, inv, b)) * rate;
+    int k = !(e >= 0.f) ? 0 : (e > (float)n ? n : (int)e + 1);
     // exact: crossing k - 1 before T, crossing k not
 #pragma unroll 1
     for (int it = 0; it < 8 && k < n; ++it) {
@@ -143,53 +143,98 @@ __device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V,
     return !(flags & RAY_MISS);
 }
 
-// Build the shared slab list of one trace: tend[s] = tau at the end of slab s, off[s] = the
-// z-fastest offset of its (i, j) column (i * SX + j * SY).  Slab 0 starts at tr.tin.  All
-// threads of the CTA take part; ends with a CTA barrier.
-__device__ void build_trace(const TraceGeo &T, const RayRec &r, float *tend, int *off, Trace &tr)
+// The xy crossings of one trace: the families x and y of plane crossings strictly inside
+// (tin, tout), crossing a of family x at fma(qx + a sx, ix, bx) (likewise y), and the start
+// column (i0, j0).  One warp walks one trace; it lays the slabs out in chunks of kChunk slots
+// in its shared memory, each chunk covering `span` of tau, which holds at most kChunk - 4
+// crossings (the two families cross |w0| + |w1| planes per unit tau).
+constexpr int kChunk = 64;
+constexpr int kWarpsPerCta = 4;  // a CTA takes kWarpsPerCta neighbouring columns
+
+struct WTrace {
+    float tin, tout;
+    float qx, sx, ix, bx, rx;  // rx, ry: crossings per unit tau
+    float qy, sy, iy, by, ry;
+    int nxc, nyc, i0, j0, di, dj;
+    float dl;    // tau covered by one lane's share of a chunk (span / 32)
+    int nchunk;
+};
+
+__device__ __forceinline__ bool trace_setup(const TraceGeo &T, const RayRec &r, WTrace &W)
 {
-    const int SX = T.nz + 2, SY = T.nx * (T.nz + 2);
     Dda<int> D;
-    tr.nslab = 0;
-    tr.tin = tr.tout = 0.f;
-    if (!dda_setup_box<int>(r, 0, T.nx, 0, T.ny, 0, 1, SX, SY, 0, D)) return;
-    tr.tin = D.tcur;
-    tr.tout = D.tout;
-    // crossings of each family strictly inside (tin, tout); the family's plane a is at
-    // fma(q + a s, inv, b)
-    const float qx = D.q0, sx = D.s0, ix = D.i0, bx = D.b0;
-    const float qy = D.q1, sy = D.s1, iy = D.i1, by = D.b1;
-    const int nxc = sx != 0.f ? count_before(D.tout, qx, sx, ix, bx, T.nx, false) : 0;
-    const int nyc = sy != 0.f ? count_before(D.tout, qy, sy, iy, by, T.ny, false) : 0;
-    const int ns = min(nxc + nyc + 1, T.max_slabs);
-    tr.nslab = ns;
-    // the start column (i0, j0) and its per-crossing steps
-    const int i0 = (D.off % SY) / SX, j0 = D.off / SY;  // D.off = i0 SX + j0 SY
-    const int di = sx > 0.f ? 1 : (sx < 0.f ? -1 : 0), dj = sy > 0.f ? 1 : (sy < 0.f ? -1 : 0);
-    // default entries (a slab list is always complete; this only keeps every offset valid)
-    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
-        tend[s] = D.tout;
-        off[s] = D.off;
+    if (!dda_setup_box<int>(r, 0, T.nx, 0, T.ny, 0, 1, 1, T.nx, 0, D)) return false;
+    W.tin = D.tcur;
+    W.tout = D.tout;
+    W.qx = D.q0;
+    W.sx = D.s0;
+    W.ix = D.i0;
+    W.bx = D.b0;
+    W.rx = fabsf(r.w0);
+    W.qy = D.q1;
+    W.sy = D.s1;
+    W.iy = D.i1;
+    W.by = D.b1;
+    W.ry = fabsf(r.w1);
+    W.nxc = W.sx != 0.f ? count_before(D.tout, W.qx, W.sx, W.ix, W.bx, W.rx, T.nx, false) : 0;
+    W.nyc = W.sy != 0.f ? count_before(D.tout, W.qy, W.sy, W.iy, W.by, W.ry, T.ny, false) : 0;
+    W.i0 = D.off % T.nx;  // D.off = i0 + j0 nx
+    W.j0 = D.off / T.nx;
+    W.di = W.sx > 0.f ? 1 : (W.sx < 0.f ? -1 : 0);
+    W.dj = W.sy > 0.f ? 1 : (W.sy < 0.f ? -1 : 0);
+    const float span = (float)(kChunk - 4) / (W.rx + W.ry);  // rx + ry > 0: the trace is a line
+    W.dl = span * (1.0f / 32.0f);
+    const float n = ceilf((W.tout - W.tin) / span);
+    W.nchunk = n >= 1.f ? (n < 1048576.f ? (int)n : 1048576) : 1;
+    return true;
+}
+
+// z-fastest offset of the column before the crossing with cx x- and cy y-crossings behind it
+__device__ __forceinline__ int col_offset(const TraceGeo &T, const WTrace &W, int cx, int cy)
+{
+    const int i = min(max(W.i0 + W.di * cx, 0), T.nx - 1), j = min(max(W.j0 + W.dj * cy, 0), T.ny - 1);
+    return i * (T.nz + 2) + j * (T.nx * (T.nz + 2));
+}
+
+// Chunk c of the warp's slab list into tend / off (slots 0 .. return value - 1).  Lane L places
+// the crossings in its share [la, lb) of the chunk's tau: its starting counts are those
+// strictly before la, and it steps through its crossings in order (x first on a tie).  Each
+// slab ends at one crossing and is stored at that crossing's rank in the merged order minus the
+// chunk's first rank; the last chunk adds the slab that ends at the exit.
+__device__ __forceinline__ int build_chunk(const TraceGeo &T, const WTrace &W, int c, int lane, float *tend,
+                                           int *off)
+{
+    const bool last = c == W.nchunk - 1;
+    const int k = c * 32 + lane;
+    const float la = __fmaf_rn((float)k, W.dl, W.tin);
+    const float lb = (last && lane == 31) ? INFINITY : __fmaf_rn((float)(k + 1), W.dl, W.tin);
+    int cx = count_before(la, W.qx, W.sx, W.ix, W.bx, W.rx, W.nxc, false);
+    int cy = count_before(la, W.qy, W.sy, W.iy, W.by, W.ry, W.nyc, false);
+    const int base = __shfl_sync(0xffffffffu, cx + cy, 0);
+#pragma unroll 1
+    for (int it = 0; it < kChunk; ++it) {
+        const float tx = cx < W.nxc ? __fmaf_rn(W.qx + (float)cx * W.sx, W.ix, W.bx) : INFINITY;
+        const float ty = cy < W.nyc ? __fmaf_rn(W.qy + (float)cy * W.sy, W.iy, W.by) : INFINITY;
+        const float t = fminf(tx, ty);
+        if (!(t < lb)) break;
+        const int slot = cx + cy - base;
+        if (slot >= 0 && slot < kChunk) {
+            tend[slot] = t;
+            off[slot] = col_offset(T, W, cx, cy);
+        }
+        if (tx <= ty) ++cx;
+        else ++cy;
     }
-    __syncthreads();
-    auto put = [&](int rank, float t, int a, int b) {
-        if (rank < 0 || rank >= ns) return;
-        const int i = min(max(i0 + di * a, 0), T.nx - 1), j = min(max(j0 + dj * b, 0), T.ny - 1);
-        tend[rank] = t;
-        off[rank] = i * SX + j * SY;
-    };
-    for (int a = threadIdx.x; a < nxc; a += blockDim.x) {
-        const float t = __fmaf_rn(qx + (float)a * sx, ix, bx);
-        const int cy = count_before(t, qy, sy, iy, by, nyc, false);  // x first on ties
-        put(a + cy, t, a, cy);
+    int n = __shfl_sync(0xffffffffu, cx + cy, 31) - base;
+    if (last) {
+        if (lane == 0 && n >= 0 && n < kChunk) {
+            tend[n] = W.tout;
+            off[n] = col_offset(T, W, W.nxc, W.nyc);
+        }
+        ++n;
     }
-    for (int b = threadIdx.x; b < nyc; b += blockDim.x) {
-        const float t = __fmaf_rn(qy + (float)b * sy, iy, by);
-        const int cx = count_before(t, qx, sx, ix, bx, nxc, true);
-        put(b + cx, t, cx, b);
-    }
-    if (threadIdx.x == 0) put(ns - 1, D.tout, nxc, nyc);
-    __syncthreads();
+    __syncwarp();
+    return min(max(n, 0), kChunk);
 }
 
 // One row: u_z(tau) = oz + fz + ez tau (index space, z counting down), clamped to
@@ -265,63 +310,82 @@ __device__ __forceinline__ void slab_split(const Row &R, float ta, float tb, flo
     oB = oxy + R.cbase + __float_as_int(mb);
 }
 
-template <int U>
-__global__ void __launch_bounds__(128) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
-                                                        float *__restrict__ sino)
+// Warp w of CTA b: column (b % ncg) * kWarpsPerCta + w, view (b / ncg) % n_views, row block
+// b / (ncg n_views) (32 rows; lane = row in the block).  The row blocks are the slowest index,
+// so the rays in flight are one block of 32 rows in a few views: a thin slab of the volume,
+// which stays in L2.  False for a warp past the last column.
+struct WarpJob {
+    int col, view, row;
+};
+
+__device__ __forceinline__ bool warp_job(const TraceGeo &T, WarpJob &J)
 {
-    extern __shared__ float sh[];
-    float *tend = sh;
-    int *off = reinterpret_cast<int *>(sh + T.max_slabs);
-    const int64_t cta = blockIdx.x;
-    const int col = (int)(cta % T.n_cols);
-    const int64_t rest = cta / T.n_cols;
-    const int view = (int)(rest % T.n_views), band = (int)(rest / T.n_views);
-    const ViewDF V = T.views[view];
+    const int64_t b = blockIdx.x;
+    const int cg = (int)(b % T.ncg);
+    const int64_t rest = b / T.ncg;
+    J.view = (int)(rest % T.n_views);
+    J.col = cg * kWarpsPerCta + (int)(threadIdx.x >> 5);
+    J.row = (int)(rest / T.n_views) * 32 + (int)(threadIdx.x & 31);
+    return J.col < T.n_cols;
+}
+
+template <int U>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
+                                                                     float *__restrict__ sino)
+{
+    __shared__ float tend_s[kWarpsPerCta][kChunk];
+    __shared__ int off_s[kWarpsPerCta][kChunk];
+    WarpJob J;
+    if (!warp_job(T, J)) return;  // the whole warp
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *tend = tend_s[w];
+    int *off = off_s[w];
+    const ViewDF V = T.views[J.view];
     RayRec r;
     DF tauF{0.f, 0.f};
-    const bool hit = trace_record(T, V, T.cols[col], r, tauF);
-    Trace tr{0.f, 0.f, 0};
-    if (hit) build_trace(T, r, tend, off, tr);  // hit is uniform over the CTA
-    const int row = band * blockDim.x + threadIdx.x;
-    if (row >= T.n_rows) return;
+    WTrace W;
     float acc = 0.f;
-    if (tr.nslab > 0) {
-        const Row R = make_row(T, V, col, row, tauF);
-        float ta = tr.tin, ma = row_floor(R, ta);
-        int s = 0;
-        for (; s + U <= tr.nslab; s += U) {
-            int oA[U], oB[U];
-            float lA[U], lB[U];
+    if (trace_record(T, V, T.cols[J.col], r, tauF) && trace_setup(T, r, W)) {  // uniform over the warp
+        const Row R = make_row(T, V, J.col, J.row, tauF);
+        float ta = W.tin, ma = row_floor(R, ta);
+        for (int c = 0; c < W.nchunk; ++c) {
+            const int n = build_chunk(T, W, c, lane, tend, off);
+            int s = 0;
+            for (; s + U <= n; s += U) {
+                int oA[U], oB[U];
+                float lA[U], lB[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const float tb = tend[s + u];
+                for (int u = 0; u < U; ++u) {
+                    const float tb = tend[s + u];
+                    const float mb = row_floor(R, tb);
+                    slab_split(R, ta, tb, ma, mb, off[s + u], oA[u], oB[u], lA[u], lB[u]);
+                    ta = tb;
+                    ma = mb;
+                }
+                float vA[U], vB[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    vA[u] = __ldg(volZ + oA[u]);
+                    vB[u] = __ldg(volZ + oB[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc = __fmaf_rn(vB[u], lB[u], __fmaf_rn(vA[u], lA[u], acc));
+            }
+            for (; s < n; ++s) {
+                const float tb = tend[s];
                 const float mb = row_floor(R, tb);
-                slab_split(R, ta, tb, ma, mb, off[s + u], oA[u], oB[u], lA[u], lB[u]);
+                int oA, oB;
+                float lA, lB;
+                slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
+                acc = __fmaf_rn(__ldg(volZ + oB), lB, __fmaf_rn(__ldg(volZ + oA), lA, acc));
                 ta = tb;
                 ma = mb;
             }
-            float vA[U], vB[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                vA[u] = __ldg(volZ + oA[u]);
-                vB[u] = __ldg(volZ + oB[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) acc = __fmaf_rn(vB[u], lB[u], __fmaf_rn(vA[u], lA[u], acc));
-        }
-        for (; s < tr.nslab; ++s) {
-            const float tb = tend[s];
-            const float mb = row_floor(R, tb);
-            int oA, oB;
-            float lA, lB;
-            slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
-            acc = __fmaf_rn(__ldg(volZ + oB), lB, __fmaf_rn(__ldg(volZ + oA), lA, acc));
-            ta = tb;
-            ma = mb;
+            __syncwarp();  // the next chunk overwrites the slots
         }
         acc = __fmul_rn(acc, R.sec);
     }
-    sino[((int64_t)view * T.n_rows + row) * T.n_cols + col] = acc;
+    if (J.row < T.n_rows) sino[((int64_t)J.view * T.n_rows + J.row) * T.n_cols + J.col] = acc;
 }
 
 // Segmented sum over runs of equal keys in neighbouring lanes (keys are ordered by lane):
@@ -337,59 +401,62 @@ __device__ __forceinline__ float run_sum(float v, int key, int lane, int runs)
     return v;
 }
 
-template <bool AGG>
-__global__ void __launch_bounds__(128) trace_adj_kernel(TraceGeo T, const float *__restrict__ sino,
-                                                        float *__restrict__ accZ)
+// Longest run of lanes in one voxel over the whole trace: neighbouring rows are at least
+// `pitch` apart in u_z (their gap is linear in tau, so its ends bound it).
+__device__ __forceinline__ int longest_run(const TraceGeo &T, const Row &R, const WTrace &W, int row, int lane)
 {
-    extern __shared__ float sh[];
-    float *tend = sh;
-    int *off = reinterpret_cast<int *>(sh + T.max_slabs);
-    const int64_t cta = blockIdx.x;
-    const int col = (int)(cta % T.n_cols);
-    const int64_t rest = cta / T.n_cols;
-    const int view = (int)(rest % T.n_views), band = (int)(rest / T.n_views);
-    const ViewDF V = T.views[view];
+    const float w0 = __fmaf_rn(R.ez, W.tin, R.fz) - R.lo, w1 = __fmaf_rn(R.ez, W.tout, R.fz) - R.lo;
+    const float n0 = __shfl_down_sync(0xffffffffu, w0, 1), n1 = __shfl_down_sync(0xffffffffu, w1, 1);
+    const bool pair = lane < 31 && row + 1 < T.n_rows;
+    float pitch = pair ? fminf(fabsf(n0 - w0), fabsf(n1 - w1)) : INFINITY;
+    if (pair && (n0 - w0) * (n1 - w1) <= 0.f) pitch = 0.f;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) pitch = fminf(pitch, __shfl_xor_sync(0xffffffffu, pitch, d));
+    return pitch > 0.04f ? min(32, 2 + (int)(1.0f / pitch)) : 32;
+}
+
+template <bool AGG>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) trace_adj_kernel(TraceGeo T, const float *__restrict__ sino,
+                                                                     float *__restrict__ accZ)
+{
+    __shared__ float tend_s[kWarpsPerCta][kChunk];
+    __shared__ int off_s[kWarpsPerCta][kChunk];
+    WarpJob J;
+    if (!warp_job(T, J)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *tend = tend_s[w];
+    int *off = off_s[w];
+    const ViewDF V = T.views[J.view];
     RayRec r;
     DF tauF{0.f, 0.f};
-    const bool hit = trace_record(T, V, T.cols[col], r, tauF);
-    Trace tr{0.f, 0.f, 0};
-    if (hit) build_trace(T, r, tend, off, tr);
-    if (tr.nslab == 0) return;  // uniform over the CTA
-    const int lane = threadIdx.x & 31;
-    const int row = band * blockDim.x + threadIdx.x;
-    const Row R = make_row(T, V, col, row, tauF);
-    const float g = R.live ? __ldg(sino + ((int64_t)view * T.n_rows + row) * T.n_cols + col) : 0.f;
+    WTrace W;
+    if (!trace_record(T, V, T.cols[J.col], r, tauF) || !trace_setup(T, r, W)) return;  // uniform
+    const Row R = make_row(T, V, J.col, J.row, tauF);
+    const float g = R.live ? __ldg(sino + ((int64_t)J.view * T.n_rows + J.row) * T.n_cols + J.col) : 0.f;
     const float gs = __fmul_rn(g, R.sec);
-    // longest run of lanes in one voxel: neighbouring rows are at least `pitch` apart in u_z
-    // over the whole trace (the gap is linear in tau, so its ends bound it)
-    int runs = 32;
-    if (AGG) {
-        const float w0 = __fmaf_rn(R.ez, tr.tin, R.fz) - R.lo, w1 = __fmaf_rn(R.ez, tr.tout, R.fz) - R.lo;
-        const float n0 = __shfl_down_sync(0xffffffffu, w0, 1), n1 = __shfl_down_sync(0xffffffffu, w1, 1);
-        float pitch = (lane < 31 && row + 1 < T.n_rows) ? fminf(fabsf(n0 - w0), fabsf(n1 - w1)) : INFINITY;
-        if ((n0 - w0) * (n1 - w1) <= 0.f && lane < 31 && row + 1 < T.n_rows) pitch = 0.f;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) pitch = fminf(pitch, __shfl_xor_sync(0xffffffffu, pitch, d));
-        runs = pitch > 0.04f ? min(32, 2 + (int)(1.0f / pitch)) : 32;
-    }
-    float ta = tr.tin, ma = row_floor(R, ta);
-    for (int s = 0; s < tr.nslab; ++s) {
-        const float tb = tend[s];
-        const float mb = row_floor(R, tb);
-        int oA, oB;
-        float lA, lB;
-        slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
-        if (lA > 0.f && gs != 0.f) red_add(accZ + oA, __fmul_rn(gs, lA));
-        float vB = __fmul_rn(gs, lB);
-        if (AGG) {
-            vB = run_sum(vB, oB, lane, runs);
-            const int kp = __shfl_up_sync(0xffffffffu, oB, 1);
-            if ((lane == 0 || kp != oB) && vB != 0.f) red_add(accZ + oB, vB);
-        } else if (vB != 0.f) {
-            red_add(accZ + oB, vB);
+    const int runs = AGG ? longest_run(T, R, W, J.row, lane) : 1;
+    float ta = W.tin, ma = row_floor(R, ta);
+    for (int c = 0; c < W.nchunk; ++c) {
+        const int n = build_chunk(T, W, c, lane, tend, off);
+        for (int s = 0; s < n; ++s) {
+            const float tb = tend[s];
+            const float mb = row_floor(R, tb);
+            int oA, oB;
+            float lA, lB;
+            slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
+            if (lA > 0.f && gs != 0.f) red_add(accZ + oA, __fmul_rn(gs, lA));
+            float vB = __fmul_rn(gs, lB);
+            if (AGG) {
+                vB = run_sum(vB, oB, lane, runs);
+                const int kp = __shfl_up_sync(0xffffffffu, oB, 1);
+                if ((lane == 0 || kp != oB) && vB != 0.f) red_add(accZ + oB, vB);
+            } else if (vB != 0.f) {
+                red_add(accZ + oB, vB);
+            }
+            ta = tb;
+            ma = mb;
         }
-        ta = tb;
-        ma = mb;
+        __syncwarp();
     }
 }
 
@@ -448,7 +515,7 @@ __global__ void __launch_bounds__(256) from_zpad_kernel(const float *__restrict_
 #define XR_TRACE_AHEAD 4
 #endif
 #ifndef XR_TRACE_AGG
-#define XR_TRACE_AGG 1
+#define XR_TRACE_AGG 0
 #endif
 
 dim3 zpad_grid(int64_t rows, int64_t cols)
@@ -456,7 +523,6 @@ dim3 zpad_grid(int64_t rows, int64_t cols)
     return dim3((unsigned)((cols + 31) / 32), (unsigned)std::min<int64_t>((rows + 31) / 32, 65535));
 }
 
-size_t trace_smem(const TraceGeo &T) { return (size_t)T.max_slabs * (sizeof(float) + sizeof(int)); }
 
 }  // namespace
 
@@ -468,8 +534,8 @@ cudaError_t launch_trace_project(const TraceGeo &T, const float *img, float *ws,
     to_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(img, ws, T.nz, cols);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t ctas = (int64_t)T.n_cols * T.n_views * T.n_bands;
-    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, T.rows_per_cta, trace_smem(T), s>>>(T, ws, sino);
+    const int64_t ctas = (int64_t)T.ncg * T.n_views * T.n_rb;
+    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(T, ws, sino);
     return cudaGetLastError();
 }
 
@@ -478,11 +544,11 @@ cudaError_t launch_trace_backproject(const TraceGeo &T, const float *sino, float
     const int64_t cols = (int64_t)T.nx * T.ny;
     cudaError_t e = cudaMemsetAsync(ws, 0, (size_t)cols * (T.nz + 2) * sizeof(float), s);
     if (e != cudaSuccess) return e;
-    const int64_t ctas = (int64_t)T.n_cols * T.n_views * T.n_bands;
+    const int64_t ctas = (int64_t)T.ncg * T.n_views * T.n_rb;
     if (XR_TRACE_AGG)
-        trace_adj_kernel<true><<<(unsigned)ctas, T.rows_per_cta, trace_smem(T), s>>>(T, sino, ws);
+        trace_adj_kernel<true><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(T, sino, ws);
     else
-        trace_adj_kernel<false><<<(unsigned)ctas, T.rows_per_cta, trace_smem(T), s>>>(T, sino, ws);
+        trace_adj_kernel<false><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(T, sino, ws);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     from_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(ws, img, T.nz, cols);

@@ -224,16 +224,11 @@ static size_t reserve_bytes(const xr_geometry *g, int batch)
 // Cone and helical scans: the column-trace walk's tables (per column: cos / sin of the fan
 // angle; per detector sample: the row's rise per unit horizontal distance) and whether the
 // walk applies: every row crosses at most one z plane per xy slab (a slab is at most the
-// (dx, dy) cell's diagonal long), the slab list fits 48 KiB of shared memory, and offsets of
-// the padded z-fastest copy fit 32 bits.  Flat detectors: tan(alpha) = u / sdd and
+// (dx, dy) cell's diagonal long) and offsets of the padded z-fastest copy fit 32 bits.  Flat detectors: tan(alpha) = u / sdd and
 // t_z = v / sqrt(sdd^2 + u^2) (eq. equispaced_cone_beam with t = u sod/sdd, h = v sod/sdd);
 // equiangular detectors: alpha = u, t_z = tan(v) (eq. equiangular_cone_beam).
 static bool kind_cone(int k) { return k >= XR_CONE && k <= XR_HELIX_ARC; }
 
-// rows per CTA of the column-trace walk (32, 64 or 128; one lane per row)
-#ifndef XR_TRACE_ROWS
-#define XR_TRACE_ROWS 128
-#endif
 
 static bool trace_tables(const GeoParams &p, std::vector<float4> &cols, std::vector<float2> &tz, TraceGeo &T)
 {
@@ -257,7 +252,6 @@ static bool trace_tables(const GeoParams &p, std::vector<float4> &cols, std::vec
     }
     const double slab_z = tzmax * sqrt(p.dx * p.dx + p.dy * p.dy) / p.dz;
     if (!(slab_z < 0.99)) return false;
-    if ((int64_t)p.nx + p.ny + 2 > 6000) return false;  // 8 B per slab in 48 KiB
     if ((int64_t)p.nx * p.ny * (p.nz + 2) >= ((int64_t)1 << 31)) return false;
     T.nx = p.nx;
     T.ny = p.ny;
@@ -265,10 +259,9 @@ static bool trace_tables(const GeoParams &p, std::vector<float4> &cols, std::vec
     T.n_views = p.n_views;
     T.n_rows = p.n_rows;
     T.n_cols = p.n_cols;
-    T.rows_per_cta = p.n_rows > 64 ? XR_TRACE_ROWS : (p.n_rows > 32 ? std::min(64, XR_TRACE_ROWS) : 32);
-    T.n_bands = (p.n_rows + T.rows_per_cta - 1) / T.rows_per_cta;
-    if ((int64_t)p.n_cols * p.n_views * T.n_bands >= ((int64_t)1 << 31)) return false;
-    T.max_slabs = p.nx + p.ny + 2;
+    T.n_rb = (p.n_rows + 31) / 32;
+    T.ncg = (p.n_cols + 3) / 4;
+    if ((int64_t)T.ncg * p.n_views * T.n_rb >= ((int64_t)1 << 31)) return false;
     T.x0 = df_from_double(p.cx - 0.5 * p.nx * p.dx);
     T.y1 = df_from_double(p.cy + 0.5 * p.ny * p.dy);
     T.z1 = df_from_double(p.cz + 0.5 * p.nz * p.dz);

@@ -212,9 +212,8 @@ cudaError_t launch_atten_plane_adj(const RayRec *rays, int64_t n_rays, int nx, i
 // for the cone and helix kinds when every row crosses at most one z plane per xy slab.
 struct TraceGeo {
     int nx, ny, nz, n_views, n_rows, n_cols;
-    int rows_per_cta;  // one lane per row: a CTA is one (view, column) and a band of rows
-    int n_bands;
-    int max_slabs;     // nx + ny + 2: the slab list's capacity in shared memory
+    int n_rb;          // blocks of 32 detector rows (a warp: one view, one column, one block)
+    int ncg;           // groups of 4 neighbouring columns (a CTA: 4 warps)
     DF x0, y1, z1, idx, idy, idz, cx, cy, D;  // planes i = 0, j = 0, k = 0; 1/d; centre; sod
     float rxy2;            // squared xy half-diagonal of the image (with a small margin)
     const ViewDF *views;   // cos / sin of the view angle, source height H
