@@ -196,13 +196,13 @@ __device__ __forceinline__ int col_offset(const TraceGeo &T, const WTrace &W, in
     return i * (T.nz + 2) + j * (T.nx * (T.nz + 2));
 }
 
-// Chunk c of the warp's slab list into tend / off (slots 0 .. return value - 1).  Lane L places
+// Chunk c of the warp's slab list into slot[] (0 .. return value - 1): x = tau at the slab's
+// end, y = the bits of its column offset.  Lane L places
 // the crossings in its share [la, lb) of the chunk's tau: its starting counts are those
 // strictly before la, and it steps through its crossings in order (x first on a tie).  Each
 // slab ends at one crossing and is stored at that crossing's rank in the merged order minus the
 // chunk's first rank; the last chunk adds the slab that ends at the exit.
-__device__ __forceinline__ int build_chunk(const TraceGeo &T, const WTrace &W, int c, int lane, float *tend,
-                                           int *off)
+__device__ __forceinline__ int build_chunk(const TraceGeo &T, const WTrace &W, int c, int lane, float2 *slot)
 {
     const bool last = c == W.nchunk - 1;
     const int k = c * 32 + lane;
@@ -217,10 +217,9 @@ __device__ __forceinline__ int build_chunk(const TraceGeo &T, const WTrace &W, i
         const float ty = cy < W.nyc ? __fmaf_rn(W.qy + (float)cy * W.sy, W.iy, W.by) : INFINITY;
         const float t = fminf(tx, ty);
         if (!(t < lb)) break;
-        const int slot = cx + cy - base;
-        if (slot >= 0 && slot < kChunk) {
-            tend[slot] = t;
-            off[slot] = col_offset(T, W, cx, cy);
+        const int k2 = cx + cy - base;
+        if (k2 >= 0 && k2 < kChunk) {
+            slot[k2] = make_float2(t, __int_as_float(col_offset(T, W, cx, cy)));
         }
         if (tx <= ty) ++cx;
         else ++cy;
@@ -228,8 +227,7 @@ __device__ __forceinline__ int build_chunk(const TraceGeo &T, const WTrace &W, i
     int n = __shfl_sync(0xffffffffu, cx + cy, 31) - base;
     if (last) {
         if (lane == 0 && n >= 0 && n < kChunk) {
-            tend[n] = W.tout;
-            off[n] = col_offset(T, W, W.nxc, W.nyc);
+            slot[n] = make_float2(W.tout, __int_as_float(col_offset(T, W, W.nxc, W.nyc)));
         }
         ++n;
     }
@@ -237,16 +235,22 @@ __device__ __forceinline__ int build_chunk(const TraceGeo &T, const WTrace &W, i
     return min(max(n, 0), kChunk);
 }
 
-// One row: u_z(tau) = oz + fz + ez tau (index space, z counting down), clamped to
-// [-0.5, nz + 0.5] so that rows outside the volume read / write the zero voxels of the
-// padded columns.
+// One row, in a z index u that grows along the walk: u(tau) = oz + fz + ez tau with ez >= 0.
+// For a row whose index u_z (counting down in z) falls along tau, u = nz - u_z: the column is
+// read from its other end.  Voxel m of u (unit [m, m + 1]) is at offset
+//   zs * (kMagicBits + m - oz) + C   (mod 2^32)
+// of its padded column, zs = 1 (C = oz - kMagicBits + 1) or zs = -1 (C = nz - oz + kMagicBits),
+// so that the magic float of floor(w) gives the offset with one multiply-add.  Clamped to
+// [-0.5, nz + 0.5], rows outside the volume fall on the zero voxels m = -1 and m = nz.
+// inside: w stays in [-1 - oz, nz + 1 - oz) over the whole trace, so no clamp is needed.
 struct Row {
     float ez, fz, iez, bz, lo, hi, sec;
-    int cbase;  // column offset of voxel oz + m: cbase + (kMagicBits + m)
-    bool live;
+    unsigned zs, C;
+    bool live, inside;
 };
 
-__device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewDF &V, int col, int row, DF tauF)
+__device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewDF &V, int col, int row, DF tauF,
+                                        float tin, float tout)
 {
     Row R;
     R.live = row < T.n_rows;
@@ -262,6 +266,7 @@ __device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewDF &V, int 
     if (fabsf(ez) < 1e-20f) ez = 0.f;
     int oz;
     float fz;
+    bool flip = false;
     if (!R.live || ez == 0.f) {
         // a horizontal row keeps one voxel: the bigger index on a plane, the last voxel on the
         // bottom face (Section 4.1); outside the volume, the zero voxel above the column
@@ -274,6 +279,11 @@ __device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewDF &V, int 
         fz = 0.5f;
         ez = 0.f;
     } else {
+        flip = ez < 0.f;
+        if (flip) {
+            uz = df_sub(DF{(float)T.nz, 0.f}, uz);
+            ez = -ez;
+        }
         df_floor_frac(uz, oz, fz);
     }
     R.ez = ez;
@@ -283,31 +293,35 @@ __device__ __forceinline__ Row make_row(const TraceGeo &T, const ViewDF &V, int 
     R.lo = -0.5f - (float)oz;
     R.hi = (float)(T.nz - oz) + 0.5f;
     R.sec = R.live ? __fsqrt_rn(__fmaf_rn(tz.hi, tz.hi, 1.0f)) : 0.f;
-    R.cbase = oz + 1 - kMagicBits;
+    R.zs = flip ? 0xffffffffu : 1u;
+    R.C = flip ? (unsigned)(T.nz - oz) + (unsigned)kMagicBits : (unsigned)(oz + 1) - (unsigned)kMagicBits;
+    const float w0 = __fmaf_rn(ez, tin, fz), w1 = __fmaf_rn(ez, tout, fz);  // w is monotone in tau
+    R.inside = ez == 0.f || (w0 >= -1.0f - (float)oz && w1 < (float)(T.nz + 1 - oz));
     return R;
 }
 
-// The voxel of the row at tau: the magic float of floor(w) (w = u_z - oz, clamped).
+// The voxel of the row at tau: the magic float of floor(w), w = u - oz (clamped if CLAMP).
+template <bool CLAMP>
 __device__ __forceinline__ float row_floor(const Row &R, float tau)
 {
-    const float w = fminf(fmaxf(__fmaf_rn(R.ez, tau, R.fz), R.lo), R.hi);
+    float w = __fmaf_rn(R.ez, tau, R.fz);
+    if (CLAMP) w = fminf(fmaxf(w, R.lo), R.hi);
     return magic_floor(w);
 }
 
 // One slab [ta, tb] of column offset oxy: voxels A (at ta) and B (at tb), their offsets and
-// lengths (in tau).  ma / mb: the magic floats of the voxel index at ta / tb.
-__device__ __forceinline__ void slab_split(const Row &R, float ta, float tb, float ma, float mb, int oxy, int &oA,
-                                           int &oB, float &lA, float &lB)
+// lengths (in tau).  ma / mb: the magic floats of the voxel index at ta / tb (mb - ma is 0 or
+// 1).  The z plane crossed inside the slab is u = mb; with no crossing, that plane lies behind
+// ta and A gets no length.  Rounding can leave lB a few ulp below zero at a crossing on tb.
+__device__ __forceinline__ void slab_split(const Row &R, float ta, float tb, float ma, float mb, int oxy,
+                                           unsigned &oA, unsigned &oB, float &lA, float &lB)
 {
-    // the z plane crossed inside the slab: the upper of the two voxel indices (the
-    // plane between voxels m and m + 1 is u_z = m + 1 when going down, m when going up:
-    // both are max(ma, mb) with m measured from oz); no crossing puts it outside [ta, tb]
-    const float pf = fmaxf(ma, mb) - kMagic;
-    const float tx = fminf(fmaxf(__fmaf_rn(pf, R.iez, R.bz), ta), tb);
+    const float tx = fmaxf(__fmaf_rn(mb - kMagic, R.iez, R.bz), ta);
     lA = __fsub_rn(tx, ta);
     lB = __fsub_rn(tb, tx);
-    oA = oxy + R.cbase + __float_as_int(ma);
-    oB = oxy + R.cbase + __float_as_int(mb);
+    const unsigned ob = (unsigned)oxy + R.C;
+    oA = R.zs * (unsigned)__float_as_int(ma) + ob;
+    oB = R.zs * (unsigned)__float_as_int(mb) + ob;
 }
 
 // Warp w of CTA b: column (b % ncg) * kWarpsPerCta + w, view (b / ncg) % n_views, row block
@@ -329,60 +343,72 @@ __device__ __forceinline__ bool warp_job(const TraceGeo &T, WarpJob &J)
     return J.col < T.n_cols;
 }
 
+// The forward walk of one row over the warp's slab list (CLAMP: some row of the warp leaves
+// the volume through its top or bottom face).  U slabs are split ahead of their 2U loads.
+template <int U, bool CLAMP>
+__device__ __forceinline__ float fwd_walk(const TraceGeo &T, const WTrace &W, const Row &R, int lane, float2 *slot,
+                                          const float *__restrict__ volZ)
+{
+    float acc = 0.f;
+    float ta = W.tin, ma = row_floor<CLAMP>(R, ta);
+    for (int c = 0; c < W.nchunk; ++c) {
+        const int n = build_chunk(T, W, c, lane, slot);
+        int s = 0;
+        for (; s + U <= n; s += U) {
+            unsigned oA[U], oB[U];
+            float lA[U], lB[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float2 sl = slot[s + u];
+                const float mb = row_floor<CLAMP>(R, sl.x);
+                slab_split(R, ta, sl.x, ma, mb, __float_as_int(sl.y), oA[u], oB[u], lA[u], lB[u]);
+                ta = sl.x;
+                ma = mb;
+            }
+            float vA[U], vB[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                vA[u] = __ldg(volZ + oA[u]);
+                vB[u] = __ldg(volZ + oB[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc = __fmaf_rn(vB[u], lB[u], __fmaf_rn(vA[u], lA[u], acc));
+        }
+        for (; s < n; ++s) {
+            const float2 sl = slot[s];
+            const float mb = row_floor<CLAMP>(R, sl.x);
+            unsigned oA, oB;
+            float lA, lB;
+            slab_split(R, ta, sl.x, ma, mb, __float_as_int(sl.y), oA, oB, lA, lB);
+            acc = __fmaf_rn(__ldg(volZ + oB), lB, __fmaf_rn(__ldg(volZ + oA), lA, acc));
+            ta = sl.x;
+            ma = mb;
+        }
+        __syncwarp();  // the next chunk overwrites the slots
+    }
+    return acc;
+}
+
 template <int U>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
                                                                      float *__restrict__ sino)
 {
-    __shared__ float tend_s[kWarpsPerCta][kChunk];
-    __shared__ int off_s[kWarpsPerCta][kChunk];
+    __shared__ float2 slot_s[kWarpsPerCta][kChunk];
     WarpJob J;
     if (!warp_job(T, J)) return;  // the whole warp
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float *tend = tend_s[w];
-    int *off = off_s[w];
+    const int lane = threadIdx.x & 31;
+    float2 *slot = slot_s[threadIdx.x >> 5];
     const ViewDF V = T.views[J.view];
     RayRec r;
     DF tauF{0.f, 0.f};
     WTrace W;
     float acc = 0.f;
     if (trace_record(T, V, T.cols[J.col], r, tauF) && trace_setup(T, r, W)) {  // uniform over the warp
-        const Row R = make_row(T, V, J.col, J.row, tauF);
-        float ta = W.tin, ma = row_floor(R, ta);
-        for (int c = 0; c < W.nchunk; ++c) {
-            const int n = build_chunk(T, W, c, lane, tend, off);
-            int s = 0;
-            for (; s + U <= n; s += U) {
-                int oA[U], oB[U];
-                float lA[U], lB[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float tb = tend[s + u];
-                    const float mb = row_floor(R, tb);
-                    slab_split(R, ta, tb, ma, mb, off[s + u], oA[u], oB[u], lA[u], lB[u]);
-                    ta = tb;
-                    ma = mb;
-                }
-                float vA[U], vB[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    vA[u] = __ldg(volZ + oA[u]);
-                    vB[u] = __ldg(volZ + oB[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) acc = __fmaf_rn(vB[u], lB[u], __fmaf_rn(vA[u], lA[u], acc));
-            }
-            for (; s < n; ++s) {
-                const float tb = tend[s];
-                const float mb = row_floor(R, tb);
-                int oA, oB;
-                float lA, lB;
-                slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
-                acc = __fmaf_rn(__ldg(volZ + oB), lB, __fmaf_rn(__ldg(volZ + oA), lA, acc));
-                ta = tb;
-                ma = mb;
-            }
-            __syncwarp();  // the next chunk overwrites the slots
-        }
+        const Row R = make_row(T, V, J.col, J.row, tauF, W.tin, W.tout);
+        if (__all_sync(0xffffffffu, R.inside))
+            acc = fwd_walk<U, false>(T, W, R, lane, slot, volZ);
+        else
+            acc = fwd_walk<U, true>(T, W, R, lane, slot, volZ);
         acc = __fmul_rn(acc, R.sec);
     }
     if (J.row < T.n_rows) sino[((int64_t)J.view * T.n_rows + J.row) * T.n_cols + J.col] = acc;
@@ -415,49 +441,60 @@ __device__ __forceinline__ int longest_run(const TraceGeo &T, const Row &R, cons
     return pitch > 0.04f ? min(32, 2 + (int)(1.0f / pitch)) : 32;
 }
 
+// The adjoint walk of one row: g * sec * length added to voxels A (at a crossing) and B.
+template <bool AGG, bool CLAMP>
+__device__ __forceinline__ void adj_walk(const TraceGeo &T, const WTrace &W, const Row &R, int lane, int runs,
+                                         float gs, float2 *slot, float *__restrict__ accZ)
+{
+    float ta = W.tin, ma = row_floor<CLAMP>(R, ta);
+    for (int c = 0; c < W.nchunk; ++c) {
+        const int n = build_chunk(T, W, c, lane, slot);
+#pragma unroll 2
+        for (int s = 0; s < n; ++s) {
+            const float2 sl = slot[s];
+            const float mb = row_floor<CLAMP>(R, sl.x);
+            unsigned oA, oB;
+            float lA, lB;
+            slab_split(R, ta, sl.x, ma, mb, __float_as_int(sl.y), oA, oB, lA, lB);
+            if (lA > 0.f) red_add(accZ + oA, __fmul_rn(gs, lA));
+            float vB = lB > 0.f ? __fmul_rn(gs, lB) : 0.f;
+            if (AGG) {
+                vB = run_sum(vB, (int)oB, lane, runs);
+                const unsigned kp = __shfl_up_sync(0xffffffffu, oB, 1);
+                if ((lane == 0 || kp != oB) && vB != 0.f) red_add(accZ + oB, vB);
+            } else if (lB > 0.f) {
+                red_add(accZ + oB, vB);
+            }
+            ta = sl.x;
+            ma = mb;
+        }
+        __syncwarp();
+    }
+}
+
 template <bool AGG>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) trace_adj_kernel(TraceGeo T, const float *__restrict__ sino,
                                                                      float *__restrict__ accZ)
 {
-    __shared__ float tend_s[kWarpsPerCta][kChunk];
-    __shared__ int off_s[kWarpsPerCta][kChunk];
+    __shared__ float2 slot_s[kWarpsPerCta][kChunk];
     WarpJob J;
     if (!warp_job(T, J)) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float *tend = tend_s[w];
-    int *off = off_s[w];
+    const int lane = threadIdx.x & 31;
+    float2 *slot = slot_s[threadIdx.x >> 5];
     const ViewDF V = T.views[J.view];
     RayRec r;
     DF tauF{0.f, 0.f};
     WTrace W;
     if (!trace_record(T, V, T.cols[J.col], r, tauF) || !trace_setup(T, r, W)) return;  // uniform
-    const Row R = make_row(T, V, J.col, J.row, tauF);
+    const Row R = make_row(T, V, J.col, J.row, tauF, W.tin, W.tout);
     const float g = R.live ? __ldg(sino + ((int64_t)J.view * T.n_rows + J.row) * T.n_cols + J.col) : 0.f;
+    if (__all_sync(0xffffffffu, g == 0.f)) return;  // nothing to spread
     const float gs = __fmul_rn(g, R.sec);
     const int runs = AGG ? longest_run(T, R, W, J.row, lane) : 1;
-    float ta = W.tin, ma = row_floor(R, ta);
-    for (int c = 0; c < W.nchunk; ++c) {
-        const int n = build_chunk(T, W, c, lane, tend, off);
-        for (int s = 0; s < n; ++s) {
-            const float tb = tend[s];
-            const float mb = row_floor(R, tb);
-            int oA, oB;
-            float lA, lB;
-            slab_split(R, ta, tb, ma, mb, off[s], oA, oB, lA, lB);
-            if (lA > 0.f && gs != 0.f) red_add(accZ + oA, __fmul_rn(gs, lA));
-            float vB = __fmul_rn(gs, lB);
-            if (AGG) {
-                vB = run_sum(vB, oB, lane, runs);
-                const int kp = __shfl_up_sync(0xffffffffu, oB, 1);
-                if ((lane == 0 || kp != oB) && vB != 0.f) red_add(accZ + oB, vB);
-            } else if (vB != 0.f) {
-                red_add(accZ + oB, vB);
-            }
-            ta = tb;
-            ma = mb;
-        }
-        __syncwarp();
-    }
+    if (__all_sync(0xffffffffu, R.inside))
+        adj_walk<AGG, false>(T, W, R, lane, runs, gs, slot, accZ);
+    else
+        adj_walk<AGG, true>(T, W, R, lane, runs, gs, slot, accZ);
 }
 
 // out[p * ld + 1 + k] = in[k * cols + p] for a [rows = nz][cols = nx ny] volume, and the two
@@ -512,7 +549,7 @@ __global__ void __launch_bounds__(256) from_zpad_kernel(const float *__restrict_
 }
 
 #ifndef XR_TRACE_AHEAD
-#define XR_TRACE_AHEAD 4
+#define XR_TRACE_AHEAD 8
 #endif
 #ifndef XR_TRACE_AGG
 #define XR_TRACE_AGG 0
