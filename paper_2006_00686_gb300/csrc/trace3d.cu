@@ -148,7 +148,13 @@ __device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V,
 // column (i0, j0).  One warp walks one trace; it lays the slabs out in chunks of kChunk slots
 // in its shared memory, each chunk covering `span` of tau, which holds at most kChunk - 4
 // crossings (the two families cross |w0| + |w1| planes per unit tau).
-constexpr int kChunk = 64;
+#ifndef XR_TRACE_CHUNK
+#define XR_TRACE_CHUNK 64
+#endif
+#ifndef XR_TRACE_MINB
+#define XR_TRACE_MINB 1
+#endif
+constexpr int kChunk = XR_TRACE_CHUNK;
 constexpr int kWarpsPerCta = 4;  // a CTA takes kWarpsPerCta neighbouring columns
 
 struct WTrace {
@@ -349,7 +355,7 @@ template <int U, bool CLAMP>
 __device__ __forceinline__ float fwd_walk(const TraceGeo &T, const WTrace &W, const Row &R, int lane, float2 *slot,
                                           const float *__restrict__ volZ)
 {
-    float acc = 0.f;
+    float acc = 0.f, accB = 0.f;  // two chains: A voxels and B voxels
     float ta = W.tin, ma = row_floor<CLAMP>(R, ta);
     for (int c = 0; c < W.nchunk; ++c) {
         const int n = build_chunk(T, W, c, lane, slot);
@@ -372,7 +378,10 @@ __device__ __forceinline__ float fwd_walk(const TraceGeo &T, const WTrace &W, co
                 vB[u] = __ldg(volZ + oB[u]);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) acc = __fmaf_rn(vB[u], lB[u], __fmaf_rn(vA[u], lA[u], acc));
+            for (int u = 0; u < U; ++u) {
+                acc = __fmaf_rn(vA[u], lA[u], acc);
+                accB = __fmaf_rn(vB[u], lB[u], accB);
+            }
         }
         for (; s < n; ++s) {
             const float2 sl = slot[s];
@@ -380,17 +389,18 @@ __device__ __forceinline__ float fwd_walk(const TraceGeo &T, const WTrace &W, co
             unsigned oA, oB;
             float lA, lB;
             slab_split(R, ta, sl.x, ma, mb, __float_as_int(sl.y), oA, oB, lA, lB);
-            acc = __fmaf_rn(__ldg(volZ + oB), lB, __fmaf_rn(__ldg(volZ + oA), lA, acc));
+            acc = __fmaf_rn(__ldg(volZ + oA), lA, acc);
+            accB = __fmaf_rn(__ldg(volZ + oB), lB, accB);
             ta = sl.x;
             ma = mb;
         }
         __syncwarp();  // the next chunk overwrites the slots
     }
-    return acc;
+    return __fadd_rn(acc, accB);
 }
 
 template <int U>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_MINB) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
                                                                      float *__restrict__ sino)
 {
     __shared__ float2 slot_s[kWarpsPerCta][kChunk];
@@ -473,7 +483,7 @@ __device__ __forceinline__ void adj_walk(const TraceGeo &T, const WTrace &W, con
 }
 
 template <bool AGG>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) trace_adj_kernel(TraceGeo T, const float *__restrict__ sino,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_MINB) trace_adj_kernel(TraceGeo T, const float *__restrict__ sino,
                                                                      float *__restrict__ accZ)
 {
     __shared__ float2 slot_s[kWarpsPerCta][kChunk];
