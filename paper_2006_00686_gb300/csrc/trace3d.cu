@@ -13,7 +13,7 @@
 // A warp takes one (view, column) and a block of 32 rows (one lane per row):
 //   1. the trace: the xy-plane crossings of the vertical plane inside the image box, merged
 //      in tau order into slabs (tau at the slab's end, column offset), laid out in chunks of
-//      64 slots in the warp's shared memory.  Each lane places the crossings of its own
+//      128 slots in the warp's shared memory.  Each lane places the crossings of its own
 //      share of a chunk's tau range: a crossing's slot is its index plus the number of
 //      crossings of the other family before it, counted exactly, so the lanes need no
 //      communication beyond the chunk's first rank;
@@ -64,24 +64,26 @@ __device__ __forceinline__ float magic_floor(float w) { return __fadd_rd(w, kMag
 // Number of crossings of one family (plane tau = fma(q0 + a s, inv, b), a = 0, 1, ...)
 // strictly before T (or_equal: at or before T), within [0, n]: an estimate from the family's
 // rate (crossings per unit tau, |w|), then exact comparisons of the same expressions the slab
-// list is built from.
-__device__ __forceinline__ int count_before(float T, float q0, float s, float inv, float b, float rate, int n,
-                                            bool or_equal)
+// list is built from.  Counts stay in float (exact below 2^24) and the estimate is truncated
+// with the magic-number add, so no int/float conversion is needed.
+__device__ __forceinline__ float count_before(float T, float q0, float s, float inv, float b, float rate, float n,
+                                              bool or_equal)
 {
-    if (n <= 0) return 0;
+    if (n <= 0.f) return 0.f;
     const float e = (T - __fmaf_rn(q0, inv, b)) * rate;
-    int k = !(e >= 0.f) ? 0 : (e > (float)n ? n : (int)e + 1);
+    // estimate: trunc(e) + 1 within [0, n]
+    float k = !(e >= 0.f) ? 0.f : (e >= n ? n : __fadd_rz(__fadd_rz(e, 8388608.0f), -8388608.0f) + 1.0f);
     // exact: crossing k - 1 before T, crossing k not
 #pragma unroll 1
     for (int it = 0; it < 8 && k < n; ++it) {
-        const float tk = __fmaf_rn(q0 + (float)k * s, inv, b);
-        if (or_equal ? (tk <= T) : (tk < T)) ++k;
+        const float tk = __fmaf_rn(__fmaf_rn(k, s, q0), inv, b);
+        if (or_equal ? (tk <= T) : (tk < T)) k += 1.f;
         else break;
     }
 #pragma unroll 1
-    for (int it = 0; it < 8 && k > 0; ++it) {
-        const float tk = __fmaf_rn(q0 + (float)(k - 1) * s, inv, b);
-        if (or_equal ? (tk > T) : (tk >= T)) --k;
+    for (int it = 0; it < 8 && k > 0.f; ++it) {
+        const float tk = __fmaf_rn(__fmaf_rn(k - 1.f, s, q0), inv, b);
+        if (or_equal ? (tk > T) : (tk >= T)) k -= 1.f;
         else break;
     }
     return k;
@@ -149,19 +151,26 @@ __device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V,
 // in its shared memory, each chunk covering `span` of tau, which holds at most kChunk - 4
 // crossings (the two families cross |w0| + |w1| planes per unit tau).
 #ifndef XR_TRACE_CHUNK
-#define XR_TRACE_CHUNK 64
+#define XR_TRACE_CHUNK 128
 #endif
 #ifndef XR_TRACE_MINB
 #define XR_TRACE_MINB 1
 #endif
+#ifndef XR_TRACE_FWD_MINB
+#define XR_TRACE_FWD_MINB 8  // 64 registers: 32 warps per SM to hide the loads' latency
+#endif
 constexpr int kChunk = XR_TRACE_CHUNK;
-constexpr int kWarpsPerCta = 4;  // a CTA takes kWarpsPerCta neighbouring columns
+#ifndef XR_TRACE_WPC
+#define XR_TRACE_WPC 4
+#endif
+constexpr int kWarpsPerCta = XR_TRACE_WPC;  // a CTA takes kWarpsPerCta neighbouring columns
 
 struct WTrace {
     float tin, tout;
     float qx, sx, ix, bx, rx;  // rx, ry: crossings per unit tau
     float qy, sy, iy, by, ry;
     int nxc, nyc, i0, j0, di, dj;
+    float fnx, fny;  // nxc, nyc as floats
     float dl;    // tau covered by one lane's share of a chunk (span / 32)
     int nchunk;
 };
@@ -182,8 +191,10 @@ __device__ __forceinline__ bool trace_setup(const TraceGeo &T, const RayRec &r, 
     W.iy = D.i1;
     W.by = D.b1;
     W.ry = fabsf(r.w1);
-    W.nxc = W.sx != 0.f ? count_before(D.tout, W.qx, W.sx, W.ix, W.bx, W.rx, T.nx, false) : 0;
-    W.nyc = W.sy != 0.f ? count_before(D.tout, W.qy, W.sy, W.iy, W.by, W.ry, T.ny, false) : 0;
+    W.fnx = W.sx != 0.f ? count_before(D.tout, W.qx, W.sx, W.ix, W.bx, W.rx, (float)T.nx, false) : 0.f;
+    W.fny = W.sy != 0.f ? count_before(D.tout, W.qy, W.sy, W.iy, W.by, W.ry, (float)T.ny, false) : 0.f;
+    W.nxc = (int)W.fnx;
+    W.nyc = (int)W.fny;
     W.i0 = D.off % T.nx;  // D.off = i0 + j0 nx
     W.j0 = D.off / T.nx;
     W.di = W.sx > 0.f ? 1 : (W.sx < 0.f ? -1 : 0);
@@ -214,27 +225,32 @@ __device__ __forceinline__ int build_chunk(const TraceGeo &T, const WTrace &W, i
     const int k = c * 32 + lane;
     const float la = __fmaf_rn((float)k, W.dl, W.tin);
     const float lb = (last && lane == 31) ? INFINITY : __fmaf_rn((float)(k + 1), W.dl, W.tin);
-    int cx = count_before(la, W.qx, W.sx, W.ix, W.bx, W.rx, W.nxc, false);
-    int cy = count_before(la, W.qy, W.sy, W.iy, W.by, W.ry, W.nyc, false);
+    float fx = count_before(la, W.qx, W.sx, W.ix, W.bx, W.rx, W.fnx, false);
+    float fy = count_before(la, W.qy, W.sy, W.iy, W.by, W.ry, W.fny, false);
+    // the next plane of each family: q + count * s (exact small integers in float)
+    float qxc = __fmaf_rn(fx, W.sx, W.qx), qyc = __fmaf_rn(fy, W.sy, W.qy);
+    int cx = (int)fx, cy = (int)fy;
     const int base = __shfl_sync(0xffffffffu, cx + cy, 0);
 #pragma unroll 1
     for (int it = 0; it < kChunk; ++it) {
-        const float tx = cx < W.nxc ? __fmaf_rn(W.qx + (float)cx * W.sx, W.ix, W.bx) : INFINITY;
-        const float ty = cy < W.nyc ? __fmaf_rn(W.qy + (float)cy * W.sy, W.iy, W.by) : INFINITY;
+        const float tx = cx < W.nxc ? __fmaf_rn(qxc, W.ix, W.bx) : INFINITY;
+        const float ty = cy < W.nyc ? __fmaf_rn(qyc, W.iy, W.by) : INFINITY;
         const float t = fminf(tx, ty);
         if (!(t < lb)) break;
         const int k2 = cx + cy - base;
-        if (k2 >= 0 && k2 < kChunk) {
-            slot[k2] = make_float2(t, __int_as_float(col_offset(T, W, cx, cy)));
+        if (k2 >= 0 && k2 < kChunk) slot[k2] = make_float2(t, __int_as_float(col_offset(T, W, cx, cy)));
+        if (tx <= ty) {
+            ++cx;
+            qxc += W.sx;
+        } else {
+            ++cy;
+            qyc += W.sy;
         }
-        if (tx <= ty) ++cx;
-        else ++cy;
     }
     int n = __shfl_sync(0xffffffffu, cx + cy, 31) - base;
     if (last) {
-        if (lane == 0 && n >= 0 && n < kChunk) {
+        if (lane == 0 && n >= 0 && n < kChunk)
             slot[n] = make_float2(W.tout, __int_as_float(col_offset(T, W, W.nxc, W.nyc)));
-        }
         ++n;
     }
     __syncwarp();
@@ -400,7 +416,7 @@ __device__ __forceinline__ float fwd_walk(const TraceGeo &T, const WTrace &W, co
 }
 
 template <int U>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_MINB) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_FWD_MINB) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
                                                                      float *__restrict__ sino)
 {
     __shared__ float2 slot_s[kWarpsPerCta][kChunk];
@@ -581,8 +597,10 @@ cudaError_t launch_trace_project(const TraceGeo &T, const float *img, float *ws,
     to_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(img, ws, T.nz, cols);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t ctas = (int64_t)T.ncg * T.n_views * T.n_rb;
-    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(T, ws, sino);
+    TraceGeo G = T;
+    G.ncg = (T.n_cols + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int64_t ctas = (int64_t)G.ncg * G.n_views * G.n_rb;
+    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(G, ws, sino);
     return cudaGetLastError();
 }
 
@@ -591,11 +609,13 @@ cudaError_t launch_trace_backproject(const TraceGeo &T, const float *sino, float
     const int64_t cols = (int64_t)T.nx * T.ny;
     cudaError_t e = cudaMemsetAsync(ws, 0, (size_t)cols * (T.nz + 2) * sizeof(float), s);
     if (e != cudaSuccess) return e;
-    const int64_t ctas = (int64_t)T.ncg * T.n_views * T.n_rb;
+    TraceGeo G = T;
+    G.ncg = (T.n_cols + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int64_t ctas = (int64_t)G.ncg * G.n_views * G.n_rb;
     if (XR_TRACE_AGG)
-        trace_adj_kernel<true><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(T, sino, ws);
+        trace_adj_kernel<true><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(G, sino, ws);
     else
-        trace_adj_kernel<false><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(T, sino, ws);
+        trace_adj_kernel<false><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(G, sino, ws);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     from_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(ws, img, T.nz, cols);

@@ -213,7 +213,7 @@ cudaError_t launch_atten_plane_adj(const RayRec *rays, int64_t n_rays, int nx, i
 struct TraceGeo {
     int nx, ny, nz, n_views, n_rows, n_cols;
     int n_rb;          // blocks of 32 detector rows (a warp: one view, one column, one block)
-    int ncg;           // groups of 4 neighbouring columns (a CTA: 4 warps)
+    int ncg;           // groups of neighbouring columns, one CTA each (set at launch)
     DF x0, y1, z1, idx, idy, idz, cx, cy, D;  // planes i = 0, j = 0, k = 0; 1/d; centre; sod
     float rxy2;            // squared xy half-diagonal of the image (with a small margin)
     const ViewDF *views;   // cos / sin of the view angle, source height H
