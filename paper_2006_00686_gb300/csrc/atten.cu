@@ -12,7 +12,7 @@
 // are compensated (Kahan), so A_k keeps the precision of its own size, not of T.
 // The direction theta is the ray's own (the record's w), so attenuation is taken towards
 // the side the ray runs to.
-#include "xray_internal.h"
+#include "xray_rays.cuh"
 
 namespace xr {
 namespace {
@@ -52,7 +52,7 @@ __device__ __forceinline__ float unit_weight(const Kahan &T, const Kahan &P, flo
 }
 
 template <int BC>
-__global__ void __launch_bounds__(256) atten_fwd_kernel(const RayRec *__restrict__ rays, int64_t n_rays, Grid grid,
+__global__ void __launch_bounds__(256) atten_fwd_kernel(RaySrc rays, int64_t n_rays, Grid grid,
                                                         const float *__restrict__ mu, const float *__restrict__ img,
                                                         int64_t img_bs, float *__restrict__ sino, int64_t sino_bs,
                                                         int batch)
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) atten_fwd_kernel(const RayRec *__restrict
 }
 
 template <int BC>
-__global__ void __launch_bounds__(256) atten_adj_kernel(const RayRec *__restrict__ rays, int64_t n_rays, Grid grid,
+__global__ void __launch_bounds__(256) atten_adj_kernel(RaySrc rays, int64_t n_rays, Grid grid,
                                                         const float *__restrict__ mu, const float *__restrict__ sino,
                                                         int64_t sino_bs, float *__restrict__ img, int64_t img_bs,
                                                         int batch)
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) atten_adj_kernel(const RayRec *__restrict
 }
 
 template <int BC>
-cudaError_t launch_atten_t(bool adjoint, const RayRec *rays, int64_t n_rays, const Grid &grid, const float *mu,
+cudaError_t launch_atten_t(bool adjoint, const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *mu,
                            const float *in, float *out, int64_t n_units, int batch, int block, cudaStream_t s)
 {
     const dim3 g((unsigned)((n_rays + block - 1) / block), (unsigned)((batch + BC - 1) / BC));
@@ -136,7 +136,7 @@ cudaError_t launch_atten_t(bool adjoint, const RayRec *rays, int64_t n_rays, con
 
 }  // namespace
 
-cudaError_t launch_attenuated(bool adjoint, const RayRec *rays, int64_t n_rays, const Grid &grid, const float *mu,
+cudaError_t launch_attenuated(bool adjoint, const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *mu,
                               const float *in, float *out, int64_t n_units, int batch, int chunk, int block,
                               cudaStream_t s)
 {

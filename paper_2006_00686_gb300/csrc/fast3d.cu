@@ -15,7 +15,7 @@
 // together, so every thread keeps U independent loads in flight instead of one.
 #include <algorithm>
 
-#include "xray_internal.h"
+#include "xray_rays.cuh"
 
 namespace xr {
 
@@ -181,7 +181,7 @@ __device__ __forceinline__ void scatter_ray(const RayRec &rr, float g, int nx, i
 }
 
 template <int U>
-__global__ void __launch_bounds__(256) fwd3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
+__global__ void __launch_bounds__(256) fwd3d_kernel(RaySrc rays, int n_rays, RayOrder ord,
                                                     int nx, int ny, int nz, const float *__restrict__ img,
                                                     const float *__restrict__ imgT, float *__restrict__ sino, int *err)
 {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(const RayRec *__restrict__ r
 }
 
 template <int U>
-__global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict__ rays, int n_rays, RayOrder ord,
+__global__ void __launch_bounds__(256) scatter3d_kernel(RaySrc rays, int n_rays, RayOrder ord,
                                                         int nx, int ny, int nz, const float *__restrict__ sino,
                                                         float *__restrict__ out, float *__restrict__ accT, int *err)
 {
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) scatter3d_kernel(const RayRec *__restrict
 // The same walks on a z-fastest copy [y][x][z] (strides nz, nx * nz, 1): the column-major
 // ray order's layout.
 template <int U>
-__global__ void __launch_bounds__(256) fwd3dz_kernel(const RayRec *__restrict__ rays, int n_threads, RayOrder ord,
+__global__ void __launch_bounds__(256) fwd3dz_kernel(RaySrc rays, int n_threads, RayOrder ord,
                                                      int nx, int ny, int nz, const float *__restrict__ imgZ,
                                                      float *__restrict__ sino, int *err)
 {
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) fwd3dz_kernel(const RayRec *__restrict__ 
 }
 
 template <int U>
-__global__ void __launch_bounds__(256) scatter3dz_kernel(const RayRec *__restrict__ rays, int n_threads,
+__global__ void __launch_bounds__(256) scatter3dz_kernel(RaySrc rays, int n_threads,
                                                          RayOrder ord, int nx, int ny, int nz,
                                                          const float *__restrict__ sino, float *__restrict__ accZ,
                                                          int *err)
@@ -296,10 +296,10 @@ __global__ void __launch_bounds__(256, ADJ ? XR_BATCH_ADJ_MIN_BLOCKS : 1) batche
             const int64_t r = first + q;
             if (r >= P.n_rays) break;
             if (!ADJ) {
-                P.sino[r] = fwd_ray<U>(P.rays[r], P.nx, P.ny, P.nz, P.img, P.aux);
+                P.sino[r] = fwd_ray<U>((*P.src)[r], P.nx, P.ny, P.nz, P.img, P.aux);
             } else {
                 const float g = __ldg(P.sino + r);
-                if (g != 0.f) scatter_ray<U>(P.rays[r], g, P.nx, P.ny, P.nz, const_cast<float *>(P.img), P.aux);
+                if (g != 0.f) scatter_ray<U>((*P.src)[r], g, P.nx, P.ny, P.nz, const_cast<float *>(P.img), P.aux);
             }
         }
     }
@@ -314,10 +314,10 @@ __global__ void __launch_bounds__(1024) flat_dda_kernel(const BatchItem *__restr
     const int64_t r = (t - P.tile_begin) * tile + threadIdx.x;
     if (r >= P.n_rays) return;
     if (!ADJ) {
-        P.sino[r] = fwd_ray<U>(P.rays[r], P.nx, P.ny, P.nz, P.img, P.aux);
+        P.sino[r] = fwd_ray<U>((*P.src)[r], P.nx, P.ny, P.nz, P.img, P.aux);
     } else {
         const float g = __ldg(P.sino + r);
-        if (g != 0.f) scatter_ray<U>(P.rays[r], g, P.nx, P.ny, P.nz, const_cast<float *>(P.img), P.aux);
+        if (g != 0.f) scatter_ray<U>((*P.src)[r], g, P.nx, P.ny, P.nz, const_cast<float *>(P.img), P.aux);
     }
 }
 
@@ -472,7 +472,7 @@ static cudaError_t launch_transpose_rc(const float *in, float *out, int64_t rows
     return cudaGetLastError();
 }
 
-cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
+cudaError_t launch_project3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
                              float *ws, float *sino, int block, int *err, cudaStream_t s)
 {
     order = fit_order(g, n_rays, order);
@@ -494,7 +494,7 @@ cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_r
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order,
+cudaError_t launch_scatter3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order,
                              const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s)
 {
     order = fit_order(g, n_rays, order);

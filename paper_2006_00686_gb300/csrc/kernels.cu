@@ -1,7 +1,7 @@
 // Ray kernels on the caller's layout: forward projection, ray-driven scatter adjoint,
 // unit-driven gather adjoint (2D) and sparse-row export.  All FP32 with FP32
 // accumulation; no tensor cores (the work is a gather along rays, not a contraction).
-#include "xray_internal.h"
+#include "xray_rays.cuh"
 
 namespace xr {
 
@@ -60,7 +60,7 @@ struct ExportVisitor {
 // ---------------------------------------------------------------------------------------
 
 template <int BC>
-__global__ void __launch_bounds__(256) project_kernel(const RayRec *__restrict__ rays, int64_t n_rays,
+__global__ void __launch_bounds__(256) project_kernel(RaySrc rays, int64_t n_rays,
                                                       Grid grid, const float *__restrict__ img,
                                                       int64_t img_bs, float *__restrict__ sino,
                                                       int64_t sino_bs, int batch)
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) project_kernel(const RayRec *__restrict__
 }
 
 template <int BC>
-__global__ void __launch_bounds__(256) scatter_kernel(const RayRec *__restrict__ rays, int64_t n_rays,
+__global__ void __launch_bounds__(256) scatter_kernel(RaySrc rays, int64_t n_rays,
                                                       Grid grid, const float *__restrict__ sino,
                                                       int64_t sino_bs, float *__restrict__ img,
                                                       int64_t img_bs, int batch)
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const RayRec *__restrict__
 }
 
 template <int BC>
-static cudaError_t launch_project_t(const RayRec *rays, int64_t n_rays, const Grid &grid,
+static cudaError_t launch_project_t(const RaySrc &rays, int64_t n_rays, const Grid &grid,
                                     const float *img, int64_t img_bs, float *sino, int64_t sino_bs,
                                     int batch, int block, cudaStream_t s)
 {
@@ -114,7 +114,7 @@ static cudaError_t launch_project_t(const RayRec *rays, int64_t n_rays, const Gr
 }
 
 template <int BC>
-static cudaError_t launch_scatter_t(const RayRec *rays, int64_t n_rays, const Grid &grid,
+static cudaError_t launch_scatter_t(const RaySrc &rays, int64_t n_rays, const Grid &grid,
                                     const float *sino, int64_t sino_bs, float *img, int64_t img_bs,
                                     int batch, int block, cudaStream_t s)
 {
@@ -123,7 +123,7 @@ static cudaError_t launch_scatter_t(const RayRec *rays, int64_t n_rays, const Gr
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const RayRec *rays, int64_t n_rays, const Grid &grid, const float *img,
+cudaError_t launch_project(const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *img,
                            int64_t img_bs, float *sino, int64_t sino_bs, int batch, int chunk,
                            int block, cudaStream_t s)
 {
@@ -136,7 +136,7 @@ cudaError_t launch_project(const RayRec *rays, int64_t n_rays, const Grid &grid,
     }
 }
 
-cudaError_t launch_backproject_scatter(const RayRec *rays, int64_t n_rays, const Grid &grid,
+cudaError_t launch_backproject_scatter(const RaySrc &rays, int64_t n_rays, const Grid &grid,
                                        const float *sino, int64_t sino_bs, float *img,
                                        int64_t img_bs, int batch, int chunk, int block,
                                        cudaStream_t s)
@@ -244,7 +244,7 @@ cudaError_t launch_backproject_gather2d(const RayRec *rays, const GeoParams &g, 
 // Sparse rows (projection-matrix export): one thread per listed ray.
 // ---------------------------------------------------------------------------------------
 
-__global__ void ray_units_kernel(const RayRec *__restrict__ rays, int64_t n_rays, Grid grid,
+__global__ void ray_units_kernel(RaySrc rays, int64_t n_rays, Grid grid,
                                  const int64_t *__restrict__ ids, int n, int cap,
                                  int64_t *__restrict__ idx, float *__restrict__ len,
                                  int32_t *__restrict__ count)
@@ -261,7 +261,7 @@ __global__ void ray_units_kernel(const RayRec *__restrict__ rays, int64_t n_rays
     count[q] = vis.n;
 }
 
-cudaError_t launch_ray_units(const RayRec *rays, int64_t n_rays, const Grid &grid, const int64_t *ids, int n,
+cudaError_t launch_ray_units(const RaySrc &rays, int64_t n_rays, const Grid &grid, const int64_t *ids, int n,
                              int cap, int64_t *idx, float *len, int32_t *count, cudaStream_t s)
 {
     const int block = 128;

@@ -103,7 +103,7 @@ xr_status fill_list(const xr_problem *probs, int32_t n, int32_t tile, int dev, W
         if (((uintptr_t)probs[i].img & 15u) || ((uintptr_t)probs[i].sino & 15u)) return XR_ERR_ALIGN;
         if (g->n_units >= ((int64_t)1 << 31)) return XR_ERR_SIZE;  // 32-bit walk offsets
         BatchItem &it = w.items[i];
-        it.rays = g->d_rays;
+        it.src = g->d_src;
         it.img = probs[i].img;
         it.sino = probs[i].sino;
         it.aux = nullptr;  // no copies: every ray reads the caller's layout

@@ -10,7 +10,7 @@
 // The rays of all views form one stream of candidates that the CTA's 256 threads take in
 // turn (thread t takes every candidate whose running index is t mod 256), so the work
 // stays balanced whatever the footprint sizes.
-#include "xray_internal.h"
+#include "xray_rays.cuh"
 
 namespace xr {
 
@@ -101,7 +101,7 @@ __device__ Foot footprint(const Geo3 &G, const ViewRec &V, float xa, float xb, f
     return F;
 }
 
-__global__ void __launch_bounds__(kBlock) tile3d_adj_kernel(const RayRec *__restrict__ rays,
+__global__ void __launch_bounds__(kBlock) tile3d_adj_kernel(RaySrc rays,
                                                             const ViewRec *__restrict__ views, Geo3 G, int ntx,
                                                             int nty, const float *__restrict__ sino, int64_t n_rays,
                                                             float *__restrict__ img, int64_t n_units)
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) tile3d_adj_kernel(const RayRec *__rest
 
 }  // namespace
 
-cudaError_t launch_tile3d_adj(const RayRec *rays, const ViewRec *views, const GeoParams &g, const float *sino,
+cudaError_t launch_tile3d_adj(const RaySrc &rays, const ViewRec *views, const GeoParams &g, const float *sino,
                               int64_t n_rays, float *img, int batch, cudaStream_t s)
 {
     Geo3 G;

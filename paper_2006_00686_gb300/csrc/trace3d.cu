@@ -13,7 +13,7 @@
 // A warp takes one (view, column) and a block of 32 rows (one lane per row):
 //   1. the trace: the xy-plane crossings of the vertical plane inside the image box, merged
 //      in tau order into slabs (tau at the slab's end, column offset), laid out in chunks of
-//      128 slots in the warp's shared memory.  Each lane places the crossings of its own
+//      256 slots in the warp's shared memory.  Each lane places the crossings of its own
 //      share of a chunk's tau range: a crossing's slot is its index plus the number of
 //      crossings of the other family before it, counted exactly, so the lanes need no
 //      communication beyond the chunk's first rank;
@@ -151,7 +151,7 @@ __device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V,
 // in its shared memory, each chunk covering `span` of tau, which holds at most kChunk - 4
 // crossings (the two families cross |w0| + |w1| planes per unit tau).
 #ifndef XR_TRACE_CHUNK
-#define XR_TRACE_CHUNK 128
+#define XR_TRACE_CHUNK 256
 #endif
 #ifndef XR_TRACE_MINB
 #define XR_TRACE_MINB 1

@@ -352,7 +352,10 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views, (size_t)p.n_views * sizeof(ViewRec));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views_df, (size_t)p.n_views * sizeof(ViewDF));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_det, n_det * sizeof(DetRec));
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
+    // cone and helical scans keep no ray table: their kernels rebuild each record from the
+    // per-view and per-detector tables (RaySrc)
+    if (e == cudaSuccess && !kind_cone(p.kind)) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_src, sizeof(RaySrc));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(int));
     if (e == cudaSuccess && !three) e = cudaMalloc(&g->d_view_tab, (size_t)p.n_views * 8 * sizeof(float));
@@ -456,7 +459,15 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     }
     if (e == cudaSuccess) e = launch_det_setup(p, g->d_det, nullptr);
     g->setup_df = make_setup_df(p);
-    if (e == cudaSuccess) e = launch_ray_setup(p, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays, nullptr);
+    g->src.tab = g->d_rays;
+    g->src.views = g->d_views_df;
+    g->src.det = g->d_det;
+    g->src.ndet = (int64_t)p.n_rows * p.n_cols;
+    g->src.g = p;
+    g->src.K = g->setup_df;
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_src, &g->src, sizeof(RaySrc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && g->d_rays)
+        e = launch_ray_setup(p, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays, nullptr);
     if (e == cudaSuccess && g->d_grec) e = launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, nullptr);
     if (e == cudaSuccess) e = slice_setup(g, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
@@ -479,6 +490,7 @@ void xr_geometry_destroy(xr_geometry *g)
     cudaFree(g->d_views_df);
     cudaFree(g->d_det);
     cudaFree(g->d_rays);
+    cudaFree(g->d_src);
     cudaFree(g->d_view_tab);
     cudaFree(g->d_grec);
     cudaFree(g->d_ws);
@@ -497,8 +509,9 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream)
 {
     if (!g) return XR_ERR_NULL;
     XR_CUDA(launch_det_setup(g->params, g->d_det, (cudaStream_t)stream));
-    XR_CUDA(launch_ray_setup(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays,
-                             (cudaStream_t)stream));
+    if (g->d_rays)
+        XR_CUDA(launch_ray_setup(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays,
+                                 (cudaStream_t)stream));
     if (g->d_grec) XR_CUDA(launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, (cudaStream_t)stream));
     XR_CUDA(slice_setup(g, (cudaStream_t)stream));
     return XR_OK;
@@ -545,7 +558,7 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
     if (!g || !info) return XR_ERR_NULL;
     info->n_rays = g->n_rays;
     info->n_units = g->n_units;
-    info->table_bytes = g->n_rays * (int64_t)sizeof(RayRec) + (int64_t)g->params.n_views * (8 * 4 + sizeof(ViewRec) + sizeof(ViewDF)) +
+    info->table_bytes = (g->d_rays ? g->n_rays * (int64_t)sizeof(RayRec) : 0) + (int64_t)g->params.n_views * (8 * 4 + sizeof(ViewRec) + sizeof(ViewDF)) +
                         (int64_t)g->params.n_rows * g->params.n_cols * (int64_t)sizeof(DetRec) +
                         (g->d_grec ? g->n_rays * (int64_t)gather_rec_bytes() : 0) + (int64_t)g->ws_bytes +
                         (g->slices.ok ? slice_n2(g) * (int64_t)(sizeof(RayRec) + gather_rec_bytes()) : 0) +
@@ -629,7 +642,7 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
         const cudaStream_t s = (cudaStream_t)stream;
         for (int b = 0; b < batch; ++b) {
             const float *img = d_img + (size_t)b * g->n_units;
-            XR_CUDA(launch_project3d(g->d_rays, g->params, g->n_rays, ray_order(g, false), img, g->d_ws,
+            XR_CUDA(launch_project3d(g->src, g->params, g->n_rays, ray_order(g, false), img, g->d_ws,
                                      d_sino + (size_t)b * g->n_rays, g->tune.block, g->d_err, s));
         }
         return XR_OK;
@@ -648,7 +661,7 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
     }
     const int chunk = pick_chunk(g, batch);
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
-    XR_CUDA(launch_project(g->d_rays, g->n_rays, make_grid(g), d_img, g->n_units, d_sino, g->n_rays, batch,
+    XR_CUDA(launch_project(g->src, g->n_rays, make_grid(g), d_img, g->n_units, d_sino, g->n_rays, batch,
                            chunk, g->tune.block, (cudaStream_t)stream));
     return XR_OK;
 }
@@ -694,7 +707,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         }
         if (kind_is3d(g->params.kind)) {
             if (batch > 65535) return XR_ERR_SIZE;
-            XR_CUDA(launch_tile3d_adj(g->d_rays, g->d_views, g->params, d_sino, g->n_rays, d_img, batch, s));
+            XR_CUDA(launch_tile3d_adj(g->src, g->d_views, g->params, d_sino, g->n_rays, d_img, batch, s));
             return XR_OK;
         }
         if (use_fast(g, batch)) {
@@ -719,7 +732,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     }
     if (!use_tiled(g, batch) && !use_fast(g, batch) && use_dda(g)) {
         for (int b = 0; b < batch; ++b)
-            XR_CUDA(launch_scatter3d(g->d_rays, g->params, g->n_rays, ray_order(g, true), d_sino + (size_t)b * g->n_rays,
+            XR_CUDA(launch_scatter3d(g->src, g->params, g->n_rays, ray_order(g, true), d_sino + (size_t)b * g->n_rays,
                                      d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, g->d_err, s));
         return XR_OK;
     }
@@ -738,7 +751,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         return XR_OK;
     }
     XR_CUDA(cudaMemsetAsync(d_img, 0, (size_t)g->n_units * batch * sizeof(float), s));
-    XR_CUDA(launch_backproject_scatter(g->d_rays, g->n_rays, make_grid(g), d_sino, g->n_rays, d_img, g->n_units,
+    XR_CUDA(launch_backproject_scatter(g->src, g->n_rays, make_grid(g), d_sino, g->n_rays, d_img, g->n_units,
                                        batch, chunk, g->tune.block, s));
     return XR_OK;
 }
@@ -777,7 +790,7 @@ xr_status xr_project_attenuated(const xr_geometry *g, const float *d_mu, const f
     }
     const int chunk = pick_chunk(g, batch);
     if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
-    XR_CUDA(launch_attenuated(false, g->d_rays, g->n_rays, make_grid(g), d_mu, d_img, d_sino, g->n_units, batch,
+    XR_CUDA(launch_attenuated(false, g->src, g->n_rays, make_grid(g), d_mu, d_img, d_sino, g->n_units, batch,
                               chunk, g->tune.block, s));
     return XR_OK;
 }
@@ -803,7 +816,7 @@ xr_status xr_backproject_attenuated(const xr_geometry *g, const float *d_mu, con
         return XR_OK;
     }
     XR_CUDA(cudaMemsetAsync(d_img, 0, (size_t)g->n_units * batch * sizeof(float), s));
-    XR_CUDA(launch_attenuated(true, g->d_rays, g->n_rays, make_grid(g), d_mu, d_sino, d_img, g->n_units, batch,
+    XR_CUDA(launch_attenuated(true, g->src, g->n_rays, make_grid(g), d_mu, d_sino, d_img, g->n_units, batch,
                               chunk, g->tune.block, s));
     return XR_OK;
 }
@@ -827,7 +840,7 @@ xr_status xr_ray_units(const xr_geometry *g, const int64_t *d_rays, int32_t n, i
 {
     if (!g || !d_rays || !d_idx || !d_len || !d_count) return XR_ERR_NULL;
     if (n < 1 || cap < 1) return XR_ERR_SIZE;
-    XR_CUDA(launch_ray_units(g->d_rays, g->n_rays, make_grid(g), d_rays, n, cap, d_idx, d_len, d_count,
+    XR_CUDA(launch_ray_units(g->src, g->n_rays, make_grid(g), d_rays, n, cap, d_idx, d_len, d_count,
                              (cudaStream_t)stream));
     return XR_OK;
 }
@@ -872,7 +885,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
             free(items);
             return XR_ERR_SIZE;
         }
-        items[i].rays = g->d_rays;
+        items[i].src = g->d_src;
         items[i].img = probs[i].img;
         items[i].sino = probs[i].sino;
         items[i].aux = nullptr;

@@ -74,15 +74,28 @@ struct SetupDF {
 
 SetupDF make_setup_df(const GeoParams &g);
 
+// Where kernels get ray records: the handle's table (tab), or -- for scans without a table --
+// rebuilt in the kernel from the per-view and per-detector tables (operator[] is defined in
+// xray_rays.cuh, which kernels that use it include).
+struct RaySrc {
+    const RayRec *tab;
+    const ViewDF *views;
+    const DetRec *det;
+    int64_t ndet;  // detector samples per view
+    GeoParams g;
+    SetupDF K;
+    __device__ __forceinline__ RayRec operator[](int64_t r) const;
+};
+
 cudaError_t launch_det_setup(const GeoParams &g, DetRec *d_det, cudaStream_t s);
 cudaError_t launch_ray_setup(const GeoParams &g, const SetupDF &c, const ViewDF *d_views, const DetRec *d_det,
                              RayRec *d_rays, int64_t n_rays, cudaStream_t s);
 
-cudaError_t launch_project(const RayRec *rays, int64_t n_rays, const Grid &grid, const float *img,
+cudaError_t launch_project(const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *img,
                            int64_t img_bs, float *sino, int64_t sino_bs, int batch, int chunk,
                            int block, cudaStream_t s);
 
-cudaError_t launch_backproject_scatter(const RayRec *rays, int64_t n_rays, const Grid &grid,
+cudaError_t launch_backproject_scatter(const RaySrc &rays, int64_t n_rays, const Grid &grid,
                                        const float *sino, int64_t sino_bs, float *img,
                                        int64_t img_bs, int batch, int chunk, int block,
                                        cudaStream_t s);
@@ -92,12 +105,12 @@ cudaError_t launch_backproject_gather2d(const RayRec *rays, const GeoParams &g, 
                                         int64_t sino_bs, float *img, int64_t img_bs, int batch,
                                         int chunk, int block, cudaStream_t s);
 
-cudaError_t launch_ray_units(const RayRec *rays, int64_t n_rays, const Grid &grid, const int64_t *ray_ids,
+cudaError_t launch_ray_units(const RaySrc &rays, int64_t n_rays, const Grid &grid, const int64_t *ray_ids,
                              int n, int cap, int64_t *idx, float *len, int32_t *count, cudaStream_t s);
 
 // One problem of a persistent batched launch (device copy).
 struct BatchItem {
-    const RayRec *rays;
+    const RaySrc *src;  // device copy of the problem's ray source
     const float *img;
     float *sino;
     float *aux;  // n_units floats: the [nz][nx][ny] copy / accumulator, or NULL (read img only)
@@ -185,15 +198,15 @@ cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int
 // on a z-fastest copy.  ws: one volume of workspace (the [z][x][y] copy, or for order 2 the
 // [y][x][z] copy), written here.  err: the handle's device error word (XR_DEVERR_* bits are
 // or-ed in), or NULL.
-cudaError_t launch_project3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
+cudaError_t launch_project3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
                              float *ws, float *sino, int block, int *err, cudaStream_t s);
 // Orders 0 and 1: zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
 // Order 2: zeroes the z-fastest accumulator accT, scatters, then writes it transposed to out.
-cudaError_t launch_scatter3d(const RayRec *rays, const GeoParams &g, int64_t n_rays, int order,
+cudaError_t launch_scatter3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order,
                              const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s);
 // Unit-driven adjoint for 3D scans (tile3d.cu): one CTA per 16^3 tile of voxels gathers
 // every ray of its detector footprint in shared memory and writes the tile once.
-cudaError_t launch_tile3d_adj(const RayRec *rays, const ViewRec *views, const GeoParams &g, const float *sino,
+cudaError_t launch_tile3d_adj(const RaySrc &rays, const ViewRec *views, const GeoParams &g, const float *sino,
                               int64_t n_rays, float *img, int batch, cudaStream_t s);
 cudaError_t launch_deinterleave_sum(const float *acc0, const float *acc1, int batch, int nx, int ny, int nz, int Bp,
                                     float *img, cudaStream_t s);
@@ -226,7 +239,7 @@ cudaError_t launch_trace_backproject(const TraceGeo &T, const float *sino, float
 
 // Attenuated transform (atten.cu): one thread per ray, `chunk` images per thread; in/out
 // in the caller's layout ([batch][units] / [batch][rays]); the adjoint adds into out.
-cudaError_t launch_attenuated(bool adjoint, const RayRec *rays, int64_t n_rays, const Grid &grid, const float *mu,
+cudaError_t launch_attenuated(bool adjoint, const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *mu,
                               const float *in, float *out, int64_t n_units, int batch, int chunk, int block,
                               cudaStream_t s);
 
@@ -245,7 +258,9 @@ struct xr_geometry {
     xr::ViewDF *d_views_df;  // the same as float pairs
     xr::SetupDF setup_df;    // scan constants of the ray setup
     xr::DetRec *d_det;       // per detector sample (det_setup_kernel)
-    xr::RayRec *d_rays;
+    xr::RayRec *d_rays;      // the ray table (NULL for cone and helical scans)
+    xr::RaySrc src;          // where kernels get ray records (the table, or rebuilt in the kernel)
+    xr::RaySrc *d_src;       // its device copy, for batch work lists
     float *d_view_tab;   // per view: 2D gather footprint data (8 floats)
     void *d_grec;        // per ray: plane constants of the 2D gather
     float *d_ws;         // workspace of the batched fast path (interleaved copies)
