@@ -95,7 +95,8 @@ typedef struct xr_geometry xr_geometry;
 typedef struct {
     int64_t n_rays;        /* n_views * n_rows * n_cols */
     int64_t n_units;       /* nx * ny * nz */
-    int64_t table_bytes;   /* device bytes held by the handle (ray table) */
+    int64_t table_bytes;   /* device bytes held by the handle (tables and workspace); cone and
+                              helical scans hold no per-ray table */
     int32_t is3d;
     int32_t device;        /* CUDA device the handle's tables live on */
     int32_t column_batch;  /* 1: a 3D parallel scan whose views all have phi_1 = 0 (or all pi):
@@ -105,6 +106,8 @@ typedef struct {
                               batch of 2D problems, one per column, on the 2D batched kernels.
                               Requires distinct columns in distinct y-slices and no column
                               plane within 1e-6 dy of a slice boundary; 0 otherwise */
+    int32_t trace_walk;    /* 1: a cone or helical scan the column-trace walk (XR_ORDER_TRACE)
+                              applies to; 0 otherwise */
 } xr_geometry_info;
 
 /* Launch tuning of a handle.  Zero fields keep the current value. */

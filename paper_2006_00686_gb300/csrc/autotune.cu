@@ -65,6 +65,8 @@ std::vector<xr_tuning> candidates(const xr_geometry *g, int batch)
     const int adjs[2] = {XR_ADJ_SCATTER, XR_ADJ_GATHER};
     const int n_adj = list ? 1 : 2;
     if (three) {
+        if (g->trace_ok)  // the column-trace walk (scatter adjoint)
+            out.push_back(xr_tuning{128, 16, XR_ADJ_SCATTER, XR_PATH_INTERLEAVED, XR_ORDER_TRACE});
         for (int order : {XR_ORDER_VIEW, XR_ORDER_ROW, XR_ORDER_COLUMN, XR_ORDER_ROWBLOCK})
             for (int a = 0; a < n_adj; ++a) out.push_back(xr_tuning{128, 16, adjs[a], XR_PATH_INTERLEAVED, order});
         out.push_back(xr_tuning{128, batch < 16 ? (batch < 2 ? 1 : 2) : 16, XR_ADJ_SCATTER, XR_PATH_RAY,

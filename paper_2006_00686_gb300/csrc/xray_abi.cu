@@ -566,6 +566,7 @@ xr_status xr_geometry_get_info(const xr_geometry *g, xr_geometry_info *info)
     info->is3d = kind_is3d(g->params.kind);
     info->device = g->device;
     info->column_batch = g->slices.ok ? 1 : 0;
+    info->trace_walk = g->trace_ok ? 1 : 0;
     return XR_OK;
 }
 

@@ -71,7 +71,11 @@ def _time(fn, reps: int, budget_s: float) -> float:
 def projector_candidates(g, batch: int) -> list:
     out = []
     if g.is3d:
-        # the volume-copy path in either ray order with either adjoint, then the caller's layout
+        # the column-trace walk of cone and helical scans (scatter adjoint), the volume-copy path
+        # in either ray order with either adjoint, then the caller's layout
+        if g.kind in ("cone", "cone_arc", "helix", "helix_arc"):
+            out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=X.XR_ADJ_SCATTER, block=128,
+                            order=X.XR_ORDER_TRACE))
         for order in (X.XR_ORDER_VIEW, X.XR_ORDER_ROW, X.XR_ORDER_COLUMN, X.XR_ORDER_ROWBLOCK):
             for adj in (X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER):
                 out.append(dict(path=X.XR_PATH_INTERLEAVED, batch_chunk=16, adjoint=adj, block=128, order=order))

@@ -42,7 +42,8 @@ class _Desc(ctypes.Structure):
 
 class _Info(ctypes.Structure):
     _fields_ = [("n_rays", ctypes.c_int64), ("n_units", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
-                ("is3d", ctypes.c_int32), ("device", ctypes.c_int32), ("column_batch", ctypes.c_int32)]
+                ("is3d", ctypes.c_int32), ("device", ctypes.c_int32), ("column_batch", ctypes.c_int32),
+                ("trace_walk", ctypes.c_int32)]
 
 
 class _Tuning(ctypes.Structure):
@@ -168,6 +169,7 @@ class Projector:
         self.n_rays, self.n_units = int(info.n_rays), int(info.n_units)
         self.table_bytes = int(info.table_bytes)
         self.column_batch = bool(info.column_batch)  # single-tilt-axis scan run as 2D column problems
+        self.trace_walk = bool(info.trace_walk)  # cone / helical scan the column-trace walk applies to
         self.device = torch.device("cuda", int(info.device))
         self.reserved = 0
         self.auto_reserve = True

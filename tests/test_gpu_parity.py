@@ -299,9 +299,10 @@ def test_fast3d_matches_ray_path(name, order):
     Pf.set_tuning(order=order)
     Pr.set_tuning(path=XR_PATH_RAY)
     yf, yr = Pf.forward(x), Pr.forward(x)
-    if Pf.column_batch:
-        # the single-tilt-axis scan runs as 2D column problems: the slab walk adds the same
-        # lengths, against t when the driving index falls along the ray
+    if Pf.column_batch or (order == 0 and Pf.trace_walk):
+        # the single-tilt-axis scan runs as 2D column problems, and the automatic order takes
+        # the column-trace walk of cone and helical scans: the same lengths by other
+        # arithmetic (the slab walk; lengths in horizontal distance times sec)
         assert Pf.reserved >= 1 and float((yf - yr).abs().max()) <= 1e-5 * float(yr.abs().max())
     else:
         assert Pf.reserved >= 1 and torch.equal(yf, yr)
