@@ -31,7 +31,13 @@ def test_candidates_cover_paths():
     g3 = inputs.Geometry("cone", 8, 8, 8, angles=np.arange(4) * 0.5, n_cols=9, n_rows=9, sod=40.0, sdd=60.0)
     c3 = tune.projector_candidates(g3, 8)
     assert {c["adjoint"] for c in c3} == {X.XR_ADJ_GATHER, X.XR_ADJ_SCATTER}
-    assert {c["order"] for c in c3} == {X.XR_ORDER_VIEW, X.XR_ORDER_ROW, X.XR_ORDER_COLUMN, X.XR_ORDER_ROWBLOCK}
+    # cone and helical scans also try the column-trace walk (scatter adjoint)
+    assert {c["order"] for c in c3} == {X.XR_ORDER_VIEW, X.XR_ORDER_ROW, X.XR_ORDER_COLUMN, X.XR_ORDER_ROWBLOCK,
+                                        X.XR_ORDER_TRACE}
+    assert all(c["adjoint"] == X.XR_ADJ_SCATTER for c in c3 if c["order"] == X.XR_ORDER_TRACE)
+    gp = inputs.Geometry("par3d", 8, 8, 8, angles=np.stack([np.arange(4) * 0.5, np.arange(4) * 0.2], axis=1),
+                         n_cols=9, n_rows=9)
+    assert X.XR_ORDER_TRACE not in {c["order"] for c in tune.projector_candidates(gp, 1)}
     assert all(c["path"] != X.XR_PATH_TILED for c in tune.projector_candidates(g3, 8))
 
 
