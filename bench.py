@@ -845,6 +845,7 @@ CASES = {"cone_384": case_cone_384, "uneven_16": case_uneven_16}
 # 3D scans at most PER_CONFIG_3D_STEPS timed steps) and a shorter oracle sample
 PER_CONFIG = ("par2d_64", "par3d_256_tilt", "cone_512", "helix_512x256", "fans_uneven_64")
 PER_CONFIG_3D_STEPS = 20
+PER_CONFIG_SHORT_STEPS = 20000
 PER_CONFIG_CPU_S = 5.0
 
 
@@ -858,6 +859,8 @@ def per_config(args, rank, world, local_rank):
         a.workload = wl
         if wl in ("cone_512", "helix_512x256"):
             a.steps = min(args.steps, PER_CONFIG_3D_STEPS)
+        if wl == "par2d_64":  # 0.03 ms steps: enough of them for the clock sampler (~0.6 s)
+            a.steps = max(args.steps, PER_CONFIG_SHORT_STEPS)
         if wl == "fans_uneven_64":
             a.tile = a.plan_block = 0
         t0 = time.perf_counter()

@@ -282,6 +282,23 @@ xr_status xr_get_device_error(const xr_geometry *g, int32_t *code);
 xr_status xr_ray_units(const xr_geometry *g, const int64_t *d_rays, int32_t n, int32_t cap,
                        int64_t *d_idx, float *d_len, int32_t *d_count, xr_stream stream);
 
+/* Compressed sparse rows (CSR) of the projection matrix for the rays [ray0, ray0 + n)
+ * (Algorithm 1/2 "Output": each ray's units I with their lengths l; Section 4.2: the matrix
+ * stored in sparse pattern).  Two passes over the same walk as xr_ray_units and the
+ * crossing-order kernels:
+ *   xr_system_rows_count writes d_row_ptr[0 .. n] (device int64, 8-byte aligned): row q (ray
+ *   ray0 + q) holds entries d_row_ptr[q] .. d_row_ptr[q + 1] - 1, d_row_ptr[0] = 0 and
+ *   d_row_ptr[n] = the number of entries (a counting kernel, then an in-place scan by one CTA;
+ *   meant for validation-sized problems);
+ *   xr_system_rows_fill then writes d_col[k] (device int64: the 1D unit index I) and d_val[k]
+ *   (device float32: the length) for every entry, each row in the order the ray crosses its
+ *   units.  The caller allocates d_col and d_val with d_row_ptr[n] elements.
+ * Stream-ordered; no allocation.  Errors: XR_ERR_NULL, XR_ERR_SIZE (n < 1, ray0 < 0 or
+ * ray0 + n > n_rays), XR_ERR_ALIGN, XR_ERR_CUDA. */
+xr_status xr_system_rows_count(const xr_geometry *g, int64_t ray0, int32_t n, int64_t *d_row_ptr, xr_stream stream);
+xr_status xr_system_rows_fill(const xr_geometry *g, int64_t ray0, int32_t n, const int64_t *d_row_ptr,
+                              int64_t *d_col, float *d_val, xr_stream stream);
+
 /* One problem of a batched launch: a geometry with its own image and sinogram. */
 typedef struct {
     const xr_geometry *geom;

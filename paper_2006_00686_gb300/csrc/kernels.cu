@@ -270,4 +270,114 @@ cudaError_t launch_ray_units(const RaySrc &rays, int64_t n_rays, const Grid &gri
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// Compressed sparse rows of the projection matrix: a counting pass, a scan of the counts into
+// row pointers, a filling pass.  Both passes walk each ray the same way, so the fill writes
+// exactly the counted entries.
+// ---------------------------------------------------------------------------------------
+
+struct CountVisitor {
+    int64_t n;
+    __device__ __forceinline__ void operator()(int64_t, float) { ++n; }
+};
+
+struct CsrVisitor {
+    int64_t *col;
+    float *val;
+    int64_t k, end;  // next slot, end of the row
+    __device__ __forceinline__ void operator()(int64_t off, float l)
+    {
+        if (k < end) {  // never false: the counting pass walked the same units
+            col[k] = off;
+            val[k] = l;
+        }
+        ++k;
+    }
+};
+
+// ptr[q + 1] = number of units ray ray0 + q crosses; ptr[0] = 0
+__global__ void csr_count_kernel(RaySrc rays, int64_t ray0, int n, Grid grid, int64_t *__restrict__ ptr)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0) ptr[0] = 0;
+    if (q >= n) return;
+    CountVisitor vis{0};
+    walk_ray(rays[ray0 + q], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, vis);
+    ptr[q + 1] = vis.n;
+}
+
+// In-place inclusive scan of a[0 .. n) by one CTA of 1024 threads, 4096 elements per round with
+// the running total carried between rounds (no scratch memory).
+__global__ void __launch_bounds__(1024) csr_scan_kernel(int64_t *__restrict__ a, int64_t n)
+{
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 4096) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * 4;
+        int64_t v[4], t = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (i0 + k < n) ? a[i0 + k] : 0;
+            t += v[k];
+            v[k] = t;  // inclusive within the thread
+        }
+        // inclusive scan of the thread totals across the warp, then across the warps
+        int64_t x = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t z = warp_tot[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, z, d);
+                if (lane >= d) z += y;
+            }
+            warp_tot[lane] = z;  // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t before = carry_s + (w > 0 ? warp_tot[w - 1] : 0) + (x - t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i0 + k < n) a[i0 + k] = before + v[k];
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s += warp_tot[31];
+        __syncthreads();
+    }
+}
+
+__global__ void csr_fill_kernel(RaySrc rays, int64_t ray0, int n, Grid grid, const int64_t *__restrict__ ptr,
+                                int64_t *__restrict__ col, float *__restrict__ val)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    CsrVisitor vis{col, val, ptr[q], ptr[q + 1]};
+    walk_ray(rays[ray0 + q], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, vis);
+}
+
+cudaError_t launch_csr_count(const RaySrc &rays, int64_t ray0, int n, const Grid &grid, int64_t *ptr, cudaStream_t s)
+{
+    const int block = 128;
+    csr_count_kernel<<<(unsigned)((n + block - 1) / block), block, 0, s>>>(rays, ray0, n, grid, ptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    csr_scan_kernel<<<1, 1024, 0, s>>>(ptr + 1, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_fill(const RaySrc &rays, int64_t ray0, int n, const Grid &grid, const int64_t *ptr,
+                            int64_t *col, float *val, cudaStream_t s)
+{
+    const int block = 128;
+    csr_fill_kernel<<<(unsigned)((n + block - 1) / block), block, 0, s>>>(rays, ray0, n, grid, ptr, col, val);
+    return cudaGetLastError();
+}
+
 }  // namespace xr

@@ -846,6 +846,33 @@ xr_status xr_ray_units(const xr_geometry *g, const int64_t *d_rays, int32_t n, i
     return XR_OK;
 }
 
+static xr_status csr_args(const xr_geometry *g, int64_t ray0, int32_t n, const void *ptr)
+{
+    if (!g || !ptr) return XR_ERR_NULL;
+    if (n < 1 || ray0 < 0 || ray0 + n > g->n_rays) return XR_ERR_SIZE;
+    if ((uintptr_t)ptr & 7u) return XR_ERR_ALIGN;
+    return XR_OK;
+}
+
+xr_status xr_system_rows_count(const xr_geometry *g, int64_t ray0, int32_t n, int64_t *d_row_ptr, xr_stream stream)
+{
+    const xr_status st = csr_args(g, ray0, n, d_row_ptr);
+    if (st != XR_OK) return st;
+    XR_CUDA(launch_csr_count(g->src, ray0, n, make_grid(g), d_row_ptr, (cudaStream_t)stream));
+    return XR_OK;
+}
+
+xr_status xr_system_rows_fill(const xr_geometry *g, int64_t ray0, int32_t n, const int64_t *d_row_ptr, int64_t *d_col,
+                              float *d_val, xr_stream stream)
+{
+    const xr_status st = csr_args(g, ray0, n, d_row_ptr);
+    if (st != XR_OK) return st;
+    if (!d_col || !d_val) return XR_ERR_NULL;
+    if (((uintptr_t)d_col & 7u) || ((uintptr_t)d_val & 3u)) return XR_ERR_ALIGN;
+    XR_CUDA(launch_csr_fill(g->src, ray0, n, make_grid(g), d_row_ptr, d_col, d_val, (cudaStream_t)stream));
+    return XR_OK;
+}
+
 }  // extern "C"
 
 struct xr_batch {

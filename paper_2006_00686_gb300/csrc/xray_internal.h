@@ -108,6 +108,11 @@ cudaError_t launch_backproject_gather2d(const RayRec *rays, const GeoParams &g, 
 cudaError_t launch_ray_units(const RaySrc &rays, int64_t n_rays, const Grid &grid, const int64_t *ray_ids,
                              int n, int cap, int64_t *idx, float *len, int32_t *count, cudaStream_t s);
 
+// CSR rows of rays [ray0, ray0 + n): count (ptr[0..n], scanned in place) and fill.
+cudaError_t launch_csr_count(const RaySrc &rays, int64_t ray0, int n, const Grid &grid, int64_t *ptr, cudaStream_t s);
+cudaError_t launch_csr_fill(const RaySrc &rays, int64_t ray0, int n, const Grid &grid, const int64_t *ptr,
+                            int64_t *col, float *val, cudaStream_t s);
+
 // One problem of a persistent batched launch (device copy).
 struct BatchItem {
     const RaySrc *src;  // device copy of the problem's ray source

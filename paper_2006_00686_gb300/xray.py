@@ -71,6 +71,8 @@ SIGNATURES = {
     "xr_backproject": (_I32, [_VP, _VP, _VP, _I32, _VP]),
     "xr_backproject_method": (_I32, [_VP, _VP, _VP, _I32, _I32, _VP]),
     "xr_ray_units": (_I32, [_VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP]),
+    "xr_system_rows_count": (_I32, [_VP, _I64, _I32, _VP, _VP]),
+    "xr_system_rows_fill": (_I32, [_VP, _I64, _I32, _VP, _VP, _VP, _VP]),
     "xr_batch_create": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _I32, ctypes.POINTER(_VP)]),
     "xr_batch_destroy": (None, [_VP]),
     "xr_batch_project": (_I32, [_VP, _VP]),
@@ -315,6 +317,22 @@ class Projector:
         if (cnt_h > cap).any():
             raise XRayError("ray_units: cap too small")
         return [(idx_h[q, :cnt_h[q]], ln_h[q, :cnt_h[q]]) for q in range(n)]
+
+
+    def system_rows(self, ray0: int = 0, n: int | None = None, stream=None):
+        """CSR rows of the projection matrix for rays [ray0, ray0 + n): (row_ptr int64 [n + 1],
+        col int64 [nnz] (1D unit index), val float32 [nnz] (length)), device tensors; each row in
+        the order the ray crosses its units.  Synchronises once to size the outputs."""
+        n = self.n_rays - ray0 if n is None else int(n)
+        ptr = torch.empty((n + 1,), dtype=torch.int64, device=self.device)
+        _check(lib().xr_system_rows_count(self._h, int(ray0), n, _ptr(ptr), _stream(stream)),
+               "xr_system_rows_count")
+        nnz = int(ptr[-1].item())
+        col = torch.empty((max(nnz, 1),), dtype=torch.int64, device=self.device)
+        val = torch.empty((max(nnz, 1),), dtype=torch.float32, device=self.device)
+        _check(lib().xr_system_rows_fill(self._h, int(ray0), n, _ptr(ptr), _ptr(col), _ptr(val), _stream(stream)),
+               "xr_system_rows_fill")
+        return ptr, col[:nnz], val[:nnz]
 
 
 class XRayFunction(torch.autograd.Function):
