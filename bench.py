@@ -464,10 +464,70 @@ def _launch_count(P, g, B):
         # detector setup, ray setup, the column problem's ray records and gather constants,
         # then per image: the slice planes, the forward, the sinogram planes, the gather
         return 4 + 4 * B
+    if P.trace_walk:
+        # detector setup (no per-ray table), then per image: the padded z-fastest copy, the
+        # trace forward, the trace adjoint and the fold of the accumulator (its zero fill is a
+        # memset)
+        return 1 + 4 * B
     # detector setup, ray setup (2D: and the gather's per-ray constants), then per image:
     # the layout copy, the forward walk, the scatter walk and the fold of the accumulator
     # (zero fills are memsets)
     return (2 if g.is3d else 3) + 4 * B
+
+
+def run_split(args, rank, world, local_rank):
+    """One scan split by views over the ranks (strong scaling): each rank sets up and projects
+    its contiguous block of views, back-projects it into a partial image, and one all-reduce
+    (NCCL) sums the partial images.  value = rays of the whole scan x images / step time
+    (max over ranks)."""
+    import torch
+
+    from paper_2006_00686_gb300 import inputs, parallel
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    builder, B, n_shapes, seed, desc = WORKLOADS[args.workload]
+    g = getattr(inputs, builder)()
+    S = parallel.ShardedProjector(g)
+    if B > 1:
+        x = inputs.phantom_batch(g, B, n_shapes, seed0=seed, device=str(dev))
+    else:
+        x = inputs.phantom(g, n_shapes, seed, device=str(dev)).float().contiguous()
+    flush = torch.empty(64 * 1024 * 1024, device=dev)
+    yb = None
+    if S.local is not None:
+        yb = torch.empty(S.local_geom.sino_shape(B if B > 1 else None), device=dev)
+
+    def make_step(xb, yblk):
+        def step(recs=None):
+            st = torch.cuda.current_stream()
+            e = _events(2) if recs is not None else None
+            if e: e[0].record(st)
+            if S.local is not None:
+                S.local.ray_setup(st)
+                S.forward(xb, out=yblk)
+            z = S.adjoint(yblk, like=xb)
+            if e: e[1].record(st)
+            if recs is not None:
+                recs.append(e)
+            return z
+        return step
+
+    step = make_step(x, yb)
+    recs, clocks, wall = _timed_loop(step, args, flush, world, local_rank)
+    ms = parallel.max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in recs])), dev)
+    rays = g.n_rays * B
+    out = {"metric": METRIC, "value": round(rays / (ms * 1e-3) / 1e9, 4), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded random-ellipse phantoms)",
+           "config": {"workload": args.workload, "geometry": desc, "split": "views",
+                      "views_per_rank": [len(v) for v in parallel.view_shards(g.n_views, world)],
+                      "collective": "one all-reduce of the partial adjoint images per step",
+                      "l2": "flushed between timed steps (256 MiB write)"},
+           "gpu_launches": None, "clocks": clocks, "wall_s": round(wall, 3)}
+    S.close()
+    return out
 
 
 def _autograd_and_sirt(P, x, y, args):
@@ -884,6 +944,9 @@ def main():
                     help="one workload only (default: the fan-beam headline plus every other scan "
                          "configuration under extra.per_config)")
     ap.add_argument("--no-per-config", action="store_true", help="the headline workload only")
+    ap.add_argument("--split", default=None, choices=["views"],
+                    help="split one scan of --workload by views over the ranks (strong scaling, one "
+                         "all-reduce of the adjoint per step) instead of one batch per rank")
     ap.add_argument("--case", default=None, help="run one profiling case (%s) and exit" % ", ".join(
         ["cone_384", "uneven_16"]))
     ap.add_argument("--adjoint", default=None, choices=["gather", "scatter"],
@@ -932,6 +995,13 @@ def main():
         torch.distributed.barrier()
     if rank != 0:
         __graft_entry__.build()  # up to date by now: only checks and imports
+    if args.split == "views":
+        out = run_split(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     out = run_ours(args, rank, world, local_rank)
     if all_configs:
         out.setdefault("extra", {})["per_config"] = per_config(args, rank, world, local_rank)
