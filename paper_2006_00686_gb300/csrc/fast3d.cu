@@ -406,7 +406,7 @@ int batched_ctas_per_sm(int block, int adjoint)
 
 cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
                            unsigned long long *counter, int adjoint, int with_aux, int grid_ctas, int block,
-                           cudaStream_t s)
+                           cudaStream_t s, bool lock2d)
 {
     const dim3 per_item(256, (unsigned)n_items);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
@@ -414,9 +414,11 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
 #ifndef XR_BATCH_FLAT
 #define XR_BATCH_FLAT 0
 #endif
-    const bool flat = (XR_BATCH_FLAT & (adjoint ? 2 : 1)) && tile <= 1024;
+    const bool flat = !lock2d && (XR_BATCH_FLAT & (adjoint ? 2 : 1)) && tile <= 1024;
     if (!adjoint) {
         if (with_aux) transpose_items_kernel<<<per_item, dim3(TT, 8), 0, s>>>(items);
+        if (lock2d)
+            return launch_batch2d(items, n_items, n_tiles, tile, counter, 0, grid_ctas, block, s);
         if (flat)
             flat_dda_kernel<kFwdAhead, false><<<(unsigned)n_tiles, tile, 0, s>>>(items, n_items, tile);
         else
@@ -424,7 +426,10 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
         return cudaGetLastError();
     }
     zero_items_kernel<<<per_item, 256, 0, s>>>(items);
-    if (flat)
+    if (lock2d) {
+        e = launch_batch2d(items, n_items, n_tiles, tile, counter, 1, grid_ctas, block, s);
+        if (e != cudaSuccess) return e;
+    } else if (flat)
         flat_dda_kernel<kAdjAhead, true><<<(unsigned)n_tiles, tile, 0, s>>>(items, n_items, tile);
     else
         batched_dda_kernel<kAdjAhead, true><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
@@ -433,8 +438,10 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
 }
 
 cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
-                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s)
+                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s,
+                                 bool lock2d)
 {
+    if (lock2d) return launch_batch2d(items, n_items, n_tiles, tile, counter, 0, grid_ctas, block, s);
     batched_dda_kernel<kFwdAhead, false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
     return cudaGetLastError();
 }

@@ -878,6 +878,7 @@ xr_status xr_system_rows_fill(const xr_geometry *g, int64_t ray0, int32_t n, con
 struct xr_batch {
     int device;
     int n;
+    bool lock2d;  // every problem is 2D: the lockstep slab walk (batch2d.cu)
     int tile, block, ctas_fwd, ctas_adj;
     int64_t n_tiles;
     BatchItem *d_items;
@@ -936,6 +937,8 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         return XR_ERR_ALLOC;
     }
     b->n = n;
+    b->lock2d = true;
+    for (int i = 0; i < n; ++i) b->lock2d = b->lock2d && !items[i].three;
     b->tile = tile;
     b->block = block;
     b->n_tiles = tiles;
@@ -960,8 +963,8 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         xr_batch_destroy(b);
         return oom ? XR_ERR_ALLOC : cuda_fail(e);
     }
-    b->ctas_fwd = sms * batched_ctas_per_sm(block, 0);
-    b->ctas_adj = sms * batched_ctas_per_sm(block, 1);
+    b->ctas_fwd = sms * (b->lock2d ? batch2d_ctas_per_sm(block, 0) : batched_ctas_per_sm(block, 0));
+    b->ctas_adj = sms * (b->lock2d ? batch2d_ctas_per_sm(block, 1) : batched_ctas_per_sm(block, 1));
     *out = b;
     return XR_OK;
 }
@@ -984,7 +987,7 @@ xr_status xr_batch_project(const xr_batch *b, xr_stream stream)
 {
     if (!b) return XR_ERR_NULL;
     XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 0, 1, b->ctas_fwd, b->block,
-                           (cudaStream_t)stream));
+                           (cudaStream_t)stream, b->lock2d));
     return XR_OK;
 }
 
@@ -992,7 +995,7 @@ xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream)
 {
     if (!b) return XR_ERR_NULL;
     XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 1, 1, b->ctas_adj, b->block,
-                           (cudaStream_t)stream));
+                           (cudaStream_t)stream, b->lock2d));
     return XR_OK;
 }
 

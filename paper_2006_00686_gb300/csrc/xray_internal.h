@@ -141,16 +141,24 @@ __device__ __forceinline__ int find_item(const BatchItem *items, int n, int64_t 
 // problem.  Forward: the [nz][nx][ny] copies are written first when the items carry aux
 // buffers; adjoint: images (and aux) are zeroed, scattered into, and aux added back.
 // The tile counter is zeroed here.
+// lock2d: every problem is 2D -- the walk kernel is batch2d_kernel (grid_ctas sized for it).
 cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
                            unsigned long long *counter, int adjoint, int with_aux, int grid_ctas, int block,
-                           cudaStream_t s);
+                           cudaStream_t s, bool lock2d = false);
 
 // Forward persistent launch over a work list already in device memory, items without aux;
 // the tile counter must be zero (no memset here).
 cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
-                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s);
+                                 unsigned long long *counter, int grid_ctas, int block, cudaStream_t s,
+                                 bool lock2d = false);
 
 int batched_ctas_per_sm(int block, int adjoint);
+
+// The same work list when every problem is 2D (batch2d.cu): the slab walk in warp lockstep,
+// 32 neighbouring rays of one problem per warp.  No copies or zero fills here.
+int batch2d_ctas_per_sm(int block, int adjoint);
+cudaError_t launch_batch2d(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                           unsigned long long *counter, int adjoint, int grid_ctas, int block, cudaStream_t s);
 
 // Batched fast path for rays with at most two active axes (fast2d.cu).
 cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,

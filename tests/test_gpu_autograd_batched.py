@@ -157,7 +157,11 @@ def test_batch_plan_matches_plain_launches():
     plan = BatchPlan(Ps, xs, ys, tile=128)
     plan.project()
     for P, x, y in zip(Ps, xs, ys):
-        assert torch.equal(y, P.forward(x))  # same walk per ray: bitwise
+        # the plan walks 2D problems slab by slab in warp lockstep, the single-image launch in
+        # crossing order: the same lengths, summed in another order when the driving index
+        # falls along the ray
+        ref = P.forward(x)
+        assert float((y - ref).abs().max()) <= 1e-5 * float(ref.abs().max())
     plan_adj = BatchPlan(Ps, zs, ys, tile=128)
     plan_adj.backproject()
     for P, z, y in zip(Ps, zs, ys):
@@ -233,7 +237,8 @@ def test_fans_uneven_64_full_size():
     ys = [torch.empty(g.sino_shape(), device="cuda") for g in geoms]
     BatchPlan(Ps, xs, ys).project()
     for q in (0, 17, 63):
-        assert torch.equal(ys[q], Ps[q].forward(xs[q]))
+        ref = Ps[q].forward(xs[q])
+        assert float((ys[q] - ref).abs().max()) <= 1e-5 * float(ref.abs().max())
         g = geoms[q]
         rays = H.sample_rays(g, 300, seed=q)
         f64 = xs[q].double().cpu().numpy().reshape(-1)

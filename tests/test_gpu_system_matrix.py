@@ -138,3 +138,41 @@ def test_single_tilt_axis_column_batch_rows(X):
     _check(g, _matrix_by_forward(P, g, 64), ref, "column batch forward")
     _check(g, _matrix_by_adjoint(P, g, 64, method=X.XR_ADJ_GATHER), ref, "column batch gather")
     P.close()
+
+
+def test_uneven_2d_batch_plan_rows(X):
+    # a persistent plan of three fans of different sizes (the lockstep slab walk of 2D work
+    # lists): column I of every problem's matrix from one-hot images, row r from one-hot
+    # sinograms, all problems in one launch per basis vector
+    geoms = [Geometry("fan2d", n, n + 2, dx=0.9, dy=1.1, cx=0.3, cy=-0.2, angles=ANGLES, n_cols=c, du=1.2,
+                      sod=60.0, sdd=90.0) for n, c in ((13, 21), (19, 29), (9, 17))]
+    Ps = [X.Projector(g) for g in geoms]
+    imgs = [torch.zeros(g.image_shape(), device="cuda") for g in geoms]
+    sinos = [torch.zeros(g.sino_shape(), device="cuda") for g in geoms]
+    fwd, adj = X.BatchPlan(Ps, imgs, sinos, tile=64), X.BatchPlan(Ps, imgs, sinos, tile=64)
+    Mf = [np.zeros((g.n_rays, g.n_units)) for g in geoms]
+    Ma = [np.zeros((g.n_rays, g.n_units)) for g in geoms]
+    for I in range(max(g.n_units for g in geoms)):
+        for g, x in zip(geoms, imgs):
+            x.zero_()
+            if I < g.n_units:
+                x.view(-1)[I] = 1.0
+        fwd.project()
+        for q, (g, y) in enumerate(zip(geoms, sinos)):
+            if I < g.n_units:
+                Mf[q][:, I] = y.double().cpu().numpy().reshape(-1)
+    for r in range(max(g.n_rays for g in geoms)):
+        for g, y in zip(geoms, sinos):
+            y.zero_()
+            if r < g.n_rays:
+                y.view(-1)[r] = 1.0
+        adj.backproject()
+        for q, (g, x) in enumerate(zip(geoms, imgs)):
+            if r < g.n_rays:
+                Ma[q][r] = x.double().cpu().numpy().reshape(-1)
+    for q, g in enumerate(geoms):
+        ref = _oracle_rows(g)
+        _check(g, Mf[q], ref, f"plan forward {q}")
+        _check(g, Ma[q], ref, f"plan adjoint {q}")
+    for P in Ps:
+        P.close()
