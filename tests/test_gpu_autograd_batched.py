@@ -237,8 +237,10 @@ def test_fans_uneven_64_full_size():
     ys = [torch.empty(g.sino_shape(), device="cuda") for g in geoms]
     BatchPlan(Ps, xs, ys).project()
     for q in (0, 17, 63):
+        # the single-image launch sums each ray in crossing order, the plan slab by slab: rays of
+        # up to ~1500 terms differ by the rounding of the two orders (the oracle bound is below)
         ref = Ps[q].forward(xs[q])
-        assert float((ys[q] - ref).abs().max()) <= 1e-5 * float(ref.abs().max())
+        assert float((ys[q] - ref).abs().max()) <= 1e-4 * float(ref.abs().max())
         g = geoms[q]
         rays = H.sample_rays(g, 300, seed=q)
         f64 = xs[q].double().cpu().numpy().reshape(-1)
