@@ -1,5 +1,8 @@
 // Persistent launch over uneven batches of 2D problems (one image each) with the slab walk in
-// warp lockstep.
+// warp lockstep: the adjoint of batch plans and of the one-call batched adjoint when every
+// problem is 2D (64 uneven fans: 39.7 ms against 71.9 ms for rays walked one by one).  The
+// forward form is kept for measurement; the plans' forward stays the crossing-order walk, which
+// measured faster for one image per problem (22.2 vs 40.6 ms).
 //
 // Warps take work items of consecutive rays of one problem from one atomic counter; a work
 // item is walked 32 rays at a time, one lane per ray.  The 32 rays are neighbouring detector
@@ -150,6 +153,7 @@ __global__ void __launch_bounds__(256) batch2d_kernel(const BatchItem *__restric
             const int64_t r = first + q0 + lane;
             const bool valid = r < P.n_rays;
             const float g = (ADJ && valid) ? __ldg(P.sino + r) : 0.f;
+            if (ADJ && __all_sync(0xffffffffu, g == 0.f)) continue;  // nothing to spread
             const float y = slab2d_warp<ADJ>(P, r, valid, g, lane);
             if (!ADJ && valid) P.sino[r] = y;
         }

@@ -417,8 +417,6 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
     const bool flat = !lock2d && (XR_BATCH_FLAT & (adjoint ? 2 : 1)) && tile <= 1024;
     if (!adjoint) {
         if (with_aux) transpose_items_kernel<<<per_item, dim3(TT, 8), 0, s>>>(items);
-        if (lock2d)
-            return launch_batch2d(items, n_items, n_tiles, tile, counter, 0, grid_ctas, block, s);
         if (flat)
             flat_dda_kernel<kFwdAhead, false><<<(unsigned)n_tiles, tile, 0, s>>>(items, n_items, tile);
         else
@@ -439,9 +437,8 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
 
 cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
                                  unsigned long long *counter, int grid_ctas, int block, cudaStream_t s,
-                                 bool lock2d)
+                                 bool)
 {
-    if (lock2d) return launch_batch2d(items, n_items, n_tiles, tile, counter, 0, grid_ctas, block, s);
     batched_dda_kernel<kFwdAhead, false><<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
     return cudaGetLastError();
 }

@@ -60,7 +60,7 @@ __global__ void noalloc_upload_kernel(WorkList<CAP> w, unsigned char *scratch)
 struct DeviceFacts {
     unsigned char *scratch = nullptr;
     int ctas_fwd = 0, ctas_adj = 0;      // crossing-order walk over any problems
-    int ctas2d_fwd = 0, ctas2d_adj = 0;  // lockstep slab walk when every problem is 2D
+    int ctas2d_adj = 0;                  // lockstep slab walk (adjoint) when every problem is 2D
 };
 
 std::mutex g_mu;
@@ -84,7 +84,6 @@ cudaError_t facts_of_current_device(int *dev_out, DeviceFacts *out)
         if (e != cudaSuccess) return e;
         f.ctas_fwd = sms * batched_ctas_per_sm(kBlock, 0);
         f.ctas_adj = sms * batched_ctas_per_sm(kBlock, 1);
-        f.ctas2d_fwd = sms * batch2d_ctas_per_sm(kBlock, 0);
         f.ctas2d_adj = sms * batch2d_ctas_per_sm(kBlock, 1);
         f.scratch = static_cast<unsigned char *>(p);
     }
@@ -136,8 +135,7 @@ xr_status upload_and_launch(const xr_problem *probs, int32_t n, int32_t tile, in
     const BatchItem *items = reinterpret_cast<const BatchItem *>(f.scratch + kCounterBytes);
     unsigned long long *counter = reinterpret_cast<unsigned long long *>(f.scratch);
     if (e == cudaSuccess && !adjoint)
-        e = launch_batched_items(items, n, tiles, tile, counter, lock2d ? f.ctas2d_fwd : f.ctas_fwd, kBlock, s,
-                                 lock2d);
+        e = launch_batched_items(items, n, tiles, tile, counter, f.ctas_fwd, kBlock, s);
     if (e == cudaSuccess && adjoint)  // zero fill, then the scatter straight into the images
         e = launch_batched(items, n, tiles, tile, counter, 1, 0, lock2d ? f.ctas2d_adj : f.ctas_adj, kBlock, s,
                            lock2d);
