@@ -1,8 +1,10 @@
-// Persistent launch over uneven batches of 2D problems (one image each) with the slab walk in
-// warp lockstep: the adjoint of batch plans and of the one-call batched adjoint when every
-// problem is 2D (64 uneven fans: 39.7 ms against 71.9 ms for rays walked one by one).  The
-// forward form is kept for measurement; the plans' forward stays the crossing-order walk, which
-// measured faster for one image per problem (22.2 vs 40.6 ms).
+// Adjoint of uneven batches of 2D problems (one image each) with the slab walk in warp
+// lockstep: batch plans and the one-call batched adjoint take it when every problem is 2D (64
+// uneven fans: 38 ms against 72 ms for rays walked one by one).  The forward stays the
+// crossing-order walk one ray at a time: the same lockstep walk as a forward measured 40.6 ms,
+// and 48 ms with eight slabs' loads issued together, against 22.1 ms -- for one image per
+// problem the lockstep's per-slab bookkeeping and its union of the lanes' slab ranges cost more
+// than its coalesced loads save, while for reductions the coalescing decides.
 //
 // Warps take work items of consecutive rays of one problem from one atomic counter; a work
 // item is walked 32 rays at a time, one lane per ray.  The 32 rays are neighbouring detector
@@ -14,8 +16,8 @@
 // the minor plane (eq. conditions_2D_1).  Every plane is the same multiply-add of (plane index,
 // 1/w, -frac/w) as in the crossing-order walk, so the lengths are that walk's.
 //
-// At a given slab the 32 lanes sit at neighbouring rows of the minor axis; the kernels read
-// (forward) or reduce into (adjoint) the layout whose fastest axis is the minor one -- the
+// At a given slab the 32 lanes sit at neighbouring rows of the minor axis; the kernel reduces
+// into the layout whose fastest axis is the minor one -- the
 // problem's y-fastest copy for rays driven along x, the image itself for rays driven along y --
 // so a warp's 32 accesses fall on a few neighbouring sectors, where rays walked one by one
 // drift apart and touch a sector each.  Lanes whose ray is axis-parallel, or driven along the
@@ -48,9 +50,10 @@ __device__ __forceinline__ float alone(const RayRec &rr, int nx, int ny, const f
     return sum;
 }
 
-// 32 rays of one 2D problem, lane = ray (valid: the lane has a ray).  Forward: returns the
-// lane's sum.  Adjoint: adds g * l into the problem's accumulators (img for rays driven along y,
-// aux -- the y-fastest [x][y] layout -- for rays driven along x; aux may be NULL, then img).
+// 32 rays of one 2D problem, lane = ray (valid: the lane has a ray): adds g * l into the
+// problem's accumulators (img for rays driven along y, aux -- the y-fastest [x][y] layout -- for
+// rays driven along x; aux may be NULL, then img).  The ADJ = false form returns the lane's
+// forward sum (kept with the adjoint so both share one walk; no launch uses it).
 template <bool ADJ>
 __device__ __forceinline__ float slab2d_warp(const BatchItem &P, int64_t r, bool valid, float g, int lane)
 {
@@ -74,67 +77,7 @@ __device__ __forceinline__ float slab2d_warp(const BatchItem &P, int64_t r, bool
     float sum = 0.f;
     const int wlo = __reduce_min_sync(0xffffffffu, lock ? W.mlo : INT_MAX);
     const int whi = __reduce_max_sync(0xffffffffu, lock ? W.mhi : INT_MIN);
-    if (lock && !ADJ) {
-        // forward: U slabs split ahead of their 2U loads (slots outside the ray's range or the
-        // image read the image's first unit with length 0)
-        constexpr int U = 8;
-        const float invA = W.invA, bA = W.bA, wB = W.wB, fB = W.fB, invB = W.invB, bB = W.bB;
-        const int mlo = W.mlo, mhi = W.mhi, oB = W.oB, NB = W.NB;
-        float p = (float)(wlo - W.oA);
-        float tcur = __fmaf_rn(p, invA, bA);
-        float sc = __fadd_rd(__fmaf_rn(wB, tcur, fB), kMagic);
-        float jc = __fadd_rn(sc, -kMagic);
-        for (int m0 = wlo; m0 <= whi; m0 += U) {
-            const float *pc[U], *pn[U];
-            float lc[U], ln[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int m = m0 + u;
-                p += 1.0f;
-                const float tn = __fmaf_rn(p, invA, bA);
-                const float sn = __fadd_rd(__fmaf_rn(wB, tn, fB), kMagic);
-                const float jn = __fadd_rn(sn, -kMagic);
-                const int rc = __float_as_int(sc) - kMagicBits + oB, rn = __float_as_int(sn) - kMagicBits + oB;
-                const bool act = m >= mlo && m <= mhi;
-                const bool one = fabsf(jn - jc) < 1.5f;
-                const bool cross = rn != rc;
-                const float tc = __fmaf_rn(fmaxf(jc, jn), invB, bB);
-                const float tcc = cross ? fminf(fmaxf(tc, fminf(tcur, tn)), fmaxf(tcur, tn)) : tn;
-                const float a = fabsf(__fsub_rn(tcc, tcur)), b = fabsf(__fsub_rn(tn, tcc));
-                const bool inc = act && one && (unsigned)rc < (unsigned)NB;
-                const bool inn = act && one && cross && (unsigned)rn < (unsigned)NB;
-                lc[u] = inc ? a : 0.f;
-                ln[u] = inn ? b : 0.f;
-                pc[u] = inc ? base + m * sA + rc * sB : base;
-                pn[u] = inn ? base + m * sA + rn * sB : base;
-                if (act && !one) {
-                    // crossing two minor planes (within rounding of a diagonal): each candidate
-                    const float tlo = W.sgA ? tn : tcur, thi = W.sgA ? tcur : tn;
-                    const int jlo = (int)fminf(jc, jn), jhi = (int)fmaxf(jc, jn);
-                    for (int j = jlo; j <= jhi; ++j) {
-                        const int jg = j + oB;
-                        if ((unsigned)jg >= (unsigned)NB) continue;
-                        const float qq = (float)j;
-                        const float tb0 = __fmaf_rn(qq + (float)W.sgB, invB, bB);
-                        const float tb1 = __fmaf_rn(qq + (float)(1 - W.sgB), invB, bB);
-                        const float l = __fsub_rn(fminf(thi, tb1), fmaxf(tlo, tb0));
-                        if (l > 0.f) sum = __fmaf_rn(__ldg(base + m * sA + jg * sB), l, sum);
-                    }
-                }
-                tcur = tn;
-                sc = sn;
-                jc = jn;
-            }
-            float vc[U], vn[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                vc[u] = __ldg(pc[u]);
-                vn[u] = __ldg(pn[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) sum = __fmaf_rn(vn[u], ln[u], __fmaf_rn(vc[u], lc[u], sum));
-        }
-    } else if (lock) {
+    if (lock) {
         const float invA = W.invA, bA = W.bA, wB = W.wB, fB = W.fB, invB = W.invB, bB = W.bB;
         const int mlo = W.mlo, mhi = W.mhi, oB = W.oB, NB = W.NB;
         float p = (float)(wlo - W.oA);

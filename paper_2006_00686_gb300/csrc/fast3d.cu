@@ -417,11 +417,6 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
     const bool flat = !lock2d && (XR_BATCH_FLAT & (adjoint ? 2 : 1)) && tile <= 1024;
     if (!adjoint) {
         if (with_aux) transpose_items_kernel<<<per_item, dim3(TT, 8), 0, s>>>(items);
-#ifndef XR_BATCH2D_FWD
-#define XR_BATCH2D_FWD 0
-#endif
-        if (lock2d && XR_BATCH2D_FWD)
-            return launch_batch2d(items, n_items, n_tiles, tile, counter, 0, grid_ctas, block, s);
         if (flat)
             flat_dda_kernel<kFwdAhead, false><<<(unsigned)n_tiles, tile, 0, s>>>(items, n_items, tile);
         else
