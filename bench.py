@@ -284,6 +284,8 @@ def _roofline(n_int, units_bytes, B, dom, dom_ms, peaks, peak_kind, traffic, tra
 TRAFFIC = {
     ("fan2d_512x16", "adjoint", "gather"): (51.5e6, "profiles/gather_pair_fan2d_512x16.md (one launch, full size)"),
     ("fan2d_512x16", "forward", "gather"): (62.4e6, "profiles/fwd_plane_fan2d_512x16.md (one launch, full size)"),
+    ("cone_512", "adjoint", "scatter"): (80.50e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
+    ("cone_512", "forward", "scatter"): (24.06e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
 }
 
 GRAPHED = ("par2d_64",)  # launch-bound steps replayed from a CUDA graph
