@@ -468,7 +468,8 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     if (e == cudaSuccess) e = cudaMemcpy(g->d_src, &g->src, sizeof(RaySrc), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && g->d_rays)
         e = launch_ray_setup(p, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays, nullptr);
-    if (e == cudaSuccess && g->d_grec) e = launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, nullptr);
+    // the quad-plane gather's per-ray constants are built when a workspace for batches of four
+    // or more is reserved (the only path that reads them), and rebuilt by later ray setups
     if (e == cudaSuccess) e = slice_setup(g, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
@@ -512,7 +513,8 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream)
     if (g->d_rays)
         XR_CUDA(launch_ray_setup(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays,
                                  (cudaStream_t)stream));
-    if (g->d_grec) XR_CUDA(launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, (cudaStream_t)stream));
+    if (g->d_grec && g->ws_batch >= 4)
+        XR_CUDA(launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, (cudaStream_t)stream));
     XR_CUDA(slice_setup(g, (cudaStream_t)stream));
     return XR_OK;
 }
@@ -542,6 +544,10 @@ xr_status xr_reserve(xr_geometry *g, int32_t max_batch)
     }
     // the borders of the interleaved copies stay zero: only interiors are ever written
     if (e == cudaSuccess) e = cudaMemset(g->d_ws, 0, got);
+    if (e == cudaSuccess && g->d_grec && max_batch >= 4) {  // the quad-plane gather's constants
+        e = launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    }
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         cudaGetLastError();
