@@ -2,7 +2,7 @@
 
 Random flat and equiangular cones and helices with off-centre anisotropic voxels, detectors
 taller than the volume (rows that enter or leave through the top and bottom faces), more
-rows than one CTA band and a ragged last band; forward per ray, adjoint image, dot test, the
+rows than one 32-row block and a ragged last block; forward per ray, adjoint image, dot test, the
 automatic choice, and scans too steep for the walk (more than one z plane per xy cell),
 which keep the crossing-order walk."""
 import math
@@ -73,7 +73,7 @@ def test_trace_walk_matches_the_oracle(X, kind, seed):
 
 @pytest.mark.parametrize("n_rows", [1, 31, 32, 33, 64, 65, 128, 129, 300])
 def test_trace_walk_row_bands(X, n_rows):
-    # one lane per row: single rows, one partial warp, whole and ragged CTA bands
+    # one lane per row: a single row, partial and whole 32-row blocks, a ragged last block
     g = _geom("cone", 7, n_rows=n_rows, n_views=6)
     P = X.Projector(g)
     P.set_tuning(order=X.XR_ORDER_TRACE)
@@ -110,4 +110,14 @@ def test_automatic_order_takes_the_trace_walk_and_steep_scans_fall_back(X):
     P = X.Projector(steep)
     P.set_tuning(order=X.XR_ORDER_TRACE)
     _check_all(X, P, steep, 4, "steep cone")
+    P.close()
+
+
+def test_full_size_cone_keeps_no_ray_table(X):
+    # the 512^3 cone with a 1024 x 768 detector and 720 views: 566 M rays; the handle holds
+    # per-view, per-column and per-sample tables only (a 32-byte record per ray would be 18 GB)
+    g = inputs.cone_512()
+    P = X.Projector(g)
+    assert P.trace_walk
+    assert P.table_bytes < 64 << 20, P.table_bytes
     P.close()
