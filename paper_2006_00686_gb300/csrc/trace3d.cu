@@ -482,14 +482,14 @@ __device__ __forceinline__ void adj_walk(const TraceGeo &T, const WTrace &W, con
             unsigned oA, oB;
             float lA, lB;
             slab_split(R, ta, sl.x, ma, mb, __float_as_int(sl.y), oA, oB, lA, lB);
-            if (lA > 0.f) red_add(accZ + oA, __fmul_rn(gs, lA));
-            float vB = lB > 0.f ? __fmul_rn(gs, lB) : 0.f;
+            red_add_if_pos(accZ + oA, __fmul_rn(gs, lA), lA);
             if (AGG) {
+                float vB = lB > 0.f ? __fmul_rn(gs, lB) : 0.f;
                 vB = run_sum(vB, (int)oB, lane, runs);
                 const unsigned kp = __shfl_up_sync(0xffffffffu, oB, 1);
                 if ((lane == 0 || kp != oB) && vB != 0.f) red_add(accZ + oB, vB);
-            } else if (lB > 0.f) {
-                red_add(accZ + oB, vB);
+            } else {
+                red_add_if_pos(accZ + oB, __fmul_rn(gs, lB), lB);
             }
             ta = sl.x;
             ma = mb;

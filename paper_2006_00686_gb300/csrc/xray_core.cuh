@@ -51,6 +51,17 @@ __device__ __forceinline__ void red_add(float *p, float v)
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
 }
 
+// red_add(p, v) when len > 0, predicated inside the instruction: a C++ `if` around the asm
+// becomes a divergent branch (with its reconvergence bookkeeping) where only some lanes add.
+__device__ __forceinline__ void red_add_if_pos(float *p, float v, float len)
+{
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.gt.f32 q, %2, 0f00000000;\n\t@q red.global.add.f32 [%0], %1;\n\t}" ::"l"(
+            __cvta_generic_to_global(p)),
+        "f"(v), "f"(len)
+        : "memory");
+}
+
 // The same for four consecutive floats (16-byte aligned): one 128-bit vector reduction.
 __device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d)
 {
