@@ -102,8 +102,8 @@ __device__ __forceinline__ float slab2d_warp(const BatchItem &P, int64_t r, bool
                     const bool inn = cross && (unsigned)rn < (unsigned)NB && ln > 0.f;
                     float *pc = base + m * sA + rc * sB, *pn = base + m * sA + rn * sB;
                     if (ADJ) {
-                        red_add_if_pos(inc ? pc : base, __fmul_rn(g, lc), inc ? lc : 0.f);
-                        red_add_if_pos(inn ? pn : base, __fmul_rn(g, ln), inn ? ln : 0.f);
+                        if (inc) red_add(pc, __fmul_rn(g, lc));
+                        if (inn) red_add(pn, __fmul_rn(g, ln));  // a branch: rarely taken (a crossing)
                     } else {
                         const float vc = inc ? __ldg(pc) : 0.f, vn = inn ? __ldg(pn) : 0.f;
                         sum = __fmaf_rn(vn, ln, __fmaf_rn(vc, lc, sum));

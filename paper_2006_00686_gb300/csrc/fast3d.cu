@@ -157,7 +157,8 @@ __device__ __forceinline__ void scatter_ray_s(const RayRec &rr, float g, int nx,
 #pragma unroll
         for (int u = 0; u < U; ++u) dda_step_t<SKIP>(D, off[u], l[u]);
 #pragma unroll
-        for (int u = 0; u < U; ++u) red_add_if_pos(base + off[u], __fmul_rn(g, l[u]), l[u]);
+        for (int u = 0; u < U; ++u)
+            if (l[u] > 0.f) red_add(base + off[u], __fmul_rn(g, l[u]));
     }
     if (err && D.tcur < D.tout) atomicOr(err, XR_DEVERR_WALK_BOUND);
 }
