@@ -156,6 +156,12 @@ __device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V,
 #ifndef XR_TRACE_MINB
 #define XR_TRACE_MINB 1
 #endif
+#ifndef XR_TRACE_ADJ_UNROLL
+#define XR_TRACE_ADJ_UNROLL 2
+#endif
+#ifndef XR_TRACE_B_ALWAYS
+#define XR_TRACE_B_ALWAYS 0
+#endif
 #ifndef XR_TRACE_FWD_MINB
 #define XR_TRACE_FWD_MINB 8  // 64 registers: 32 warps per SM to hide the loads' latency
 #endif
@@ -475,7 +481,7 @@ __device__ __forceinline__ void adj_walk(const TraceGeo &T, const WTrace &W, con
     float ta = W.tin, ma = row_floor<CLAMP>(R, ta);
     for (int c = 0; c < W.nchunk; ++c) {
         const int n = build_chunk(T, W, c, lane, slot);
-#pragma unroll 2
+#pragma unroll XR_TRACE_ADJ_UNROLL
         for (int s = 0; s < n; ++s) {
             const float2 sl = slot[s];
             const float mb = row_floor<CLAMP>(R, sl.x);
@@ -488,6 +494,10 @@ __device__ __forceinline__ void adj_walk(const TraceGeo &T, const WTrace &W, con
                 vB = run_sum(vB, (int)oB, lane, runs);
                 const unsigned kp = __shfl_up_sync(0xffffffffu, oB, 1);
                 if ((lane == 0 || kp != oB) && vB != 0.f) red_add(accZ + oB, vB);
+            } else if (XR_TRACE_B_ALWAYS) {
+                // B gets a length on all but grazing slabs: an unpredicated reduction (a length a
+                // few ulp below zero at a crossing on the slab's end adds a rounding-sized term)
+                red_add(accZ + oB, __fmul_rn(gs, lB));
             } else {
                 red_add_if_pos(accZ + oB, __fmul_rn(gs, lB), lB);
             }
