@@ -162,6 +162,7 @@ __device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V,
 #ifndef XR_TRACE_B_ALWAYS
 #define XR_TRACE_B_ALWAYS 0
 #endif
+constexpr int kAdjUnroll = XR_TRACE_ADJ_UNROLL;
 #ifndef XR_TRACE_FWD_MINB
 #define XR_TRACE_FWD_MINB 8  // 64 registers: 32 warps per SM to hide the loads' latency
 #endif
@@ -481,7 +482,7 @@ __device__ __forceinline__ void adj_walk(const TraceGeo &T, const WTrace &W, con
     float ta = W.tin, ma = row_floor<CLAMP>(R, ta);
     for (int c = 0; c < W.nchunk; ++c) {
         const int n = build_chunk(T, W, c, lane, slot);
-#pragma unroll XR_TRACE_ADJ_UNROLL
+#pragma unroll(kAdjUnroll)
         for (int s = 0; s < n; ++s) {
             const float2 sl = slot[s];
             const float mb = row_floor<CLAMP>(R, sl.x);
