@@ -425,7 +425,7 @@ cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles,
     }
     zero_items_kernel<<<per_item, 256, 0, s>>>(items);
     if (lock2d) {
-        e = launch_batch2d(items, n_items, n_tiles, tile, counter, 1, grid_ctas, block, s);
+        e = launch_batch2d_adjoint(items, n_items, n_tiles, tile, counter, grid_ctas, block, s);
         if (e != cudaSuccess) return e;
     } else if (flat)
         flat_dda_kernel<kAdjAhead, true><<<(unsigned)n_tiles, tile, 0, s>>>(items, n_items, tile);

@@ -84,7 +84,7 @@ cudaError_t facts_of_current_device(int *dev_out, DeviceFacts *out)
         if (e != cudaSuccess) return e;
         f.ctas_fwd = sms * batched_ctas_per_sm(kBlock, 0);
         f.ctas_adj = sms * batched_ctas_per_sm(kBlock, 1);
-        f.ctas2d_adj = sms * batch2d_ctas_per_sm(kBlock, 1);
+        f.ctas2d_adj = sms * batch2d_ctas_per_sm(kBlock);
         f.scratch = static_cast<unsigned char *>(p);
     }
     *dev_out = dev;

@@ -160,7 +160,7 @@ __device__ __forceinline__ bool trace_record(const TraceGeo &T, const ViewDF &V,
 #define XR_TRACE_ADJ_UNROLL 2
 #endif
 #ifndef XR_TRACE_B_ALWAYS
-#define XR_TRACE_B_ALWAYS 0
+#define XR_TRACE_B_ALWAYS 1
 #endif
 constexpr int kAdjUnroll = XR_TRACE_ADJ_UNROLL;
 #ifndef XR_TRACE_FWD_MINB

@@ -970,7 +970,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         return oom ? XR_ERR_ALLOC : cuda_fail(e);
     }
     b->ctas_fwd = sms * batched_ctas_per_sm(block, 0);
-    b->ctas_adj = sms * (b->lock2d ? batch2d_ctas_per_sm(block, 1) : batched_ctas_per_sm(block, 1));
+    b->ctas_adj = sms * (b->lock2d ? batch2d_ctas_per_sm(block) : batched_ctas_per_sm(block, 1));
     *out = b;
     return XR_OK;
 }

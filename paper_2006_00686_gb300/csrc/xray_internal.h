@@ -157,11 +157,11 @@ cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_
 
 int batched_ctas_per_sm(int block, int adjoint);
 
-// The same work list when every problem is 2D (batch2d.cu): the slab walk in warp lockstep,
-// 32 neighbouring rays of one problem per warp.  No copies or zero fills here.
-int batch2d_ctas_per_sm(int block, int adjoint);
-cudaError_t launch_batch2d(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
-                           unsigned long long *counter, int adjoint, int grid_ctas, int block, cudaStream_t s);
+// The adjoint of a work list whose problems are all 2D (batch2d.cu): the slab walk in warp
+// lockstep, 32 neighbouring rays of one problem per warp.  No copies or zero fills here.
+int batch2d_ctas_per_sm(int block);
+cudaError_t launch_batch2d_adjoint(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                                   unsigned long long *counter, int grid_ctas, int block, cudaStream_t s);
 
 // Batched fast path for rays with at most two active axes (fast2d.cu).
 cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,
