@@ -318,6 +318,12 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
                           xr_batch **out);
 void xr_batch_destroy(xr_batch *b);
 
+/* The ray setup of every problem of the plan (what xr_ray_setup does for one handle, for the
+ * tables the plan's kernels read: each problem's detector-sample table and, where the problem
+ * keeps one, its ray table) in two launches over all problems: one thread per detector sample,
+ * then one per ray.  Stream-ordered, no allocation.  Errors: XR_ERR_NULL, XR_ERR_CUDA. */
+xr_status xr_batch_ray_setup(const xr_batch *b, xr_stream stream);
+
 /* Forward projection of every problem of the plan: one persistent launch whose CTAs (one
  * set per SM, as many as fit) take tiles from one atomic counter until none is left. */
 xr_status xr_batch_project(const xr_batch *b, xr_stream stream);

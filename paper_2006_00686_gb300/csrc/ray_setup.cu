@@ -25,10 +25,9 @@
 
 namespace xr {
 
-__global__ void det_setup_kernel(GeoParams g, DetRec *__restrict__ out)
+// The detector part of detector sample d (row d / n_cols, column d % n_cols).
+__device__ DetRec det_record(const GeoParams &g, int64_t d)
 {
-    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= (int64_t)g.n_rows * g.n_cols) return;
     const int c = (int)(d % g.n_cols), row = (int)(d / g.n_cols);
     const double u = (c - 0.5 * (g.n_cols - 1)) * g.du + g.u0;
     const double w = (row - 0.5 * (g.n_rows - 1)) * g.dv + g.v0;
@@ -74,7 +73,47 @@ __global__ void det_setup_kernel(GeoParams g, DetRec *__restrict__ out)
     R.sa = to_df(sa);
     R.cb = to_df(cb);
     R.sb = to_df(sb);
-    out[d] = R;
+    return R;
+}
+
+__global__ void det_setup_kernel(GeoParams g, DetRec *__restrict__ out)
+{
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= (int64_t)g.n_rows * g.n_cols) return;
+    out[d] = det_record(g, d);
+}
+
+// Ray setup of every problem of a batch plan in two launches (detector samples, then rays):
+// thread k works on global index k of the concatenated per-problem index ranges.
+__device__ __forceinline__ int setup_item(const SetupItem *items, int n, int64_t k, bool rays)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((rays ? items[mid].ray_begin : items[mid].det_begin) <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void batch_det_setup_kernel(const SetupItem *__restrict__ items, int n, int64_t total)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const SetupItem &S = items[setup_item(items, n, k, false)];
+    const int64_t d = k - S.det_begin;
+    S.det[d] = det_record(S.g, d);
+}
+
+__global__ void batch_ray_setup_kernel(const SetupItem *__restrict__ items, int n, int64_t total)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const SetupItem &S = items[setup_item(items, n, k, true)];
+    const int64_t r = k - S.ray_begin;
+    const int64_t ndet = (int64_t)S.g.n_rows * S.g.n_cols;
+    const int64_t v = r / ndet;
+    S.rays[r] = ray_record(S.g, S.K, S.views[v], S.det[r - v * ndet]);
 }
 
 // blockIdx.y = view (when the views fit the grid's y extent), x: detector samples.
@@ -97,6 +136,16 @@ __global__ void ray_setup_flat_kernel(GeoParams g, SetupDF K, const ViewDF *__re
     const int64_t ndet = (int64_t)g.n_rows * g.n_cols;
     const int64_t v = r / ndet;
     out[r] = ray_record(g, K, views[v], det[r - v * ndet]);
+}
+
+cudaError_t launch_batch_setup(const SetupItem *items, int n, int64_t n_det, int64_t n_rays, cudaStream_t s)
+{
+    const int block = 128;
+    if (n_det > 0) batch_det_setup_kernel<<<(unsigned)((n_det + block - 1) / block), block, 0, s>>>(items, n, n_det);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n_rays <= 0) return e;
+    batch_ray_setup_kernel<<<(unsigned)((n_rays + block - 1) / block), block, 0, s>>>(items, n, n_rays);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_det_setup(const GeoParams &g, DetRec *d_det, cudaStream_t s)

@@ -885,6 +885,8 @@ struct xr_batch {
     int device;
     int n;
     bool lock2d;  // every problem is 2D: the lockstep slab walk (batch2d.cu)
+    SetupItem *d_setup;          // per problem: the ray setup's work (xr_batch_ray_setup)
+    int64_t setup_det, setup_rays;  // detector samples and table rays over all problems
     int tile, block, ctas_fwd, ctas_adj;
     int64_t n_tiles;
     BatchItem *d_items;
@@ -954,6 +956,30 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_aux, (size_t)aux_units * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_setup, sizeof(SetupItem) * (size_t)n);
+    if (e == cudaSuccess) {
+        // the ray setup of every problem: detector tables, and ray tables where kept
+        SetupItem *si = (SetupItem *)malloc(sizeof(SetupItem) * (size_t)n);
+        if (!si) e = cudaErrorMemoryAllocation;
+        int64_t nd = 0, nr = 0;
+        for (int i = 0; e == cudaSuccess && i < n; ++i) {
+            const xr_geometry *g = probs[i].geom;
+            si[i].g = g->params;
+            si[i].K = g->setup_df;
+            si[i].views = g->d_views_df;
+            si[i].det = g->d_det;
+            si[i].rays = g->d_rays;
+            si[i].det_begin = nd;
+            si[i].ray_begin = nr;
+            nd += (int64_t)g->params.n_rows * g->params.n_cols;
+            if (g->d_rays) nr += g->n_rays;
+        }
+        b->setup_det = nd;
+        b->setup_rays = nr;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_setup, si, sizeof(SetupItem) * (size_t)n, cudaMemcpyHostToDevice);
+        free(si);
+    }
     if (e == cudaSuccess) {
         int64_t at = 0;
         for (int i = 0; i < n; ++i) {
@@ -985,8 +1011,16 @@ void xr_batch_destroy(xr_batch *b)
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
     cudaFree(b->d_aux);
+    cudaFree(b->d_setup);
     cudaSetDevice(prev);
     delete b;
+}
+
+xr_status xr_batch_ray_setup(const xr_batch *b, xr_stream stream)
+{
+    if (!b) return XR_ERR_NULL;
+    XR_CUDA(launch_batch_setup(b->d_setup, b->n, b->setup_det, b->setup_rays, (cudaStream_t)stream));
+    return XR_OK;
 }
 
 xr_status xr_batch_project(const xr_batch *b, xr_stream stream)

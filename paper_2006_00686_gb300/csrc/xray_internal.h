@@ -88,6 +88,21 @@ struct RaySrc {
 };
 
 cudaError_t launch_det_setup(const GeoParams &g, DetRec *d_det, cudaStream_t s);
+
+// One problem of a plan's ray setup (device copy): its detector table, and its ray table when
+// it keeps one (rays == NULL: the detector table only), at offsets det_begin / ray_begin of the
+// concatenated index ranges.
+struct SetupItem {
+    GeoParams g;
+    SetupDF K;
+    const ViewDF *views;
+    DetRec *det;
+    RayRec *rays;
+    int64_t det_begin, ray_begin;
+};
+// Every item's detector samples (n_det in total) in one launch, then every item's rays (n_rays
+// in total, items with a ray table only) in one launch.
+cudaError_t launch_batch_setup(const SetupItem *items, int n, int64_t n_det, int64_t n_rays, cudaStream_t s);
 cudaError_t launch_ray_setup(const GeoParams &g, const SetupDF &c, const ViewDF *d_views, const DetRec *d_det,
                              RayRec *d_rays, int64_t n_rays, cudaStream_t s);
 

@@ -76,6 +76,7 @@ SIGNATURES = {
     "xr_batch_create": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _I32, ctypes.POINTER(_VP)]),
     "xr_batch_destroy": (None, [_VP]),
     "xr_batch_project": (_I32, [_VP, _VP]),
+    "xr_batch_ray_setup": (_I32, [_VP, _VP]),
     "xr_batch_backproject": (_I32, [_VP, _VP]),
     "xr_project_batched_noalloc": (_I32, [ctypes.POINTER(_Problem), _I32, _I32, _VP]),
     "xr_read_probe": (_I32, [_VP, ctypes.c_int64, _I32, _VP, _I32, _VP]),
@@ -391,6 +392,10 @@ class BatchPlan:
         h = ctypes.c_void_p()
         _check(lib().xr_batch_create(arr, n, int(tile), int(block), ctypes.byref(h)), "xr_batch_create")
         self._h = h
+
+    def ray_setup(self, stream=None):
+        """Every problem's ray setup (detector and ray tables) in two launches."""
+        _check(lib().xr_batch_ray_setup(self._h, _stream(stream)), "xr_batch_ray_setup")
 
     def project(self, stream=None):
         _check(lib().xr_batch_project(self._h, _stream(stream)), "xr_batch_project")
