@@ -176,3 +176,36 @@ def test_uneven_2d_batch_plan_rows(X):
         _check(g, Ma[q], ref, f"plan adjoint {q}")
     for P in Ps:
         P.close()
+
+
+@pytest.mark.parametrize("kind", ["cone", "helix"])
+def test_trace_walk_rays_on_grid_planes(X, kind):
+    # even grids centred at the origin and an odd detector: at the axis-parallel views the
+    # central column's vertical plane is a grid plane (x = 0 or y = 0), and the central row is
+    # horizontal at a z plane (z = 0, helix: the source heights are whole voxels).  Those rays lie
+    # on planes: the ambiguity rule of Section 4.1 gives them the units with the bigger index, at
+    # full lengths, so the unit sets must match the oracle exactly there
+    ang = np.array([0.0, pi / 2, pi, 3 * pi / 2, pi / 4, 0.9])
+    kw = dict(angles=ang, n_cols=21, n_rows=15, du=1.0, dv=1.0, sod=40.0, sdd=64.0)
+    if kind == "helix":
+        kw["src_z"] = np.array([0.0, 1.0, -1.0, 2.0, 0.0, -2.0])
+    g = Geometry(kind, 16, 16, 12, **kw)
+    ref = _oracle_rows(g)
+    P = X.Projector(g)
+    assert P.trace_walk
+    P.set_tuning(order=X.XR_ORDER_TRACE)
+    Mf = _matrix_by_forward(P, g, 64)
+    Ma = _matrix_by_adjoint(P, g, 64, method=X.XR_ADJ_SCATTER)
+    _check(g, Mf, ref, f"{kind} on-plane forward")
+    _check(g, Ma, ref, f"{kind} on-plane adjoint")
+    # the central column at the axis-parallel views, every row: exactly the oracle's units
+    views = g.n_rows * g.n_cols
+    for v in range(4):
+        for row in range(g.n_rows):
+            r = v * views + row * g.n_cols + g.n_cols // 2
+            i_ref, l_ref = ref[r]
+            for M in (Mf, Ma):
+                nz = np.nonzero(M[r])[0]
+                np.testing.assert_array_equal(nz, i_ref)
+                np.testing.assert_allclose(M[r][nz], l_ref, atol=H.grazing_delta(g))
+    P.close()
