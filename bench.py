@@ -282,7 +282,8 @@ def _roofline(n_int, units_bytes, B, dom, dom_ms, peaks, peak_kind, traffic, tra
 # kernel, from the ncu captures summarised under profiles/: (workload, phase, method) ->
 # (bytes, note).  Only kernels unchanged since their capture are listed.
 TRAFFIC = {
-    ("fan2d_512x16", "adjoint", "gather"): (51.5e6, "profiles/gather_pair_fan2d_512x16.md (one launch, full size)"),
+    ("fan2d_512x16", "adjoint", "gather"): (70.1e6, "profiles/gather_stage_fan2d_512x16.md (one launch of the staged "
+                                                    "gather, full size; the records pass before it is not included)"),
     ("fan2d_512x16", "forward", "gather"): (62.4e6, "profiles/fwd_plane_fan2d_512x16.md (one launch, full size)"),
     ("cone_512", "adjoint", "scatter"): (80.50e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
     ("cone_512", "forward", "scatter"): (24.06e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
@@ -423,7 +424,7 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
         config = _config({"adjoint": method, "batch_chunk": P.tuning()["batch_chunk"], "block": args.block})
         # per step: detector setup, ray setup, the gather's per-ray constants, image
         # interleave, forward walk, then either the scatter walk + its de-interleave (two
-        # accumulator memsets are not kernels) or the sinogram interleave + gather
+        # accumulator memsets are not kernels) or the gather records + the staged gather
         launches = 7
     else:
         config = {"workload": workload, "geometry": desc, "image": list(g.image_shape()),
@@ -464,7 +465,7 @@ def _launch_count(P, g, B):
     """Kernels of the repo launched per step on the single-image and column paths."""
     if P.column_batch:
         # detector setup, ray setup, the column problem's ray records and gather constants,
-        # then per image: the slice planes, the forward, the sinogram planes, the gather
+        # then per image: the slice planes, the forward, the gather records, the staged gather
         return 4 + 4 * B
     if P.trace_walk:
         # detector setup (no per-ray table), then per image: the padded z-fastest copy, the

@@ -269,8 +269,11 @@ xr_status xr_backproject_attenuated(const xr_geometry *g, const float *d_mu, con
  * handle's kernels since the last call, then cleared.  XR_DEVERR_WALK_BOUND: a ray's walk on
  * the single-image fast path reached its step bound (nx + ny + nz + 2 units) before the
  * image box's exit -- a ray record inconsistent with the grid; its sum is then incomplete.
+ * XR_DEVERR_WAIT_BOUND: a kernel's wait for its own asynchronous copies into shared memory
+ * (the staged gather adjoint of 2D batches) ran out of its bound (about 2 s); the pixels of
+ * the waiting warp are then NaN.
  * Synchronises the handle's device.  Errors: XR_ERR_NULL, XR_ERR_CUDA. */
-enum { XR_DEVERR_WALK_BOUND = 1 };
+enum { XR_DEVERR_WALK_BOUND = 1, XR_DEVERR_WAIT_BOUND = 2 };
 xr_status xr_get_device_error(const xr_geometry *g, int32_t *code);
 
 /* Sparse rows of the projection matrix (Algorithm 1/2 "Output", Section 4.2): for each of

@@ -21,6 +21,7 @@
 // values the walk uses; the rare step that crosses two rows falls back to the general
 // per-candidate formula.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "xray_internal.h"
@@ -30,6 +31,7 @@
 #ifndef XR_FWD_MIN_BLOCKS
 #define XR_FWD_MIN_BLOCKS 4
 #endif
+
 
 namespace xr {
 
@@ -61,25 +63,6 @@ __global__ void deinterleave_sum_kernel(const float *__restrict__ il0, const flo
         if (b + 1 < batch) img[(int64_t)(b + 1) * n + u] = a.y + c.y;
         if (b + 2 < batch) img[(int64_t)(b + 2) * n + u] = a.z + c.z;
         if (b + 3 < batch) img[(int64_t)(b + 3) * n + u] = a.w + c.w;
-    }
-}
-
-// user sinograms [B][n_rays] -> [chunk][Bp/4][n_rays][4]: the 4 images of one quad of one ray
-// are one float4, and neighbouring rays' float4 of the same quad are neighbours in memory.
-__global__ void interleave_sino_kernel(const float *__restrict__ sino, int batch, int64_t n_rays, int Bp,
-                                       float *__restrict__ out)
-{
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
-    const int chunk = blockIdx.y;
-    for (int b4 = 0; b4 < Bp; b4 += 4) {
-        float4 v;
-        const int b = chunk * Bp + b4;
-        v.x = (b + 0 < batch) ? __ldg(sino + (int64_t)(b + 0) * n_rays + r) : 0.f;
-        v.y = (b + 1 < batch) ? __ldg(sino + (int64_t)(b + 1) * n_rays + r) : 0.f;
-        v.z = (b + 2 < batch) ? __ldg(sino + (int64_t)(b + 2) * n_rays + r) : 0.f;
-        v.w = (b + 3 < batch) ? __ldg(sino + (int64_t)(b + 3) * n_rays + r) : 0.f;
-        reinterpret_cast<float4 *>(out)[((int64_t)chunk * (Bp / 4) + b4 / 4) * n_rays + r] = v;
     }
 }
 
@@ -321,7 +304,7 @@ __global__ void __launch_bounds__(256, XR_FWD_MIN_BLOCKS) fwd_fast2_kernel(const
 }
 
 // ---------------------------------------------------------------------------------------
-// Per-ray records of the gather adjoint (gather_pair_kernel below)
+// Per-ray plane constants of the gather adjoint (gather_stage_kernel below)
 // ---------------------------------------------------------------------------------------
 
 // Per-ray plane constants of both in-plane axes, t(plane q of axis a) = fma(q - o_a, inv_a, b_a),
@@ -352,15 +335,6 @@ __global__ void gather_prep_kernel(const RayRec *__restrict__ rays, int64_t n_ra
 // ---------------------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------------------
-
-cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,
-                                   cudaStream_t s)
-{
-    const int chunks = (batch + Bp - 1) / Bp;
-    interleave_sino_kernel<<<dim3((unsigned)((n_rays + 255) / 256), chunks), 256, 0, s>>>(sino, batch, n_rays,
-                                                                                         Bp, out);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, float *acc0,
                                  float *acc1, size_t acc_bytes, int Bp, const float *sino, float *img, int batch,
@@ -574,22 +548,19 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
     }
 }
 
-// Gather adjoint on the quad planes: one thread per pair of horizontally adjacent pixels
-// (i, j), (i+1, j) of one row (the last pixel of an odd row alone), all 4*NQ images.  Per
-// view the thread projects the pair's box (its four corners) onto the detector; for every bin
-// whose centre lies in that footprint it loads the ray's plane constants and the bin's NQ
-// sinogram quads once and adds l * g to both pixels.  The lengths are C_up - C_low of each
-// pixel from the same plane crossings the forward uses (x planes i, i+1, i+2 and y planes j,
-// j+1, each one FMA); a bin that misses a pixel gives C_up <= C_low there and adds nothing.
-// One bin per step: measured against two bins per step and against one pixel per thread
-// (fan beam 512^2 x 16: 2.17 vs 2.24 and 2.34 ms).  sil: sinogram planes [Q][n_rays][4]
-// (interleave_sino_kernel with Bp = 4 * Q, one chunk); blockIdx.y = group of NQ planes.
+// Gather adjoint: one thread per pair of horizontally adjacent pixels (i, j), (i+1, j) of one
+// row (the last pixel of an odd row alone), all 4*NQ images of a group.  Per view the thread
+// projects the pair's box (its four corners) onto the detector; for every bin whose centre lies
+// in that footprint it reads the ray's plane constants and the bin's NQ sinogram quads once and
+// adds l * g to both pixels.  The lengths are C_up - C_low of each pixel from the same plane
+// crossings the forward uses (x planes i, i+1, i+2 and y planes j, j+1, each one FMA); a bin
+// that misses a pixel gives C_up <= C_low there and adds nothing.
 //
-// The views are split into nch chunks inside each CTA of 256 threads: thread = (pair, chunk),
-// 256 / nch pairs per CTA, each warp on 32 pairs of one chunk.  The chunks' sums are added
-// in chunk order through shared memory by the chunk-0 threads, so the result does not depend
-// on scheduling.  nch multiplies the threads of the launch; the host picks it so that the
-// CTAs fill whole waves of the GPU (512^2 pairs on 152 SMs: 1.68 waves of one-chunk CTAs).
+// The views are split into nch chunks inside each CTA of 256 threads, each warp on one chunk.
+// The chunks' sums are added in chunk order through shared memory by the chunk-0 threads, so
+// the result does not depend on scheduling.  nch multiplies the threads of the launch; the
+// host picks it so that the CTAs fill whole waves of the GPU (512^2 pairs on 152 SMs: 1.68
+// waves of one-chunk CTAs).
 constexpr int kGatherThreads = 256;
 
 // Where image b of the gather goes: the user layout ([b][rows][nx]) when slice_of is NULL;
@@ -607,107 +578,206 @@ struct ImgMap {
     __device__ __forceinline__ int64_t row(int nx) const { return slice_of ? row_stride : nx; }
 };
 
-template <int NQ, int KIND>
-__global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_pair_kernel(
-    const RayRec *__restrict__ rays, const float4 *__restrict__ grec, GeoParams g, const float *__restrict__ vt,
-    const float4 *__restrict__ sil, int64_t n_rays, float *__restrict__ img, int batch, int nch, ImgMap om)
+// ---------------------------------------------------------------------------------------
+// Staged gather: the per-view data of a warp's pixel tile in shared memory
+// ---------------------------------------------------------------------------------------
+//
+// The bins' data come from gather records: record r of group y holds the group's NQ quads of
+// sinogram values of ray r, then GA[r] and GB[r], padded to an odd number of 16-byte words
+// (rec_words), so that the
+// records of neighbouring bins start in different bank groups of shared memory.  A warp owns an
+// 8 x 8 pixel tile (4 pairs x 8 rows, lane = pair (lane & 3) of row (lane >> 2)) and walks its
+// chunk of views; for each view the union of the lanes' candidate bins is one range [cA, cA +
+// nb) of that view's records, which one bulk asynchronous copy (cp.async.bulk, completion
+// counted in bytes on an mbarrier) brings into a shared-memory stage.  kGStages stages per warp
+// keep the next view's copy in flight while the lanes read the current one, so the inner loop
+// waits on shared memory, not on L2.  A view whose range exceeds kGStageBins bins (steep
+// magnification, fine detector) is read from the records in global memory directly.  Waits are
+// bounded (kWaitCycles); a wait that runs out sets XR_DEVERR_WAIT_BOUND in the error word, and
+// the warp stops, waits (bounded) for the copies it still has in flight and writes NaN sums for
+// its pixels.
+//
+// Measured on the fan beam 512^2 x 16 images: 1.53 ms, against 1.95 ms for the same sums with
+// every bin's data loaded from L2 (one pair per thread, 32 pairs of a row per warp: 4.7
+// long-scoreboard stalls per issued instruction at 25% occupancy) and 1.81 ms with six copies
+// per view (sinogram planes and constants as separate arrays).  Two stages per warp measured
+// as fast as three or four; two bins per loop step (128 registers) and an interval footprint
+// (two reciprocals instead of four corner divisions, 30% more candidate bins) were slower.
+constexpr int kGStageBins = 32;  // bins per staged view: 8 x 8 pixels of C2 project onto <= 25
+#ifndef XR_GATHER_STAGES
+#define XR_GATHER_STAGES 2
+#endif
+constexpr int kGStages = XR_GATHER_STAGES;  // views per warp in flight or being read
+constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
+
+// 16-byte words of one gather record: NQ quads, GA, GB (+ padding to an odd count)
+template <int NQ>
+__host__ __device__ constexpr int rec_words()
 {
-    extern __shared__ float red[];  // [nch - 1][8 * NQ][ppc]
-    const int tpr = (g.nx + 1) >> 1;  // threads per row
-    const int ppc = kGatherThreads / nch;  // pairs per CTA
-    const int pl = threadIdx.x % ppc, chunk = threadIdx.x / ppc;
-    const int t = (int)(blockIdx.x * ppc + pl);
-    const bool live = t < tpr * g.ny;
-    const int j = live ? t / tpr : 0, i = live ? 2 * (t - j * tpr) : 0;
-    const bool hasB = live && i + 1 < g.nx;
-    const int n_pix = g.nx * g.ny;
-    const int q0 = blockIdx.y * NQ;
-    const int nr = (int)n_rays;
-    const float4 *S = sil + (int64_t)q0 * nr;
-    const float4 *GA = grec;
-    const float2 *GB = reinterpret_cast<const float2 *>(grec + n_rays);
-    const float4 *V4 = reinterpret_cast<const float4 *>(vt);
-    float4 accA[NQ], accB[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) accA[q] = accB[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // the pair's box: centre and half sizes
-    const int w = hasB ? 2 : 1;
-    const float xc = (float)(g.cx + (i + 0.5 * w - 0.5 * g.nx) * g.dx);
-    const float yc = (float)(g.cy + (0.5 * g.ny - j - 0.5) * g.dy);
-    const float hx = (float)(0.5 * w * g.dx), hy = (float)(0.5 * g.dy);
-    const float half = 0.5f * (float)(g.n_cols - 1);
-    const float inv_du = (float)(1.0 / g.du), u0 = (float)g.u0, sdd = (float)g.sdd;
-    const float fi = (float)i, fj = (float)j;
-    const int ncols = g.n_cols;
-    const int v0 = (int)((int64_t)chunk * g.n_views / nch);
-    const int v1 = live ? (int)((int64_t)(chunk + 1) * g.n_views / nch) : v0;
-    for (int v = v0, vbase = v0 * ncols; v < v1; ++v, vbase += ncols) {
-        const float4 e0 = __ldg(V4 + 2 * v);
-        const float4 e1 = __ldg(V4 + 2 * v + 1);
-        float umin, umax;
-        if (KIND == XR_PAR2D) {
-            const float uc = e0.x * xc + e0.y * yc, hw = fabsf(e0.x) * hx + fabsf(e0.y) * hy;
-            umin = uc - hw;
-            umax = uc + hw;
+    return (NQ + 2) | 1;
+}
+
+template <int NQ>
+struct GStage {
+    // per warp and stage: kGStageBins records; header: the mbarriers, (cA, nb) and the lanes' bin
+    // ranges
+    static constexpr int kBytes = kGStageBins * rec_words<NQ>() * 16;
+    static constexpr int kWarps = kGatherThreads / 32;
+    static constexpr int kMeta = kWarps * kGStages * 8;
+    static constexpr int kRange = kMeta + kWarps * kGStages * 16;
+    static constexpr int kHeader = kRange + kWarps * kGStages * 32 * 8;
+    static constexpr int kSmem = kHeader + kWarps * kGStages * kBytes;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// The waiting thread is suspended until the phase completes or the hint (1 ms) runs out, so a
+// warp that waits for its copies issues nothing meanwhile.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(1000000u)
+        : "memory");
+    return done != 0;
+}
+
+// true when the phase with this parity completed; false after kWaitCycles
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// Called by the whole warp with the same operands in every lane; one lane, the one elect.sync
+// picks, arrives on the stage's mbarrier expecting `bytes` and issues the copy of `bytes`
+// (> 0, a multiple of 16) from global src to shared dst (both 16-byte aligned).
+__device__ __forceinline__ void stage_copy_elect(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%3], %2;\n\t"
+        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n\t}" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// The same without a copy: the stage's phase completes at once.
+__device__ __forceinline__ void stage_arrive_elect(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// Detector bins [c0, c1] (clamped to the detector) that the box (centre (xc, yc), half sizes
+// (hx, hy)) projects onto in a view, widened by margin bins on each side.  The constants are
+// FP32 copies made on the host (FP64 arithmetic in a kernel's prologue costs ~16 cycles per
+// warp instruction on this GPU).
+struct BinMap {
+    float x_left, y_top, dx, dy;  // the image's left and top edges, unit sizes
+    float sdd, u0, inv_du, half;  // detector: source distance, offset, 1 / spacing, (n_cols - 1) / 2
+    int ncols;
+};
+
+static BinMap bin_map(const GeoParams &g)
+{
+    return BinMap{(float)(g.cx - 0.5 * g.nx * g.dx), (float)(g.cy + 0.5 * g.ny * g.dy), (float)g.dx, (float)g.dy,
+                  (float)g.sdd, (float)g.u0, (float)(1.0 / g.du), 0.5f * (float)(g.n_cols - 1), g.n_cols};
+}
+
+template <int KIND>
+__device__ __forceinline__ void box_bins(const float4 e0, const float4 e1, float xc, float yc, float hx, float hy,
+                                         const BinMap &bm, float margin, int &c0, int &c1)
+{
+    float umin, umax;
+    if (KIND == XR_PAR2D) {
+        const float uc = e0.x * xc + e0.y * yc, hw = fabsf(e0.x) * hx + fabsf(e0.y) * hy;
+        umin = uc - hw;
+        umax = uc + hw;
+    } else {
+        // the projections of the box's four corners from the source (exact footprint)
+        const float rx = xc - e0.x, ry = yc - e0.y;
+        const float depth = rx * e0.z + ry * e0.w, lat = rx * e1.x + ry * e1.y;
+        const float dpx = hx * e0.z, dpy = hy * e0.w, dlx = hx * e1.x, dly = hy * e1.y;
+        const float a0 = __fdividef(lat - dlx - dly, depth - dpx - dpy);
+        const float a1 = __fdividef(lat + dlx - dly, depth + dpx - dpy);
+        const float a2 = __fdividef(lat - dlx + dly, depth - dpx + dpy);
+        const float a3 = __fdividef(lat + dlx + dly, depth + dpx + dpy);
+        const float a = fminf(fminf(a0, a1), fminf(a2, a3)), b = fmaxf(fmaxf(a0, a1), fmaxf(a2, a3));
+        if (KIND == XR_FAN2D) {
+            umin = bm.sdd * a;
+            umax = bm.sdd * b;
         } else {
-            // the projections of the box's four corners from the source (exact footprint)
-            const float rx = xc - e0.x, ry = yc - e0.y;
-            const float depth = rx * e0.z + ry * e0.w, lat = rx * e1.x + ry * e1.y;
-            const float dpx = hx * e0.z, dpy = hy * e0.w, dlx = hx * e1.x, dly = hy * e1.y;
-            const float a0 = __fdividef(lat - dlx - dly, depth - dpx - dpy);
-            const float a1 = __fdividef(lat + dlx - dly, depth + dpx - dpy);
-            const float a2 = __fdividef(lat - dlx + dly, depth - dpx + dpy);
-            const float a3 = __fdividef(lat + dlx + dly, depth + dpx + dpy);
-            const float a = fminf(fminf(a0, a1), fminf(a2, a3)), b = fmaxf(fmaxf(a0, a1), fmaxf(a2, a3));
-            if (KIND == XR_FAN2D) {
-                umin = sdd * a;
-                umax = sdd * b;
-            } else {
-                umin = atanf(a);
-                umax = atanf(b);
-            }
-        }
-        const float c0f = fminf(fmaxf((umin - u0) * inv_du + half - 1e-3f, -1.0f), 4.0e6f);
-        const float c1f = fminf(fmaxf((umax - u0) * inv_du + half + 1e-3f, -1.0f), 4.0e6f);
-        const int c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
-        const int c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, ncols - 1);
-        for (int c = c0; c <= c1; ++c) {
-            const int r = vbase + c;
-            const float4 ga = __ldg(GA + r);
-            const float2 gb = __ldg(GB + r);
-            float4 sv[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) sv[q] = __ldg(S + q * nr + r);
-            float la, lb;
-            if (ga.x != 0.f && ga.z != 0.f) {
-                // plane crossings t = fma(q - o, 1/w, -f/w): x planes i, i+1, i+2; y planes j, j+1
-                const float qx = fi - gb.x, qy = fj - gb.y;
-                const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
-                const float tx2 = __fmaf_rn(qx + 2.0f, ga.x, ga.y);
-                const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
-                const float ylo = fminf(ty0, ty1), yhi = fmaxf(ty0, ty1);
-                la = __fsub_rn(fminf(fmaxf(tx0, tx1), yhi), fmaxf(fminf(tx0, tx1), ylo));
-                lb = __fsub_rn(fminf(fmaxf(tx1, tx2), yhi), fmaxf(fminf(tx1, tx2), ylo));
-            } else {
-                // a ray parallel to an axis: the walk's own unit lengths (rare)
-                la = lb = 0.f;
-                Walk W;
-                if (walk_setup(rays[r], g.nx, g.ny, 1, 1, g.nx, (int64_t)g.nx * g.ny, W)) {
-                    la = walk_unit_length(W, i, j, 0);
-                    if (hasB) lb = walk_unit_length(W, i + 1, j, 0);
-                }
-            }
-            la = la > 0.f ? la : 0.f;
-            lb = (hasB && lb > 0.f) ? lb : 0.f;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                fma4(accA[q], sv[q], la);
-                fma4(accB[q], sv[q], lb);
-            }
+            umin = atanf(a);
+            umax = atanf(b);
         }
     }
+    const float c0f = fminf(fmaxf((umin - bm.u0) * bm.inv_du + bm.half - margin, -1.0f), 4.0e6f);
+    const float c1f = fminf(fmaxf((umax - bm.u0) * bm.inv_du + bm.half + margin, -1.0f), 4.0e6f);
+    c0 = max(__float_as_int(__fadd_ru(c0f, kMagic)) - kMagicBits, 0);
+    c1 = min(__float_as_int(__fadd_rd(c1f, kMagic)) - kMagicBits, bm.ncols - 1);
+}
+
+// One candidate bin of a pixel pair: the lengths of ray r in pixels (i, j) and (i + 1, j) from
+// the ray's plane constants (ga, gb), spread with the bin's NQ quads of sinogram values.
+template <int NQ>
+__device__ __forceinline__ void pair_bin(const float4 ga, const float2 gb, const float4 (&sv)[NQ], float fi, float fj,
+                                         int i, int j, bool hasB, const RayRec *__restrict__ rays, int r, int nx, int ny,
+                                         float4 (&accA)[NQ], float4 (&accB)[NQ])
+{
+    float la, lb;
+    if (ga.x != 0.f && ga.z != 0.f) {
+        // plane crossings t = fma(q - o, 1/w, -f/w): x planes i, i+1, i+2; y planes j, j+1
+        const float qx = fi - gb.x, qy = fj - gb.y;
+        const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
+        const float tx2 = __fmaf_rn(qx + 2.0f, ga.x, ga.y);
+        const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
+        const float ylo = fminf(ty0, ty1), yhi = fmaxf(ty0, ty1);
+        la = __fsub_rn(fminf(fmaxf(tx0, tx1), yhi), fmaxf(fminf(tx0, tx1), ylo));
+        lb = __fsub_rn(fminf(fmaxf(tx1, tx2), yhi), fmaxf(fminf(tx1, tx2), ylo));
+    } else {
+        // a ray parallel to an axis: the walk's own unit lengths (rare)
+        la = lb = 0.f;
+        Walk W;
+        if (walk_setup(rays[r], nx, ny, 1, 1, nx, (int64_t)nx * ny, W)) {
+            la = walk_unit_length(W, i, j, 0);
+            if (hasB) lb = walk_unit_length(W, i + 1, j, 0);
+        }
+    }
+    la = la > 0.f ? la : 0.f;
+    lb = (hasB && lb > 0.f) ? lb : 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        fma4(accA[q], sv[q], la);
+        fma4(accB[q], sv[q], lb);
+    }
+}
+
+// The chunks' sums of one pair go to its chunk-0 thread in chunk order (red: [nch - 1][8 NQ]
+// [ppc] floats), which writes the pair's pixels of every image of the group.
+template <int NQ>
+__device__ __forceinline__ void gather_finish(float4 (&accA)[NQ], float4 (&accB)[NQ], float *red, int nch, int chunk,
+                                              int pl, int ppc, bool live, bool hasB, int i, int j, int q0, int batch,
+                                              int nx, int n_pix, const ImgMap &om, float *__restrict__ img)
+{
     if (nch > 1) {
-        // chunks 1..nch-1 hand their sums to the chunk-0 thread of the same pair
         if (chunk > 0) {
             float *r = red + (size_t)(chunk - 1) * 8 * NQ * ppc + pl;
 #pragma unroll
@@ -739,24 +809,191 @@ __global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_pair_k
             }
         }
     }
-    if (live) {
+    if (!live) return;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int b = 4 * (q0 + q);
-            const float a4[4] = {accA[q].x, accA[q].y, accA[q].z, accA[q].w};
-            const float b4[4] = {accB[q].x, accB[q].y, accB[q].z, accB[q].w};
+    for (int q = 0; q < NQ; ++q) {
+        const int b = 4 * (q0 + q);
+        const float a4[4] = {accA[q].x, accA[q].y, accA[q].z, accA[q].w};
+        const float b4[4] = {accB[q].x, accB[q].y, accB[q].z, accB[q].w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (b + k < batch) {
-                    const int64_t base = om.image(b + k, n_pix);
-                    if (base < 0) continue;
-                    float *o = img + base + (int64_t)j * om.row(g.nx) + i;
-                    o[0] = a4[k];
-                    if (hasB) o[1] = b4[k];
-                }
+        for (int k = 0; k < 4; ++k) {
+            if (b + k < batch) {
+                const int64_t base = om.image(b + k, n_pix);
+                if (base < 0) continue;
+                float *o = img + base + (int64_t)j * om.row(nx) + i;
+                o[0] = a4[k];
+                if (hasB) o[1] = b4[k];
             }
         }
     }
+}
+
+// Gather records of group y = blockIdx.y (see the staged gather below) from the sinograms --
+// value of image b, ray r at sino[b * sb + r * sr] -- and the plane constants; images past the
+// batch read as zero.
+template <int NQ>
+__global__ void gather_records_kernel(const float *__restrict__ sino, int64_t sb, int64_t sr, int batch,
+                                      int64_t n_rays, const float4 *__restrict__ grec, float4 *__restrict__ rec)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    constexpr int W = rec_words<NQ>();
+    float4 *o = rec + ((int64_t)blockIdx.y * n_rays + r) * W;
+    const int b0 = 4 * NQ * (int)blockIdx.y;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int b = b0 + 4 * q + k;
+            v[k] = b < batch ? __ldg(sino + b * sb + r * sr) : 0.f;
+        }
+        o[q] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    o[NQ] = __ldg(grec + r);
+    const float2 gb = __ldg(reinterpret_cast<const float2 *>(grec + n_rays) + r);
+    o[NQ + 1] = make_float4(gb.x, gb.y, 0.f, 0.f);
+#pragma unroll
+    for (int w = NQ + 2; w < W; ++w) o[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// CTA of 256 threads = tpc warp tiles x nch view chunks (tpc * nch = 8); warp w takes tile
+// blockIdx.x * tpc + w % tpc (tiles row-major over the image, 8 x 8 pixels) and views
+// [chunk * n_views / nch, (chunk + 1) * n_views / nch) of chunk w / tpc.  A view's staged bin
+// range is the union of the lanes' own candidate ranges, which each lane computes once, when
+// the view's copy is issued, and keeps in shared memory until it reads the stage.
+template <int NQ, int KIND>
+__global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_stage_kernel(
+    const RayRec *__restrict__ rays, GeoParams g, BinMap bm, const float *__restrict__ vt,
+    const float4 *__restrict__ rec, int64_t n_rays, float *__restrict__ img, int batch, int nch, ImgMap om,
+    int *__restrict__ err)
+{
+    using L = GStage<NQ>;
+    constexpr int W = rec_words<NQ>();
+    extern __shared__ __align__(128) unsigned char gsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tpc = (kGatherThreads / 32) / nch;
+    const int chunk = warp / tpc, wt = warp - chunk * tpc;
+    const int ppc = 32 * tpc, pl = wt * 32 + lane;
+    const int tpr = (g.nx + 1) >> 1;  // pairs per row
+    const int tiles_x = (tpr + 3) >> 2;
+    const int tile = (int)blockIdx.x * tpc + wt;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int pi = 4 * tx + (lane & 3), j = 8 * ty + (lane >> 2);
+    const bool live = pi < tpr && j < g.ny;
+    const int i = 2 * pi;
+    const bool hasB = live && i + 1 < g.nx;
+    const bool tile_live = 8 * ty < g.ny;  // warp-uniform
+    const int n_pix = g.nx * g.ny;
+    const int q0 = blockIdx.y * NQ;
+    const float4 *R = rec + (int64_t)blockIdx.y * n_rays * W;
+    const float4 *V4 = reinterpret_cast<const float4 *>(vt);
+    const int ncols = bm.ncols;
+    // the pair's box: centre and half sizes
+    const float w = hasB ? 2.0f : 1.0f;
+    const float fi = (float)i, fj = (float)j;
+    const float xc = __fmaf_rn(fi + 0.5f * w, bm.dx, bm.x_left), yc = __fmaf_rn(-(fj + 0.5f), bm.dy, bm.y_top);
+    const float hx = 0.5f * w * bm.dx, hy = 0.5f * bm.dy;
+    float4 accA[NQ], accB[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) accA[q] = accB[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    uint64_t *bar = reinterpret_cast<uint64_t *>(gsm) + warp * kGStages;
+    int2 *meta = reinterpret_cast<int2 *>(gsm + L::kMeta) + warp * kGStages;
+    int2 *rng = reinterpret_cast<int2 *>(gsm + L::kRange) + warp * kGStages * 32;
+    unsigned char *stage0 = gsm + L::kHeader + (size_t)warp * kGStages * L::kBytes;
+    const int v0 = (int)((int64_t)chunk * g.n_views / nch), v1 = (int)((int64_t)(chunk + 1) * g.n_views / nch);
+
+    // stage s <- view v: the lanes' bin ranges and the records of their union [cA, cA + nb)
+    auto issue = [&](int v, int s) {
+        int c0 = INT_MAX, c1 = INT_MIN;
+        if (live) {
+            const float4 e0 = __ldg(V4 + 2 * v), e1 = __ldg(V4 + 2 * v + 1);
+            box_bins<KIND>(e0, e1, xc, yc, hx, hy, bm, 1e-3f, c0, c1);
+            if (c0 > c1) {
+                c0 = INT_MAX;
+                c1 = INT_MIN;
+            }
+        }
+        rng[s * 32 + lane] = make_int2(c0, c1);
+        const int cA = __reduce_min_sync(0xffffffffu, c0), cB = __reduce_max_sync(0xffffffffu, c1);
+        const int nb = cB >= cA ? cB - cA + 1 : 0;
+        const int code = nb > kGStageBins ? -1 : nb;  // bins staged; -1: read directly
+        if (lane == 0) meta[s] = make_int2(cA, code);
+        if (code > 0)
+            stage_copy_elect(stage0 + s * L::kBytes, R + ((int64_t)v * ncols + cA) * W, (unsigned)(nb * W * 16),
+                             bar + s);
+        else
+            stage_arrive_elect(bar + s);
+    };
+
+    if (tile_live) {
+        if (lane == 0) {
+            for (int s = 0; s < kGStages; ++s) mbar_init(bar + s, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+        unsigned phase = 0, pending = 0;  // per stage: parity of its next completion; copies in flight
+        bool dead = false;
+        for (int s = 0; s < kGStages - 1 && v0 + s < v1; ++s) {
+            issue(v0 + s, s);
+            pending |= 1u << s;
+        }
+        int s = 0;
+        for (int v = v0; v < v1; ++v) {
+            __syncwarp();  // every lane is done with stage s - 1 (view v - 1)
+            const int sn = s == 0 ? kGStages - 1 : s - 1;
+            if (v + kGStages - 1 < v1) {
+                issue(v + kGStages - 1, sn);
+                pending |= 1u << sn;
+            }
+            const bool ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                dead = true;
+                break;
+            }
+            phase ^= 1u << s;
+            pending &= ~(1u << s);
+            const int2 m = meta[s];
+            const int2 cr = rng[s * 32 + lane];
+            const int vb = v * ncols;
+            // records of bins cr.x .. cr.y: in the stage (m.y > 0) or in global memory (m.y < 0)
+            if (m.y > 0) {
+                const float4 *st = reinterpret_cast<const float4 *>(stage0 + s * L::kBytes);
+                int c = cr.x;
+                for (; c <= cr.y; ++c) {
+                    const float4 *o = st + (c - m.x) * W;
+                    float4 sv[NQ];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) sv[q] = o[q];
+                    const float4 gb = o[NQ + 1];
+                    pair_bin<NQ>(o[NQ], make_float2(gb.x, gb.y), sv, fi, fj, i, j, hasB, rays, vb + c, g.nx, g.ny,
+                                 accA, accB);
+                }
+            } else if (m.y < 0) {
+                for (int c = cr.x; c <= cr.y; ++c) {
+                    const float4 *o = R + (int64_t)(vb + c) * W;
+                    float4 sv[NQ];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) sv[q] = __ldg(o + q);
+                    const float4 gb = __ldg(o + NQ + 1);
+                    pair_bin<NQ>(__ldg(o + NQ), make_float2(gb.x, gb.y), sv, fi, fj, i, j, hasB, rays, vb + c, g.nx,
+                                 g.ny, accA, accB);
+                }
+            }
+            s = s + 1 == kGStages ? 0 : s + 1;
+        }
+        if (dead) {
+            // stop: wait (bounded) for this warp's copies still in flight
+            if (lane == 0 && err) atomicOr(err, XR_DEVERR_WAIT_BOUND);
+            for (int q = 0; q < kGStages; ++q)
+                if ((pending >> q) & 1u) mbar_wait_bounded(bar + q, (phase >> q) & 1u);
+            accA[0].x = __int_as_float(0x7fc00000);  // NaN in the sums of the warp's pixels
+        }
+    }
+    __syncthreads();  // every warp is done with its stages: the chunk sums reuse them
+    gather_finish<NQ>(accA, accB, reinterpret_cast<float *>(gsm + L::kHeader), nch, chunk, pl, ppc, live, hasB, i, j,
+                      q0, batch, g.nx, n_pix, om, img);
 }
 
 cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny, int nz, float *il0, float *il1,
@@ -814,33 +1051,71 @@ static int gather_chunks(int64_t pairs, int groups, int blocks_per_sm, int n_vie
     return 1;
 }
 
-cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
-                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s,
-                                const int *slice_of, int64_t slice_stride, int64_t row_stride)
+// The staged kernel takes more than 48 KB of dynamic shared memory: opt in once per device.
+template <int NQ, int KIND>
+static cudaError_t stage_smem_optin()
 {
-    const ImgMap om{slice_of, slice_stride, row_stride};
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(gather_stage_kernel<NQ, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GStage<NQ>::kSmem);
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
+
+size_t gather_records_bytes(int batch, int nq, int64_t n_rays)
+{
     const int Q = (batch + 3) / 4;
     const int groups = (Q + nq - 1) / nq;
-    const int64_t pairs = (int64_t)((g.nx + 1) / 2) * g.ny;
-    const int nch = gather_chunks(pairs, groups, nq >= 2 ? 2 : 3, g.n_views);  // 1, 2, 4 or 8
-    const int ppc = kGatherThreads / nch;
-    const dim3 grid((unsigned)((pairs + ppc - 1) / ppc), (unsigned)groups);
-    const size_t smem = (size_t)(nch - 1) * 8 * nq * ppc * sizeof(float);
+    const int words = nq == 4 ? rec_words<4>() : (nq == 2 ? rec_words<2>() : rec_words<1>());
+    return (size_t)groups * (size_t)n_rays * (size_t)words * 16;
+}
+
+cudaError_t launch_gather_staged(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
+                                 const float *sino, int64_t n_rays, float *img, int batch, int nq, void *recs,
+                                 cudaStream_t s, int *err, int64_t sb, int64_t sr, const int *slice_of,
+                                 int64_t slice_stride, int64_t row_stride)
+{
+    const ImgMap om{slice_of, slice_stride, row_stride};
+    if (sb < 0) {
+        sb = n_rays;
+        sr = 1;
+    }
+    const int Q = (batch + 3) / 4;
+    const int groups = (Q + nq - 1) / nq;
     const float4 *G = reinterpret_cast<const float4 *>(grec);
-    const float4 *S = reinterpret_cast<const float4 *>(sil);
-#define XR_GP(NQV, K) \
-    gather_pair_kernel<NQV, K><<<grid, kGatherThreads, smem, s>>>(rays, G, g, vt, S, n_rays, img, batch, nch, om)
-#define XR_GP_K(K)                     \
-    do {                               \
-        if (nq == 4) XR_GP(4, K);      \
-        else if (nq == 2) XR_GP(2, K); \
-        else XR_GP(1, K);              \
+    float4 *Rw = reinterpret_cast<float4 *>(recs);
+    const int64_t tiles = (int64_t)(((g.nx + 1) / 2 + 3) / 4) * ((g.ny + 7) / 8);
+    const int nch = gather_chunks(32 * tiles, groups, nq >= 2 ? 2 : 3, g.n_views);  // 1, 2, 4 or 8
+    const int tpc = (kGatherThreads / 32) / nch;
+    const dim3 grid((unsigned)((tiles + tpc - 1) / tpc), (unsigned)groups);
+    const dim3 rgrid((unsigned)((n_rays + 255) / 256), (unsigned)groups);
+    const BinMap bm = bin_map(g);
+    cudaError_t e = cudaSuccess;
+#define XR_GS(NQV, K)                                                                                               \
+    do {                                                                                                            \
+        e = stage_smem_optin<NQV, K>();                                                                             \
+        if (e != cudaSuccess) break;                                                                                \
+        gather_records_kernel<NQV><<<rgrid, 256, 0, s>>>(sino, sb, sr, batch, n_rays, G, Rw);                      \
+        gather_stage_kernel<NQV, K><<<grid, kGatherThreads, GStage<NQV>::kSmem, s>>>(rays, g, bm, vt, Rw, n_rays,  \
+                                                                                     img, batch, nch, om, err);     \
     } while (0)
-    if (g.kind == XR_PAR2D) XR_GP_K(XR_PAR2D);
-    else if (g.kind == XR_FAN2D) XR_GP_K(XR_FAN2D);
-    else XR_GP_K(XR_FAN2D_ARC);
-#undef XR_GP_K
-#undef XR_GP
+#define XR_GS_K(K)                     \
+    do {                               \
+        if (nq == 4) XR_GS(4, K);      \
+        else if (nq == 2) XR_GS(2, K); \
+        else XR_GS(1, K);              \
+    } while (0)
+    if (g.kind == XR_PAR2D) XR_GS_K(XR_PAR2D);
+    else if (g.kind == XR_FAN2D) XR_GS_K(XR_FAN2D);
+    else XR_GS_K(XR_FAN2D_ARC);
+#undef XR_GS_K
+#undef XR_GS
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -73,22 +73,6 @@ __global__ void slice_planes_kernel(const float *__restrict__ vol, int nx, int n
     il1[(int64_t)q * np + (int64_t)ip * pz + kp] = v;
 }
 
-// 3D sinogram [n2][n_cols] -> sinogram planes [Q][n2][4] (plane q: columns 4q..4q+3).
-__global__ void slice_sino_kernel(const float *__restrict__ sino, int64_t n2, int n_cols, float4 *__restrict__ sil)
-{
-    const int64_t r2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r2 >= n2) return;
-    const int q = blockIdx.y;
-    const float *row = sino + r2 * n_cols + 4 * q;
-    const int left = n_cols - 4 * q;
-    float4 v;
-    v.x = __ldg(row);
-    v.y = left > 1 ? __ldg(row + 1) : 0.f;
-    v.z = left > 2 ? __ldg(row + 2) : 0.f;
-    v.w = left > 3 ? __ldg(row + 3) : 0.f;
-    sil[(int64_t)q * n2 + r2] = v;
-}
-
 // ---------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------
@@ -172,14 +156,6 @@ cudaError_t launch_slice_planes(const float *vol, int nx, int ny, int nz, const 
     const int Q = (n_img + 3) / 4;
     slice_planes_kernel<<<dim3((unsigned)((np + 255) / 256), (unsigned)Q), 256, 0, s>>>(
         vol, nx, ny, nz, slice_of, n_img, reinterpret_cast<float4 *>(il0), reinterpret_cast<float4 *>(il1));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_slice_sino(const float *sino, int64_t n2, int n_cols, float *sil, cudaStream_t s)
-{
-    const int Q = (n_cols + 3) / 4;
-    slice_sino_kernel<<<dim3((unsigned)((n2 + 255) / 256), (unsigned)Q), 256, 0, s>>>(sino, n2, n_cols,
-                                                                                     reinterpret_cast<float4 *>(sil));
     return cudaGetLastError();
 }
 

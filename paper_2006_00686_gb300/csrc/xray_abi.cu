@@ -120,11 +120,16 @@ static size_t padded_units(const xr_geometry *g)
     return (size_t)(g->params.nx + 4) * (size_t)(g->params.ny + 4) * (size_t)g->params.nz;
 }
 
+// Two chunks of quad planes (the forward's images, or the scatter's accumulators), then the
+// gather records of the batch for any plane count the tuning may pick (at least one chunk of
+// sinograms: the attenuated path keeps its attenuation planes there).
 static size_t fast_ws_bytes(const xr_geometry *g, int batch)
 {
     const int Bp = fast_chunk(batch);
     const size_t padded = (size_t)((batch + Bp - 1) / Bp) * Bp;
-    return padded * sizeof(float) * (2 * padded_units(g) + (size_t)g->n_rays);
+    size_t tail = padded * sizeof(float) * (size_t)g->n_rays;
+    for (int nq = 1; nq <= 4; nq *= 2) tail = std::max(tail, gather_records_bytes((int)padded, nq, g->n_rays));
+    return padded * sizeof(float) * 2 * padded_units(g) + tail;
 }
 
 // The batched fast path applies when the workspace holds the batch and the batch is >= 4.
@@ -181,18 +186,22 @@ static int ray_order(const xr_geometry *g, bool adjoint)
     return 0;
 }
 
-// Single-tilt-axis parallel scans: the column images as quad planes in both orders and the
-// sinogram planes.  Planes are padded to a multiple of 4 (the forward and the gather walk up
-// to 4 planes per thread).
+// Single-tilt-axis parallel scans: the column images as quad planes in both orders (the
+// forward) and the gather records (the adjoint).  Planes are padded to a multiple of 4 (the
+// forward walks up to 4 planes per thread).
 static int64_t slice_n2(const xr_geometry *g) { return (int64_t)g->params.n_views * g->params.n_rows; }
 static int64_t slice_np(const xr_geometry *g)
 {
     return (int64_t)(g->params.nx + 2 * XR_IL_PAD) * (g->params.nz + 2 * XR_IL_PAD);
 }
 static int64_t slice_planes(const xr_geometry *g) { return (int64_t)((g->params.n_cols + 15) / 16) * 4; }
+// Two sets of column-image planes (the forward), then the gather records of one volume's
+// columns for any plane count the tuning may pick.
 static size_t slice_ws_bytes(const xr_geometry *g)
 {
-    return (size_t)slice_planes(g) * sizeof(float4) * (size_t)(2 * slice_np(g) + slice_n2(g));
+    size_t tail = 0;
+    for (int nq = 1; nq <= 4; nq *= 2) tail = std::max(tail, gather_records_bytes(g->params.n_cols, nq, slice_n2(g)));
+    return (size_t)slice_planes(g) * sizeof(float4) * (size_t)(2 * slice_np(g)) + tail;
 }
 
 // The batch-of-columns path of single-tilt-axis parallel scans (32-bit offsets in a plane,
@@ -701,14 +710,14 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         if (use_slices(g)) {
             // one 2D gather per detector column, written into the column's y-slice
             const GeoParams &p = g->params;
-            float *sil = g->d_ws + 8 * slice_planes(g) * slice_np(g);
+            float *recs = g->d_ws + 8 * slice_planes(g) * slice_np(g);
             for (int b = 0; b < batch; ++b) {
                 float *img = d_img + (size_t)b * g->n_units;
                 if (!g->slices.surjective) XR_CUDA(cudaMemsetAsync(img, 0, (size_t)g->n_units * sizeof(float), s));
-                XR_CUDA(launch_slice_sino(d_sino + (size_t)b * g->n_rays, slice_n2(g), p.n_cols, sil, s));
-                XR_CUDA(launch_gather_plane(g->d_rays2, g->d_grec2, g->slices.g2, g->d_vt2, sil, slice_n2(g), img,
-                                            p.n_cols, plane_nq(g, p.n_cols), s, g->d_slice_of, p.nx,
-                                            (int64_t)p.ny * p.nx));
+                // column c of 2D ray r2 at sino[r2 * n_cols + c]
+                XR_CUDA(launch_gather_staged(g->d_rays2, g->d_grec2, g->slices.g2, g->d_vt2, d_sino + (size_t)b * g->n_rays,
+                                             slice_n2(g), img, p.n_cols, plane_nq(g, p.n_cols), recs, s, g->d_err, 1,
+                                             p.n_cols, g->d_slice_of, p.nx, (int64_t)p.ny * p.nx));
             }
             return XR_OK;
         }
@@ -718,12 +727,11 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
             return XR_OK;
         }
         if (use_fast(g, batch)) {
-            const int Q = (batch + 3) / 4;
+            // the staged gather on records built after the forward's planes in the workspace
             const size_t padded = (size_t)((batch + fast_chunk(batch) - 1) / fast_chunk(batch)) * fast_chunk(batch);
-            float *sil = g->d_ws + 2 * padded * padded_units(g);
-            XR_CUDA(launch_interleave_sino(d_sino, batch, g->n_rays, 4 * Q, sil, s));
-            XR_CUDA(launch_gather_plane(g->d_rays, g->d_grec, g->params, g->d_view_tab, sil, g->n_rays, d_img, batch,
-                                        plane_nq(g, batch), s));
+            float *recs = g->d_ws + 2 * padded * padded_units(g);
+            XR_CUDA(launch_gather_staged(g->d_rays, g->d_grec, g->params, g->d_view_tab, d_sino, g->n_rays, d_img,
+                                         batch, plane_nq(g, batch), recs, s, g->d_err));
             return XR_OK;
         }
         XR_CUDA(launch_backproject_gather2d(g->d_rays, g->params, make_grid(g), g->d_view_tab, d_sino, g->n_rays,

@@ -179,8 +179,6 @@ cudaError_t launch_batch2d_adjoint(const BatchItem *items, int n_items, int64_t 
                                    unsigned long long *counter, int grid_ctas, int block, cudaStream_t s);
 
 // Batched fast path for rays with at most two active axes (fast2d.cu).
-cudaError_t launch_interleave_sino(const float *sino, int batch, int64_t n_rays, int Bp, float *out,
-                                   cudaStream_t s);
 cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, float *acc0,
                                  float *acc1, size_t acc_bytes, int Bp, const float *sino, float *img, int batch,
                                  int block, cudaStream_t s);
@@ -193,11 +191,17 @@ cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny
 cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
                                  const float *il1, float *sino, int batch, int nq, cudaStream_t s, int64_t sb = -1,
                                  int64_t sr = 1);
-// The gather writes image b to the user layout, or (slice_of != NULL) to y-slice slice_of[b]
-// of a volume (pixel (i, j) of the image at slice * slice_stride + j * row_stride + i).
-cudaError_t launch_gather_plane(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
-                                const float *sil, int64_t n_rays, float *img, int batch, int nq, cudaStream_t s,
-                                const int *slice_of = nullptr, int64_t slice_stride = 0, int64_t row_stride = 0);
+// The gather adjoint of a batch of sinograms (image b, ray r at sino[b * sb + r * sr]; sb < 0:
+// the user layout [batch][n_rays]): builds the gather records (gather_records_bytes(batch, nq,
+// n_rays) bytes at recs, 16-byte aligned) and reads them through shared-memory stages.  Image b
+// goes to the user layout, or (slice_of != NULL) to y-slice slice_of[b] of a volume (pixel
+// (i, j) of the image at slice * slice_stride + j * row_stride + i).  err: the handle's device
+// error word.
+size_t gather_records_bytes(int batch, int nq, int64_t n_rays);
+cudaError_t launch_gather_staged(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
+                                 const float *sino, int64_t n_rays, float *img, int batch, int nq, void *recs,
+                                 cudaStream_t s, int *err, int64_t sb = -1, int64_t sr = 1,
+                                 const int *slice_of = nullptr, int64_t slice_stride = 0, int64_t row_stride = 0);
 
 // Single-tilt-axis parallel scans as batches of 2D problems, one per detector column
 // (slices.cu).  slice_of[c]: the y-slice of column c's ray plane, or -1 outside the volume;
@@ -215,8 +219,6 @@ bool slice_plan(const xr_geometry_desc *d, SlicePlan *sp);
 cudaError_t launch_slice_rays(const RayRec *rays3, int64_t n2, int n_cols, int c_rep, RayRec *rays2, cudaStream_t s);
 cudaError_t launch_slice_planes(const float *vol, int nx, int ny, int nz, const int *slice_of, int n_img, float *il0,
                                 float *il1, cudaStream_t s);
-cudaError_t launch_slice_sino(const float *sino, int64_t n2, int n_cols, float *sil, cudaStream_t s);
-
 // Tiled forward / adjoint for 2D scans and batches (tile2d.cu); in: user-layout input,
 // out: user-layout output (cleared inside).
 cudaError_t launch_tile2d(const RayRec *rays, const GeoParams &g, const float *vt, const float *in, float *out,
