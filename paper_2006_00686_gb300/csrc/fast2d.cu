@@ -770,6 +770,26 @@ __device__ __forceinline__ void pair_bin(const float4 ga, const float2 gb, const
     }
 }
 
+// pair_bin for a ray that is not parallel to an axis (a missing ray gives 0): the plane
+// crossings only.  x2: 2 for a pair, 1 for a lone last pixel (then pixel B's length is 0).
+template <int NQ>
+__device__ __forceinline__ void pair_bin_planes(const float4 ga, const float4 gb, const float4 *sv, float fi, float fj,
+                                                float x2, float4 (&accA)[NQ], float4 (&accB)[NQ])
+{
+    const float qx = fi - gb.x, qy = fj - gb.y;
+    const float tx0 = __fmaf_rn(qx, ga.x, ga.y), tx1 = __fmaf_rn(qx + 1.0f, ga.x, ga.y);
+    const float tx2 = __fmaf_rn(qx + x2, ga.x, ga.y);
+    const float ty0 = __fmaf_rn(qy, ga.z, ga.w), ty1 = __fmaf_rn(qy + 1.0f, ga.z, ga.w);
+    const float ylo = fminf(ty0, ty1), yhi = fmaxf(ty0, ty1);
+    const float la = fmaxf(__fsub_rn(fminf(fmaxf(tx0, tx1), yhi), fmaxf(fminf(tx0, tx1), ylo)), 0.f);
+    const float lb = fmaxf(__fsub_rn(fminf(fmaxf(tx1, tx2), yhi), fmaxf(fminf(tx1, tx2), ylo)), 0.f);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        fma4(accA[q], sv[q], la);
+        fma4(accB[q], sv[q], lb);
+    }
+}
+
 // The chunks' sums of one pair go to its chunk-0 thread in chunk order (red: [nch - 1][8 NQ]
 // [ppc] floats), which writes the pair's pixels of every image of the group.
 template <int NQ>
@@ -833,7 +853,8 @@ __device__ __forceinline__ void gather_finish(float4 (&accA)[NQ], float4 (&accB)
 // batch read as zero.
 template <int NQ>
 __global__ void gather_records_kernel(const float *__restrict__ sino, int64_t sb, int64_t sr, int batch,
-                                      int64_t n_rays, const float4 *__restrict__ grec, float4 *__restrict__ rec)
+                                      int64_t n_rays, const RayRec *__restrict__ rays, const float4 *__restrict__ grec,
+                                      float4 *__restrict__ rec)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
@@ -850,9 +871,13 @@ __global__ void gather_records_kernel(const float *__restrict__ sino, int64_t sb
         }
         o[q] = make_float4(v[0], v[1], v[2], v[3]);
     }
-    o[NQ] = __ldg(grec + r);
+    const float4 ga = __ldg(grec + r);
+    o[NQ] = ga;
     const float2 gb = __ldg(reinterpret_cast<const float2 *>(grec + n_rays) + r);
-    o[NQ + 1] = make_float4(gb.x, gb.y, 0.f, 0.f);
+    // z = 1: a ray parallel to an axis, whose lengths only the walk gives (the plane-crossing
+    // form gives 0 for it, as for a ray that misses the image)
+    const bool walk = (ga.x == 0.f || ga.z == 0.f) && !(__ldg(&rays[r].flags) & RAY_MISS);
+    o[NQ + 1] = make_float4(gb.x, gb.y, walk ? 1.f : 0.f, 0.f);
 #pragma unroll
     for (int w = NQ + 2; w < W; ++w) o[w] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -894,6 +919,7 @@ __global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_stage_
     const float fi = (float)i, fj = (float)j;
     const float xc = __fmaf_rn(fi + 0.5f * w, bm.dx, bm.x_left), yc = __fmaf_rn(-(fj + 0.5f), bm.dy, bm.y_top);
     const float hx = 0.5f * w * bm.dx, hy = 0.5f * bm.dy;
+    const float x2 = w;  // the pair's right edge, in x planes from i
     float4 accA[NQ], accB[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) accA[q] = accB[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -960,15 +986,23 @@ __global__ void __launch_bounds__(kGatherThreads, NQ >= 2 ? 2 : 3) gather_stage_
             // records of bins cr.x .. cr.y: in the stage (m.y > 0) or in global memory (m.y < 0)
             if (m.y > 0) {
                 const float4 *st = reinterpret_cast<const float4 *>(stage0 + s * L::kBytes);
-                int c = cr.x;
-                for (; c <= cr.y; ++c) {
-                    const float4 *o = st + (c - m.x) * W;
-                    float4 sv[NQ];
+                // a ray of the staged range that needs the walk (lane k looks at record k)
+                const bool walk = __any_sync(0xffffffffu, lane < m.y && st[lane * W + NQ + 1].z != 0.f);
+                if (!walk) {
+                    for (int c = cr.x; c <= cr.y; ++c) {
+                        const float4 *o = st + (c - m.x) * W;
+                        pair_bin_planes<NQ>(o[NQ], o[NQ + 1], o, fi, fj, x2, accA, accB);
+                    }
+                } else {
+                    for (int c = cr.x; c <= cr.y; ++c) {
+                        const float4 *o = st + (c - m.x) * W;
+                        float4 sv[NQ];
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) sv[q] = o[q];
-                    const float4 gb = o[NQ + 1];
-                    pair_bin<NQ>(o[NQ], make_float2(gb.x, gb.y), sv, fi, fj, i, j, hasB, rays, vb + c, g.nx, g.ny,
-                                 accA, accB);
+                        for (int q = 0; q < NQ; ++q) sv[q] = o[q];
+                        const float4 gb = o[NQ + 1];
+                        pair_bin<NQ>(o[NQ], make_float2(gb.x, gb.y), sv, fi, fj, i, j, hasB, rays, vb + c, g.nx,
+                                     g.ny, accA, accB);
+                    }
                 }
             } else if (m.y < 0) {
                 for (int c = cr.x; c <= cr.y; ++c) {
@@ -1100,7 +1134,7 @@ cudaError_t launch_gather_staged(const RayRec *rays, const void *grec, const Geo
     do {                                                                                                            \
         e = stage_smem_optin<NQV, K>();                                                                             \
         if (e != cudaSuccess) break;                                                                                \
-        gather_records_kernel<NQV><<<rgrid, 256, 0, s>>>(sino, sb, sr, batch, n_rays, G, Rw);                      \
+        gather_records_kernel<NQV><<<rgrid, 256, 0, s>>>(sino, sb, sr, batch, n_rays, rays, G, Rw);                \
         gather_stage_kernel<NQV, K><<<grid, kGatherThreads, GStage<NQV>::kSmem, s>>>(rays, g, bm, vt, Rw, n_rays,  \
                                                                                      img, batch, nch, om, err);     \
     } while (0)
