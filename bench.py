@@ -282,7 +282,7 @@ def _roofline(n_int, units_bytes, B, dom, dom_ms, peaks, peak_kind, traffic, tra
 # kernel, from the ncu captures summarised under profiles/: (workload, phase, method) ->
 # (bytes, note).  Only kernels unchanged since their capture are listed.
 TRAFFIC = {
-    ("fan2d_512x16", "adjoint", "gather"): (70.1e6, "profiles/gather_stage_fan2d_512x16.md (one launch of the staged "
+    ("fan2d_512x16", "adjoint", "gather"): (69.5e6, "profiles/gather_stage_fan2d_512x16.md (one launch of the staged "
                                                     "gather, full size; the records pass before it is not included)"),
     ("fan2d_512x16", "forward", "gather"): (62.4e6, "profiles/fwd_plane_fan2d_512x16.md (one launch, full size)"),
     ("cone_512", "adjoint", "scatter"): (80.50e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
