@@ -382,6 +382,14 @@ xr_status xr_read_probe(const float *d_buf, int64_t n_floats, int32_t reps, floa
  * Errors: XR_ERR_NULL, XR_ERR_SIZE, XR_ERR_CUDA. */
 xr_status xr_fma_probe(int32_t iters, float *d_sink, int32_t sink_floats, int64_t *flop, xr_stream stream);
 
+/* Self-test of the bounded waits (the paper has no counterpart): one warp of the current device
+ * waits, with the wait the staged gather uses for its asynchronous copies, on an mbarrier
+ * that nothing completes, giving up after `cycles` SM clock cycles (1 .. 2e10); *timed_out
+ * (host) receives 1 when the wait gave up -- the expected result -- and 0 otherwise.  The
+ * device stays usable.  Synchronises the current device.
+ * Errors: XR_ERR_NULL, XR_ERR_SIZE, XR_ERR_CUDA. */
+xr_status xr_wait_bound_selftest(int64_t cycles, int32_t *timed_out);
+
 /* Text of a status code (static storage). */
 const char *xr_status_string(xr_status s);
 

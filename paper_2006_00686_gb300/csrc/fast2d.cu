@@ -651,13 +651,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
     return done != 0;
 }
 
-// true when the phase with this parity completed; false after kWaitCycles
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+// true when the phase with this parity completed; false after `limit` SM clock cycles
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit = kWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -1083,6 +1083,27 @@ static int gather_chunks(int64_t pairs, int groups, int blocks_per_sm, int n_vie
     for (int k = 0; k < 4; ++k)
         if (cost[k] <= 1.05 * best) return cand[k];
     return 1;
+}
+
+// The bounded wait of the staged gather on an mbarrier that nothing completes (a test of its
+// way out): one warp; out[0] = 1 when every lane gave up after `limit` cycles, 0 otherwise.
+__global__ void wait_selftest_kernel(long long limit, int *__restrict__ out)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+    const bool gave_up = __all_sync(0xffffffffu, !ok);
+    if (threadIdx.x == 0) out[0] = gave_up ? 1 : 0;
+}
+
+cudaError_t launch_wait_selftest(long long limit, int *d_out, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 32, 0, s>>>(limit, d_out);
+    return cudaGetLastError();
 }
 
 // The staged kernel takes more than 48 KB of dynamic shared memory: opt in once per device.

@@ -82,3 +82,18 @@ extern "C" xr_status xr_fma_probe(int32_t iters, float *d_sink, int32_t sink_flo
     return XR_OK;
 }
 
+extern "C" xr_status xr_wait_bound_selftest(int64_t cycles, int32_t *timed_out)
+{
+    if (!timed_out) return XR_ERR_NULL;
+    if (cycles < 1 || cycles > 20000000000ll) return XR_ERR_SIZE;
+    int *d = nullptr;
+    PROBE_CUDA(cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) e = xr::launch_wait_selftest((long long)cycles, d, nullptr);
+    int h = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return xr_fail_cuda(e);
+    *timed_out = h;
+    return XR_OK;
+}

@@ -198,6 +198,9 @@ cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int
 // (i, j) of the image at slice * slice_stride + j * row_stride + i).  err: the handle's device
 // error word.
 size_t gather_records_bytes(int batch, int nq, int64_t n_rays);
+// One warp waits on an mbarrier that nothing completes with the staged gather's bounded wait
+// (bound `limit` SM cycles); *d_out = 1 when the wait gave up.
+cudaError_t launch_wait_selftest(long long limit, int *d_out, cudaStream_t s);
 cudaError_t launch_gather_staged(const RayRec *rays, const void *grec, const GeoParams &g, const float *vt,
                                  const float *sino, int64_t n_rays, float *img, int batch, int nq, void *recs,
                                  cudaStream_t s, int *err, int64_t sb = -1, int64_t sr = 1,

@@ -85,6 +85,7 @@ SIGNATURES = {
     "xr_backproject_batched": (_I32, [ctypes.POINTER(_Problem), _I32, _VP]),
     "xr_tune": (_I32, [_VP, ctypes.c_char_p]),
     "xr_get_device_error": (_I32, [_VP, ctypes.POINTER(_I32)]),
+    "xr_wait_bound_selftest": (_I32, [ctypes.c_int64, ctypes.POINTER(_I32)]),
     "xr_project_attenuated": (_I32, [_VP, _VP, _VP, _VP, _I32, _VP]),
     "xr_backproject_attenuated": (_I32, [_VP, _VP, _VP, _VP, _I32, _VP]),
     "xr_status_string": (ctypes.c_char_p, [_I32]),
@@ -413,6 +414,14 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def wait_bound_selftest(cycles: int = 2_000_000) -> bool:
+    """True when the library's bounded wait on an mbarrier that nothing completes gave up
+    after `cycles` SM clock cycles (xr_wait_bound_selftest)."""
+    out = _I32(-1)
+    _check(lib().xr_wait_bound_selftest(int(cycles), ctypes.byref(out)), "xr_wait_bound_selftest")
+    return out.value == 1
 
 
 def read_bandwidth(n_bytes: int = 64 << 20, reps: int = 20, trials: int = 5) -> float:

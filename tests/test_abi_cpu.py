@@ -96,6 +96,10 @@ def test_null_arguments(X):
     assert L.xr_system_rows_fill(None, 0, 1, None, None, None, None) == 1
     assert L.xr_batch_project(None, None) == 1
     assert L.xr_batch_ray_setup(None, None) == 1
+    assert L.xr_wait_bound_selftest(1000, None) == 1
+    out = ctypes.c_int32(-1)
+    assert L.xr_wait_bound_selftest(0, ctypes.byref(out)) == L.xr_wait_bound_selftest(-5, ctypes.byref(out)) != 0
+    assert out.value == -1
     assert L.xr_batch_create(None, 1, 0, 0, ctypes.byref(h)) == 1
     L.xr_geometry_destroy(None)
     L.xr_batch_destroy(None)
