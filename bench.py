@@ -398,6 +398,31 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
                      "dev_out": [yb, zb],
                      "host_out": [torch.empty(yb.shape, pin_memory=True), torch.empty(zb.shape, pin_memory=True)]})
     e2e = parallel.max_over_ranks(_e2e(sets, args, flush), dev)
+    plain = None
+    if B > 1 and not atten:
+        # the plain form: the same step with one launch set per image (single-image path)
+        def plain_step(recs):
+            stream = torch.cuda.current_stream()
+            e = _events(4) if recs is not None else None
+            if e: e[0].record(stream)
+            P.ray_setup(stream)
+            if e: e[1].record(stream)
+            for b in range(B):
+                P.forward(x[b], out=y[b], stream=stream)
+            if e: e[2].record(stream)
+            for b in range(B):
+                P.adjoint(y[b], out=z[b], stream=stream)
+            if e: e[3].record(stream)
+            if recs is not None:
+                recs.append(e)
+
+        prec, _, _ = _timed_loop(plain_step, args, flush, world, local_rank)
+        pms = parallel.max_over_ranks(float(np.mean([a.elapsed_time(d) for a, b, c, d in prec])), dev)
+        plain = {"value": round(rays_step * world / (pms * 1e-3) / 1e9, 4), "ms_per_step": round(pms, 4),
+                 "kernel_ms": {"ray_setup": round(float(np.mean([a.elapsed_time(b) for a, b, c, d in prec])), 4),
+                               "forward": round(float(np.mean([b.elapsed_time(c) for a, b, c, d in prec])), 4),
+                               "adjoint": round(float(np.mean([c.elapsed_time(d) for a, b, c, d in prec])), 4)},
+                 "form": f"{B} single-image forward and adjoint launch sets per step"}
 
     peaks, peak_kind = _peaks()
     fwd, adj = float(np.mean(fwd_ms)), float(np.mean(adj_ms))
@@ -452,6 +477,9 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
            "clocks": clocks, "roofline": roof, "wall_s": round(wall, 3)}
     if use_graph:
         out["eager_ms_per_step"] = round(eager_ms, 4)
+    if plain is not None:
+        out["plain"] = plain
+        out["batched_over_plain"] = round(plain["ms_per_step"] / ms, 3)
     if extra:
         out["extra"] = extra
     if rank == 0 and not args.no_cpu_baseline:
