@@ -746,9 +746,18 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
         return XR_OK;
     }
     if (!use_tiled(g, batch) && !use_fast(g, batch) && use_dda(g)) {
-        for (int b = 0; b < batch; ++b)
-            XR_CUDA(launch_scatter3d(g->src, g->params, g->n_rays, ray_order(g, true), d_sino + (size_t)b * g->n_rays,
-                                     d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, g->d_err, s));
+        // 2D scans in the ray order: the slab walk with 32 neighbouring rays per warp in
+        // lockstep (its reductions fall on neighbouring words); 3D scans: the crossing-order walk
+        const bool lock = !kind_is3d(g->params.kind) && ray_order(g, true) <= 1;
+        for (int b = 0; b < batch; ++b) {
+            const float *sb = d_sino + (size_t)b * g->n_rays;
+            float *ib = d_img + (size_t)b * g->n_units;
+            if (lock)
+                XR_CUDA(launch_scatter2d_lock(g->d_src, g->n_rays, g->params.nx, g->params.ny, sb, ib, g->d_ws, s));
+            else
+                XR_CUDA(launch_scatter3d(g->src, g->params, g->n_rays, ray_order(g, true), sb, ib, g->d_ws,
+                                         g->tune.block, g->d_err, s));
+        }
         return XR_OK;
     }
     if (use_tiled(g, batch)) {

@@ -177,6 +177,9 @@ int batched_ctas_per_sm(int block, int adjoint);
 int batch2d_ctas_per_sm(int block);
 cudaError_t launch_batch2d_adjoint(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
                                    unsigned long long *counter, int grid_ctas, int block, cudaStream_t s);
+// The same walk for one problem described by P (a kernel parameter): warp w takes rays
+// 32w .. 32w + 31.  P.img and P.aux must be zeroed.
+cudaError_t launch_batch2d_adjoint_one(const BatchItem &P, cudaStream_t s);
 
 // Batched fast path for rays with at most two active axes (fast2d.cu).
 cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, float *acc0,
@@ -236,6 +239,11 @@ cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int
 // or-ed in), or NULL.
 cudaError_t launch_project3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
                              float *ws, float *sino, int block, int *err, cudaStream_t s);
+// The single-image adjoint of a 2D scan with the lockstep slab walk (batch2d.cu): zeroes `out`
+// and `accT` (the [nx][ny] copy), scatters, then adds accT (transposed) into out.  d_src: the
+// handle's device copy of its ray source.
+cudaError_t launch_scatter2d_lock(const RaySrc *d_src, int64_t n_rays, int nx, int ny, const float *sino, float *out,
+                                  float *accT, cudaStream_t s);
 // Orders 0 and 1: zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
 // Order 2: zeroes the z-fastest accumulator accT, scatters, then writes it transposed to out.
 cudaError_t launch_scatter3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order,
