@@ -480,6 +480,10 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
     if plain is not None:
         out["plain"] = plain
         out["batched_over_plain"] = round(plain["ms_per_step"] / ms, 3)
+    if "autograd_fwd_bwd_ms" in extra:
+        # the differentiable form against the plain forward + adjoint through the C ABI
+        extra["plain_fwd_adj_ms"] = round(fwd + adj, 3)
+        extra["autograd_over_plain"] = round((fwd + adj) / extra["autograd_fwd_bwd_ms"], 3)
     if extra:
         out["extra"] = extra
     if rank == 0 and not args.no_cpu_baseline:
