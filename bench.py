@@ -290,6 +290,7 @@ TRAFFIC = {
 }
 
 GRAPHED = ("par2d_64",)  # launch-bound steps replayed from a CUDA graph
+FUSED = ("par2d_64",)  # steps whose forward and adjoint run as one launch (xr_project_backproject)
 
 
 def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
@@ -331,22 +332,27 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
     atten = workload.endswith("_atten")
     mu = (0.02 + 0.05 * inputs.phantom(g, 4, 900, device=str(dev))).float().contiguous() if atten else None
 
-    def make_step(xb, yb, zb):
+    def make_step(xb, yb, zb, fused=False):
         def step(recs=None):
             stream = torch.cuda.current_stream()  # the capture stream inside graphed()
             e = _events(4) if recs is not None else None
             if e: e[0].record(stream)
             P.ray_setup(stream)
             if e: e[1].record(stream)
-            if atten:
+            if fused:
+                # forward and adjoint of its result in one launch; the adjoint phase is empty
+                P.forward_adjoint(xb, sino_out=yb, img_out=zb, stream=stream)
+                if e: e[2].record(stream)
+            elif atten:
                 P.forward_attenuated(xb, mu, out=yb, stream=stream)
             else:
                 P.forward(xb, out=yb, stream=stream)
-            if e: e[2].record(stream)
-            if atten:
-                P.adjoint_attenuated(yb, mu, out=zb, stream=stream)
-            else:
-                P.adjoint(yb, out=zb, stream=stream)
+            if not fused:
+                if e: e[2].record(stream)
+                if atten:
+                    P.adjoint_attenuated(yb, mu, out=zb, stream=stream)
+                else:
+                    P.adjoint(yb, out=zb, stream=stream)
             if e: e[3].record(stream)
             if recs is not None:
                 recs.append(e)
@@ -371,7 +377,8 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
                 recs.append(e)
         return replay
 
-    step = make_step(x, y, z)
+    use_fused = workload in FUSED and not atten
+    step = make_step(x, y, z, fused=use_fused)
     use_graph = workload in GRAPHED
 
     # per-phase kernel times from eager steps; the step time from the graph where used
@@ -387,13 +394,21 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
     ms = parallel.max_over_ranks(float(np.mean(step_ms)), dev)
     rays_step = g.n_rays * B
     value = rays_step * world / (ms * 1e-3) / 1e9
+    separate = None
+    if use_fused:
+        # the same step with the forward and the adjoint as separate calls
+        sep = make_step(x, y, z)
+        srecs, _, _ = _timed_loop(graphed(sep) if use_graph else sep, args, flush, world, local_rank)
+        sms = parallel.max_over_ranks(float(np.mean([r[0].elapsed_time(r[-1]) for r in srecs])), dev)
+        separate = {"value": round(rays_step * world / (sms * 1e-3) / 1e9, 4), "ms_per_step": round(sms, 4),
+                    "form": "ray setup, xr_project, xr_backproject" + (" (graph replay)" if use_graph else "")}
 
     # end to end through the C ABI with host buffers: pinned H2D of the images, the step,
     # D2H of the sinograms and the adjoint images, all inside the timed region
     x_h = x.cpu().pin_memory()
     sets = []
     for xb, yb, zb in ((x, y, z), (x.clone(), torch.empty_like(y), torch.empty_like(z))):
-        st = make_step(xb, yb, zb)
+        st = make_step(xb, yb, zb, fused=use_fused)
         sets.append({"step": graphed(st) if use_graph else st, "host_in": [x_h], "dev_in": [xb],
                      "dev_out": [yb, zb],
                      "host_out": [torch.empty(yb.shape, pin_memory=True), torch.empty(zb.shape, pin_memory=True)]})
@@ -437,7 +452,12 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
         method = "gather" if adj_mode == XR_ADJ_GATHER else "scatter"
     traffic, note = TRAFFIC.get((workload, dom, method), (None, None))
     n_int = _intersections(g, P)
-    roof = _roofline(n_int, 4.0 * (g.n_units + g.n_rays) * B, B, dom, dom_ms, peaks, peak_kind, traffic, note)
+    if use_fused:
+        # one launch walks every ray twice: the forward's and the adjoint's bytes
+        dom, dom_ms, method = "forward+adjoint (one launch)", fwd, "scatter"
+        roof = _roofline(2 * n_int, 4.0 * (g.n_units + g.n_rays) * B, B, dom, dom_ms, peaks, peak_kind, None, None)
+    else:
+        roof = _roofline(n_int, 4.0 * (g.n_units + g.n_rays) * B, B, dom, dom_ms, peaks, peak_kind, traffic, note)
 
     extra = {}
     if atten:
@@ -459,7 +479,9 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
                   "l2": "flushed between timed steps (256 MiB write)"}
         if use_graph:
             config["cuda_graph"] = "each step replayed from one captured graph"
-        launches = _launch_count(P, g, B)
+        launches = _launch_count(P, g, B, fused=use_fused)
+        if use_fused:
+            config["adjoint"] = "scatter, in the forward's launch (xr_project_backproject)"
         if workload == "par3d_256_tilt":
             extra = _autograd_and_sirt(P, x, y, args)
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -472,11 +494,16 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
                    "method": "pinned copies in and out on two more streams, two buffer sets, L2 flushed "
                              "per step, whole loop timed"},
            "gpu_launches": args.steps * launches,
-           "kernel_ms": {"ray_setup": round(float(np.mean(setup_ms)), 4), "forward": round(fwd, 4),
-                         "adjoint": round(adj, 4)},
+           "kernel_ms": ({"ray_setup": round(float(np.mean(setup_ms)), 4), "forward_adjoint": round(fwd, 4)}
+                         if use_fused else
+                         {"ray_setup": round(float(np.mean(setup_ms)), 4), "forward": round(fwd, 4),
+                          "adjoint": round(adj, 4)}),
            "clocks": clocks, "roofline": roof, "wall_s": round(wall, 3)}
     if use_graph:
         out["eager_ms_per_step"] = round(eager_ms, 4)
+    if separate is not None:
+        out["separate"] = separate
+        out["fused_over_separate"] = round(separate["ms_per_step"] / ms, 3)
     if plain is not None:
         out["plain"] = plain
         out["batched_over_plain"] = round(plain["ms_per_step"] / ms, 3)
@@ -493,8 +520,14 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
     return out
 
 
-def _launch_count(P, g, B):
+def _launch_count(P, g, B, fused=False):
     """Kernels of the repo launched per step on the single-image and column paths."""
+    # detector setup, ray setup (parallel and fan scans: a per-ray table), and for 2D scans
+    # reserved for 4 or more images the gather's per-ray constants
+    setup = 1 + (0 if g.kind in ("cone", "cone_arc", "helix", "helix_arc") else 1) + \
+        (1 if not g.is3d and P.reserved >= 4 else 0)
+    if fused:
+        return setup + 1  # the fused forward + adjoint (its zero fill is a memset)
     if P.column_batch:
         # detector setup, ray setup, the column problem's ray records and gather constants,
         # then per image: the slice planes, the forward, the gather records, the staged gather
@@ -504,10 +537,9 @@ def _launch_count(P, g, B):
         # trace forward, the trace adjoint and the fold of the accumulator (its zero fill is a
         # memset)
         return 1 + 4 * B
-    # detector setup, ray setup (2D: and the gather's per-ray constants), then per image:
-    # the layout copy, the forward walk, the scatter walk and the fold of the accumulator
-    # (zero fills are memsets)
-    return (2 if g.is3d else 3) + 4 * B
+    # then per image: the layout copy, the forward walk, the scatter walk and the fold of the
+    # accumulator (zero fills are memsets)
+    return setup + 4 * B
 
 
 def run_split(args, rank, world, local_rank):

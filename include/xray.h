@@ -250,6 +250,20 @@ xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img
 xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float *d_img,
                                 int32_t batch, int32_t method, xr_stream stream);
 
+/* Forward projection and the adjoint of its result in one launch (the operators of
+ * xr_project and xr_backproject, composed; the paper has no counterpart): sino = A img and
+ * out = A^T sino, i.e. out = A^T A img.  One thread per ray sums its units (eq.
+ * Xray_transform_image), writes sino[b][r], then walks the same units again adding
+ * l_I(r) * sino[b][r] into out (atomics, so the order of the additions, and the last bits of
+ * out, may differ from run to run).  Meant for problems too small to fill the GPU, whose
+ * separate calls are bound by their launches; any scan and batch.  d_img: [batch][n_units],
+ * d_sino: [batch][n_rays] (overwritten), d_out: [batch][n_units] (overwritten), float32,
+ * device, 16-byte aligned, none overlapping another.
+ * Errors: XR_ERR_NULL, XR_ERR_BATCH, XR_ERR_ALIGN, XR_ERR_ARG (overlapping buffers),
+ * XR_ERR_SIZE, XR_ERR_CUDA. */
+xr_status xr_project_backproject(const xr_geometry *g, const float *d_img, float *d_sino, float *d_out,
+                                 int32_t batch, xr_stream stream);
+
 /* Attenuated transform: the generalized Radon transform of eq. generalizedRadontransform
  * with the exponential attenuation weight of the SPECT case (Section 1),
  * Phi(theta, x, t) = exp(-int_t^inf mu(x + s theta) ds), for an attenuation image d_mu

@@ -392,7 +392,33 @@ __global__ void __launch_bounds__(256) add_transposed_items_kernel(const BatchIt
 constexpr int kFwdAhead = XR_FWD3D_AHEAD;
 constexpr int kAdjAhead = XR_ADJ3D_AHEAD;
 
+// Forward and the adjoint of its result in one pass per (ray, image): the single-image walks
+// on the caller's layout (no copies), y written to sino, then y * l spread into out (zeroed
+// by the caller).  blockIdx.y: the image.
+__global__ void __launch_bounds__(256) fwd_adj_kernel(RaySrc rays, int n_rays, int nx, int ny, int nz,
+                                                      const float *__restrict__ img, float *__restrict__ sino,
+                                                      float *__restrict__ out, int64_t n_units, int *err)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // no wrap near 2^31
+    if (t >= n_rays) return;
+    const int r = (int)t;
+    const int64_t b = blockIdx.y;
+    const RayRec rr = rays[r];
+    const float v = fwd_ray<kFwdAhead>(rr, nx, ny, nz, img + b * n_units, nullptr, err);
+    sino[b * n_rays + r] = v;
+    if (v != 0.f) scatter_ray<kAdjAhead>(rr, v, nx, ny, nz, out + b * n_units, nullptr, err);
+}
+
 }  // namespace
+
+cudaError_t launch_fwd_adj(const RaySrc &rays, const GeoParams &g, int64_t n_rays, const float *img, float *sino,
+                           float *out, int batch, int block, int *err, cudaStream_t s)
+{
+    const int64_t n_units = (int64_t)g.nx * g.ny * g.nz;
+    const dim3 grid((unsigned)((n_rays + block - 1) / block), (unsigned)batch);
+    fwd_adj_kernel<<<grid, block, 0, s>>>(rays, (int)n_rays, g.nx, g.ny, g.nz, img, sino, out, n_units, err);
+    return cudaGetLastError();
+}
 
 int batched_ctas_per_sm(int block, int adjoint)
 {

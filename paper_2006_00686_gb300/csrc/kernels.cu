@@ -103,6 +103,40 @@ __global__ void __launch_bounds__(256) scatter_kernel(RaySrc rays, int64_t n_ray
     walk_ray(rays[r], grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, vis);
 }
 
+// Forward, then the adjoint of the forward's result, in one pass per ray: the thread sums its
+// ray (y = A x, written to sino) and walks the same units again spreading y * l into out
+// (zeroed by the caller): out = A^T A x.  The two walks are the kernels' above.
+template <int BC>
+__global__ void __launch_bounds__(256) project_backproject_kernel(RaySrc rays, int64_t n_rays, Grid grid,
+                                                                  const float *__restrict__ img, int64_t img_bs,
+                                                                  float *__restrict__ sino, int64_t sino_bs,
+                                                                  float *__restrict__ out, int64_t out_bs, int batch)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int b0 = blockIdx.y * BC;
+    const RayRec rr = rays[r];
+    FwdVisitor<BC> f;
+    f.img = img + b0 * img_bs;
+    f.bs = img_bs;
+    f.nb = min(BC, batch - b0);
+#pragma unroll
+    for (int b = 0; b < BC; ++b) f.acc[b] = 0.f;
+    walk_ray(rr, grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, f);
+    ScatterVisitor<BC> sv;
+    sv.img = out + b0 * out_bs;
+    sv.bs = out_bs;
+    sv.nb = f.nb;
+    bool any = false;
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+        sv.g[b] = b < f.nb ? f.acc[b] : 0.f;
+        if (b < f.nb) sino[(b0 + b) * sino_bs + r] = f.acc[b];
+        any |= sv.g[b] != 0.f;
+    }
+    if (any) walk_ray(rr, grid.nx, grid.ny, grid.nz, grid.sx, grid.sy, grid.sz, grid.three, sv);
+}
+
 template <int BC>
 static cudaError_t launch_project_t(const RaySrc &rays, int64_t n_rays, const Grid &grid,
                                     const float *img, int64_t img_bs, float *sino, int64_t sino_bs,
@@ -133,6 +167,30 @@ cudaError_t launch_project(const RaySrc &rays, int64_t n_rays, const Grid &grid,
     case 4: return launch_project_t<4>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
     case 2: return launch_project_t<2>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
     default: return launch_project_t<1>(rays, n_rays, grid, img, img_bs, sino, sino_bs, batch, block, s);
+    }
+}
+
+template <int BC>
+static cudaError_t launch_project_backproject_t(const RaySrc &rays, int64_t n_rays, const Grid &grid,
+                                                const float *img, int64_t img_bs, float *sino, int64_t sino_bs,
+                                                float *out, int64_t out_bs, int batch, int block, cudaStream_t s)
+{
+    const dim3 g((unsigned)((n_rays + block - 1) / block), (unsigned)((batch + BC - 1) / BC));
+    project_backproject_kernel<BC><<<g, block, 0, s>>>(rays, n_rays, grid, img, img_bs, sino, sino_bs, out, out_bs,
+                                                       batch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_backproject(const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *img,
+                                       int64_t img_bs, float *sino, int64_t sino_bs, float *out, int64_t out_bs,
+                                       int batch, int chunk, int block, cudaStream_t s)
+{
+    switch (chunk) {
+    case 16: return launch_project_backproject_t<16>(rays, n_rays, grid, img, img_bs, sino, sino_bs, out, out_bs, batch, block, s);
+    case 8: return launch_project_backproject_t<8>(rays, n_rays, grid, img, img_bs, sino, sino_bs, out, out_bs, batch, block, s);
+    case 4: return launch_project_backproject_t<4>(rays, n_rays, grid, img, img_bs, sino, sino_bs, out, out_bs, batch, block, s);
+    case 2: return launch_project_backproject_t<2>(rays, n_rays, grid, img, img_bs, sino, sino_bs, out, out_bs, batch, block, s);
+    default: return launch_project_backproject_t<1>(rays, n_rays, grid, img, img_bs, sino, sino_bs, out, out_bs, batch, block, s);
     }
 }
 

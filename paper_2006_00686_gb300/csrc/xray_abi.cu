@@ -790,6 +790,31 @@ xr_status xr_backproject(const xr_geometry *g, const float *d_sino, float *d_img
     return xr_backproject_method(g, d_sino, d_img, batch, XR_ADJ_AUTO, stream);
 }
 
+xr_status xr_project_backproject(const xr_geometry *g, const float *d_img, float *d_sino, float *d_out,
+                                 int32_t batch, xr_stream stream)
+{
+    if (!g || !d_img || !d_sino || !d_out) return XR_ERR_NULL;
+    if (batch < 1) return XR_ERR_BATCH;
+    if (!aligned16(d_img) || !aligned16(d_sino) || !aligned16(d_out)) return XR_ERR_ALIGN;
+    // out is written while other threads still read img and sino: the three must not overlap
+    const uintptr_t i0 = (uintptr_t)d_img, i1 = i0 + (uintptr_t)g->n_units * batch * sizeof(float);
+    const uintptr_t s0 = (uintptr_t)d_sino, s1 = s0 + (uintptr_t)g->n_rays * batch * sizeof(float);
+    const uintptr_t o0 = (uintptr_t)d_out, o1 = o0 + (uintptr_t)g->n_units * batch * sizeof(float);
+    if ((o0 < i1 && i0 < o1) || (o0 < s1 && s0 < o1) || (i0 < s1 && s0 < i1)) return XR_ERR_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    XR_CUDA(cudaMemsetAsync(d_out, 0, (size_t)g->n_units * batch * sizeof(float), s));
+    if (g->n_rays < ((int64_t)1 << 31) && batch <= 65535) {
+        // the single-image walks (units generated ahead of their loads and reductions)
+        XR_CUDA(launch_fwd_adj(g->src, g->params, g->n_rays, d_img, d_sino, d_out, batch, 128, g->d_err, s));
+        return XR_OK;
+    }
+    const int chunk = pick_chunk(g, batch);
+    if ((batch + chunk - 1) / chunk > 65535) return XR_ERR_SIZE;
+    XR_CUDA(launch_project_backproject(g->src, g->n_rays, make_grid(g), d_img, g->n_units, d_sino, g->n_rays, d_out,
+                                       g->n_units, batch, chunk, g->tune.block, s));
+    return XR_OK;
+}
+
 // Attenuated transform of a 2D batch on the interleaved layouts: the batched fast path's
 // workspace, with room after the two image copies for the map's two padded copies.
 static bool use_atten_planes(const xr_geometry *g, int batch)

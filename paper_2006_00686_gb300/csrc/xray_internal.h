@@ -110,6 +110,12 @@ cudaError_t launch_project(const RaySrc &rays, int64_t n_rays, const Grid &grid,
                            int64_t img_bs, float *sino, int64_t sino_bs, int batch, int chunk,
                            int block, cudaStream_t s);
 
+// Both operators in one pass per ray: sino = A img, then out += A^T sino (out zeroed by the
+// caller), `chunk` images per thread.
+cudaError_t launch_project_backproject(const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *img,
+                                       int64_t img_bs, float *sino, int64_t sino_bs, float *out, int64_t out_bs,
+                                       int batch, int chunk, int block, cudaStream_t s);
+
 cudaError_t launch_backproject_scatter(const RaySrc &rays, int64_t n_rays, const Grid &grid,
                                        const float *sino, int64_t sino_bs, float *img,
                                        int64_t img_bs, int batch, int chunk, int block,
@@ -244,6 +250,11 @@ cudaError_t launch_project3d(const RaySrc &rays, const GeoParams &g, int64_t n_r
 // handle's device copy of its ray source.
 cudaError_t launch_scatter2d_lock(const RaySrc *d_src, int64_t n_rays, int nx, int ny, const float *sino, float *out,
                                   float *accT, cudaStream_t s);
+// Forward, then the adjoint of its result, per (ray, image) with the single-image walks on the
+// caller's layout: sino = A img, out += A^T sino (out zeroed by the caller).  n_rays < 2^31,
+// batch <= 65535.
+cudaError_t launch_fwd_adj(const RaySrc &rays, const GeoParams &g, int64_t n_rays, const float *img, float *sino,
+                           float *out, int batch, int block, int *err, cudaStream_t s);
 // Orders 0 and 1: zeroes `out` and `accT`, scatters, then adds accT (transposed) into out.
 // Order 2: zeroes the z-fastest accumulator accT, scatters, then writes it transposed to out.
 cudaError_t launch_scatter3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order,

@@ -70,6 +70,7 @@ SIGNATURES = {
     "xr_project": (_I32, [_VP, _VP, _VP, _I32, _VP]),
     "xr_backproject": (_I32, [_VP, _VP, _VP, _I32, _VP]),
     "xr_backproject_method": (_I32, [_VP, _VP, _VP, _I32, _I32, _VP]),
+    "xr_project_backproject": (_I32, [_VP, _VP, _VP, _VP, _I32, _VP]),
     "xr_ray_units": (_I32, [_VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP]),
     "xr_system_rows_count": (_I32, [_VP, _I64, _I32, _VP, _VP]),
     "xr_system_rows_fill": (_I32, [_VP, _I64, _I32, _VP, _VP, _VP, _VP]),
@@ -131,6 +132,14 @@ def _ptr(t: torch.Tensor):
 def _need_cuda(t: torch.Tensor, name: str):
     if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
         raise XRayError(f"{name} must be a contiguous float32 CUDA tensor")
+
+
+def _need_out(t: torch.Tensor, shape: tuple, name: str):
+    """An output buffer: a contiguous float32 CUDA tensor holding exactly prod(shape) floats
+    (the kernels write that many)."""
+    _need_cuda(t, name)
+    if t.numel() != int(np.prod(shape)):
+        raise XRayError(f"{name} has {t.numel()} elements, expected {int(np.prod(shape))} (shape {tuple(shape)})")
 
 
 def _desc(geom: Geometry):
@@ -248,7 +257,7 @@ class Projector:
         shape = self.geom.sino_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=img.device, dtype=torch.float32)
-        _need_cuda(out, "out")
+        _need_out(out, shape, "out")
         _check(lib().xr_project(self._h, _ptr(img), _ptr(out), max(b, 1), _stream(stream)), "xr_project")
         return out
 
@@ -260,10 +269,26 @@ class Projector:
         shape = self.geom.image_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=sino.device, dtype=torch.float32)
-        _need_cuda(out, "out")
+        _need_out(out, shape, "out")
         _check(lib().xr_backproject_method(self._h, _ptr(sino), _ptr(out), max(b, 1), int(method),
                                            _stream(stream)), "xr_backproject")
         return out
+
+    def forward_adjoint(self, img: torch.Tensor, sino_out: torch.Tensor | None = None,
+                        img_out: torch.Tensor | None = None, stream=None):
+        """Both operators in one launch (xr_project_backproject): returns (sino, img_out) with
+        sino = A img and img_out = A^T sino, for problems too small to fill the GPU."""
+        _need_cuda(img, "img")
+        b = self._batch_of(img, self.geom.image_shape(), "img")
+        if sino_out is None:
+            sino_out = torch.empty(self.geom.sino_shape(b if b else None), device=img.device, dtype=torch.float32)
+        if img_out is None:
+            img_out = torch.empty(self.geom.image_shape(b if b else None), device=img.device, dtype=torch.float32)
+        _need_out(sino_out, self.geom.sino_shape(b if b else None), "sino_out")
+        _need_out(img_out, self.geom.image_shape(b if b else None), "img_out")
+        _check(lib().xr_project_backproject(self._h, _ptr(img), _ptr(sino_out), _ptr(img_out), max(b, 1),
+                                            _stream(stream)), "xr_project_backproject")
+        return sino_out, img_out
 
     __call__ = forward
 
@@ -280,7 +305,7 @@ class Projector:
         shape = self.geom.sino_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=img.device, dtype=torch.float32)
-        _need_cuda(out, "out")
+        _need_out(out, shape, "out")
         _check(lib().xr_project_attenuated(self._h, _ptr(mu), _ptr(img), _ptr(out), max(b, 1), _stream(stream)),
                "xr_project_attenuated")
         return out
@@ -297,7 +322,7 @@ class Projector:
         shape = self.geom.image_shape(b if b else None)
         if out is None:
             out = torch.empty(shape, device=sino.device, dtype=torch.float32)
-        _need_cuda(out, "out")
+        _need_out(out, shape, "out")
         _check(lib().xr_backproject_attenuated(self._h, _ptr(mu), _ptr(sino), _ptr(out), max(b, 1),
                                                _stream(stream)), "xr_backproject_attenuated")
         return out

@@ -97,6 +97,7 @@ def test_null_arguments(X):
     assert L.xr_batch_project(None, None) == 1
     assert L.xr_batch_ray_setup(None, None) == 1
     assert L.xr_wait_bound_selftest(1000, None) == 1
+    assert L.xr_project_backproject(None, None, None, None, 1, None) == 1
     out = ctypes.c_int32(-1)
     assert L.xr_wait_bound_selftest(0, ctypes.byref(out)) == L.xr_wait_bound_selftest(-5, ctypes.byref(out)) != 0
     assert out.value == -1

@@ -1,0 +1,71 @@
+"""Forward and adjoint in one launch (xr_project_backproject): the sinogram against the oracle's
+forward, the image against the oracle's adjoint of that sinogram; and the binding's checks of
+output buffers."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2006_00686_gb300 import inputs
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    from paper_2006_00686_gb300 import xray
+    return xray
+
+
+GEOMS = {
+    "par2d_64": inputs.par2d_64,
+    "fan2d_96": lambda: H.fan2d_small(96, 60),
+    "cone_32": lambda: H.cone_small(32, 12),
+    "helix_32": lambda: H.helix_small(32, 16, 12, 2),
+}
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+@pytest.mark.parametrize("batch", [1, 3])
+def test_forward_adjoint_in_one_launch(X, name, batch):
+    g = GEOMS[name]()
+    f = torch.stack([inputs.phantom(g, 6, 20 + b) for b in range(batch)])
+    f = f[0] if batch == 1 else f
+    P = X.Projector(g)
+    y, z = P.forward_adjoint(f.cuda())
+    f64 = f.numpy().astype(np.float64).reshape(batch, -1)
+    yh = y.cpu().numpy().reshape(batch, -1)
+    zh = z.cpu().numpy().reshape(batch, -1)
+    y_ref = O.forward(g, f64).reshape(batch, -1)
+    scale = O.forward(g, np.abs(f64)).reshape(batch, -1)
+    z_ref = np.asarray(O.adjoint(g, yh.astype(np.float64))).reshape(batch, -1)
+    for b in range(batch):
+        H.check_rays(g, yh[b], y_ref[b], scale[b], float(np.abs(f64[b]).max()), f"{name}[{b}] fused forward")
+        H.check_adjoint(zh[b], z_ref[b], f"{name}[{b}] fused adjoint")
+    # the separate calls give the same sinogram and, up to the order of additions, the image
+    y2 = P.forward(f.cuda())
+    z2 = P.adjoint(y2)
+    assert float((y2 - y).abs().max()) <= 1e-5 * float(y.abs().max())
+    assert float((z2 - z).abs().max()) <= 1e-4 * float(z.abs().max())
+    P.close()
+
+
+def test_output_buffers_are_checked(X):
+    g = inputs.par2d_64()
+    P = X.Projector(g)
+    x = torch.ones(g.image_shape(), device="cuda")
+    with pytest.raises(X.XRayError):
+        P.forward(x, out=torch.empty(g.n_rays - 1, device="cuda"))
+    with pytest.raises(X.XRayError):
+        P.adjoint(torch.ones(g.sino_shape(), device="cuda"), out=torch.empty(10, device="cuda"))
+    with pytest.raises(X.XRayError):
+        P.forward_adjoint(x, img_out=torch.empty(g.n_units + 4, device="cuda"))
+    # overlapping buffers are refused by the library (XR_ERR_ARG)
+    buf = torch.empty(g.n_units + g.n_rays, device="cuda")
+    with pytest.raises(X.XRayError):
+        P.forward_adjoint(x, sino_out=buf[:g.n_rays], img_out=x)
+    P.close()
