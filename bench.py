@@ -522,16 +522,16 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
 
 def _launch_count(P, g, B, fused=False):
     """Kernels of the repo launched per step on the single-image and column paths."""
-    # detector setup, ray setup (parallel and fan scans: a per-ray table), and for 2D scans
+    # detector setup, ray setup (2D scans and ray lists: a per-ray table), and for 2D scans
     # reserved for 4 or more images the gather's per-ray constants
-    setup = 1 + (0 if g.kind in ("cone", "cone_arc", "helix", "helix_arc") else 1) + \
+    setup = 1 + (0 if g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc") else 1) + \
         (1 if not g.is3d and P.reserved >= 4 else 0)
     if fused:
         return setup + 1  # the fused forward + adjoint (its zero fill is a memset)
     if P.column_batch:
-        # detector setup, ray setup, the column problem's ray records and gather constants,
-        # then per image: the slice planes, the forward, the gather records, the staged gather
-        return 4 + 4 * B
+        # detector setup, the column problem's ray records and gather constants, then per
+        # image: the slice planes, the forward, the gather records, the staged gather
+        return 3 + 4 * B
     if P.trace_walk:
         # detector setup (no per-ray table), then per image: the padded z-fastest copy, the
         # trace forward, the trace adjoint and the fold of the accumulator (its zero fill is a

@@ -95,8 +95,8 @@ typedef struct xr_geometry xr_geometry;
 typedef struct {
     int64_t n_rays;        /* n_views * n_rows * n_cols */
     int64_t n_units;       /* nx * ny * nz */
-    int64_t table_bytes;   /* device bytes held by the handle (tables and workspace); cone and
-                              helical scans hold no per-ray table */
+    int64_t table_bytes;   /* device bytes held by the handle (tables and workspace); 3D parallel,
+                              cone and helical scans hold no per-ray table */
     int32_t is3d;
     int32_t device;        /* CUDA device the handle's tables live on */
     int32_t column_batch;  /* 1: a 3D parallel scan whose views all have phi_1 = 0 (or all pi):
@@ -165,7 +165,8 @@ enum { XR_ORDER_AUTO = 0, XR_ORDER_VIEW = 1, XR_ORDER_ROW = 2, XR_ORDER_COLUMN =
  * batch of single-tilt-axis scans.  RAY: one thread per ray on the caller's layout. */
 enum { XR_PATH_AUTO = 0, XR_PATH_TILED = 1, XR_PATH_INTERLEAVED = 2, XR_PATH_RAY = 3 };
 
-/* Validate `desc`, allocate the handle and its ray table on the current CUDA device and run
+/* Validate `desc`, allocate the handle and its tables (a per-ray table for 2D scans and ray
+ * lists; 3D scans rebuild each ray's record in the kernels) on the current CUDA device and run
  * the ray-setup kernel once (ray parameters from eq. 2Dparalleltofan(_2),
  * equiangular/equispaced_cone_beam, Helical_cone_beam_*, in double precision), then
  * synchronise that device.  On error *out is set to NULL.
@@ -176,8 +177,8 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out);
 void xr_geometry_destroy(xr_geometry *g);
 
 /* Re-run the per-geometry ray setup on `stream`: the detector-sample kernel (the
- * transcendental part of the transformation formulas) and the per-ray kernel (rebuilds the
- * ray table in place). */
+ * transcendental part of the transformation formulas) and, for handles with a ray table, the
+ * per-ray kernel (rebuilds the table in place). */
 xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
 
 /* Reserve the handle's workspace for batches of up to max_batch images (allocates on the

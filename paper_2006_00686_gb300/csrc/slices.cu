@@ -19,13 +19,12 @@
 #include <cmath>
 #include <vector>
 
-#include "xray_internal.h"
+#include "xray_rays.cuh"
 
 namespace xr {
 
 // 2D ray r2 = the 3D ray (r2, column c_rep) with (w, f, o) of z moved to the y slots.
-__global__ void slice_rays_kernel(const RayRec *__restrict__ rays3, int64_t n2, int n_cols, int c_rep,
-                                  RayRec *__restrict__ rays2)
+__global__ void slice_rays_kernel(RaySrc rays3, int64_t n2, int n_cols, int c_rep, RayRec *__restrict__ rays2)
 {
     const int64_t r2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r2 >= n2) return;
@@ -143,7 +142,7 @@ bool slice_plan(const xr_geometry_desc *d, SlicePlan *sp)
     return sp->ok;
 }
 
-cudaError_t launch_slice_rays(const RayRec *rays3, int64_t n2, int n_cols, int c_rep, RayRec *rays2, cudaStream_t s)
+cudaError_t launch_slice_rays(const RaySrc &rays3, int64_t n2, int n_cols, int c_rep, RayRec *rays2, cudaStream_t s)
 {
     slice_rays_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(rays3, n2, n_cols, c_rep, rays2);
     return cudaGetLastError();

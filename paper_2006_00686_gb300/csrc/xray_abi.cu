@@ -289,7 +289,7 @@ static bool trace_tables(const GeoParams &p, std::vector<float4> &cols, std::vec
 static cudaError_t slice_setup(xr_geometry *g, cudaStream_t s)
 {
     if (!g->slices.ok) return cudaSuccess;
-    cudaError_t e = launch_slice_rays(g->d_rays, slice_n2(g), g->params.n_cols, g->slices.c_rep, g->d_rays2, s);
+    cudaError_t e = launch_slice_rays(g->src, slice_n2(g), g->params.n_cols, g->slices.c_rep, g->d_rays2, s);
     if (e == cudaSuccess) e = launch_gather_prep(g->d_rays2, slice_n2(g), g->d_grec2, s);
     return e;
 }
@@ -361,9 +361,11 @@ xr_status xr_geometry_create(const xr_geometry_desc *desc, xr_geometry **out)
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views, (size_t)p.n_views * sizeof(ViewRec));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views_df, (size_t)p.n_views * sizeof(ViewDF));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_det, n_det * sizeof(DetRec));
-    // cone and helical scans keep no ray table: their kernels rebuild each record from the
-    // per-view and per-detector tables (RaySrc)
-    if (e == cudaSuccess && !kind_cone(p.kind)) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
+    // 3D parallel, cone and helical scans keep no ray table: their kernels rebuild each record
+    // from the per-view and per-detector tables (RaySrc); 2D scans and ray lists keep one (the
+    // 2D batched kernels and the ray lists' per-ray parameters read it)
+    const bool table = !kind_cone(p.kind) && p.kind != XR_PAR3D;
+    if (e == cudaSuccess && table) e = cudaMalloc(&g->d_rays, (size_t)g->n_rays * sizeof(RayRec));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_src, sizeof(RaySrc));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(int));

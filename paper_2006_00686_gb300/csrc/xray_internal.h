@@ -228,7 +228,7 @@ struct SlicePlan {
     GeoParams g2{};
 };
 bool slice_plan(const xr_geometry_desc *d, SlicePlan *sp);
-cudaError_t launch_slice_rays(const RayRec *rays3, int64_t n2, int n_cols, int c_rep, RayRec *rays2, cudaStream_t s);
+cudaError_t launch_slice_rays(const RaySrc &rays3, int64_t n2, int n_cols, int c_rep, RayRec *rays2, cudaStream_t s);
 cudaError_t launch_slice_planes(const float *vol, int nx, int ny, int nz, const int *slice_of, int n_img, float *il0,
                                 float *il1, cudaStream_t s);
 // Tiled forward / adjoint for 2D scans and batches (tile2d.cu); in: user-layout input,
