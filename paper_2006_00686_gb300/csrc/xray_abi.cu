@@ -953,6 +953,8 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
     if (tile == 0) tile = 256;
     if (block == 0) block = 256;
     if (tile < 32 || tile > 65536 || (tile & 31) || block < 64 || block > 256 || (block & 31)) return XR_ERR_ARG;
+    int dev = 0;
+    XR_CUDA(cudaGetDevice(&dev));
     BatchItem *items = (BatchItem *)malloc(sizeof(BatchItem) * (size_t)n);
     if (!items) return XR_ERR_ALLOC;
     int64_t tiles = 0, aux_units = 0;
@@ -961,6 +963,10 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         if (!g || !probs[i].img || !probs[i].sino) {
             free(items);
             return XR_ERR_NULL;
+        }
+        if (g->device != dev) {  // the plan's launches run on the current device
+            free(items);
+            return XR_ERR_ARG;
         }
         if (!aligned16(probs[i].img) || !aligned16(probs[i].sino)) {
             free(items);

@@ -234,10 +234,19 @@ class Projector:
         _check(lib().xr_ray_setup(self._h, _stream(stream)), "xr_ray_setup")
 
     # -- operators ------------------------------------------------------------------------
+    def _here(self, *named):
+        """Every (tensor, name) pair lives on the projector's device (kernels run there)."""
+        for t, name in named:
+            if t.device != self.device:
+                raise XRayError(f"{name} is on {t.device}, the projector on {self.device}")
+
     def _batch_of(self, t: torch.Tensor, unit_shape: tuple, name: str) -> int:
+        """0 for one unbatched image or sinogram, else the batch size (an empty batch raises)."""
         if tuple(t.shape) == unit_shape:
             return 0
         if t.dim() == len(unit_shape) + 1 and tuple(t.shape[1:]) == unit_shape:
+            if t.shape[0] < 1:
+                raise XRayError(f"{name} is an empty batch")
             return int(t.shape[0])
         raise XRayError(f"{name} has shape {tuple(t.shape)}, expected {unit_shape} or (B,)+{unit_shape}")
 
@@ -258,6 +267,7 @@ class Projector:
         if out is None:
             out = torch.empty(shape, device=img.device, dtype=torch.float32)
         _need_out(out, shape, "out")
+        self._here((img, "img"), (out, "out"))
         _check(lib().xr_project(self._h, _ptr(img), _ptr(out), max(b, 1), _stream(stream)), "xr_project")
         return out
 
@@ -270,6 +280,7 @@ class Projector:
         if out is None:
             out = torch.empty(shape, device=sino.device, dtype=torch.float32)
         _need_out(out, shape, "out")
+        self._here((sino, "sino"), (out, "out"))
         _check(lib().xr_backproject_method(self._h, _ptr(sino), _ptr(out), max(b, 1), int(method),
                                            _stream(stream)), "xr_backproject")
         return out
@@ -286,6 +297,7 @@ class Projector:
             img_out = torch.empty(self.geom.image_shape(b if b else None), device=img.device, dtype=torch.float32)
         _need_out(sino_out, self.geom.sino_shape(b if b else None), "sino_out")
         _need_out(img_out, self.geom.image_shape(b if b else None), "img_out")
+        self._here((img, "img"), (sino_out, "sino_out"), (img_out, "img_out"))
         _check(lib().xr_project_backproject(self._h, _ptr(img), _ptr(sino_out), _ptr(img_out), max(b, 1),
                                             _stream(stream)), "xr_project_backproject")
         return sino_out, img_out
@@ -306,6 +318,7 @@ class Projector:
         if out is None:
             out = torch.empty(shape, device=img.device, dtype=torch.float32)
         _need_out(out, shape, "out")
+        self._here((img, "img"), (mu, "mu"), (out, "out"))
         _check(lib().xr_project_attenuated(self._h, _ptr(mu), _ptr(img), _ptr(out), max(b, 1), _stream(stream)),
                "xr_project_attenuated")
         return out
@@ -323,6 +336,7 @@ class Projector:
         if out is None:
             out = torch.empty(shape, device=sino.device, dtype=torch.float32)
         _need_out(out, shape, "out")
+        self._here((sino, "sino"), (mu, "mu"), (out, "out"))
         _check(lib().xr_backproject_attenuated(self._h, _ptr(mu), _ptr(sino), _ptr(out), max(b, 1),
                                                _stream(stream)), "xr_backproject_attenuated")
         return out
@@ -413,6 +427,7 @@ class BatchPlan:
             _need_cuda(y, "sino")
             if x.numel() != p.n_units or y.numel() != p.n_rays:
                 raise XRayError(f"problem {q}: buffer sizes do not match its geometry")
+            p._here((x, f"problem {q} img"), (y, f"problem {q} sino"))
             arr[q] = _Problem(p.handle.value, x.data_ptr(), y.data_ptr())
         self._keep = (list(projectors), list(images), list(sinos))
         h = ctypes.c_void_p()
