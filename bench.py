@@ -53,19 +53,23 @@ def _config(extra=None):
 # ----------------------------------------------------------------------------------------
 
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # csv lines, each led by the sample's own timestamp
+        self.window = None  # (start, end) wall-clock times of the timed region
+
+    def mark(self, start: float, end: float):
+        self.window = (start, end)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -77,6 +81,15 @@ class ClockSampler:
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
 
+    @staticmethod
+    def _when(ln: str) -> float:
+        """Wall-clock time of a sample (nvidia-smi's 'YYYY/MM/DD HH:MM:SS.mmm'), -inf if unreadable."""
+        import datetime
+        try:
+            return datetime.datetime.strptime(ln.split(",")[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return float("-inf")
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -86,24 +99,37 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        """Clocks of the samples taken during the timed region; a region shorter than the
+        sampling interval takes the samples of the warm-up steps before it and of the timed
+        steps (the same load), and says so."""
+        lines = list(self.lines)
+        window = "timed steps"
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [ln for ln in lines if t0 - 0.01 <= self._when(ln) <= t1 + 0.01]
+            if inside:
+                lines = inside
+            else:
+                lines = [ln for ln in lines if self._when(ln) <= t1 + 0.01]
+                window = "warm-up and timed steps (timed region shorter than the sampling interval)"
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             p = [x.strip() for x in ln.split(",")]
-            if len(p) < 9:
+            if len(p) < 10:
                 continue
             try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
+                sm.append(float(p[2]))
+                mx.append(float(p[3]))
             except ValueError:
                 continue
-            for name, val in zip(names, p[5:9]):
+            for name, val in zip(names, p[6:10]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clocks not sampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": window}
 
 
 # ----------------------------------------------------------------------------------------
@@ -154,20 +180,21 @@ def _timed_loop(step, args, flush, world, local_rank):
     """W untimed steps, then K timed steps (L2 flushed before each, outside its events);
     returns per-step lists of event pairs per phase, the clock summary and the wall time."""
     import torch
-    for _ in range(args.warmup):
-        step(None)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     recs = []
-    with ClockSampler(local_rank) as clk:
-        t0 = time.perf_counter()
+    with ClockSampler(local_rank) as clk:  # sampling from the warm-up on
+        for _ in range(args.warmup):
+            step(None)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0, w0 = time.perf_counter(), time.time()
         for _ in range(args.steps):
             flush.fill_(1.0)
             step(recs)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        clk.mark(w0, time.time())
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
