@@ -318,6 +318,8 @@ TRAFFIC = {
                                                         "quad-plane forward, full size)"),
     ("cone_512", "adjoint", "scatter"): (80.50e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
     ("cone_512", "forward", "scatter"): (24.06e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
+    ("helix_512x256", "forward", "scatter"): (1.256e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
+    ("helix_512x256", "adjoint", "scatter"): (3.387e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
 }
 
 GRAPHED = ("par2d_64",)  # launch-bound steps replayed from a CUDA graph
