@@ -184,17 +184,19 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
 /* Reserve the handle's workspace for batches of up to max_batch images (allocates on the
  * handle's device and synchronises it; do this outside stream capture).
  * 2D scans: with a workspace, xr_project and the adjoint take the batched fast path for
- * batches of 4 or more: the images (or sinograms) of each chunk of 16 are first
- * interleaved so that one unit's values sit in one 64-byte line, in two spatial orders
- * (x fastest and y fastest), and one thread walks each ray for up to 16 images.
- * Workspace bytes: 4 * padded_batch * (2 * (nx+4)(ny+4)nz + n_rays).
+ * batches of 4 or more: the forward interleaves the images of each chunk of 16 so that one
+ * unit's values sit in one 64-byte line, in two spatial orders (x fastest and y fastest), and
+ * one thread walks each ray for up to 16 images; the gather adjoint builds per-ray records of
+ * the sinograms (16 values and the ray's plane constants) after those planes.
+ * Workspace bytes: 4 * padded_batch * 2 * (nx+4)(ny+4)nz + 12 * padded_batch * n_rays.
  * 3D scans: the workspace is one [nz][nx][ny] copy of a volume (4 * n_units bytes, any
  * batch); each image is copied into it and every ray reads whichever of the two layouts
  * has its warp's neighbouring rays in neighbouring words; the scatter adjoint uses it as a
  * second accumulator.  Single-tilt-axis parallel scans (xr_geometry_info.column_batch)
- * reserve the larger of that and 16 * P * (2 (nx+4)(nz+4) + n_views * n_rows) bytes,
- * P = 4 * ceil(n_cols / 16): the column images as quad planes and the sinogram planes; when
- * that allocation fails the single-image copy is reserved and the 3D walk runs.
+ * reserve the larger of that and 16 * P * 2 (nx+4)(nz+4) + 48 * P * n_views * n_rows bytes
+ * (P = 4 * ceil(n_cols / 16)): the column images as quad planes, then the gather records of the
+ * columns (the largest record set any tuning needs); when that allocation fails the
+ * single-image copy is reserved and the 3D walk runs.
  * Without a workspace, or for larger batches, the calls use the one-thread-per-ray kernels
  * on the caller's layout (same lengths).
  * Errors: XR_ERR_NULL, XR_ERR_BATCH, XR_ERR_ALLOC, XR_ERR_CUDA. */

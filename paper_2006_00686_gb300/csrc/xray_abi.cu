@@ -697,9 +697,9 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
     }
     if (method == XR_ADJ_AUTO) {
         // measured on GB300: 3D scatter 438 ms vs tiled gather 682 ms (circular cone 512^3);
-        // single-tilt-axis scans as 2D column problems: the pair gather (C3 1.36 ms vs the 3D
-        // scatter 2.76 ms); 2D: the quad-plane gather beats the vector-atomic scatter (1.97
-        // vs 2.94 ms, fan beam 512^2 x 16), one image: the scatter
+        // single-tilt-axis scans as 2D column problems: the staged gather (C3 1.19 ms vs the 3D
+        // scatter 2.76 ms); 2D: the staged gather beats the vector-atomic scatter (1.44 vs
+        // 2.94 ms, fan beam 512^2 x 16), one image: the scatter
         if (kind_is3d(g->params.kind))
             method = use_slices(g) ? XR_ADJ_GATHER : XR_ADJ_SCATTER;
         else
