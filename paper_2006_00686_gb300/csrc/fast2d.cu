@@ -427,8 +427,12 @@ __global__ void interleave_planes_kernel(const float *__restrict__ img, int batc
 
 // Forward: one thread per ray, NQ planes (4*NQ images) per thread; blockIdx.y = group of
 // NQ planes.  il0/il1: plane layout; sino: image b, ray r at sino[b * sb + r * sr] (the
-// user layout: sb = n_rays, sr = 1).
-template <int NQ>
+// user layout: sb = n_rays, sr = 1).  ONLY_CROSS: a slab that stays in one row reads that row
+// once (the second row's loads sit in a branch taken by the lanes that cross into it): the
+// L1 data path, which bounds this kernel, then carries fewer bytes, at the cost of the branch
+// -- faster for the single-tilt-axis column problems (C3 1.04 vs 1.12 ms), slower for the fan
+// batch (1.20 vs 1.16 ms).
+template <int NQ, bool ONLY_CROSS>
 __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plane_kernel(const RayRec *__restrict__ rays,
                                                                            int64_t n_rays, int nx, int ny, int nz,
                                                                            const float4 *__restrict__ il0,
@@ -486,6 +490,21 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
                 // instructions and register spills, 1.255 vs 1.157 ms at fan beam 512^2 x 16.)
                 const float4 *pc = act ? pA + moff + rc * sB : zero_unit;
                 const float4 *pn = act ? pA + moff + rn * sB : zero_unit;
+                if (ONLY_CROSS) {
+                // the second row only where the lane's slab crosses into it (ln > 0 only there)
+                float4 vc[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) vc[q] = __ldg(pc + (int64_t)q * np);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) fma4(acc[q], vc[q], lc);
+                if (cross && act) {
+                    float4 vn[NQ];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) vn[q] = __ldg(pn + (int64_t)q * np);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) fma4(acc[q], vn[q], ln);
+                }
+                } else {
                 float4 vc[NQ], vn[NQ];
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
@@ -496,6 +515,7 @@ __global__ void __launch_bounds__(256, NQ >= 4 ? 3 : XR_FWD_MIN_BLOCKS) fwd_plan
                 for (int q = 0; q < NQ; ++q) {
                     fma4(acc[q], vc[q], lc);
                     fma4(acc[q], vn[q], ln);
+                }
                 }
             } else if (act) {
                 // crossing two rows (within rounding of a diagonal): per-candidate formula
@@ -1041,7 +1061,7 @@ cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny
 
 cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
                                  const float *il1, float *sino, int batch, int nq, cudaStream_t s, int64_t sb,
-                                 int64_t sr)
+                                 int64_t sr, bool only_cross)
 {
     const int Q = (batch + 3) / 4;
     const int groups = (Q + nq - 1) / nq;
@@ -1053,9 +1073,17 @@ cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int
     }
     // both strides fit 32 bits: n_rays < 2^31 and n_cols on the batched paths
     const int isb = (int)sb, isr = (int)sr;
-    if (nq == 4) fwd_plane_kernel<4><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, isb, isr);
-    else if (nq == 2) fwd_plane_kernel<2><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, isb, isr);
-    else fwd_plane_kernel<1><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, isb, isr);
+#define XR_FP(NQV, OC) fwd_plane_kernel<NQV, OC><<<grid, 256, 0, s>>>(rays, n_rays, nx, ny, nz, a, b, Q, sino, batch, isb, isr)
+    if (only_cross) {
+        if (nq == 4) XR_FP(4, true);
+        else if (nq == 2) XR_FP(2, true);
+        else XR_FP(1, true);
+    } else {
+        if (nq == 4) XR_FP(4, false);
+        else if (nq == 2) XR_FP(2, false);
+        else XR_FP(1, false);
+    }
+#undef XR_FP
     return cudaGetLastError();
 }
 

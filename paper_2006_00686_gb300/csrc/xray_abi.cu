@@ -645,7 +645,7 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
                                         il0, il1, s));
             XR_CUDA(launch_project_plane(g->d_rays2, slice_n2(g), p.nx, p.nz, 1, il0, il1,
                                          d_sino + (size_t)b * g->n_rays, p.n_cols, plane_nq(g, p.n_cols), s, 1,
-                                         p.n_cols));
+                                         p.n_cols, true));
         }
         return XR_OK;
     }

@@ -197,9 +197,10 @@ cudaError_t launch_gather_prep(const RayRec *rays, int64_t n_rays, void *grec, c
 cudaError_t launch_interleave_planes(const float *img, int batch, int nx, int ny, int nz, float *il0, float *il1,
                                      cudaStream_t s);
 // The forward writes image b, ray r at sino[b * sb + r * sr] (sb < 0: the user layout).
+// only_cross: a slab that stays in one row reads it once (see fwd_plane_kernel).
 cudaError_t launch_project_plane(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, const float *il0,
                                  const float *il1, float *sino, int batch, int nq, cudaStream_t s, int64_t sb = -1,
-                                 int64_t sr = 1);
+                                 int64_t sr = 1, bool only_cross = false);
 // The gather adjoint of a batch of sinograms (image b, ray r at sino[b * sb + r * sr]; sb < 0:
 // the user layout [batch][n_rays]): builds the gather records (gather_records_bytes(batch, nq,
 // n_rays) bytes at recs, 16-byte aligned) and reads them through shared-memory stages.  Image b
