@@ -409,12 +409,103 @@ __global__ void __launch_bounds__(256) fwd_adj_kernel(RaySrc rays, int n_rays, i
     if (v != 0.f) scatter_ray<kAdjAhead>(rr, v, nx, ny, nz, out + b * n_units, nullptr, err);
 }
 
+// The walks of fwd_ray_s / scatter_ray_s restricted to the box [lo, hi) of the grid (the grid's
+// own planes, so every voxel keeps its length); base points at the box's first voxel.
+template <int U, int SKIP>
+__device__ __forceinline__ float fwd_box_s(const RayRec &rr, const int3 lo, const int3 hi, int nx, int ny, int nz,
+                                           const float *__restrict__ base, int sx, int sy, int sz)
+{
+    Dda<int> D;
+    float acc = 0.f;
+    if (dda_setup_box<int>(rr, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, sx, sy, sz, D)) {
+        for (int g = dda_max_steps(nx, ny, nz) / U + 1; g > 0 && D.tcur < D.tout; --g) {
+            int off[U];
+            float l[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) dda_step_t<SKIP>(D, off[u], l[u]);
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = l[u] > 0.f ? __ldg(base + off[u]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc = __fmaf_rn(v[u], l[u], acc);
+        }
+    }
+    return acc;
+}
+
+template <int U, int SKIP>
+__device__ __forceinline__ void scatter_box_s(const RayRec &rr, float g, const int3 lo, const int3 hi, int nx, int ny,
+                                              int nz, float *__restrict__ base, int sx, int sy, int sz)
+{
+    Dda<int> D;
+    if (!dda_setup_box<int>(rr, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, sx, sy, sz, D)) return;
+    for (int k = dda_max_steps(nx, ny, nz) / U + 1; k > 0 && D.tcur < D.tout; --k) {
+        int off[U];
+        float l[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) dda_step_t<SKIP>(D, off[u], l[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (l[u] > 0.f) red_add(base + off[u], __fmul_rn(g, l[u]));
+    }
+}
+
+// fwd_adj_kernel with two threads per (ray, image) for problems that leave most of the GPU idle:
+// the threads of a pair (neighbouring lanes) take the two halves of the grid on either side of
+// the middle plane of the ray's driving axis (its largest |w|); their sums add up to the ray's
+// (one shuffle, reached by every lane of the warp outside the walks' branches), and each spreads
+// that sum over its own half.
+__global__ void __launch_bounds__(256) fwd_adj_split_kernel(RaySrc rays, int n_rays, int nx, int ny, int nz,
+                                                            const float *__restrict__ img, float *__restrict__ sino,
+                                                            float *__restrict__ out, int64_t n_units)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = t >> 1;
+    const int h = (int)(t & 1);
+    const bool valid = r < n_rays;  // the same for both threads of a pair
+    if (!__any_sync(0xffffffffu, valid)) return;  // the whole warp
+    const int64_t b = blockIdx.y;
+    RayRec rr{};  // an invalid lane's zero record crosses nothing
+    if (valid) rr = rays[r];
+    const float a0 = fabsf(rr.w0), a1 = fabsf(rr.w1), a2 = fabsf(rr.w2);
+    const int ax = (a0 >= a1 && a0 >= a2) ? 0 : (a1 >= a2 ? 1 : 2);
+    int3 lo = make_int3(0, 0, 0), hi = make_int3(nx, ny, nz);
+    const int mid = (ax == 0 ? nx : (ax == 1 ? ny : nz)) / 2;
+    if (ax == 0) (h ? lo.x : hi.x) = mid;
+    else if (ax == 1) (h ? lo.y : hi.y) = mid;
+    else (h ? lo.z : hi.z) = mid;
+    const int64_t corner = lo.x + (int64_t)lo.y * nx + (int64_t)lo.z * nx * ny;
+    const float *im = img + b * n_units + corner;
+    float *o = out + b * n_units + corner;
+    const int sy = nx, sz = nx * ny;
+    float part;
+    if (rr.w2 == 0.f) part = fwd_box_s<kFwdAhead, 2>(rr, lo, hi, nx, ny, nz, im, 1, sy, sz);
+    else if (rr.w1 == 0.f) part = fwd_box_s<kFwdAhead, 1>(rr, lo, hi, nx, ny, nz, im, 1, sy, sz);
+    else part = fwd_box_s<kFwdAhead, 0>(rr, lo, hi, nx, ny, nz, im, 1, sy, sz);
+    const float v = part + __shfl_xor_sync(0xffffffffu, part, 1);
+    if (!valid) return;
+    if (h == 0) sino[b * n_rays + r] = v;
+    if (v == 0.f) return;
+    if (rr.w2 == 0.f) scatter_box_s<kAdjAhead, 2>(rr, v, lo, hi, nx, ny, nz, o, 1, sy, sz);
+    else if (rr.w1 == 0.f) scatter_box_s<kAdjAhead, 1>(rr, v, lo, hi, nx, ny, nz, o, 1, sy, sz);
+    else scatter_box_s<kAdjAhead, 0>(rr, v, lo, hi, nx, ny, nz, o, 1, sy, sz);
+}
+
 }  // namespace
 
 cudaError_t launch_fwd_adj(const RaySrc &rays, const GeoParams &g, int64_t n_rays, const float *img, float *sino,
                            float *out, int batch, int block, int *err, cudaStream_t s)
 {
     const int64_t n_units = (int64_t)g.nx * g.ny * g.nz;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (n_rays * batch <= 256 * (int64_t)sms && 2 * n_rays < ((int64_t)1 << 31)) {
+        // a problem this small leaves the GPU mostly idle: two threads per ray halve each
+        // thread's walk
+        const dim3 grid((unsigned)((2 * n_rays + block - 1) / block), (unsigned)batch);
+        fwd_adj_split_kernel<<<grid, block, 0, s>>>(rays, (int)n_rays, g.nx, g.ny, g.nz, img, sino, out, n_units);
+        return cudaGetLastError();
+    }
     const dim3 grid((unsigned)((n_rays + block - 1) / block), (unsigned)batch);
     fwd_adj_kernel<<<grid, block, 0, s>>>(rays, (int)n_rays, g.nx, g.ny, g.nz, img, sino, out, n_units, err);
     return cudaGetLastError();

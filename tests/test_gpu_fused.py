@@ -1,6 +1,7 @@
 """Forward and adjoint in one launch (xr_project_backproject): the sinogram against the oracle's
-forward, the image against the oracle's adjoint of that sinogram; and the binding's checks of
-output buffers."""
+forward, the image against the oracle's adjoint of that sinogram -- for problems of up to 256
+rays per SM two threads share a ray (one per half of the grid along its driving axis), above
+that one thread walks it; and the binding's checks of output buffers."""
 import math
 
 import numpy as np
@@ -40,6 +41,7 @@ def _rays(kind):
 GEOMS = {
     "par2d_64": inputs.par2d_64,
     "fan2d_96": lambda: H.fan2d_small(96, 60),
+    "fan2d_128": lambda: H.fan2d_small(128, 180),  # above 256 rays per SM: one thread per ray
     "par3d_24": lambda: H.par3d_small(24),
     "cone_32": lambda: H.cone_small(32, 12),
     "helix_32": lambda: H.helix_small(32, 16, 12, 2),
