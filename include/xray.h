@@ -259,7 +259,9 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
  * Xray_transform_image), writes sino[b][r], then walks the same units again adding
  * l_I(r) * sino[b][r] into out (atomics, so the order of the additions, and the last bits of
  * out, may differ from run to run).  Meant for problems too small to fill the GPU, whose
- * separate calls are bound by their launches; any scan and batch.  d_img: [batch][n_units],
+ * separate calls are bound by their launches; any scan and batch.  Up to 256 rays per SM
+ * (rays x batch), two threads share each ray, one per half of the grid along the ray's
+ * driving axis, and add their halves' sums before spreading them.  d_img: [batch][n_units],
  * d_sino: [batch][n_rays] (overwritten), d_out: [batch][n_units] (overwritten), float32,
  * device, 16-byte aligned, none overlapping another.
  * Errors: XR_ERR_NULL, XR_ERR_BATCH, XR_ERR_ALIGN, XR_ERR_ARG (overlapping buffers),
