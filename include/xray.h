@@ -189,6 +189,10 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
  * one thread walks each ray for up to 16 images; the gather adjoint builds per-ray records of
  * the sinograms (16 values and the ray's plane constants) after those planes.
  * Workspace bytes: 4 * padded_batch * 2 * (nx+4)(ny+4)nz + 12 * padded_batch * n_rays.
+ * For fewer than 4 images the 2D workspace is 4 * (nx (ny+4) + ny (nx+4)) bytes: the
+ * accumulator planes of the single-image adjoint (one per driving axis, rows padded by two on
+ * each side), into which 32 neighbouring rays per warp reduce slab by slab in lockstep when
+ * the scan has 1024 rays per SM or more; the forward's transposed copy fits in the same bytes.
  * 3D scans: the workspace is one [nz][nx][ny] copy of a volume (4 * n_units bytes, any
  * batch); each image is copied into it and every ray reads whichever of the two layouts
  * has its warp's neighbouring rays in neighbouring words; the scatter adjoint uses it as a

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libxray.so")
-SOURCES = ["ray_setup.cu", "kernels.cu", "fast2d.cu", "tile2d.cu", "fast3d.cu", "tile3d.cu", "xray_abi.cu", "noalloc.cu", "probe.cu", "atten.cu", "atten2d.cu", "autotune.cu", "slices.cu", "trace3d.cu", "batch2d.cu"]
+SOURCES = ["ray_setup.cu", "kernels.cu", "fast2d.cu", "tile2d.cu", "fast3d.cu", "tile3d.cu", "xray_abi.cu", "noalloc.cu", "probe.cu", "atten.cu", "atten2d.cu", "autotune.cu", "slices.cu", "trace3d.cu", "batch2d.cu", "slab2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,10 +1,12 @@
-// Adjoint of 2D problems (one image each) with the slab walk in warp lockstep: batch plans and
-// the one-call batched adjoint take it when every problem is 2D (64 uneven fans: 38 ms against
-// 72 ms for rays walked one by one), and so does the single-image adjoint of a 2D scan.  The forward stays the
-// crossing-order walk one ray at a time: the same lockstep walk as a forward measured 40.6 ms,
-// and 48 ms with eight slabs' loads issued together, against 22.1 ms -- for one image per
-// problem the lockstep's per-slab bookkeeping and its union of the lanes' slab ranges cost more
-// than its coalesced loads save, while for reductions the coalescing decides.
+// Adjoint of 2D problems (one image each) with the slab walk in warp lockstep, reduced
+// straight into the caller's images: the one-call batched adjoint (xr_backproject_batched),
+// which holds no per-problem planes, takes it when every problem is 2D (64 uneven fans: 38 ms
+// against 72 ms for rays walked one by one).  Batch plans and single images, which hold
+// padded accumulator planes, take the leaner form of this walk in slab2d.cu.  The forward
+// stays the crossing-order walk one ray at a time: the same lockstep walk as a forward
+// measured 40.6 ms, and 48 ms with eight slabs' loads issued together, against 22.1 ms -- for
+// one image per problem the lockstep's per-slab bookkeeping and its union of the lanes' slab
+// ranges cost more than its coalesced loads save, while for reductions the coalescing decides.
 //
 // Warps take work items of consecutive rays of one problem from one atomic counter; a work
 // item is walked 32 rays at a time, one lane per ray.  The 32 rays are neighbouring detector
@@ -145,26 +147,7 @@ __global__ void __launch_bounds__(256) batch2d_adj_kernel(const BatchItem *__res
     }
 }
 
-// One 2D problem on its own (the single-image adjoint): warp w takes rays 32w .. 32w + 31.
-__global__ void __launch_bounds__(256) batch2d_adj_one_kernel(BatchItem P)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane;
-    if (first >= P.n_rays) return;  // the whole warp
-    const int64_t r = first + lane;
-    const bool valid = r < P.n_rays;
-    const float g = valid ? __ldg(P.sino + r) : 0.f;
-    if (__all_sync(0xffffffffu, g == 0.f)) return;  // nothing to spread
-    slab2d_adjoint(P, r, valid, g);
-}
-
 }  // namespace
-
-cudaError_t launch_batch2d_adjoint_one(const BatchItem &P, cudaStream_t s)
-{
-    batch2d_adj_one_kernel<<<(unsigned)((P.n_rays + 255) / 256), 256, 0, s>>>(P);
-    return cudaGetLastError();
-}
 
 int batch2d_ctas_per_sm(int block)
 {

@@ -615,30 +615,6 @@ cudaError_t launch_project3d(const RaySrc &rays, const GeoParams &g, int64_t n_r
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter2d_lock(const RaySrc *d_src, int64_t n_rays, int nx, int ny, const float *sino, float *out,
-                                  float *accT, cudaStream_t s)
-{
-    const size_t bytes = (size_t)nx * ny * sizeof(float);
-    cudaError_t e = cudaMemsetAsync(out, 0, bytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(accT, 0, bytes, s);
-    if (e != cudaSuccess) return e;
-    BatchItem P{};
-    P.src = d_src;
-    P.img = out;
-    P.sino = const_cast<float *>(sino);
-    P.aux = accT;
-    P.nx = nx;
-    P.ny = ny;
-    P.nz = 1;
-    P.three = 0;
-    P.n_rays = n_rays;
-    e = launch_batch2d_adjoint_one(P, s);
-    if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((nx + TT - 1) / TT), (unsigned)((ny + TT - 1) / TT), 1u);
-    add_transposed_kernel<<<grid, dim3(TT, 8), 0, s>>>(accT, out, nx, ny);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_scatter3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order,
                              const float *sino, float *out, float *accT, int block, int *err, cudaStream_t s)
 {

@@ -213,6 +213,40 @@ static bool use_slices(const xr_geometry *g)
            (g->params.n_cols + 3) / 4 <= 65535;  // planes index gridDim.y
 }
 
+// The adjoint of single images of 2D scans in the ray order (neighbouring rays of a view in a
+// warp) that fill the GPU, 1024 rays per SM or more: the lockstep slab walk into padded
+// accumulator planes in the workspace (slab2d.cu).  Smaller scans, where the longest warp
+// decides the time, keep the crossing-order walk one ray per thread (parallel 64^2: 23 vs
+// 25 us).
+static bool use_slab2d(const xr_geometry *g)
+{
+    if (kind_is3d(g->params.kind) || g->tune.path == XR_PATH_RAY || !g->d_ws) return false;
+    const int64_t floats = slab2d_acc_floats(g->params.nx, g->params.ny);
+    if (g->ws_bytes < (size_t)floats * sizeof(float) || floats >= ((int64_t)1 << 31) ||
+        g->n_rays >= ((int64_t)1 << 31) || ray_order(g, true) > 1)
+        return false;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return g->n_rays >= 1024 * (int64_t)sms;
+}
+
+static BatchItem slab_item(const xr_geometry *g, const float *img, float *sino)
+{
+    BatchItem P{};
+    P.src = g->d_src;
+    P.img = img;
+    P.sino = sino;
+    P.aux = g->d_ws;
+    P.nx = g->params.nx;
+    P.ny = g->params.ny;
+    P.nz = 1;
+    P.n_rays = g->n_rays;
+    return P;
+}
+
 // The column-trace walk of cone and helical scans (workspace: the padded z-fastest copy).
 static bool use_trace(const xr_geometry *g)
 {
@@ -224,6 +258,8 @@ static size_t reserve_bytes(const xr_geometry *g, int batch)
 {
     if (kind_is3d(g->params.kind) || batch < 4) {
         size_t one = (size_t)g->n_units * sizeof(float);
+        if (!kind_is3d(g->params.kind))  // the single-image adjoint's accumulator planes
+            one = std::max(one, (size_t)slab2d_acc_floats(g->params.nx, g->params.ny) * sizeof(float));
         if (g->trace_ok) one = std::max(one, trace_ws_bytes(g->params));
         return g->slices.ok ? std::max(one, slice_ws_bytes(g)) : one;
     }
@@ -747,23 +783,17 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
                                              g->d_ws, s));
         return XR_OK;
     }
+    if (!use_tiled(g, batch) && !use_fast(g, batch) && use_slab2d(g)) {
+        for (int b = 0; b < batch; ++b)
+            XR_CUDA(launch_slab2d_adjoint_one(slab_item(g, d_img + (size_t)b * g->n_units,
+                                                        const_cast<float *>(d_sino) + (size_t)b * g->n_rays),
+                                              s));
+        return XR_OK;
+    }
     if (!use_tiled(g, batch) && !use_fast(g, batch) && use_dda(g)) {
-        // 2D scans in the ray order that fill the GPU (1024 rays per SM or more): the slab walk
-        // with 32 neighbouring rays per warp in lockstep (its reductions fall on neighbouring
-        // words; fan 512^2: 0.47 vs 0.85 ms); smaller ones, where the longest warp decides the
-        // time, and 3D scans: the crossing-order walk (parallel 64^2: 23 vs 25 us)
-        int sms = 0;
-        XR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
-        const bool lock = !kind_is3d(g->params.kind) && ray_order(g, true) <= 1 && g->n_rays >= 1024 * (int64_t)sms;
-        for (int b = 0; b < batch; ++b) {
-            const float *sb = d_sino + (size_t)b * g->n_rays;
-            float *ib = d_img + (size_t)b * g->n_units;
-            if (lock)
-                XR_CUDA(launch_scatter2d_lock(g->d_src, g->n_rays, g->params.nx, g->params.ny, sb, ib, g->d_ws, s));
-            else
-                XR_CUDA(launch_scatter3d(g->src, g->params, g->n_rays, ray_order(g, true), sb, ib, g->d_ws,
-                                         g->tune.block, g->d_err, s));
-        }
+        for (int b = 0; b < batch; ++b)
+            XR_CUDA(launch_scatter3d(g->src, g->params, g->n_rays, ray_order(g, true), d_sino + (size_t)b * g->n_rays,
+                                     d_img + (size_t)b * g->n_units, g->d_ws, g->tune.block, g->d_err, s));
         return XR_OK;
     }
     if (use_tiled(g, batch)) {
@@ -932,14 +962,15 @@ xr_status xr_system_rows_fill(const xr_geometry *g, int64_t ray0, int32_t n, con
 struct xr_batch {
     int device;
     int n;
-    bool lock2d;  // every problem is 2D: the lockstep slab walk (batch2d.cu)
+    bool lock2d;  // every problem is 2D: the adjoint is the lockstep slab walk (slab2d.cu)
+    int sms;
     SetupItem *d_setup;          // per problem: the ray setup's work (xr_batch_ray_setup)
     int64_t setup_det, setup_rays;  // detector samples and table rays over all problems
     int tile, block, ctas_fwd, ctas_adj;
     int64_t n_tiles;
     BatchItem *d_items;
     unsigned long long *d_counter;
-    float *d_aux;  // every problem's [nz][nx][ny] copy / accumulator, back to back
+    float *d_aux;  // every problem's [nz][nx][ny] copy / accumulator (2D: also the adjoint's planes), back to back
 };
 
 extern "C" {
@@ -957,6 +988,13 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
     XR_CUDA(cudaGetDevice(&dev));
     BatchItem *items = (BatchItem *)malloc(sizeof(BatchItem) * (size_t)n);
     if (!items) return XR_ERR_ALLOC;
+    bool all2d = true;
+    for (int i = 0; i < n; ++i) all2d = all2d && probs[i].geom && !kind_is3d(probs[i].geom->params.kind);
+    // floats of problem g's aux buffer, a multiple of 4 (every buffer 16-byte aligned)
+    auto aux_floats = [all2d](const xr_geometry *g) -> int64_t {
+        const int64_t f = all2d ? std::max(g->n_units, slab2d_acc_floats(g->params.nx, g->params.ny)) : g->n_units;
+        return (f + 3) & ~(int64_t)3;
+    };
     int64_t tiles = 0, aux_units = 0;
     for (int i = 0; i < n; ++i) {
         const xr_geometry *g = probs[i].geom;
@@ -972,7 +1010,8 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
             free(items);
             return XR_ERR_ALIGN;
         }
-        if (g->n_units >= ((int64_t)1 << 31)) {  // the walk indexes one problem with 32 bits
+        if (g->n_units >= ((int64_t)1 << 31) ||  // the walks index one problem with 32 bits
+            (all2d && slab2d_acc_floats(g->params.nx, g->params.ny) >= ((int64_t)1 << 31))) {
             free(items);
             return XR_ERR_SIZE;
         }
@@ -987,7 +1026,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         items[i].n_rays = g->n_rays;
         items[i].tile_begin = tiles;
         tiles += (g->n_rays + tile - 1) / tile;
-        aux_units += (g->n_units + 3) & ~(int64_t)3;  // keep every copy 16-byte aligned
+        aux_units += aux_floats(g);
     }
     if (n > 65535) {
         free(items);
@@ -999,14 +1038,14 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         return XR_ERR_ALLOC;
     }
     b->n = n;
-    b->lock2d = true;
-    for (int i = 0; i < n; ++i) b->lock2d = b->lock2d && !items[i].three;
+    b->lock2d = all2d;
     b->tile = tile;
     b->block = block;
     b->n_tiles = tiles;
     int sms = 0;
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->sms = sms;
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_aux, (size_t)aux_units * sizeof(float));
@@ -1038,7 +1077,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         int64_t at = 0;
         for (int i = 0; i < n; ++i) {
             items[i].aux = b->d_aux + at;
-            at += (probs[i].geom->n_units + 3) & ~(int64_t)3;
+            at += aux_floats(probs[i].geom);
         }
         e = cudaMemcpy(b->d_items, items, sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice);
     }
@@ -1050,7 +1089,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         return oom ? XR_ERR_ALLOC : cuda_fail(e);
     }
     b->ctas_fwd = sms * batched_ctas_per_sm(block, 0);
-    b->ctas_adj = sms * (b->lock2d ? batch2d_ctas_per_sm(block) : batched_ctas_per_sm(block, 1));
+    b->ctas_adj = sms * (b->lock2d ? slab2d_ctas_per_sm(block) : batched_ctas_per_sm(block, 1));
     *out = b;
     return XR_OK;
 }
@@ -1081,15 +1120,19 @@ xr_status xr_batch_project(const xr_batch *b, xr_stream stream)
 {
     if (!b) return XR_ERR_NULL;
     XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 0, 1, b->ctas_fwd, b->block,
-                           (cudaStream_t)stream, b->lock2d));
+                           (cudaStream_t)stream));
     return XR_OK;
 }
 
 xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream)
 {
     if (!b) return XR_ERR_NULL;
-    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 1, 1, b->ctas_adj, b->block,
-                           (cudaStream_t)stream, b->lock2d));
+    if (b->lock2d)
+        XR_CUDA(launch_slab2d_adjoint(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, b->ctas_adj, b->block,
+                                      b->sms, (cudaStream_t)stream));
+    else
+        XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 1, 1, b->ctas_adj, b->block,
+                               (cudaStream_t)stream));
     return XR_OK;
 }
 

@@ -162,7 +162,8 @@ __device__ __forceinline__ int find_item(const BatchItem *items, int n, int64_t 
 // problem.  Forward: the [nz][nx][ny] copies are written first when the items carry aux
 // buffers; adjoint: images (and aux) are zeroed, scattered into, and aux added back.
 // The tile counter is zeroed here.
-// lock2d: every problem is 2D -- the adjoint's walk is batch2d_kernel (grid_ctas sized for it).
+// lock2d: every problem is 2D -- the adjoint's walk is batch2d_adj_kernel straight into the
+// images (grid_ctas sized for it; the no-allocation entry points, which hold no planes).
 // The forward keeps the crossing-order walk: for one image per problem the lockstep slab walk
 // measured slower (64 uneven fans: 40.6 vs 22.2 ms), its adjoint faster (39.7 vs 71.9 ms).
 cudaError_t launch_batched(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
@@ -179,13 +180,26 @@ cudaError_t launch_batched_items(const BatchItem *items, int n_items, int64_t n_
 int batched_ctas_per_sm(int block, int adjoint);
 
 // The adjoint of a work list whose problems are all 2D (batch2d.cu): the slab walk in warp
-// lockstep, 32 neighbouring rays of one problem per warp.  No copies or zero fills here.
+// lockstep, 32 neighbouring rays of one problem per warp, reduced straight into the images
+// (and aux copies, where given).  No copies or zero fills here.
 int batch2d_ctas_per_sm(int block);
 cudaError_t launch_batch2d_adjoint(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
                                    unsigned long long *counter, int grid_ctas, int block, cudaStream_t s);
-// The same walk for one problem described by P (a kernel parameter): warp w takes rays
-// 32w .. 32w + 31.  P.img and P.aux must be zeroed.
-cudaError_t launch_batch2d_adjoint_one(const BatchItem &P, cudaStream_t s);
+
+// The lockstep slab-walk adjoint of 2D problems (slab2d.cu): floats of one problem's
+// accumulator planes (one per driving axis, every column padded with rows -2 .. N_B + 1).
+__host__ __device__ inline int64_t slab2d_acc_floats(int nx, int ny)
+{
+    return (int64_t)nx * (ny + 4) + (int64_t)ny * (nx + 4);
+}
+// One problem, its planes at P.aux (slab2d_acc_floats, 16-byte aligned): zeroes them, walks
+// 32 neighbouring rays per warp, then writes their sum into P.img.
+cudaError_t launch_slab2d_adjoint_one(const BatchItem &P, cudaStream_t s);
+// The same for a work list of 2D problems (persistent launch over an atomic tile counter,
+// zeroed here), each item's planes at its aux.
+int slab2d_ctas_per_sm(int block);
+cudaError_t launch_slab2d_adjoint(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                                  unsigned long long *counter, int grid_ctas, int block, int sms, cudaStream_t s);
 
 // Batched fast path for rays with at most two active axes (fast2d.cu).
 cudaError_t launch_scatter_fast2(const RayRec *rays, int64_t n_rays, int nx, int ny, int nz, float *acc0,
@@ -246,11 +260,6 @@ cudaError_t launch_transpose_xy(const float *in, float *out, int nx, int ny, int
 // or-ed in), or NULL.
 cudaError_t launch_project3d(const RaySrc &rays, const GeoParams &g, int64_t n_rays, int order, const float *img,
                              float *ws, float *sino, int block, int *err, cudaStream_t s);
-// The single-image adjoint of a 2D scan with the lockstep slab walk (batch2d.cu): zeroes `out`
-// and `accT` (the [nx][ny] copy), scatters, then adds accT (transposed) into out.  d_src: the
-// handle's device copy of its ray source.
-cudaError_t launch_scatter2d_lock(const RaySrc *d_src, int64_t n_rays, int nx, int ny, const float *sino, float *out,
-                                  float *accT, cudaStream_t s);
 // Forward, then the adjoint of its result, per (ray, image) with the single-image walks on the
 // caller's layout: sino = A img, out += A^T sino (out zeroed by the caller).  n_rays < 2^31,
 // batch <= 65535.

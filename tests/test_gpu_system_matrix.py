@@ -102,6 +102,48 @@ def test_2d_batched_forward_and_gather_rows(X, kind):
     P.close()
 
 
+@pytest.mark.parametrize("kind", ["par2d", "fan2d", "fan2d_arc"])
+def test_single_image_2d_pair_walk_rows(X, kind):
+    # one image per call on a 2D scan with 1024 rays per SM or more: the lockstep slab walk
+    # on pair planes (forward and adjoint), the configuration of the plain single-image
+    # launches.  The forward of every one-hot image gives the matrix's columns, kept at a
+    # sample of rays (every ray of the four axis views, 1200 others); the adjoint of one-hot
+    # sinograms gives the rows of 300 sampled rays
+    v = np.arange(720, dtype=np.float64)
+    kw = dict(dx=0.9, dy=1.1, cx=0.7, cy=-0.4, n_cols=241)
+    if kind == "par2d":
+        # u0: every ray of the axis views at least 0.005 from a grid line (no tie to break)
+        g = Geometry(kind, 23, 19, angles=2 * pi * v / 720, du=0.13, u0=0.025, **kw)
+    elif kind == "fan2d":
+        g = Geometry(kind, 23, 19, angles=2 * pi * v / 720, du=0.3, sod=60.0, sdd=90.0, **kw)
+    else:
+        g = Geometry(kind, 23, 19, angles=2 * pi * v / 720, du=0.0035, sod=60.0, sdd=90.0, **kw)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert g.n_rays >= 1024 * sms
+    rng = np.random.default_rng(11)
+    axis = np.concatenate([np.arange(241) + 241 * k for k in (0, 180, 360, 540)])
+    rays = np.unique(np.concatenate([axis, rng.choice(g.n_rays, 1200, replace=False)]))
+    P = X.Projector(g)
+    Mf = np.zeros((len(rays), g.n_units))
+    rt = torch.from_numpy(rays).cuda()
+    for I in range(g.n_units):
+        e = torch.zeros(g.n_units, device="cuda")
+        e[I] = 1.0
+        Mf[:, I] = P.forward(e.reshape(g.image_shape())).reshape(-1)[rt].double().cpu().numpy()
+    ref_all = {int(r): O.ray_units(g, int(r)) for r in rays}
+    graze = H.check_unit_sets(g, _rows_from_dense(Mf), [ref_all[int(r)] for r in rays])
+    assert graze <= max(4, sum(len(ref_all[int(r)][0]) for r in rays) // 500), graze
+    sample = rng.choice(rays, 300, replace=False)
+    Ma = np.zeros((len(sample), g.n_units))
+    for q, r in enumerate(sample):
+        y = torch.zeros(g.n_rays, device="cuda")
+        y[int(r)] = 1.0
+        Ma[q] = P.adjoint(y.reshape(g.sino_shape()), method=X.XR_ADJ_SCATTER).reshape(-1).double().cpu().numpy()
+    graze = H.check_unit_sets(g, _rows_from_dense(Ma), [ref_all[int(r)] for r in sample])
+    assert graze <= max(4, sum(len(ref_all[int(r)][0]) for r in sample) // 500), graze
+    P.close()
+
+
 def _geom3d(kind):
     kw = dict(dx=0.9, dy=1.1, dz=0.8, cx=0.6, cy=-0.5, cz=0.3, angles=ANGLES, n_cols=21, n_rows=15,
               sod=50.0, sdd=80.0)
