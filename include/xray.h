@@ -189,10 +189,12 @@ xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
  * one thread walks each ray for up to 16 images; the gather adjoint builds per-ray records of
  * the sinograms (16 values and the ray's plane constants) after those planes.
  * Workspace bytes: 4 * padded_batch * 2 * (nx+4)(ny+4)nz + 12 * padded_batch * n_rays.
- * For fewer than 4 images the 2D workspace is 4 * (nx (ny+4) + ny (nx+4)) bytes: the
- * accumulator planes of the single-image adjoint (one per driving axis, rows padded by two on
- * each side), into which 32 neighbouring rays per warp reduce slab by slab in lockstep when
- * the scan has 1024 rays per SM or more; the forward's transposed copy fits in the same bytes.
+ * For fewer than 4 images the 2D workspace is 8 * (nx (ny+6) + ny (nx+6)) bytes.  When the
+ * scan has 1024 rays per SM or more, the forward writes pair planes there (for each driving
+ * axis, every column's pairs of neighbouring pixels, three rows of padding on each side) and
+ * walks one ray per thread slab by slab on them, one 64-bit load per slab; the adjoint
+ * zeroes two accumulator planes there (rows padded by two on each side), into which 32
+ * neighbouring rays per warp reduce slab by slab in lockstep, and sums them into the image.
  * 3D scans: the workspace is one [nz][nx][ny] copy of a volume (4 * n_units bytes, any
  * batch); each image is copied into it and every ray reads whichever of the two layouts
  * has its warp's neighbouring rays in neighbouring words; the scatter adjoint uses it as a
@@ -351,18 +353,25 @@ void xr_batch_destroy(xr_batch *b);
 xr_status xr_batch_ray_setup(const xr_batch *b, xr_stream stream);
 
 /* Forward projection of every problem of the plan: one persistent launch whose CTAs (one
- * set per SM, as many as fit) take tiles from one atomic counter until none is left. */
+ * set per SM, as many as fit) take tiles from one atomic counter until none is left.  When
+ * every problem is 2D, one launch first writes each problem's pair planes (every column's
+ * pairs of neighbouring pixels) and the rays walk slab by slab on them, one 64-bit load per
+ * slab; otherwise the rays walk in crossing order. */
 xr_status xr_batch_project(const xr_batch *b, xr_stream stream);
 
 /* Adjoint of every problem of the plan (ray-driven scatter after one zeroing launch):
- * overwrites every problem's img with the adjoint of its sino. */
+ * overwrites every problem's img with the adjoint of its sino.  When every problem is 2D,
+ * 32 neighbouring rays per warp reduce slab by slab in lockstep into padded accumulator planes,
+ * which one more launch sums into the images. */
 xr_status xr_batch_backproject(const xr_batch *b, xr_stream stream);
 
 /* Batched forward projection that allocates nothing (the paper has no counterpart; this
  * serves callers that cannot call cudaMalloc where they project: code running during a
  * global-mode stream capture, hosts whose allocator owns the whole device pool, loops that
- * cannot afford the synchronisation of an allocation).  Same result as xr_batch_project on
- * the same problems, but the work list and tile counter live in one fixed array in device
+ * cannot afford the synchronisation of an allocation).  Each ray is walked in crossing order on
+ * the caller's layout, as xr_project walks one problem without pair planes: its sums are those
+ * of that walk bit for bit, and those of xr_batch_project within rounding (a plan of 2D
+ * problems sums the same lengths slab by slab).  The work list and tile counter live in one fixed array in device
  * memory that the library reserves on every device that loads it, until the process exits
  * (XR_NOALLOC_MAX_PROBLEMS work-list entries, about 16 KiB).  The caller still passes and
  * owns every image and sinogram.

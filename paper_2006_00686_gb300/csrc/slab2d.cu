@@ -48,6 +48,22 @@ constexpr int kMagicBits = 0x4B400000;
 
 constexpr int kPadRows = 4;  // rows -2, -1 and N_B, N_B + 1 around every column
 
+// One ray alone (crossing-order walk) on a layout with strides (sx, sy): its sum.
+__device__ __forceinline__ float fwd_alone(const RayRec &rr, int nx, int ny, const float *__restrict__ img, int sx,
+                                           int sy)
+{
+    Dda<int> D;
+    float acc = 0.f;
+    if (!dda_setup<int>(rr, nx, ny, 1, sx, sy, nx * ny, D)) return 0.f;
+    for (int k = dda_max_steps(nx, ny, 1); k > 0 && D.tcur < D.tout; --k) {
+        int off;
+        float l;
+        dda_step(D, off, l);
+        if (l > 0.f) acc = __fmaf_rn(__ldg(img + off), l, acc);
+    }
+    return acc;
+}
+
 // One ray alone: g * l added into a layout with strides (sx, sy).
 __device__ __forceinline__ void adj_alone(const RayRec &rr, int nx, int ny, float *acc, int sx, int sy, float g)
 {
@@ -238,6 +254,187 @@ __global__ void __launch_bounds__(256) zero_items_kernel(const BatchItem *__rest
         a[u] = 0.f;
 }
 
+// ---- the forward: one ray per thread on pair planes -----------------------------------------
+//
+// Pair planes (per problem, the x-driving plane first): column m of the plane of axis A holds,
+// at entry e = j + kPairPad, the pair (v(m, j), v(m, j + 1)) of pixels of rows j and j + 1
+// along B, for j = -kPairPad .. N_B + kPairPad - 1, with v = 0 outside the image.  A thread
+// walks its ray's own driving range in the direction in which u_B grows, so that at every slab
+// the lower row j = floor(u_B) at the slab's start is the pair's first pixel and the B plane
+// j + 1 splits the slab into the two pixels' lengths: one 64-bit load and no selection per
+// slab.  Over a ray's driving range (its box interval and one slab on either side, |slope| <= 1)
+// u_B stays within 2 of [0, N_B], inside the padding; the entry is also clamped to the plane,
+// so no load leaves it.
+
+constexpr int kPairPad = 3;
+#ifndef XR_SLAB_FWD_AHEAD
+#define XR_SLAB_FWD_AHEAD 4
+#endif
+constexpr int kFwdAhead = XR_SLAB_FWD_AHEAD;  // slabs split ahead of their loads
+
+__host__ __device__ __forceinline__ int pair_ld(int nb) { return nb + 2 * kPairPad; }
+
+// One ray's sum over the image (img: [ny][nx], for rays parallel to an axis; pairs: its planes).
+__device__ __forceinline__ float slab_fwd_ray(const RayRec &rr, int nx, int ny, const float *__restrict__ img,
+                                              const float2 *__restrict__ pairs)
+{
+    Walk W;
+    if (!walk_setup(rr, nx, ny, 1, 1, nx, (int64_t)nx * ny, W)) return 0.f;
+    if (W.nact != 2) return fwd_alone(rr, nx, ny, img, 1, nx);
+    const int ld = pair_ld(W.NB);
+    const float2 *plane = pairs + (W.axA == 0 ? 0 : (int64_t)nx * pair_ld(ny));
+    const unsigned emax = (unsigned)(W.NA * ld - 1);
+    // walk m up when u_B grows with it (w_A and w_B of one sign), else down; s = sign(w_B) t
+    // grows along the walk and u_B = |w_B| s + f_B grows with s
+    const bool upm = (W.wB > 0.f) == (W.sgA == 0);
+    const float sg = W.wB > 0.f ? 1.0f : -1.0f;
+    const float invA = sg * W.invA, bA = sg * W.bA, wB = sg * W.wB, fB = W.fB;
+    const float invB = sg * W.invB, bB = sg * W.bB;
+    const float dp = upm ? 1.0f : -1.0f;
+    const int dld = upm ? ld : -ld;
+    const int n = W.mhi - W.mlo + 1;
+    float p = (float)((upm ? W.mlo : W.mhi + 1) - W.oA);  // the first slab's starting plane
+    // entry of row j from its magic float: column offset + bits - kMagicBits + oB + kPairPad
+    int moff = (upm ? W.mlo : W.mhi) * ld + (W.oB + kPairPad - kMagicBits);
+    float sc = __fmaf_rn(p, invA, bA);
+    float mc = __fadd_rd(__fmaf_rn(wB, sc, fB), kMagic);
+    float acc0 = 0.f, acc1 = 0.f;
+    int k = 0;
+    for (; k + kFwdAhead <= n; k += kFwdAhead) {
+        unsigned e[kFwdAhead];
+        float lx[kFwdAhead], ly[kFwdAhead];
+#pragma unroll
+        for (int u = 0; u < kFwdAhead; ++u) {
+            p += dp;
+            const float sn = __fmaf_rn(p, invA, bA);
+            const float mn = __fadd_rd(__fmaf_rn(wB, sn, fB), kMagic);
+            const float ts = fminf(fmaxf(__fmaf_rn(mc - (kMagic - 1.0f), invB, bB), sc), sn);
+            lx[u] = __fsub_rn(ts, sc);
+            ly[u] = __fsub_rn(sn, ts);
+            e[u] = min((unsigned)(moff + __float_as_int(mc)), emax);
+            moff += dld;
+            sc = sn;
+            mc = mn;
+        }
+        float2 v[kFwdAhead];
+#pragma unroll
+        for (int u = 0; u < kFwdAhead; ++u) v[u] = __ldg(plane + e[u]);
+#pragma unroll
+        for (int u = 0; u < kFwdAhead; ++u) {
+            acc0 = __fmaf_rn(v[u].x, lx[u], acc0);
+            acc1 = __fmaf_rn(v[u].y, ly[u], acc1);
+        }
+    }
+    for (; k < n; ++k) {
+        p += dp;
+        const float sn = __fmaf_rn(p, invA, bA);
+        const float mn = __fadd_rd(__fmaf_rn(wB, sn, fB), kMagic);
+        const float ts = fminf(fmaxf(__fmaf_rn(mc - (kMagic - 1.0f), invB, bB), sc), sn);
+        const float2 v = __ldg(plane + min((unsigned)(moff + __float_as_int(mc)), emax));
+        acc0 = __fmaf_rn(v.x, __fsub_rn(ts, sc), acc0);
+        acc1 = __fmaf_rn(v.y, __fsub_rn(sn, ts), acc1);
+        moff += dld;
+        sc = sn;
+        mc = mn;
+    }
+    return __fadd_rn(acc0, acc1);
+}
+
+__global__ void __launch_bounds__(256) slab_fwd_one_kernel(BatchItem P, const float2 *__restrict__ pairs)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P.n_rays) return;
+    P.sino[r] = slab_fwd_ray((*P.src)[r], P.nx, P.ny, P.img, pairs);
+}
+
+// The batch plan's persistent forward: work items of `tile` consecutive rays of one problem,
+// one ray per thread; each item's pair planes at its aux.
+__global__ void __launch_bounds__(256) slab_fwd_batch_kernel(const BatchItem *__restrict__ items, int n_items,
+                                                             int64_t n_tiles, int tile,
+                                                             unsigned long long *__restrict__ counter)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)n_tiles) break;
+        const BatchItem &P = items[find_item(items, n_items, (int64_t)t)];
+        const int64_t first = ((int64_t)t - P.tile_begin) * tile;
+        for (int q = lane; q < tile; q += 32) {
+            const int64_t r = first + q;
+            if (r >= P.n_rays) break;
+            P.sino[r] = slab_fwd_ray((*P.src)[r], P.nx, P.ny, P.img, reinterpret_cast<const float2 *>(P.aux));
+        }
+    }
+}
+
+// Tiles of one problem's pair planes: the x-driving plane's (columns x, entries e), then the
+// y-driving plane's.
+__host__ __device__ __forceinline__ int pair_tiles_x(int nx, int ny) { return ((nx + PT - 1) / PT) * ((pair_ld(ny) + PT - 1) / PT); }
+__host__ __device__ __forceinline__ int pair_tiles_y(int nx, int ny) { return ((ny + PT - 1) / PT) * ((pair_ld(nx) + PT - 1) / PT); }
+
+// v(x, y) of an [ny][nx] image, 0 outside
+__device__ __forceinline__ float pix(const float *__restrict__ img, int nx, int ny, int x, int y)
+{
+    return (x >= 0 && x < nx && y >= 0 && y < ny) ? __ldg(img + (int64_t)y * nx + x) : 0.f;
+}
+
+// Tile b of one problem's pair planes (blocks of 32 x 8 threads).
+__device__ __forceinline__ void build_tile(const float *__restrict__ img, int nx, int ny, float2 *__restrict__ pairs,
+                                           int b, float (*s)[PT + 1])
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tX = pair_tiles_x(nx, ny);
+    if (b < tX) {
+        // plane X: columns x0 .. x0 + 31, entries e0 .. e0 + 31 (rows j = e - kPairPad); the
+        // image's rows e0 - kPairPad .. e0 - kPairPad + 32 staged so that reads run along x and
+        // writes along e
+        const int ldx = pair_ld(ny);
+        const int ntx = (nx + PT - 1) / PT;
+        const int x0 = (b % ntx) * PT, e0 = (b / ntx) * PT;
+        for (int rr = ty; rr < PT + 1; rr += blockDim.y) s[rr][tx] = pix(img, nx, ny, x0 + tx, e0 - kPairPad + rr);
+        __syncthreads();
+        const int e = e0 + tx;
+        for (int c = ty; c < PT; c += blockDim.y) {
+            const int x = x0 + c;
+            if (x < nx && e < ldx) pairs[(int64_t)x * ldx + e] = make_float2(s[tx][c], s[tx + 1][c]);
+        }
+    } else {
+        // plane Y: columns y, entries e (rows i = e - kPairPad), both read along x
+        const int ldy = pair_ld(nx);
+        const int bb = b - tX;
+        const int nte = (ldy + PT - 1) / PT;
+        const int e = (bb % nte) * PT + tx, y0 = (bb / nte) * PT;
+        float2 *py = pairs + (int64_t)nx * pair_ld(ny);
+        if (e < ldy)
+            for (int c = ty; c < PT; c += blockDim.y) {
+                const int y = y0 + c;
+                if (y < ny)
+                    py[(int64_t)y * ldy + e] = make_float2(pix(img, nx, ny, e - kPairPad, y),
+                                                           pix(img, nx, ny, e - kPairPad + 1, y));
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256) build_items_kernel(const BatchItem *__restrict__ items)
+{
+    __shared__ float s[PT + 1][PT + 1];
+    const BatchItem &P = items[blockIdx.y];
+    const int n = pair_tiles_x(P.nx, P.ny) + pair_tiles_y(P.nx, P.ny);
+    for (int b = blockIdx.x; b < n; b += gridDim.x) {
+        __syncthreads();
+        build_tile(P.img, P.nx, P.ny, reinterpret_cast<float2 *>(P.aux), b, s);
+    }
+}
+
+__global__ void __launch_bounds__(256) build_one_kernel(const float *__restrict__ img, int nx, int ny,
+                                                        float2 *__restrict__ pairs)
+{
+    __shared__ float s[PT + 1][PT + 1];
+    build_tile(img, nx, ny, pairs, blockIdx.x, s);
+}
+
 }  // namespace
 
 cudaError_t launch_slab2d_adjoint_one(const BatchItem &P, cudaStream_t s)
@@ -250,11 +447,34 @@ cudaError_t launch_slab2d_adjoint_one(const BatchItem &P, cudaStream_t s)
     return cudaGetLastError();
 }
 
-int slab2d_ctas_per_sm(int block)
+int slab2d_ctas_per_sm(int block, bool adjoint)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, slab_batch_kernel, block, 0);
+    if (adjoint)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, slab_batch_kernel, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, slab_fwd_batch_kernel, block, 0);
     return n > 0 ? n : 1;
+}
+
+cudaError_t launch_slab2d_project_one(const BatchItem &P, cudaStream_t s)
+{
+    float2 *pairs = reinterpret_cast<float2 *>(P.aux);
+    build_one_kernel<<<(unsigned)(pair_tiles_x(P.nx, P.ny) + pair_tiles_y(P.nx, P.ny)), dim3(PT, 8), 0, s>>>(
+        P.img, P.nx, P.ny, pairs);
+    slab_fwd_one_kernel<<<(unsigned)((P.n_rays + 255) / 256), 256, 0, s>>>(P, pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab2d_project(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                                  unsigned long long *counter, int grid_ctas, int block, int sms, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const dim3 per_item((unsigned)std::max(1, 4 * sms / std::max(1, n_items)), (unsigned)n_items);
+    build_items_kernel<<<per_item, dim3(PT, 8), 0, s>>>(items);
+    slab_fwd_batch_kernel<<<grid_ctas, block, 0, s>>>(items, n_items, n_tiles, tile, counter);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_slab2d_adjoint(const BatchItem *items, int n_items, int64_t n_tiles, int tile,

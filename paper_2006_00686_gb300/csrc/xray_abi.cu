@@ -213,15 +213,16 @@ static bool use_slices(const xr_geometry *g)
            (g->params.n_cols + 3) / 4 <= 65535;  // planes index gridDim.y
 }
 
-// The adjoint of single images of 2D scans in the ray order (neighbouring rays of a view in a
-// warp) that fill the GPU, 1024 rays per SM or more: the lockstep slab walk into padded
-// accumulator planes in the workspace (slab2d.cu).  Smaller scans, where the longest warp
-// decides the time, keep the crossing-order walk one ray per thread (parallel 64^2: 23 vs
-// 25 us).
-static bool use_slab2d(const xr_geometry *g)
+// Single images of 2D scans in the ray order (neighbouring rays of a view in a warp) that
+// fill the GPU, 1024 rays per SM or more (slab2d.cu): the adjoint walks 32 rays per warp in
+// lockstep into padded accumulator planes in the workspace, the forward one ray per thread on
+// pair planes there.  Smaller scans, where the longest warp and the extra launch decide the
+// time, keep the crossing-order walk one ray per thread (parallel 64^2: 23 vs 25 us).
+static bool use_slab2d(const xr_geometry *g, bool adjoint)
 {
     if (kind_is3d(g->params.kind) || g->tune.path == XR_PATH_RAY || !g->d_ws) return false;
-    const int64_t floats = slab2d_acc_floats(g->params.nx, g->params.ny);
+    const int64_t floats = adjoint ? slab2d_acc_floats(g->params.nx, g->params.ny)
+                                   : slab2d_pair_floats(g->params.nx, g->params.ny);
     if (g->ws_bytes < (size_t)floats * sizeof(float) || floats >= ((int64_t)1 << 31) ||
         g->n_rays >= ((int64_t)1 << 31) || ray_order(g, true) > 1)
         return false;
@@ -258,8 +259,10 @@ static size_t reserve_bytes(const xr_geometry *g, int batch)
 {
     if (kind_is3d(g->params.kind) || batch < 4) {
         size_t one = (size_t)g->n_units * sizeof(float);
-        if (!kind_is3d(g->params.kind))  // the single-image adjoint's accumulator planes
-            one = std::max(one, (size_t)slab2d_acc_floats(g->params.nx, g->params.ny) * sizeof(float));
+        if (!kind_is3d(g->params.kind))  // the single-image planes (adjoint and forward)
+            one = std::max(one, (size_t)std::max(slab2d_acc_floats(g->params.nx, g->params.ny),
+                                                 slab2d_pair_floats(g->params.nx, g->params.ny)) *
+                                    sizeof(float));
         if (g->trace_ok) one = std::max(one, trace_ws_bytes(g->params));
         return g->slices.ok ? std::max(one, slice_ws_bytes(g)) : one;
     }
@@ -692,6 +695,13 @@ xr_status xr_project(const xr_geometry *g, const float *d_img, float *d_sino, in
                                          d_sino + (size_t)b * g->n_rays, s));
         return XR_OK;
     }
+    if (!use_fast(g, batch) && use_slab2d(g, false)) {
+        for (int b = 0; b < batch; ++b)
+            XR_CUDA(launch_slab2d_project_one(slab_item(g, d_img + (size_t)b * g->n_units,
+                                                        d_sino + (size_t)b * g->n_rays),
+                                              (cudaStream_t)stream));
+        return XR_OK;
+    }
     if (!use_fast(g, batch) && use_dda(g)) {
         const cudaStream_t s = (cudaStream_t)stream;
         for (int b = 0; b < batch; ++b) {
@@ -783,7 +793,7 @@ xr_status xr_backproject_method(const xr_geometry *g, const float *d_sino, float
                                              g->d_ws, s));
         return XR_OK;
     }
-    if (!use_tiled(g, batch) && !use_fast(g, batch) && use_slab2d(g)) {
+    if (!use_tiled(g, batch) && !use_fast(g, batch) && use_slab2d(g, true)) {
         for (int b = 0; b < batch; ++b)
             XR_CUDA(launch_slab2d_adjoint_one(slab_item(g, d_img + (size_t)b * g->n_units,
                                                         const_cast<float *>(d_sino) + (size_t)b * g->n_rays),
@@ -992,7 +1002,9 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
     for (int i = 0; i < n; ++i) all2d = all2d && probs[i].geom && !kind_is3d(probs[i].geom->params.kind);
     // floats of problem g's aux buffer, a multiple of 4 (every buffer 16-byte aligned)
     auto aux_floats = [all2d](const xr_geometry *g) -> int64_t {
-        const int64_t f = all2d ? std::max(g->n_units, slab2d_acc_floats(g->params.nx, g->params.ny)) : g->n_units;
+        const int64_t f = all2d ? std::max(slab2d_acc_floats(g->params.nx, g->params.ny),
+                                           slab2d_pair_floats(g->params.nx, g->params.ny))
+                                : g->n_units;
         return (f + 3) & ~(int64_t)3;
     };
     int64_t tiles = 0, aux_units = 0;
@@ -1011,7 +1023,7 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
             return XR_ERR_ALIGN;
         }
         if (g->n_units >= ((int64_t)1 << 31) ||  // the walks index one problem with 32 bits
-            (all2d && slab2d_acc_floats(g->params.nx, g->params.ny) >= ((int64_t)1 << 31))) {
+            (all2d && slab2d_pair_floats(g->params.nx, g->params.ny) >= ((int64_t)1 << 31))) {
             free(items);
             return XR_ERR_SIZE;
         }
@@ -1088,8 +1100,8 @@ xr_status xr_batch_create(const xr_problem *probs, int32_t n, int32_t tile, int3
         xr_batch_destroy(b);
         return oom ? XR_ERR_ALLOC : cuda_fail(e);
     }
-    b->ctas_fwd = sms * batched_ctas_per_sm(block, 0);
-    b->ctas_adj = sms * (b->lock2d ? slab2d_ctas_per_sm(block) : batched_ctas_per_sm(block, 1));
+    b->ctas_fwd = sms * (b->lock2d ? slab2d_ctas_per_sm(block, false) : batched_ctas_per_sm(block, 0));
+    b->ctas_adj = sms * (b->lock2d ? slab2d_ctas_per_sm(block, true) : batched_ctas_per_sm(block, 1));
     *out = b;
     return XR_OK;
 }
@@ -1119,8 +1131,12 @@ xr_status xr_batch_ray_setup(const xr_batch *b, xr_stream stream)
 xr_status xr_batch_project(const xr_batch *b, xr_stream stream)
 {
     if (!b) return XR_ERR_NULL;
-    XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 0, 1, b->ctas_fwd, b->block,
-                           (cudaStream_t)stream));
+    if (b->lock2d)
+        XR_CUDA(launch_slab2d_project(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, b->ctas_fwd, b->block,
+                                      b->sms, (cudaStream_t)stream));
+    else
+        XR_CUDA(launch_batched(b->d_items, b->n, b->n_tiles, b->tile, b->d_counter, 0, 1, b->ctas_fwd, b->block,
+                               (cudaStream_t)stream));
     return XR_OK;
 }
 

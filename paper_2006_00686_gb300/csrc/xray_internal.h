@@ -197,8 +197,17 @@ __host__ __device__ inline int64_t slab2d_acc_floats(int nx, int ny)
 cudaError_t launch_slab2d_adjoint_one(const BatchItem &P, cudaStream_t s);
 // The same for a work list of 2D problems (persistent launch over an atomic tile counter,
 // zeroed here), each item's planes at its aux.
-int slab2d_ctas_per_sm(int block);
+int slab2d_ctas_per_sm(int block, bool adjoint);
 cudaError_t launch_slab2d_adjoint(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
+                                  unsigned long long *counter, int grid_ctas, int block, int sms, cudaStream_t s);
+// The forward of 2D problems with one image each: pair planes of every column (floats:
+// slab2d_pair_floats) built from P.img at P.aux, then one ray per thread slab by slab.
+__host__ __device__ inline int64_t slab2d_pair_floats(int nx, int ny)
+{
+    return 2 * ((int64_t)nx * (ny + 6) + (int64_t)ny * (nx + 6));
+}
+cudaError_t launch_slab2d_project_one(const BatchItem &P, cudaStream_t s);
+cudaError_t launch_slab2d_project(const BatchItem *items, int n_items, int64_t n_tiles, int tile,
                                   unsigned long long *counter, int grid_ctas, int block, int sms, cudaStream_t s);
 
 // Batched fast path for rays with at most two active axes (fast2d.cu).

@@ -3,10 +3,12 @@
 It exists for callers that cannot call cudaMalloc where they project -- code running
 during a global-mode stream capture, hosts whose allocator owns the whole device pool,
 loops that cannot afford an allocation's synchronisation -- and keeps its work list in a
-fixed array that the library reserves on the device.  Its output must equal that of the
-allocating entry point (xr_batch_project) on the same problems, on two calls in a row
-(the second call must not see anything left over from the first).  This file is collected
-last on purpose."""
+fixed array that the library reserves on the device.  It walks every ray in crossing order
+on the caller's layout, as xr_project does for one problem of these sizes, so its output must
+equal that of the allocating entry point bit for bit, on two calls in a row (the second call
+must not see anything left over from the first).  A batch plan of the same 2D problems walks
+slabs on pair planes instead: the same lengths summed in another order, equal within the
+parity tolerance.  This file is collected last on purpose."""
 import ctypes
 import math
 
@@ -45,12 +47,21 @@ def _problems(X, Ps, xs, ys):
     return arr
 
 
+def _references(X, Ps, xs, geoms):
+    """Each problem's xr_project (bitwise reference), checked against one batch plan."""
+    ref = [P.forward(x) for P, x in zip(Ps, xs)]
+    plan = [torch.empty(g.sino_shape(), device="cuda") for g in geoms]
+    X.BatchPlan(Ps, xs, plan).project()
+    for r, q in zip(ref, plan):
+        assert float((r - q).abs().max()) <= 1e-5 * float(r.abs().max())
+    return ref
+
+
 def _check_against_allocating_entry_point(X, sides, seed):
     geoms = _fans(sides)
     Ps = [X.Projector(g) for g in geoms]
     xs = [inputs.phantom(g, 6, seed + q).cuda() for q, g in enumerate(geoms)]
-    ref = [torch.empty(g.sino_shape(), device="cuda") for g in geoms]
-    X.BatchPlan(Ps, xs, ref).project()
+    ref = _references(X, Ps, xs, geoms)
     out = [torch.full(g.sino_shape(), float("nan"), device="cuda") for g in geoms]
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     st = X.lib().xr_project_batched_noalloc(_problems(X, Ps, xs, out), len(Ps), 128, stream)
@@ -76,8 +87,7 @@ def test_noalloc_runs_inside_a_global_mode_capture_without_allocating(X):
     geoms = _fans([80, 56, 112])
     Ps = [X.Projector(g) for g in geoms]
     xs = [inputs.phantom(g, 6, 900 + q).cuda() for q, g in enumerate(geoms)]
-    ref = [torch.empty(g.sino_shape(), device="cuda") for g in geoms]
-    X.BatchPlan(Ps, xs, ref).project()
+    ref = _references(X, Ps, xs, geoms)
     out = [torch.zeros(g.sino_shape(), device="cuda") for g in geoms]
     arr = _problems(X, Ps, xs, out)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
