@@ -29,12 +29,14 @@
 // other walks, so the lengths are theirs; each lane measures t as s = +-t, the sign making s
 // grow with the driving index.
 //
-// Measured on GB300 (64 uneven fans, one plan): 29.2 ms, against 32.4 ms with one 64-bit
+// Measured on GB300 (64 uneven fans, one plan): 29.0 ms, against 32.4 ms with one 64-bit
 // reduction of the pair (row j, row j + 1) per slab into pair planes (half of whose bytes are
 // zeros where the slab crosses no row) and 35.7 ms for the earlier lockstep walk into the
 // image and its transposed copy.  A forward on pair planes (one 64-bit load per slab) was
 // slower than the crossing-order walk one ray per thread for one image (32.3 vs 25.1 ms for
-// the 64 plain forwards): the ALU pipe bounds its per-slab bookkeeping.
+// the 64 plain forwards): the ALU pipe bounds its per-slab bookkeeping.  A warp whose lanes all
+// see u_B move the same way along m could walk m in the direction that makes it grow and drop
+// the row selection from every slab: 28.98 vs 29.12 ms, not kept.
 #include <algorithm>
 
 #include "xray_rays.cuh"
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(256) zero_items_kernel(const BatchItem *__rest
 
 constexpr int kPairPad = 3;
 #ifndef XR_SLAB_FWD_AHEAD
-#define XR_SLAB_FWD_AHEAD 4
+#define XR_SLAB_FWD_AHEAD 8  // 4: 2-3% slower (64 uneven fans: 13.97 vs 13.74 ms)
 #endif
 constexpr int kFwdAhead = XR_SLAB_FWD_AHEAD;  // slabs split ahead of their loads
 
