@@ -315,8 +315,6 @@ TRAFFIC = {
     ("par3d_256_tilt", "adjoint", "gather"): (118.4e6, "profiles/column_batch_par3d_256_tilt.md (one launch of the "
                                                         "staged gather, full size; the records pass is not included)"),
     ("cone_512", "adjoint", "scatter"): (80.50e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
-    ("cone_512", "forward", "scatter"): (24.06e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
-    ("helix_512x256", "forward", "scatter"): (1.256e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
     ("helix_512x256", "adjoint", "scatter"): (3.387e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
 }
 

@@ -31,7 +31,9 @@
 // the z-fastest volume copy, at neighbouring heights, so their loads (forward) or
 // reductions (adjoint) fall on a few neighbouring sectors.  The copy has one zero voxel above
 // and below each column: a row outside the volume in z is clamped onto them, so rows that
-// enter or leave through the top or bottom face need no extra test.
+// enter or leave through the top or bottom face need no extra test.  The forward reads the
+// copy as pair columns (entry e holds voxels e and e + 1), so a slab's two voxels come in one
+// 64-bit load: circular cone 512^3 174 vs 182 ms, helix 512^2 x 256 60 vs 69 ms.
 //
 // The adjoint adds g * sec * length into a z-fastest accumulator with one reduction per
 // (row, voxel).  XR_TRACE_AGG=1 builds the warp-aggregated form instead: lanes whose B voxels
@@ -422,9 +424,84 @@ __device__ __forceinline__ float fwd_walk(const TraceGeo &T, const WTrace &W, co
     return __fadd_rn(acc, accB);
 }
 
+#ifndef XR_TRACE_PAIRS
+#define XR_TRACE_PAIRS 1
+#endif
+
+// The forward walk on pair columns: entry e of a padded column holds (z(e), z(e + 1)), so
+// voxel m of a row and voxel m + 1 come in one 64-bit load, at the entry of m (the entry of
+// m + 1 for a row read from the column's far end, whose pair then holds (m + 1, m)).  The z
+// plane m + 1 splits the slab: voxel m gets the part before it, voxel m + 1 the rest -- with
+// no crossing the plane lies past the slab's end and voxel m gets it all (a horizontal row:
+// plane at +infinity).  FLIP: 0 no row of the warp is read from the far end, 1 every row, 2
+// some (a per-row select).
+template <int U, bool CLAMP, int FLIP>
+__device__ __forceinline__ float fwd_walk_pairs(const TraceGeo &T, const WTrace &W, const Row &R, int lane,
+                                                float2 *slot, const float2 *__restrict__ volP)
+{
+    float acc0 = 0.f, acc1 = 0.f;  // two chains: the pairs' first and second voxels
+    const bool flip = R.zs != 1u;
+    const float bz = R.ez != 0.f ? R.bz : INFINITY;
+    const unsigned C = R.C - (flip ? 1u : 0u);  // the pair's entry: that of m, or of m + 1
+    float ta = W.tin, ma = row_floor<CLAMP>(R, ta);
+    for (int c = 0; c < W.nchunk; ++c) {
+        const int n = build_chunk(T, W, c, lane, slot);
+        int s = 0;
+        for (; s + U <= n; s += U) {
+            int e[U];
+            float l0[U], l1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float2 sl = slot[s + u];
+                const float mb = row_floor<CLAMP>(R, sl.x);
+                const float tx = fminf(fmaxf(__fmaf_rn(ma - (kMagic - 1.0f), R.iez, bz), ta), sl.x);
+                const float a = __fsub_rn(tx, ta), b = __fsub_rn(sl.x, tx);
+                l0[u] = FLIP == 0 ? a : (FLIP == 1 ? b : (flip ? b : a));
+                l1[u] = FLIP == 0 ? b : (FLIP == 1 ? a : (flip ? a : b));
+                e[u] = (int)(R.zs * (unsigned)__float_as_int(ma) + ((unsigned)__float_as_int(sl.y) + C));
+                ta = sl.x;
+                ma = mb;
+            }
+            float2 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = __ldg(volP + e[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                acc0 = __fmaf_rn(v[u].x, l0[u], acc0);
+                acc1 = __fmaf_rn(v[u].y, l1[u], acc1);
+            }
+        }
+        for (; s < n; ++s) {
+            const float2 sl = slot[s];
+            const float mb = row_floor<CLAMP>(R, sl.x);
+            const float tx = fminf(fmaxf(__fmaf_rn(ma - (kMagic - 1.0f), R.iez, bz), ta), sl.x);
+            const float a = __fsub_rn(tx, ta), b = __fsub_rn(sl.x, tx);
+            const float2 v = __ldg(volP + (int)(R.zs * (unsigned)__float_as_int(ma) +
+                                                ((unsigned)__float_as_int(sl.y) + C)));
+            acc0 = __fmaf_rn(v.x, FLIP == 0 ? a : (FLIP == 1 ? b : (flip ? b : a)), acc0);
+            acc1 = __fmaf_rn(v.y, FLIP == 0 ? b : (FLIP == 1 ? a : (flip ? a : b)), acc1);
+            ta = sl.x;
+            ma = mb;
+        }
+        __syncwarp();  // the next chunk overwrites the slots
+    }
+    return __fadd_rn(acc0, acc1);
+}
+
+template <int U, bool CLAMP>
+__device__ __forceinline__ float fwd_walk_pairs_any(const TraceGeo &T, const WTrace &W, const Row &R, int lane,
+                                                    float2 *slot, const float2 *__restrict__ volP)
+{
+    const unsigned fm = __ballot_sync(0xffffffffu, R.zs != 1u);
+    if (fm == 0u) return fwd_walk_pairs<U, CLAMP, 0>(T, W, R, lane, slot, volP);
+    if (fm == 0xffffffffu) return fwd_walk_pairs<U, CLAMP, 1>(T, W, R, lane, slot, volP);
+    return fwd_walk_pairs<U, CLAMP, 2>(T, W, R, lane, slot, volP);
+}
+
 template <int U>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_FWD_MINB) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
                                                                      float *__restrict__ sino)
+// volZ: the padded z-fastest copy, or (XR_TRACE_PAIRS) its pair columns
 {
     __shared__ float2 slot_s[kWarpsPerCta][kChunk];
     WarpJob J;
@@ -438,10 +515,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_FWD_MINB) trace_fw
     float acc = 0.f;
     if (trace_record(T, V, T.cols[J.col], r, tauF) && trace_setup(T, r, W)) {  // uniform over the warp
         const Row R = make_row(T, V, J.col, J.row, tauF, W.tin, W.tout);
+#if XR_TRACE_PAIRS
+        const float2 *volP = reinterpret_cast<const float2 *>(volZ);
+        if (__all_sync(0xffffffffu, R.inside))
+            acc = fwd_walk_pairs_any<U, false>(T, W, R, lane, slot, volP);
+        else
+            acc = fwd_walk_pairs_any<U, true>(T, W, R, lane, slot, volP);
+#else
         if (__all_sync(0xffffffffu, R.inside))
             acc = fwd_walk<U, false>(T, W, R, lane, slot, volZ);
         else
             acc = fwd_walk<U, true>(T, W, R, lane, slot, volZ);
+#endif
         acc = __fmul_rn(acc, R.sec);
     }
     if (J.row < T.n_rows) sino[((int64_t)J.view * T.n_rows + J.row) * T.n_cols + J.col] = acc;
@@ -562,6 +647,33 @@ __global__ void __launch_bounds__(256) to_zpad_kernel(const float *__restrict__ 
     }
 }
 
+// Pair columns of a [rows = nz][cols = nx ny] volume: out[p * ld + e] = (z(e), z(e + 1)) for
+// e = 0 .. ld - 1 (ld = nz + 2), z(0) = 0, z(1 + k) = in[k * cols + p], z(nz + 1) = z(nz + 2) = 0;
+// out[-1] (a leading pair the caller allocates) = (0, 0).  Rows e0 - 1 .. e0 + 31 of a tile are
+// staged so that reads run along p and writes along e.
+__global__ void __launch_bounds__(256) to_zpairs_kernel(const float *__restrict__ in, float2 *__restrict__ out,
+                                                        int64_t rows, int64_t cols)
+{
+    __shared__ float tile[33][33];
+    const int64_t ld = rows + 2;
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int64_t e_tiles = (ld + 31) / 32;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) out[-1] = make_float2(0.f, 0.f);
+    for (int64_t ty = blockIdx.y; ty < e_tiles; ty += gridDim.y) {
+        const int64_t e0 = ty * 32;
+        for (int rr = threadIdx.y; rr < 33; rr += blockDim.y) {
+            const int64_t k = e0 + rr - 1, c = c0 + threadIdx.x;  // z(e0 + rr) = in[k] for 0 <= k < rows
+            tile[rr][threadIdx.x] = (k >= 0 && k < rows && c < cols) ? in[k * cols + c] : 0.f;
+        }
+        __syncthreads();
+        for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
+            const int64_t c = c0 + dc, e = e0 + threadIdx.x;
+            if (c < cols && e < ld) out[c * ld + e] = make_float2(tile[threadIdx.x][dc], tile[threadIdx.x + 1][dc]);
+        }
+        __syncthreads();
+    }
+}
+
 // out[k * cols + p] = acc[p * ld + 1 + k] (the padding voxels are dropped)
 __global__ void __launch_bounds__(256) from_zpad_kernel(const float *__restrict__ acc, float *__restrict__ out,
                                                         int64_t rows, int64_t cols)
@@ -600,18 +712,31 @@ dim3 zpad_grid(int64_t rows, int64_t cols)
 
 }  // namespace
 
-size_t trace_ws_bytes(const GeoParams &g) { return (size_t)g.nx * g.ny * (size_t)(g.nz + 2) * sizeof(float); }
+// The adjoint's padded z-fastest accumulator (floats), or the forward's pair columns after one
+// leading pair
+size_t trace_ws_bytes(const GeoParams &g)
+{
+    const size_t units = (size_t)g.nx * g.ny * (size_t)(g.nz + 2);
+    return XR_TRACE_PAIRS ? (units + 1) * sizeof(float2) : units * sizeof(float);
+}
 
 cudaError_t launch_trace_project(const TraceGeo &T, const float *img, float *ws, float *sino, cudaStream_t s)
 {
     const int64_t cols = (int64_t)T.nx * T.ny;
+#if XR_TRACE_PAIRS
+    float2 *pairs = reinterpret_cast<float2 *>(ws) + 1;
+    to_zpairs_kernel<<<zpad_grid(T.nz + 2, cols), dim3(32, 8), 0, s>>>(img, pairs, T.nz, cols);
+    const float *vol = reinterpret_cast<const float *>(pairs);
+#else
     to_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(img, ws, T.nz, cols);
+    const float *vol = ws;
+#endif
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     TraceGeo G = T;
     G.ncg = (T.n_cols + kWarpsPerCta - 1) / kWarpsPerCta;
     const int64_t ctas = (int64_t)G.ncg * G.n_views * G.n_rb;
-    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(G, ws, sino);
+    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(G, vol, sino);
     return cudaGetLastError();
 }
 
