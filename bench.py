@@ -314,8 +314,10 @@ TRAFFIC = {
     ("fan2d_512x16", "forward", "gather"): (62.4e6, "profiles/fwd_plane_fan2d_512x16.md (one launch, full size)"),
     ("par3d_256_tilt", "adjoint", "gather"): (118.4e6, "profiles/column_batch_par3d_256_tilt.md (one launch of the "
                                                         "staged gather, full size; the records pass is not included)"),
-    ("cone_512", "adjoint", "scatter"): (80.50e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
-    ("helix_512x256", "adjoint", "scatter"): (3.387e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
+    ("cone_512", "adjoint", "scatter"): (79.91e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
+    ("cone_512", "forward", "scatter"): (164.33e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
+    ("helix_512x256", "forward", "scatter"): (9.409e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
+    ("helix_512x256", "adjoint", "scatter"): (3.378e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
 }
 
 GRAPHED = ("par2d_64",)  # launch-bound steps replayed from a CUDA graph
