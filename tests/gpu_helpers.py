@@ -6,6 +6,13 @@ Tolerances (FP32 kernel vs FP64 oracle):
   eps_ray = 32 * 2^-24 * T * max|f| covers rays whose sum is tiny next to their scale: the
   kernel's plane crossings are floats measured from the ray's foot point, |t| <= T (the
   image half-diagonal), so every length carries an absolute error of a few ulp(T).
+  Rays nearly parallel to an axis add a term: a plane of the minor axis B is crossed at
+  t = fma(q, 1/w_B, -f_B/w_B), and rounding the constant -f_B/w_B (f_B < 1) alone moves it
+  by up to 2^-24 / |w_B|, so a crossing carries an absolute error of about
+  2^-24 (2|t| + 1/|w_B|).  Each B crossing moves length between two units
+  (|v_a - v_b| <= max|f|), and the box's entry and exit on B faces move the chord's ends:
+  eps_cond = 4 * 2^-24 / |w_B| * max|f| where the caller passes the rays' minor index slopes
+  (check_rays(..., w_min=...)); it exceeds eps_ray only on images a few units across.
 * adjoint image: max |z - z_ref| <= 1e-4 * max |z_ref|.
 * dot product:   |<Ax, y> - <x, A^T y>| <= 1e-5 * |<Ax, y>| (both reductions in float64).
 * unit sets:     bit-exact for units whose length exceeds delta = 16 * 2^-24 * T on both
@@ -36,9 +43,21 @@ def grazing_delta(g: Geometry) -> float:
     return 16.0 * U32 * half_diag(g)
 
 
-def check_rays(g, y_gpu, y_ref, scale, fmax, what=""):
-    """Assert the per-ray bound; return the worst error in units of the tolerance."""
+def minor_slope_2d(g: Geometry, rays) -> np.ndarray:
+    """Smallest index-space slope |w| of each listed 2D ray (its direction's smaller component
+    over the larger unit side; 0 for rays parallel to an axis), from the oracle's (s, phi)."""
+    from oracle import oracle as O
+    phi = np.array([O.ray_params(g, int(r))[1] for r in rays])
+    return np.minimum(np.abs(np.sin(phi)), np.abs(np.cos(phi))) / max(g.dx, g.dy)
+
+
+def check_rays(g, y_gpu, y_ref, scale, fmax, what="", w_min=None):
+    """Assert the per-ray bound; return the worst error in units of the tolerance.  w_min: the
+    rays' minor index slopes (minor_slope_2d), for the near-axis term."""
     tol = ray_tol(g, scale, fmax)
+    if w_min is not None:
+        w = np.asarray(w_min, np.float64)
+        tol = tol + np.where(w > 1e-9, 4.0 * U32 * fmax / np.maximum(w, 1e-9), 0.0)
     err = np.abs(np.asarray(y_gpu, np.float64) - y_ref)
     ratio = err / tol
     worst = int(np.argmax(ratio))
