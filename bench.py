@@ -553,9 +553,10 @@ def run_ours(args, rank, world, local_rank, workload=None, cpu_budget=None):
 
 def _launch_count(P, g, B, fused=False):
     """Kernels of the repo launched per step on the single-image and column paths."""
-    # detector setup, ray setup (2D scans and ray lists: a per-ray table), and for 2D scans
-    # reserved for 4 or more images the gather's per-ray constants
-    setup = 1 + (0 if g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc") else 1) + \
+    # detector setup, ray setup (2D scans and ray lists: a per-ray table; parallel beams and ray
+    # lists build both tables in one launch), and for 2D scans reserved for 4 or more images the
+    # gather's per-ray constants
+    setup = 1 + (0 if g.kind in ("par3d", "cone", "cone_arc", "helix", "helix_arc", "par2d", "rays2d") else 1) + \
         (1 if not g.is3d and P.reserved >= 4 else 0)
     if fused:
         return setup + 1  # the fused forward + adjoint (its zero fill is a memset)

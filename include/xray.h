@@ -178,7 +178,9 @@ void xr_geometry_destroy(xr_geometry *g);
 
 /* Re-run the per-geometry ray setup on `stream`: the detector-sample kernel (the
  * transcendental part of the transformation formulas) and, for handles with a ray table, the
- * per-ray kernel (rebuilds the table in place). */
+ * per-ray kernel (rebuilds the table in place).  2D parallel beams and 2D ray lists of up to
+ * 65535 views, whose detector part needs no transcendentals, build both tables in one launch
+ * with the same records. */
 xr_status xr_ray_setup(xr_geometry *g, xr_stream stream);
 
 /* Reserve the handle's workspace for batches of up to max_batch images (allocates on the

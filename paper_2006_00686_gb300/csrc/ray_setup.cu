@@ -127,6 +127,22 @@ __global__ void ray_setup_kernel(GeoParams g, SetupDF K, const ViewDF *__restric
     out[(int64_t)v * ndet + d] = ray_record(g, K, views[v], det[d]);
 }
 
+// Parallel beams and ray lists: the detector part has no transcendentals (s = u), so each ray
+// computes its detector record itself, and view 0's threads also store it -- the ray setup in
+// one launch instead of two, the same records bit for bit (a launch-bound step, parallel beam
+// 64^2: one dependent launch fewer per step).
+__global__ void ray_setup_inline_kernel(GeoParams g, SetupDF K, const ViewDF *__restrict__ views,
+                                        DetRec *__restrict__ det, RayRec *__restrict__ out)
+{
+    const int ndet = g.n_rows * g.n_cols;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndet) return;
+    const int v = blockIdx.y;
+    const DetRec R = det_record(g, d);
+    if (v == 0) det[d] = R;
+    out[(int64_t)v * ndet + d] = ray_record(g, K, views[v], R);
+}
+
 // The same over a 1D grid, for scans with more views than the grid's y extent.
 __global__ void ray_setup_flat_kernel(GeoParams g, SetupDF K, const ViewDF *__restrict__ views,
                                       const DetRec *__restrict__ det, RayRec *__restrict__ out, int64_t n_rays)
@@ -167,6 +183,21 @@ cudaError_t launch_ray_setup(const GeoParams &g, const SetupDF &c, const ViewDF 
         ray_setup_flat_kernel<<<(unsigned)((n_rays + block - 1) / block), block, 0, s>>>(g, c, d_views, d_det, d_rays,
                                                                                         n_rays);
     }
+    return cudaGetLastError();
+}
+
+bool ray_setup_inline_ok(const GeoParams &g)
+{
+    return (g.kind == XR_PAR2D || g.kind == XR_RAYS2D) && g.n_views <= 65535;
+}
+
+cudaError_t launch_ray_setup_inline(const GeoParams &g, const SetupDF &c, const ViewDF *d_views, DetRec *d_det,
+                                    RayRec *d_rays, cudaStream_t s)
+{
+    const int block = 128;
+    const int64_t ndet = (int64_t)g.n_rows * g.n_cols;
+    const dim3 grid((unsigned)((ndet + block - 1) / block), (unsigned)g.n_views);
+    ray_setup_inline_kernel<<<grid, block, 0, s>>>(g, c, d_views, d_det, d_rays);
     return cudaGetLastError();
 }
 

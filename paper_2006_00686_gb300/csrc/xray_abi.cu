@@ -559,10 +559,15 @@ void xr_geometry_destroy(xr_geometry *g)
 xr_status xr_ray_setup(xr_geometry *g, xr_stream stream)
 {
     if (!g) return XR_ERR_NULL;
-    XR_CUDA(launch_det_setup(g->params, g->d_det, (cudaStream_t)stream));
-    if (g->d_rays)
-        XR_CUDA(launch_ray_setup(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays,
-                                 (cudaStream_t)stream));
+    if (g->d_rays && ray_setup_inline_ok(g->params)) {
+        XR_CUDA(launch_ray_setup_inline(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays,
+                                        (cudaStream_t)stream));
+    } else {
+        XR_CUDA(launch_det_setup(g->params, g->d_det, (cudaStream_t)stream));
+        if (g->d_rays)
+            XR_CUDA(launch_ray_setup(g->params, g->setup_df, g->d_views_df, g->d_det, g->d_rays, g->n_rays,
+                                     (cudaStream_t)stream));
+    }
     if (g->d_grec && g->ws_batch >= 4)
         XR_CUDA(launch_gather_prep(g->d_rays, g->n_rays, g->d_grec, (cudaStream_t)stream));
     XR_CUDA(slice_setup(g, (cudaStream_t)stream));

@@ -105,6 +105,11 @@ struct SetupItem {
 cudaError_t launch_batch_setup(const SetupItem *items, int n, int64_t n_det, int64_t n_rays, cudaStream_t s);
 cudaError_t launch_ray_setup(const GeoParams &g, const SetupDF &c, const ViewDF *d_views, const DetRec *d_det,
                              RayRec *d_rays, int64_t n_rays, cudaStream_t s);
+// Parallel beams and ray lists (whose detector part needs no transcendentals), up to 65535
+// views: the detector table and the ray table in one launch, the same records as the two.
+bool ray_setup_inline_ok(const GeoParams &g);
+cudaError_t launch_ray_setup_inline(const GeoParams &g, const SetupDF &c, const ViewDF *d_views, DetRec *d_det,
+                                    RayRec *d_rays, cudaStream_t s);
 
 cudaError_t launch_project(const RaySrc &rays, int64_t n_rays, const Grid &grid, const float *img,
                            int64_t img_bs, float *sino, int64_t sino_bs, int batch, int chunk,
