@@ -306,6 +306,7 @@ struct TraceGeo {
     int nx, ny, nz, n_views, n_rows, n_cols;
     int n_rb;          // blocks of 32 detector rows (a warp: one view, one column, one block)
     int ncg;           // groups of neighbouring columns, one CTA each (set at launch)
+    int split;         // parts of the columns taken in turn within a row block (set at launch)
     DF x0, y1, z1, idx, idy, idz, cx, cy, D;  // planes i = 0, j = 0, k = 0; 1/d; centre; sod
     float rxy2;            // squared xy half-diagonal of the image (with a small margin)
     const ViewDF *views;   // cos / sin of the view angle, source height H
