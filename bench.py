@@ -315,6 +315,8 @@ TRAFFIC = {
     ("par3d_256_tilt", "adjoint", "gather"): (118.4e6, "profiles/column_batch_par3d_256_tilt.md (one launch of the "
                                                         "staged gather, full size; the records pass is not included)"),
     ("cone_512", "adjoint", "scatter"): (79.91e9, "profiles/trace3d_cone_512_dram.md (one launch, full size)"),
+    ("cone_512", "forward", "scatter"): (13.49e9, "profiles/trace3d_cone_512_dram.md (one launch of the two-part "
+                                                 "forward, full size)"),
     ("helix_512x256", "adjoint", "scatter"): (3.378e9, "profiles/trace3d_helix_512x256_dram.md (one launch, full size)"),
 }
 
