@@ -220,6 +220,21 @@ def test_uniform_disc_converges_to_chord():
     np.testing.assert_allclose(got, 2 * np.sqrt(R * R - s * s), atol=3.0)
 
 
+def test_uniform_ball_converges_to_chord():
+    # Not a parity pin either: the 3D analogue of the disc.  A point-sampled ball of radius R
+    # projects, along a ray at distance rho from its centre, to 2 sqrt(R^2 - rho^2) as O(d);
+    # oblique directions (phi1, phi2) and both detector offsets exercise the 3D parameters
+    n, R = 72, 28.0
+    c = np.arange(n) - (n - 1) / 2
+    f = ((c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2) <= R * R).astype(np.float64)
+    f = f.reshape(-1)
+    for phi1, phi2, s1, s2 in ((0.31, 0.47, 0.0, 0.0), (1.13, -0.62, 9.4, -7.1), (2.71, 0.05, -17.3, 12.2),
+                               (0.0, 0.0, 21.6, 3.3)):
+        g = Geometry("par3d", n, n, n, angles=np.array([[phi1, phi2]]), n_cols=1, n_rows=1, u0=s1, v0=s2)
+        rho2 = s1 * s1 + s2 * s2
+        assert O.forward(g, f)[0] == pytest.approx(2 * math.sqrt(R * R - rho2), abs=3.0)
+
+
 # ---------------------------------------------------------------------------------------
 # Ray lists: rays given by their own parameters (Section 4.3)
 # ---------------------------------------------------------------------------------------
