@@ -1,6 +1,7 @@
-// The adjoint of 2D problems with one image each (a single image of a 2D scan, or the problems
-// of a batch plan): 32 neighbouring rays per warp walked slab by slab in lockstep, reduced into
-// padded accumulator planes, one plane per driving axis.
+// The forward and the adjoint of 2D problems with one image each (a single image of a 2D scan,
+// or the problems of a batch plan), walked slab by slab.  The adjoint: 32 neighbouring rays per
+// warp in lockstep, reduced into padded accumulator planes, one plane per driving axis (this
+// part of the file).  The forward: one ray per thread on pair planes (the part further below).
 //
 // A ray driven along axis A (the axis with the largest index-space slope, Section 4.3) crosses
 // at most one plane of the other axis B inside a slab [m, m + 1] of A: the pixels it meets
@@ -32,9 +33,10 @@
 // Measured on GB300 (64 uneven fans, one plan): 29.0 ms, against 32.4 ms with one 64-bit
 // reduction of the pair (row j, row j + 1) per slab into pair planes (half of whose bytes are
 // zeros where the slab crosses no row) and 35.7 ms for the earlier lockstep walk into the
-// image and its transposed copy.  A forward on pair planes (one 64-bit load per slab) was
-// slower than the crossing-order walk one ray per thread for one image (32.3 vs 25.1 ms for
-// the 64 plain forwards): the ALU pipe bounds its per-slab bookkeeping.  A warp whose lanes all
+// image and its transposed copy.  A forward in this lockstep form, on pair planes (coalesced
+// 64-bit loads, a row selection per slab), was slower than the crossing-order walk one ray per
+// thread for one image (32.3 vs 25.1 ms for the 64 plain forwards; the ALU pipe bounds its
+// per-slab bookkeeping); the per-thread pair-plane forward below takes 16.6 ms.  A warp whose lanes all
 // see u_B move the same way along m could walk m in the direction that makes it grow and drop
 // the row selection from every slab: 28.98 vs 29.12 ms, not kept.
 #include <algorithm>
