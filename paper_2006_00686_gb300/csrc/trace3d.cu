@@ -389,60 +389,6 @@ __device__ __forceinline__ bool warp_job(const TraceGeo &T, WarpJob &J)
     return J.col < T.n_cols;
 }
 
-// The forward walk of one row over the warp's slab list (CLAMP: some row of the warp leaves
-// the volume through its top or bottom face).  U slabs are split ahead of their 2U loads.
-template <int U, bool CLAMP>
-__device__ __forceinline__ float fwd_walk(const TraceGeo &T, const WTrace &W, const Row &R, int lane, float2 *slot,
-                                          const float *__restrict__ volZ)
-{
-    float acc = 0.f, accB = 0.f;  // two chains: A voxels and B voxels
-    float ta = W.tin, ma = row_floor<CLAMP>(R, ta);
-    for (int c = 0; c < W.nchunk; ++c) {
-        const int n = build_chunk(T, W, c, lane, slot);
-        int s = 0;
-        for (; s + U <= n; s += U) {
-            unsigned oA[U], oB[U];
-            float lA[U], lB[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const float2 sl = slot[s + u];
-                const float mb = row_floor<CLAMP>(R, sl.x);
-                slab_split(R, ta, sl.x, ma, mb, __float_as_int(sl.y), oA[u], oB[u], lA[u], lB[u]);
-                ta = sl.x;
-                ma = mb;
-            }
-            float vA[U], vB[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                vA[u] = __ldg(volZ + oA[u]);
-                vB[u] = __ldg(volZ + oB[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                acc = __fmaf_rn(vA[u], lA[u], acc);
-                accB = __fmaf_rn(vB[u], lB[u], accB);
-            }
-        }
-        for (; s < n; ++s) {
-            const float2 sl = slot[s];
-            const float mb = row_floor<CLAMP>(R, sl.x);
-            unsigned oA, oB;
-            float lA, lB;
-            slab_split(R, ta, sl.x, ma, mb, __float_as_int(sl.y), oA, oB, lA, lB);
-            acc = __fmaf_rn(__ldg(volZ + oA), lA, acc);
-            accB = __fmaf_rn(__ldg(volZ + oB), lB, accB);
-            ta = sl.x;
-            ma = mb;
-        }
-        __syncwarp();  // the next chunk overwrites the slots
-    }
-    return __fadd_rn(acc, accB);
-}
-
-#ifndef XR_TRACE_PAIRS
-#define XR_TRACE_PAIRS 1
-#endif
-
 // The forward walk on pair columns: entry e of a padded column holds (z(e), z(e + 1)), so
 // voxel m of a row and voxel m + 1 come in one 64-bit load, at the entry of m (the entry of
 // m + 1 for a row read from the column's far end, whose pair then holds (m + 1, m)).  The z
@@ -514,9 +460,9 @@ __device__ __forceinline__ float fwd_walk_pairs_any(const TraceGeo &T, const WTr
 }
 
 template <int U>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_FWD_MINB) trace_fwd_kernel(TraceGeo T, const float *__restrict__ volZ,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_FWD_MINB) trace_fwd_kernel(TraceGeo T, const float2 *__restrict__ volP,
                                                                      float *__restrict__ sino)
-// volZ: the padded z-fastest copy, or (XR_TRACE_PAIRS) its pair columns
+// volP: the pair columns of the padded z-fastest copy
 {
     __shared__ float2 slot_s[kWarpsPerCta][kChunk];
     WarpJob J;
@@ -530,18 +476,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_FWD_MINB) trace_fw
     float acc = 0.f;
     if (trace_record(T, V, T.cols[J.col], r, tauF) && trace_setup(T, r, W)) {  // uniform over the warp
         const Row R = make_row(T, V, J.col, J.row, tauF, W.tin, W.tout);
-#if XR_TRACE_PAIRS
-        const float2 *volP = reinterpret_cast<const float2 *>(volZ);
         if (__all_sync(0xffffffffu, R.inside))
             acc = fwd_walk_pairs_any<U, false>(T, W, R, lane, slot, volP);
         else
             acc = fwd_walk_pairs_any<U, true>(T, W, R, lane, slot, volP);
-#else
-        if (__all_sync(0xffffffffu, R.inside))
-            acc = fwd_walk<U, false>(T, W, R, lane, slot, volZ);
-        else
-            acc = fwd_walk<U, true>(T, W, R, lane, slot, volZ);
-#endif
         acc = __fmul_rn(acc, R.sec);
     }
     if (J.row < T.n_rows) sino[((int64_t)J.view * T.n_rows + J.row) * T.n_cols + J.col] = acc;
@@ -634,34 +572,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, XR_TRACE_MINB) trace_adj_ke
         adj_walk<AGG, true>(T, W, R, lane, runs, gs, slot, accZ);
 }
 
-// out[p * ld + 1 + k] = in[k * cols + p] for a [rows = nz][cols = nx ny] volume, and the two
-// zero voxels out[p * ld] and out[p * ld + nz + 1] of every column (ld = nz + 2).
-__global__ void __launch_bounds__(256) to_zpad_kernel(const float *__restrict__ in, float *__restrict__ out,
-                                                      int64_t rows, int64_t cols)
-{
-    __shared__ float tile[32][33];
-    const int64_t ld = rows + 2;
-    const int64_t c0 = (int64_t)blockIdx.x * 32;
-    const int64_t row_tiles = (rows + 31) / 32;
-    for (int64_t ty = blockIdx.y; ty < row_tiles; ty += gridDim.y) {
-        const int64_t r0 = ty * 32;
-        for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
-            const int64_t r = r0 + dr, c = c0 + threadIdx.x;
-            if (r < rows && c < cols) tile[dr][threadIdx.x] = in[r * cols + c];
-        }
-        __syncthreads();
-        for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
-            const int64_t c = c0 + dc, r = r0 + threadIdx.x;
-            if (r < rows && c < cols) {
-                out[c * ld + 1 + r] = tile[threadIdx.x][dc];
-                if (r == 0) out[c * ld] = 0.f;
-                if (r == rows - 1) out[c * ld + rows + 1] = 0.f;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // Pair columns of a [rows = nz][cols = nx ny] volume: out[p * ld + e] = (z(e), z(e + 1)) for
 // e = 0 .. ld - 1 (ld = nz + 2), z(0) = 0, z(1 + k) = in[k * cols + p], z(nz + 1) = z(nz + 2) = 0;
 // out[-1] (a leading pair the caller allocates) = (0, 0).  Rows e0 - 1 .. e0 + 31 of a tile are
@@ -732,27 +642,21 @@ dim3 zpad_grid(int64_t rows, int64_t cols)
 size_t trace_ws_bytes(const GeoParams &g)
 {
     const size_t units = (size_t)g.nx * g.ny * (size_t)(g.nz + 2);
-    return XR_TRACE_PAIRS ? (units + 1) * sizeof(float2) : units * sizeof(float);
+    return (units + 1) * sizeof(float2);
 }
 
 cudaError_t launch_trace_project(const TraceGeo &T, const float *img, float *ws, float *sino, cudaStream_t s)
 {
     const int64_t cols = (int64_t)T.nx * T.ny;
-#if XR_TRACE_PAIRS
     float2 *pairs = reinterpret_cast<float2 *>(ws) + 1;
     to_zpairs_kernel<<<zpad_grid(T.nz + 2, cols), dim3(32, 8), 0, s>>>(img, pairs, T.nz, cols);
-    const float *vol = reinterpret_cast<const float *>(pairs);
-#else
-    to_zpad_kernel<<<zpad_grid(T.nz, cols), dim3(32, 8), 0, s>>>(img, ws, T.nz, cols);
-    const float *vol = ws;
-#endif
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     TraceGeo G = T;
     G.ncg = (T.n_cols + kWarpsPerCta - 1) / kWarpsPerCta;
     G.split = kFwdSplit;
     const int64_t ctas = (int64_t)col_groups_per_part(G.ncg, G.split) * G.split * G.n_views * G.n_rb;
-    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(G, vol, sino);
+    trace_fwd_kernel<XR_TRACE_AHEAD><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, s>>>(G, pairs, sino);
     return cudaGetLastError();
 }
 
